@@ -1,0 +1,111 @@
+"""Oracle GEMM: C = A B by its definition (Sec. 2.4; CDAG of Sec. 5.1).
+
+Test infrastructure only (see the package docstring).  The arithmetic lives in
+gemm_oracle.c; this module compiles it with gcc (no fused multiply-add
+contraction, no fast-math) and calls it through ctypes.
+
+Pins (tests/test_oracle_gemm.py): exact integer products against Python
+integers, identity / diagonal / rank-1 closed forms, exact rational arithmetic
+(fractions) on tiny inputs for Dot2, the classical bound |C_naive - C| <= gamma_k
+|A||B| for the naive loop, and Freivalds catching a planted error.
+"""
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gemm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libgemm_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build():
+    """Compile the C oracle (idempotent; rebuilds when the source is newer)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                           "-shared", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            d = ctypes.POINTER(ctypes.c_double)
+            i64 = ctypes.c_int64
+            for name in ("oracle_gemm_naive", "oracle_gemm_dot2"):
+                f = getattr(lib, name)
+                f.argtypes = [i64, i64, i64, d, i64, d, i64, d, i64]
+                f.restype = None
+            lib.oracle_dot2_pairs.argtypes = [i64, i64, d, d, d]
+            lib.oracle_dot2_pairs.restype = None
+            lib.oracle_freivalds.argtypes = [i64, i64, i64, d, i64, d, i64, d, i64, d, d, d, d, d]
+            lib.oracle_freivalds.restype = None
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def gemm(A, B, method="dot2"):
+    """C = A B in FP64.  method: 'naive' (partial-sum chain t=0..k-1) or 'dot2'."""
+    A, B = _f64(A), _f64(B)
+    m, k = A.shape
+    k2, n = B.shape
+    assert k == k2
+    C = np.zeros((m, n), dtype=np.float64)
+    if m and n:
+        fn = {"naive": _load().oracle_gemm_naive, "dot2": _load().oracle_gemm_dot2}[method]
+        fn(m, n, k, _ptr(A), max(k, 1), _ptr(B), max(n, 1), _ptr(C), max(n, 1))
+    return C
+
+
+def dot2_pairs(arows, bcols):
+    """out[p] = sum_t arows[p,t] * bcols[p,t], compensated (Dot2)."""
+    arows, bcols = _f64(arows), _f64(bcols)
+    count, k = arows.shape
+    assert bcols.shape == (count, k)
+    out = np.zeros(count, dtype=np.float64)
+    if count:
+        _load().oracle_dot2_pairs(count, k, _ptr(arows), _ptr(bcols), _ptr(out))
+    return out
+
+
+def freivalds(A, B, C, x):
+    """Return (r, scale): r = C x - A (B x) and scale = |A|(|B||x|), in Dot2."""
+    A, B, C, x = _f64(A), _f64(B), _f64(C), _f64(x)
+    m, k = A.shape
+    n = B.shape[1]
+    bx = np.zeros(k)
+    absbx = np.zeros(k)
+    r = np.zeros(m)
+    scale = np.zeros(m)
+    _load().oracle_freivalds(m, n, k, _ptr(A), max(k, 1), _ptr(B), max(n, 1), _ptr(C), max(n, 1),
+                             _ptr(x), _ptr(bx), _ptr(absbx), _ptr(r), _ptr(scale))
+    return r, scale
+
+
+def normwise_rel_error(C_hat, C_ref):
+    """||C_hat - C_ref||_F / ||C_ref||_F over the entries given (flattened)."""
+    C_hat = np.asarray(C_hat, dtype=np.float64).ravel()
+    C_ref = np.asarray(C_ref, dtype=np.float64).ravel()
+    den = np.linalg.norm(C_ref)
+    num = np.linalg.norm(C_hat - C_ref)
+    return 0.0 if num == 0.0 else (num / den if den else np.inf)
