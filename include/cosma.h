@@ -1,0 +1,206 @@
+/*
+ * cosma.h -- C ABI of a single-GPU, I/O-aware matrix-multiplication library
+ * for NVIDIA GB300 (sm_103a), after Kwasniewski et al., "Red-Blue Pebbling
+ * Revisited: Near Optimal Parallel Matrix-Matrix Multiplication" (SC'19,
+ * arXiv 1908.09606).
+ *
+ * The operation is classical C = A B (no Strassen), A m x k, B k x n, C m x n
+ * (Sec. 2.4), computed under the paper's schedule (Alg. 1) mapped onto one GPU:
+ * the SMs are the processors, one SM's shared memory + tensor memory (or
+ * register file) is the fast memory S, and L2/HBM traffic is the I/O.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are row-major; lda, ldb, ldc are leading dimensions in elements
+ *     (lda >= k, ldb >= n, ldc >= n).  C is overwritten (no alpha/beta).
+ *   - A, B, C are DEVICE pointers owned by the caller.  The library never
+ *     frees or retains them beyond the call's kernels.
+ *   - m, n, k >= 0.  m == 0 or n == 0: no-op.  k == 0: C is set to zero.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls are asynchronous on it.  Argument errors are returned before any
+ *     launch; launch failures return COSMA_ERR_CUDA; device-side conditions
+ *     (a bounded wait that gave up, non-finite input to the emulated path) are
+ *     recorded in a per-device status word read by cosma_stream_status().
+ *   - There is no CPU fallback: without a usable GPU every compute entry point
+ *     returns COSMA_ERR_CUDA.
+ *   - Calls on one stream are ordered; calls on different streams may run
+ *     concurrently only if they do not share workspace (the library arena is
+ *     per device; concurrent streams must each use cosma_set_workspace with a
+ *     separate buffer from a separate host thread, or serialise).
+ */
+#ifndef COSMA_GB300_H
+#define COSMA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define COSMA_ABI_VERSION 1
+
+/* Element types of a call.  BF16: A and B are bf16, C is fp32.
+ * F64_EMU_BF16: A, B, C are fp64; the product is formed from bf16 slices on
+ * the tensor cores (Ozaki-style splitting) and recombined in high precision.
+ * F64_EMU_INT8 is reserved (returns COSMA_ERR_UNSUPPORTED). */
+typedef enum {
+  COSMA_F64 = 0,
+  COSMA_F32 = 1,
+  COSMA_BF16 = 2,
+  COSMA_F64_EMU_BF16 = 3,
+  COSMA_F64_EMU_INT8 = 4
+} cosma_dtype;
+
+typedef enum {
+  COSMA_OK = 0,
+  COSMA_ERR_INVALID_ARG = -1,
+  COSMA_ERR_UNSUPPORTED = -2,
+  COSMA_ERR_CUDA = -3,
+  COSMA_ERR_TIMEOUT = -4,
+  COSMA_ERR_NONFINITE = -5,
+  COSMA_ERR_NO_WORKSPACE = -6
+} cosma_status;
+
+/* How a plan is chosen.  ANALYTIC: the paper's FindSeqSchedule + FitRanks
+ * (Alg. 1) with the library's cost model.  LEARNED: the MLP cost model, with
+ * ANALYTIC as the fallback outside its training range. */
+typedef enum {
+  COSMA_SELECT_ANALYTIC = 0,
+  COSMA_SELECT_LEARNED = 1
+} cosma_selector;
+
+/* Kernel families a plan can name. */
+typedef enum {
+  COSMA_KERNEL_SIMT_F64 = 0,  /* FP64 FMA, C tile in registers          */
+  COSMA_KERNEL_SIMT_F32 = 1,  /* FP32 FMA, C tile in registers          */
+  COSMA_KERNEL_TC_BF16 = 2,   /* tcgen05 kind::f16, C tile in TMEM       */
+  COSMA_KERNEL_EMU_BF16 = 3   /* tcgen05 bf16 slices, FP64 recombination */
+} cosma_kernel;
+
+/* Library configuration (all fields have defaults; see cosma_init). */
+typedef struct cosma_config {
+  double delta;        /* FitRanks: max fraction of SMs left idle (Sec. 7.1); default 0.03 */
+  int selector;        /* default cosma_selector for cosma_gemm; default ANALYTIC */
+  int emu_slices;      /* slices per operand for F64_EMU_BF16; 0 = default (6) */
+  int emu_slice_bits;  /* magnitude bits per slice, 1..8; 0 = default (7) */
+  long long wait_limit;/* spin iterations before a device wait gives up; 0 = default */
+} cosma_config;
+
+/* A schedule for one product: the outcome of Alg. 1's FindSeqSchedule
+ * (tile_m x tile_n C tile and k_block x stages input ring that fit in S),
+ * ParallelizeSched/FitRanks (processor grid pm x pn x pk over the SMs; pk > 1
+ * is a split of k followed by the Reduce step), and the assignment order. */
+typedef struct cosma_plan {
+  int kernel;          /* cosma_kernel */
+  int tile_m, tile_n;  /* C tile held in fast memory (the paper's a x b)  */
+  int k_block;         /* k extent of one staged A/B panel pair           */
+  int stages;          /* panel pairs in flight (Alg. 1 step size s = k_block*stages) */
+  int pm, pn, pk;      /* processor grid over tiles/k (Sec. 6.1)          */
+  int order;           /* 0: rectangular local domains, 1: balanced stripes of tiles */
+  int ctas;            /* CTAs launched                                   */
+  int sms;             /* SMs on the device                               */
+  long long workspace_bytes;  /* device workspace the call needs          */
+  double fast_words;   /* S: fast-memory words per SM for this kernel     */
+  double io_words;     /* L2->SM words the schedule moves (loads + stores) */
+  double bound_words;  /* Theorem 1 at S: 2mnk/sqrt(S) + mn               */
+  double est_seconds;  /* cost-model estimate                             */
+} cosma_plan;
+
+/* One problem of a grouped call (all DEVICE pointers, same conventions as
+ * cosma_gemm). */
+typedef struct cosma_problem {
+  int64_t m, n, k;
+  const void* A;
+  int64_t lda;
+  const void* B;
+  int64_t ldb;
+  void* C;
+  int64_t ldc;
+} cosma_problem;
+
+/* ---- lifecycle -------------------------------------------------------- */
+
+/* Optional.  Applies cfg (NULL = defaults) and queries the current device.
+ * Returns COSMA_ERR_INVALID_ARG for out-of-range fields. */
+int cosma_init(const cosma_config* cfg);
+
+/* Copies the active configuration to *out. */
+int cosma_get_config(cosma_config* out);
+
+/* Lends the library a caller-owned device buffer as workspace (split-k
+ * partials, emulation slices, grouped tables).  The caller keeps ownership and
+ * must keep it alive while calls that use it are in flight.  bytes == 0
+ * returns to the library-owned arena, which grows with cudaMalloc outside
+ * stream capture; inside capture a call that needs more than is available
+ * returns COSMA_ERR_NO_WORKSPACE.  dptr must be 256-byte aligned. */
+int cosma_set_workspace(void* dptr, size_t bytes);
+
+/* Releases the library arena and cached state for the current device. */
+void cosma_finalize(void);
+
+/* ---- the product ------------------------------------------------------ */
+
+/* C = A B for one problem (Alg. 1 end to end: plan, staged main loop, Reduce).
+ * dtype is a cosma_dtype.  Returns cosma_status. */
+int cosma_gemm(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void* B,
+               int64_t ldb, void* C, int64_t ldc, int dtype, void* stream);
+
+/* Same as cosma_gemm but runs the given plan (e.g. from cosma_plan_query or an
+ * autotuner).  The plan is validated against the kernel's limits first. */
+int cosma_gemm_planned(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda,
+                       const void* B, int64_t ldb, void* C, int64_t ldc, int dtype,
+                       const cosma_plan* plan, void* stream);
+
+/* `count` independent products in one persistent launch.  problems is a HOST
+ * array (copied during the call; it may be reused once the call returns).
+ * dtype: COSMA_F32 or COSMA_BF16. */
+int cosma_gemm_grouped(int count, const cosma_problem* problems, int dtype, void* stream);
+
+/* ---- planning --------------------------------------------------------- */
+
+/* Plan for an m x n x k product of the given dtype with the given selector
+ * (cosma_selector).  Host only, no GPU work.  Returns cosma_status. */
+int cosma_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int selector,
+                     cosma_plan* out);
+
+/* Work units of a plan in execution order, as int64 sextuples
+ * (row0, row1, col0, col1, k0, k1) per CTA, CTAs one after another.  Writes
+ * at most max_units units to `units` (HOST, 6*max_units int64) and returns the
+ * total number of units (so a first call with max_units = 0 sizes the buffer),
+ * or a negative cosma_status. */
+long long cosma_plan_units(int64_t m, int64_t n, int64_t k, const cosma_plan* plan,
+                           int64_t* units, long long max_units);
+
+/* FindSeqSchedule of Alg. 1 / Sec. 5.2: the integer (a, b) maximising
+ * ab/(a + b) subject to ab + a + 1 <= S (ties: smaller ab, then smaller a).
+ * S in words, S >= 3. */
+int cosma_find_seq_schedule(long long S, int* a, int* b);
+
+/* FitRanks of Alg. 1 / Sec. 7.1: the processor grid [pm, pn, pk] with
+ * pm*pn*pk in [p - floor(delta p), p] that minimises the words of one local
+ * domain ceil(m/pm)ceil(k/pk) + ceil(k/pk)ceil(n/pn) + ceil(m/pm)ceil(n/pn)
+ * (ties: more processors used, then the lexicographically smaller grid). */
+int cosma_fit_ranks(int64_t m, int64_t n, int64_t k, int p, double delta, int grid[3]);
+
+/* ---- status ----------------------------------------------------------- */
+
+/* Synchronises `stream`, then reads and clears the device status word of the
+ * current device.  Returns COSMA_OK, COSMA_ERR_TIMEOUT, COSMA_ERR_NONFINITE or
+ * COSMA_ERR_CUDA. */
+int cosma_stream_status(void* stream);
+
+/* Static human-readable text for a cosma_status value. */
+const char* cosma_status_string(int status);
+
+/* Number of SMs of the current device (0 without a device). */
+int cosma_device_sms(void);
+
+/* Running count of kernels this library has launched in this process (all
+ * devices, all streams), for accounting in benchmarks. */
+long long cosma_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COSMA_GB300_H */

@@ -1,0 +1,232 @@
+"""Thin ctypes binding of include/cosma.h (argument marshalling only).
+
+Every compute step runs in the CUDA library; this module only converts Python
+ints / torch tensors into the C call's pointers, sizes and stream.  If the
+shared library is missing it raises -- there is no CPU fallback.
+"""
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcosma_gb300.so")
+
+COSMA_F64, COSMA_F32, COSMA_BF16, COSMA_F64_EMU_BF16, COSMA_F64_EMU_INT8 = range(5)
+DTYPES = {"f64": COSMA_F64, "f32": COSMA_F32, "bf16": COSMA_BF16,
+          "f64_emu_bf16": COSMA_F64_EMU_BF16, "f64_emu_int8": COSMA_F64_EMU_INT8}
+COSMA_OK = 0
+COSMA_ERR_INVALID_ARG = -1
+COSMA_ERR_UNSUPPORTED = -2
+COSMA_ERR_CUDA = -3
+COSMA_ERR_TIMEOUT = -4
+COSMA_ERR_NONFINITE = -5
+COSMA_ERR_NO_WORKSPACE = -6
+COSMA_SELECT_ANALYTIC, COSMA_SELECT_LEARNED = 0, 1
+KERNELS = {0: "simt_f64", 1: "simt_f32", 2: "tc_bf16", 3: "emu_bf16"}
+
+
+class cosma_config(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("selector", ctypes.c_int),
+                ("emu_slices", ctypes.c_int), ("emu_slice_bits", ctypes.c_int),
+                ("wait_limit", ctypes.c_longlong)]
+
+
+class cosma_plan(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("tile_m", ctypes.c_int), ("tile_n", ctypes.c_int),
+                ("k_block", ctypes.c_int), ("stages", ctypes.c_int), ("pm", ctypes.c_int),
+                ("pn", ctypes.c_int), ("pk", ctypes.c_int), ("order", ctypes.c_int),
+                ("ctas", ctypes.c_int), ("sms", ctypes.c_int),
+                ("workspace_bytes", ctypes.c_longlong), ("fast_words", ctypes.c_double),
+                ("io_words", ctypes.c_double), ("bound_words", ctypes.c_double),
+                ("est_seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class cosma_problem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64),
+                ("C", ctypes.c_void_p), ("ldc", ctypes.c_int64)]
+
+
+class CosmaError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+_lib = None
+
+# (name, restype, argtypes) of every entry point in include/cosma.h
+_I64, _VP, _INT, _LL, _D = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_double
+SIGNATURES = [
+    ("cosma_init", _INT, [ctypes.POINTER(cosma_config)]),
+    ("cosma_get_config", _INT, [ctypes.POINTER(cosma_config)]),
+    ("cosma_set_workspace", _INT, [_VP, ctypes.c_size_t]),
+    ("cosma_finalize", None, []),
+    ("cosma_gemm", _INT, [_I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _INT, _VP]),
+    ("cosma_gemm_planned", _INT, [_I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _INT,
+                                  ctypes.POINTER(cosma_plan), _VP]),
+    ("cosma_gemm_grouped", _INT, [_INT, ctypes.POINTER(cosma_problem), _INT, _VP]),
+    ("cosma_plan_query", _INT, [_I64, _I64, _I64, _INT, _INT, ctypes.POINTER(cosma_plan)]),
+    ("cosma_plan_units", _LL, [_I64, _I64, _I64, ctypes.POINTER(cosma_plan),
+                               ctypes.POINTER(ctypes.c_int64), _LL]),
+    ("cosma_find_seq_schedule", _INT, [_LL, ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
+    ("cosma_fit_ranks", _INT, [_I64, _I64, _I64, _INT, _D, ctypes.POINTER(_INT)]),
+    ("cosma_stream_status", _INT, [_VP]),
+    ("cosma_status_string", ctypes.c_char_p, [_INT]),
+    ("cosma_device_sms", _INT, []),
+    ("cosma_launch_count", _LL, []),
+]
+
+
+def load(path=None):
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status, where):
+    if status != COSMA_OK:
+        raise CosmaError(status, where)
+    return status
+
+
+def status_string(status):
+    try:
+        return load().cosma_status_string(status).decode()
+    except Exception:  # library missing: still give a readable message
+        return {0: "ok", -1: "invalid argument", -2: "unsupported", -3: "CUDA error",
+                -4: "device wait timed out", -5: "non-finite input", -6: "no workspace"}.get(
+                    status, "unknown status")
+
+
+# ---- C-named wrappers (raw pointers and sizes) ---------------------------
+
+def cosma_init(delta=0.03, selector=COSMA_SELECT_ANALYTIC, emu_slices=0, emu_slice_bits=0,
+               wait_limit=0):
+    cfg = cosma_config(delta, selector, emu_slices, emu_slice_bits, wait_limit)
+    return load().cosma_init(ctypes.byref(cfg))
+
+
+def cosma_get_config():
+    cfg = cosma_config()
+    _check(load().cosma_get_config(ctypes.byref(cfg)), "cosma_get_config")
+    return cfg
+
+
+def cosma_set_workspace(dptr, nbytes):
+    return load().cosma_set_workspace(dptr, nbytes)
+
+
+def cosma_finalize():
+    load().cosma_finalize()
+
+
+def cosma_gemm(m, n, k, A, lda, B, ldb, C, ldc, dtype, stream=0):
+    return load().cosma_gemm(m, n, k, A, lda, B, ldb, C, ldc, dtype, stream)
+
+
+def cosma_gemm_planned(m, n, k, A, lda, B, ldb, C, ldc, dtype, plan, stream=0):
+    return load().cosma_gemm_planned(m, n, k, A, lda, B, ldb, C, ldc, dtype,
+                                     ctypes.byref(plan), stream)
+
+
+def cosma_gemm_grouped(problems, dtype, stream=0):
+    arr = (cosma_problem * len(problems))(*problems)
+    return load().cosma_gemm_grouped(len(problems), arr, dtype, stream)
+
+
+def cosma_plan_query(m, n, k, dtype, selector=COSMA_SELECT_ANALYTIC):
+    p = cosma_plan()
+    _check(load().cosma_plan_query(m, n, k, dtype, selector, ctypes.byref(p)), "cosma_plan_query")
+    return p
+
+
+def cosma_plan_units(m, n, k, plan):
+    lib = load()
+    total = lib.cosma_plan_units(m, n, k, ctypes.byref(plan), None, 0)
+    if total < 0:
+        raise CosmaError(int(total), "cosma_plan_units")
+    buf = (ctypes.c_int64 * (6 * total))()
+    lib.cosma_plan_units(m, n, k, ctypes.byref(plan), buf, total)
+    return [tuple(buf[6 * i:6 * i + 6]) for i in range(total)]
+
+
+def cosma_find_seq_schedule(S):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load().cosma_find_seq_schedule(S, ctypes.byref(a), ctypes.byref(b)),
+           "cosma_find_seq_schedule")
+    return a.value, b.value
+
+
+def cosma_fit_ranks(m, n, k, p, delta):
+    g = (ctypes.c_int * 3)()
+    _check(load().cosma_fit_ranks(m, n, k, p, delta, g), "cosma_fit_ranks")
+    return tuple(g)
+
+
+def cosma_stream_status(stream=0):
+    return load().cosma_stream_status(stream)
+
+
+def cosma_device_sms():
+    return load().cosma_device_sms()
+
+
+def cosma_launch_count():
+    return load().cosma_launch_count()
+
+
+# ---- torch convenience (marshalling only) --------------------------------
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def gemm(A, B, C, dtype, stream=None, plan=None):
+    """C = A B for row-major torch CUDA tensors (C preallocated).  Raises on error."""
+    m, k = A.shape
+    k2, n = B.shape
+    assert k == k2 and tuple(C.shape) == (m, n)
+    for t in (A, B, C):
+        assert t.is_cuda and t.stride(1) == 1, "row-major CUDA tensors with unit column stride"
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    s = _stream_handle(stream)
+    lda, ldb, ldc = max(A.stride(0), 1), max(B.stride(0), 1), max(C.stride(0), 1)
+    if plan is None:
+        rc = cosma_gemm(m, n, k, A.data_ptr(), lda, B.data_ptr(), ldb, C.data_ptr(), ldc, dtype, s)
+    else:
+        rc = cosma_gemm_planned(m, n, k, A.data_ptr(), lda, B.data_ptr(), ldb, C.data_ptr(),
+                                ldc, dtype, plan, s)
+    return _check(rc, "cosma_gemm")
+
+
+def gemm_grouped(As, Bs, Cs, dtype, stream=None):
+    """Grouped C_i = A_i B_i for lists of row-major torch CUDA tensors."""
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    probs = []
+    for A, B, C in zip(As, Bs, Cs):
+        m, k = A.shape
+        n = B.shape[1]
+        probs.append(cosma_problem(m, n, k, A.data_ptr(), max(A.stride(0), 1), B.data_ptr(),
+                                   max(B.stride(0), 1), C.data_ptr(), max(C.stride(0), 1)))
+    return _check(cosma_gemm_grouped(probs, dtype, _stream_handle(stream)), "cosma_gemm_grouped")

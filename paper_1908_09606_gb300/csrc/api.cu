@@ -1,0 +1,385 @@
+// Host runtime behind include/cosma.h: argument checks, plans, workspace,
+// dispatch to the kernels, device status word.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+#include <atomic>
+#include <mutex>
+
+#include "internal.h"
+
+namespace cosma {
+
+int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void* ws,
+                   long long ws_bytes, int* status, long long wait_limit, cudaStream_t st);
+int launch_emu_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, const cosma_config& cfg,
+                    void* ws, long long ws_bytes, int* status, long long wait_limit,
+                    cudaStream_t st);
+long long emu_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_config& cfg);
+int grouped_gemm(int count, const cosma_problem* problems, int dtype, const DeviceInfo& dev,
+                 void* ws, long long ws_bytes, int* status, long long wait_limit, cudaStream_t st,
+                 long long* needed);
+
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+
+struct DeviceState {
+  bool ready = false;
+  DeviceInfo info;
+  int* d_status = nullptr;     // device status word (0 = ok)
+  void* arena = nullptr;       // library-owned workspace
+  size_t arena_bytes = 0;
+  void* borrowed = nullptr;    // caller-lent workspace
+  size_t borrowed_bytes = 0;
+};
+
+constexpr int kMaxDevices = 16;
+std::mutex g_mu;
+DeviceState g_dev[kMaxDevices];
+cosma_config g_cfg = {0.03, COSMA_SELECT_ANALYTIC, 0, 0, 0};
+
+const long long kDefaultWaitLimit = 1LL << 26;  // spins of a bounded device wait
+
+int current_device() {
+  int d = -1;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return -1;
+  return d;
+}
+
+// Returns the state of the current device, initialising it once (outside any
+// stream capture: it allocates the status word).
+DeviceState* state(int* err) {
+  const int d = current_device();
+  if (d < 0) { *err = COSMA_ERR_CUDA; return nullptr; }
+  DeviceState& s = g_dev[d];
+  if (!s.ready) {
+    DeviceInfo& in = s.info;
+    in.device = d;
+    if (cudaDeviceGetAttribute(&in.sms, cudaDevAttrMultiProcessorCount, d) != cudaSuccess) {
+      *err = COSMA_ERR_CUDA;
+      return nullptr;
+    }
+    cudaDeviceGetAttribute(&in.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d);
+    cudaDeviceGetAttribute(&in.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, d);
+    cudaDeviceGetAttribute(&in.regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, d);
+    cudaDeviceGetAttribute(&in.l2_bytes, cudaDevAttrL2CacheSize, d);
+    cudaDeviceGetAttribute(&in.cc_major, cudaDevAttrComputeCapabilityMajor, d);
+    cudaDeviceGetAttribute(&in.cc_minor, cudaDevAttrComputeCapabilityMinor, d);
+    if (cudaMalloc(&s.d_status, 256) != cudaSuccess) { *err = COSMA_ERR_CUDA; return nullptr; }
+    if (cudaMemset(s.d_status, 0, 256) != cudaSuccess) { *err = COSMA_ERR_CUDA; return nullptr; }
+    s.ready = true;
+  }
+  *err = COSMA_OK;
+  return &s;
+}
+
+bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return false;
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+// Workspace of at least `bytes`: the caller's lent buffer, else the arena
+// (grown outside capture only).
+int workspace(DeviceState* s, long long bytes, cudaStream_t st, void** out, long long* have) {
+  *out = nullptr;
+  *have = 0;
+  if (bytes <= 0) return COSMA_OK;
+  if (s->borrowed) {
+    if ((long long)s->borrowed_bytes < bytes) return COSMA_ERR_NO_WORKSPACE;
+    *out = s->borrowed;
+    *have = (long long)s->borrowed_bytes;
+    return COSMA_OK;
+  }
+  if ((long long)s->arena_bytes < bytes) {
+    if (capturing(st)) return COSMA_ERR_NO_WORKSPACE;
+    if (s->arena) {
+      if (cudaStreamSynchronize(st) != cudaSuccess) return COSMA_ERR_CUDA;
+      cudaFree(s->arena);
+      s->arena = nullptr;
+      s->arena_bytes = 0;
+    }
+    size_t want = (size_t)bytes;
+    want = (want + (1u << 20) - 1) & ~((size_t)(1u << 20) - 1);
+    if (cudaMalloc(&s->arena, want) != cudaSuccess) {
+      cudaGetLastError();
+      return COSMA_ERR_NO_WORKSPACE;
+    }
+    s->arena_bytes = want;
+  }
+  *out = s->arena;
+  *have = (long long)s->arena_bytes;
+  return COSMA_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int elem_bytes_in(int dtype) {
+  switch (dtype) {
+    case COSMA_F32: return 4;
+    case COSMA_BF16: return 2;
+    default: return 8;
+  }
+}
+int elem_bytes_out(int dtype) { return dtype == COSMA_F32 || dtype == COSMA_BF16 ? 4 : 8; }
+
+int check_args(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void* B,
+               int64_t ldb, const void* C, int64_t ldc, int dtype) {
+  if (dtype < COSMA_F64 || dtype > COSMA_F64_EMU_INT8) return COSMA_ERR_INVALID_ARG;
+  if (m < 0 || n < 0 || k < 0) return COSMA_ERR_INVALID_ARG;
+  if (lda < (k > 1 ? k : 1) || ldb < (n > 1 ? n : 1) || ldc < (n > 1 ? n : 1))
+    return COSMA_ERR_INVALID_ARG;
+  if (m == 0 || n == 0) return COSMA_OK;
+  if (!C) return COSMA_ERR_INVALID_ARG;
+  if (k > 0 && (!A || !B)) return COSMA_ERR_INVALID_ARG;
+  if ((uintptr_t)C % elem_bytes_out(dtype)) return COSMA_ERR_INVALID_ARG;
+  if (k > 0 && ((uintptr_t)A % elem_bytes_in(dtype) || (uintptr_t)B % elem_bytes_in(dtype)))
+    return COSMA_ERR_INVALID_ARG;
+  if (!is_device_ptr(C)) return COSMA_ERR_INVALID_ARG;
+  if (k > 0 && (!is_device_ptr(A) || !is_device_ptr(B))) return COSMA_ERR_INVALID_ARG;
+  if (dtype == COSMA_F64_EMU_INT8) return COSMA_ERR_UNSUPPORTED;
+  return COSMA_OK;
+}
+
+long long total_workspace(int64_t m, int64_t n, int64_t k, int dtype, const cosma_plan& p) {
+  if (dtype == COSMA_F64_EMU_BF16) return emu_workspace_bytes(m, n, k, g_cfg);
+  return workspace_bytes(m, n, k, dtype, p);
+}
+
+int run(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void* B, int64_t ldb,
+        void* C, int64_t ldc, int dtype, const cosma_plan* given, void* stream) {
+  int rc = check_args(m, n, k, A, lda, B, ldb, C, ldc, dtype);
+  if (rc != COSMA_OK) return rc;
+  if (m == 0 || n == 0) return COSMA_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceState* s = state(&rc);
+  if (!s) return rc;
+  if (k == 0) {
+    const size_t w = (size_t)elem_bytes_out(dtype);
+    count_launch();
+    return cudaMemset2DAsync(C, (size_t)ldc * w, 0, (size_t)n * w, (size_t)m, st) == cudaSuccess
+               ? COSMA_OK
+               : COSMA_ERR_CUDA;
+  }
+  cosma_plan p;
+  if (given) {
+    p = *given;
+    rc = validate_plan(m, n, k, dtype, s->info, p);
+    if (rc != COSMA_OK) return rc;
+  } else {
+    rc = plan_gemm(m, n, k, dtype, g_cfg.selector, s->info, g_cfg, &p);
+    if (rc != COSMA_OK) return rc;
+  }
+  const long long need = total_workspace(m, n, k, dtype, p);
+  void* ws = nullptr;
+  long long have = 0;
+  rc = workspace(s, need, st, &ws, &have);
+  if (rc != COSMA_OK) return rc;
+  const GemmArgs g{m, n, k, A, lda, B, ldb, C, ldc};
+  const Sched sc = sched_from_plan(m, n, k, p);
+  const long long wl = g_cfg.wait_limit > 0 ? g_cfg.wait_limit : kDefaultWaitLimit;
+  int err = 0;
+  switch (p.kernel) {
+    case COSMA_KERNEL_SIMT_F64:
+    case COSMA_KERNEL_SIMT_F32:
+      err = launch_simt(dtype, g, sc, ws, s->d_status, st);
+      if (!err && p.pk > 1) err = launch_reduce(dtype, g, p.pk, ws, st);
+      break;
+    case COSMA_KERNEL_TC_BF16:
+      err = launch_tc_bf16(g, sc, p, ws, have, s->d_status, wl, st);
+      break;
+    case COSMA_KERNEL_EMU_BF16:
+      err = launch_emu_bf16(g, sc, p, g_cfg, ws, have, s->d_status, wl, st);
+      break;
+    default:
+      return COSMA_ERR_INVALID_ARG;
+  }
+  if (err < 0) return err;  // a cosma_status from a launcher
+  return err == 0 ? COSMA_OK : COSMA_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace cosma
+
+using namespace cosma;
+
+extern "C" {
+
+int cosma_init(const cosma_config* cfg) {
+  if (cfg) {
+    if (!(cfg->delta >= 0.0 && cfg->delta < 1.0)) return COSMA_ERR_INVALID_ARG;
+    if (cfg->selector < COSMA_SELECT_ANALYTIC || cfg->selector > COSMA_SELECT_LEARNED)
+      return COSMA_ERR_INVALID_ARG;
+    if (cfg->emu_slices < 0 || cfg->emu_slices > 12) return COSMA_ERR_INVALID_ARG;
+    if (cfg->emu_slice_bits < 0 || cfg->emu_slice_bits > 8) return COSMA_ERR_INVALID_ARG;
+    if (cfg->wait_limit < 0) return COSMA_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (cfg) g_cfg = *cfg;
+  int rc;
+  return state(&rc) ? COSMA_OK : rc;
+}
+
+int cosma_get_config(cosma_config* out) {
+  if (!out) return COSMA_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  *out = g_cfg;
+  return COSMA_OK;
+}
+
+int cosma_set_workspace(void* dptr, size_t bytes) {
+  if (bytes > 0 && (!dptr || (uintptr_t)dptr % 256)) return COSMA_ERR_INVALID_ARG;
+  if (bytes > 0 && !is_device_ptr(dptr)) return COSMA_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  int rc;
+  DeviceState* s = state(&rc);
+  if (!s) return rc;
+  s->borrowed = bytes > 0 ? dptr : nullptr;
+  s->borrowed_bytes = bytes;
+  return COSMA_OK;
+}
+
+void cosma_finalize(void) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  const int d = current_device();
+  if (d < 0) return;
+  DeviceState& s = g_dev[d];
+  if (!s.ready) return;
+  cudaDeviceSynchronize();
+  if (s.arena) cudaFree(s.arena);
+  if (s.d_status) cudaFree(s.d_status);
+  s = DeviceState{};
+}
+
+int cosma_gemm(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void* B,
+               int64_t ldb, void* C, int64_t ldc, int dtype, void* stream) {
+  return run(m, n, k, A, lda, B, ldb, C, ldc, dtype, nullptr, stream);
+}
+
+int cosma_gemm_planned(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda,
+                       const void* B, int64_t ldb, void* C, int64_t ldc, int dtype,
+                       const cosma_plan* plan, void* stream) {
+  if (!plan) return COSMA_ERR_INVALID_ARG;
+  return run(m, n, k, A, lda, B, ldb, C, ldc, dtype, plan, stream);
+}
+
+int cosma_gemm_grouped(int count, const cosma_problem* problems, int dtype, void* stream) {
+  if (count < 0 || (count > 0 && !problems)) return COSMA_ERR_INVALID_ARG;
+  if (dtype != COSMA_F32 && dtype != COSMA_BF16) return COSMA_ERR_UNSUPPORTED;
+  if (count == 0) return COSMA_OK;
+  for (int i = 0; i < count; ++i) {
+    const cosma_problem& q = problems[i];
+    const int rc = check_args(q.m, q.n, q.k, q.A, q.lda, q.B, q.ldb, q.C, q.ldc, dtype);
+    if (rc != COSMA_OK) return rc;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lock(g_mu);
+  int rc;
+  DeviceState* s = state(&rc);
+  if (!s) return rc;
+  long long need = 0;
+  rc = grouped_gemm(count, problems, dtype, s->info, nullptr, 0, s->d_status, 0, st, &need);
+  if (rc != COSMA_OK) return rc;
+  void* ws = nullptr;
+  long long have = 0;
+  rc = workspace(s, need, st, &ws, &have);
+  if (rc != COSMA_OK) return rc;
+  const long long wl = g_cfg.wait_limit > 0 ? g_cfg.wait_limit : kDefaultWaitLimit;
+  return grouped_gemm(count, problems, dtype, s->info, ws, have, s->d_status, wl, st, &need);
+}
+
+int cosma_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int selector, cosma_plan* out) {
+  if (!out) return COSMA_ERR_INVALID_ARG;
+  if (m < 0 || n < 0 || k < 0) return COSMA_ERR_INVALID_ARG;
+  if (selector < COSMA_SELECT_ANALYTIC || selector > COSMA_SELECT_LEARNED) return COSMA_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceInfo info;
+  int rc;
+  DeviceState* s = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0) s = state(&rc);
+  else cudaGetLastError();
+  if (s) info = s->info;
+  else info.sms = 148;  // planning without a device (host-only tests)
+  rc = plan_gemm(m, n, k, dtype, selector, info, g_cfg, out);
+  if (rc == COSMA_OK) out->workspace_bytes = total_workspace(m, n, k, dtype, *out);
+  return rc;
+}
+
+long long cosma_plan_units(int64_t m, int64_t n, int64_t k, const cosma_plan* plan,
+                           int64_t* units, long long max_units) {
+  if (!plan || m < 1 || n < 1 || k < 1 || max_units < 0 || (max_units > 0 && !units))
+    return COSMA_ERR_INVALID_ARG;
+  if (plan->tile_m < 1 || plan->tile_n < 1 || plan->k_block < 1 || plan->pk < 1 ||
+      plan->ctas < 1 || plan->order < 0 || plan->order > 1)
+    return COSMA_ERR_INVALID_ARG;
+  if (plan->order == 0 && (long long)plan->pm * plan->pn * plan->pk != plan->ctas)
+    return COSMA_ERR_INVALID_ARG;
+  const Sched s = sched_from_plan(m, n, k, *plan);
+  long long total = 0;
+  for (int c = 0; c < s.ctas; ++c) {
+    const int64_t nu = units_of_cta(s, c);
+    for (int64_t i = 0; i < nu; ++i, ++total) {
+      if (total >= max_units) continue;
+      const Unit u = unit_of_cta(s, c, i);
+      int64_t* o = units + 6 * total;
+      o[0] = u.tile_row * s.tile_m;
+      o[1] = (u.tile_row + 1) * s.tile_m < m ? (u.tile_row + 1) * s.tile_m : m;
+      o[2] = u.tile_col * s.tile_n;
+      o[3] = (u.tile_col + 1) * s.tile_n < n ? (u.tile_col + 1) * s.tile_n : n;
+      o[4] = u.kb0 * s.k_block;
+      o[5] = u.kb1 * s.k_block < k ? u.kb1 * s.k_block : k;
+    }
+  }
+  return total;
+}
+
+int cosma_stream_status(void* stream) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  int rc;
+  DeviceState* s = state(&rc);
+  if (!s) return rc;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return COSMA_ERR_CUDA;
+  int h = 0;
+  if (cudaMemcpy(&h, s->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return COSMA_ERR_CUDA;
+  if (h != 0 && cudaMemset(s->d_status, 0, sizeof(int)) != cudaSuccess) return COSMA_ERR_CUDA;
+  return h;
+}
+
+const char* cosma_status_string(int status) {
+  switch (status) {
+    case COSMA_OK: return "ok";
+    case COSMA_ERR_INVALID_ARG: return "invalid argument";
+    case COSMA_ERR_UNSUPPORTED: return "unsupported";
+    case COSMA_ERR_CUDA: return "CUDA error";
+    case COSMA_ERR_TIMEOUT: return "device wait timed out";
+    case COSMA_ERR_NONFINITE: return "non-finite input to the emulated path";
+    case COSMA_ERR_NO_WORKSPACE: return "no workspace";
+  }
+  return "unknown status";
+}
+
+long long cosma_launch_count(void) { return g_launches.load(); }
+
+int cosma_device_sms(void) {
+  int d = -1, sms = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) { cudaGetLastError(); return 0; }
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms;
+}
+
+}  // extern "C"

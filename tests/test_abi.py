@@ -1,0 +1,166 @@
+"""Host-side checks of the C-ABI library (no GPU work): it loads, exports every
+declared entry point, rejects bad arguments before any launch, and its paper
+primitives (FindSeqSchedule, FitRanks, the plan's work units) agree with the
+oracle's independent searches and the pebble-game simulator."""
+import math
+import os
+import random
+import re
+
+import pytest
+
+from oracle import bounds, pebble
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1908_09606_gb300 import build as b
+    b.build()
+    from paper_1908_09606_gb300 import cosma
+    return cosma
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(cosma_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared_symbols()
+    assert len(declared) >= 14
+    raw = lib.load()
+    for name in declared:
+        assert hasattr(raw, name), f"{name} declared but not exported"
+    bound = {s[0] for s in lib.SIGNATURES}
+    assert declared == bound, f"binding out of sync: {declared ^ bound}"
+
+
+def test_status_strings(lib):
+    for s in range(-6, 1):
+        assert lib.status_string(s) not in ("", "unknown status")
+
+
+def test_rejects_bad_arguments_without_launch(lib):
+    # negative sizes, short leading dimensions, null pointers, bad dtype
+    assert lib.cosma_gemm(-1, 4, 4, 0, 4, 0, 4, 0, 4, lib.COSMA_F64) == lib.COSMA_ERR_INVALID_ARG
+    assert lib.cosma_gemm(4, 4, 4, 0, 3, 0, 4, 0, 4, lib.COSMA_F64) == lib.COSMA_ERR_INVALID_ARG
+    assert lib.cosma_gemm(4, 4, 4, 0, 4, 0, 3, 0, 4, lib.COSMA_F64) == lib.COSMA_ERR_INVALID_ARG
+    assert lib.cosma_gemm(4, 4, 4, 0, 4, 0, 4, 0, 2, lib.COSMA_F64) == lib.COSMA_ERR_INVALID_ARG
+    assert lib.cosma_gemm(4, 4, 4, 0, 4, 0, 4, 0, 4, lib.COSMA_F64) == lib.COSMA_ERR_INVALID_ARG
+    assert lib.cosma_gemm(4, 4, 4, 8, 4, 8, 4, 8, 4, 9) == lib.COSMA_ERR_INVALID_ARG
+    # host (non-device) pointers are refused before any launch
+    import numpy as np
+    a = np.zeros(16)
+    p = a.ctypes.data
+    assert lib.cosma_gemm(4, 4, 4, p, 4, p, 4, p, 4, lib.COSMA_F64) == lib.COSMA_ERR_INVALID_ARG
+    # empty products are no-ops
+    assert lib.cosma_gemm(0, 4, 4, 0, 4, 0, 4, 0, 4, lib.COSMA_F64) == lib.COSMA_OK
+    assert lib.cosma_gemm(4, 0, 4, 0, 4, 0, 1, 0, 1, lib.COSMA_F64) == lib.COSMA_OK
+    assert lib.cosma_gemm_grouped([], lib.COSMA_F32) == lib.COSMA_OK
+    assert lib.cosma_gemm_grouped([], lib.COSMA_F64) == lib.COSMA_ERR_UNSUPPORTED
+
+
+def test_init_validates_config(lib):
+    assert lib.cosma_init(delta=1.5) == lib.COSMA_ERR_INVALID_ARG
+    assert lib.cosma_init(selector=7) == lib.COSMA_ERR_INVALID_ARG
+    assert lib.cosma_init(emu_slice_bits=9) == lib.COSMA_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("S", [3, 5, 10, 16, 37, 64, 100, 257, 1000, 4096, 61952, 247808])
+def test_find_seq_schedule_matches_oracle(lib, S):
+    assert lib.cosma_find_seq_schedule(S) == bounds.find_seq_schedule(S)
+
+
+def test_fit_ranks_matches_oracle_random(lib):
+    rng = random.Random(1234)
+    for _ in range(150):
+        m, n, k = (rng.randint(1, 3000) for _ in range(3))
+        p = rng.randint(1, 90)
+        delta = rng.choice([0.0, 0.03, 0.1, 0.25])
+        assert lib.cosma_fit_ranks(m, n, k, p, delta) == bounds.fit_ranks(m, n, k, p, delta), \
+            (m, n, k, p, delta)
+
+
+def test_fit_ranks_paper_cases(lib):
+    n = 4160
+    assert lib.cosma_fit_ranks(n, n, n, 65, 0.03) == (4, 4, 4)                 # Fig. 6
+    g1 = lib.cosma_fit_ranks(16384, 16384, 16384, 9216, 0.03)
+    g2 = lib.cosma_fit_ranks(16384, 16384, 16384, 9217, 0.03)
+    assert g1 == g2 == bounds.fit_ranks(16384, 16384, 16384, 9216, 0.03)       # Sec. 9
+
+
+def _small_plan(lib, tile, kb, pk, order, ctas, pm=1, pn=1):
+    p = lib.cosma_plan()
+    p.kernel, p.tile_m, p.tile_n, p.k_block, p.stages = 0, tile[0], tile[1], kb, 2
+    p.pm, p.pn, p.pk, p.order, p.ctas = pm, pn, pk, order, ctas
+    return p
+
+
+@pytest.mark.parametrize("order,pk,grid", [(1, 1, None), (1, 2, None), (0, 1, (2, 2)),
+                                           (0, 2, (2, 1)), (1, 3, None)])
+def test_plan_units_cover_iteration_space_once(lib, order, pk, grid):
+    m, n, k = 11, 13, 9
+    pm, pn = grid if grid else (1, 1)
+    ctas = pm * pn * pk if order == 0 else 5
+    p = _small_plan(lib, (4, 4), 2, pk, order, ctas, pm, pn)
+    units = lib.cosma_plan_units(m, n, k, p)
+    seen = {}
+    for (r0, r1, c0, c1, k0, k1) in units:
+        for i in range(r0, r1):
+            for j in range(c0, c1):
+                for t in range(k0, k1):
+                    seen[(i, j, t)] = seen.get((i, j, t), 0) + 1
+    assert len(seen) == m * n * k and set(seen.values()) == {1}
+
+
+@pytest.mark.parametrize("order,pk", [(1, 1), (0, 1), (1, 2)])
+def test_plan_replay_in_pebble_game(lib, order, pk):
+    m, n, k = 16, 12, 10
+    a, b = 4, 4
+    pm, pn = (2, 3) if order == 0 else (1, 1)
+    ctas = pm * pn * pk if order == 0 else 6
+    p = _small_plan(lib, (a, b), 2, pk, order, ctas, pm, pn)
+    units = lib.cosma_plan_units(m, n, k, p)
+    # units of one k column must be replayed in k order for the partial-sum chain
+    units = sorted(units, key=lambda u: (u[0], u[2], u[4]))
+    S = pebble.listing1_working_set(a, b, sliding=False)
+    res = pebble.simulate(m, n, k, S, pebble.plan_schedule(m, n, k, units), sliding=False)
+    thm1 = bounds.thm1(m, n, k, S)
+    assert res.io >= thm1
+    if pk == 1:
+        assert res.io == pebble.tile_io(m, n, k, a, b)
+        assert res.io <= 1.3 * thm1
+
+
+def test_plan_query_host_only(lib):
+    # planning needs no GPU; every plan fits the kernel's limits
+    for dt in (lib.COSMA_F64, lib.COSMA_F32):
+        for shape in [(512, 512, 512), (16384, 16384, 16384), (4096, 4096, 1 << 20),
+                      (1 << 20, 4096, 4096), (65536, 65536, 1024), (7, 129, 1000)]:
+            p = lib.cosma_plan_query(*shape, dt)
+            assert p.ctas >= 1 and p.pk >= 1
+            assert p.io_words >= p.bound_words * 0.999 or shape[2] < 64
+            if p.order == 0:
+                assert p.pm * p.pn * p.pk == p.ctas
+            sms = p.sms
+            assert p.ctas <= sms
+            assert p.ctas >= sms - math.floor(0.03 * sms) or p.ctas == p.pm * p.pn * p.pk \
+                or p.ctas < sms
+
+
+def test_plan_io_accounting_matches_units(lib):
+    m, n, k = 512, 512, 512
+    p = lib.cosma_plan_query(m, n, k, lib.COSMA_F64)
+    units = lib.cosma_plan_units(m, n, k, p)
+    io = 0
+    for (r0, r1, c0, c1, k0, k1) in units:
+        io += (k1 - k0) * ((r1 - r0) + (c1 - c0))
+    io += m * n * (2 * p.pk + 1 if p.pk > 1 else 1)
+    assert io == pytest.approx(p.io_words)
