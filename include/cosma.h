@@ -156,6 +156,31 @@ int cosma_gemm_planned(int64_t m, int64_t n, int64_t k, const void* A, int64_t l
  * dtype: COSMA_F32 or COSMA_BF16. */
 int cosma_gemm_grouped(int count, const cosma_problem* problems, int dtype, void* stream);
 
+/* ---- allocation-free variant ------------------------------------------ */
+
+/* Size of the device array cosma_gemm_splitk_static uses for its partial sums
+ * (32 MiB, reserved on every GPU that loads the library until process exit). */
+#define COSMA_STATIC_SCRATCH_BYTES (32u << 20)
+
+/* C = A B (dtype COSMA_F64 or COSMA_F32) with k split into pk slices whose
+ * partial products go to a fixed, statically allocated device array, then a
+ * fixed-order Reduce; the call never allocates device memory (no cudaMalloc,
+ * no library arena).  The paper has no counterpart: it exists for callers
+ * that cannot allocate once running -- graph capture in the global mode,
+ * programs that own all device memory through their own pool, loops that
+ * cannot take cudaMalloc's implicit synchronisation.
+ *   pk >= 1 and at most ceil(k / k_block) of the planned tile
+ *   (else COSMA_ERR_INVALID_ARG); pk * m * n * sizeof(element) must not exceed
+ *   COSMA_STATIC_SCRATCH_BYTES (else COSMA_ERR_NO_WORKSPACE, nothing launched).
+ *   Other arguments and errors as cosma_gemm.
+ * The first call on a device looks the array's address up (cudaGetSymbolAddress)
+ * with that device current; make it before any stream capture.  All calls share
+ * the array and it keeps the last call's contents: calls whose kernels overlap
+ * on the GPU (other streams or threads) race on it and must be serialised. */
+int cosma_gemm_splitk_static(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda,
+                             const void* B, int64_t ldb, void* C, int64_t ldc, int dtype,
+                             int pk, void* stream);
+
 /* ---- planning --------------------------------------------------------- */
 
 /* Plan for an m x n x k product of the given dtype with the given selector

@@ -79,7 +79,10 @@ SIGNATURES = [
     ("cosma_status_string", ctypes.c_char_p, [_INT]),
     ("cosma_device_sms", _INT, []),
     ("cosma_launch_count", _LL, []),
+    ("cosma_gemm_splitk_static", _INT, [_I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64,
+                                        _INT, _INT, _VP]),
 ]
+COSMA_STATIC_SCRATCH_BYTES = 32 << 20
 
 
 def load(path=None):
@@ -148,6 +151,10 @@ def cosma_gemm_planned(m, n, k, A, lda, B, ldb, C, ldc, dtype, plan, stream=0):
 def cosma_gemm_grouped(problems, dtype, stream=0):
     arr = (cosma_problem * len(problems))(*problems)
     return load().cosma_gemm_grouped(len(problems), arr, dtype, stream)
+
+
+def cosma_gemm_splitk_static(m, n, k, A, lda, B, ldb, C, ldc, dtype, pk, stream=0):
+    return load().cosma_gemm_splitk_static(m, n, k, A, lda, B, ldb, C, ldc, dtype, pk, stream)
 
 
 def cosma_plan_query(m, n, k, dtype, selector=COSMA_SELECT_ANALYTIC):
