@@ -34,6 +34,7 @@ WORKLOADS = {
     "largeM": (1 << 20, 4096, 4096),
     "flat": (65536, 65536, 1024),
     "emu8192": (8192, 8192, 8192),
+    "4096": (4096, 4096, 4096),
     "512": (512, 512, 512),
 }
 DEFAULT_DTYPE = "f64"

@@ -83,7 +83,7 @@ typedef struct cosma_config {
   int selector;        /* default cosma_selector for cosma_gemm; default ANALYTIC */
   int emu_slices;      /* slices per operand for F64_EMU_BF16; 0 = default (6) */
   int emu_slice_bits;  /* magnitude bits per slice, 1..8; 0 = default (7) */
-  long long wait_limit;/* spin iterations before a device wait gives up; 0 = default */
+  long long wait_limit;/* clock cycles before a device wait gives up; 0 = default (2^31, ~1 s) */
 } cosma_config;
 
 /* A schedule for one product: the outcome of Alg. 1's FindSeqSchedule

@@ -16,6 +16,7 @@ int launch_emu_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, cons
                     void* ws, long long ws_bytes, int* status, long long wait_limit,
                     cudaStream_t st);
 long long emu_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_config& cfg);
+long long tc_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_plan& p, bool pack_a);
 int grouped_gemm(int count, const cosma_problem* problems, int dtype, const DeviceInfo& dev,
                  void* ws, long long ws_bytes, int* status, long long wait_limit, cudaStream_t st,
                  long long* needed);
@@ -40,7 +41,7 @@ std::mutex g_mu;
 DeviceState g_dev[kMaxDevices];
 cosma_config g_cfg = {0.03, COSMA_SELECT_ANALYTIC, 0, 0, 0};
 
-const long long kDefaultWaitLimit = 1LL << 26;  // spins of a bounded device wait
+const long long kDefaultWaitLimit = 1LL << 31;  // clock cycles (~1 s) before a device wait gives up
 
 int current_device() {
   int d = -1;
@@ -150,8 +151,13 @@ int check_args(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, cons
   return COSMA_OK;
 }
 
-long long total_workspace(int64_t m, int64_t n, int64_t k, int dtype, const cosma_plan& p) {
+long long total_workspace(int64_t m, int64_t n, int64_t k, int dtype, const cosma_plan& p,
+                          const void* A = nullptr, int64_t lda = 0) {
   if (dtype == COSMA_F64_EMU_BF16) return emu_workspace_bytes(m, n, k, g_cfg);
+  if (dtype == COSMA_BF16) {
+    const bool pack_a = A && ((reinterpret_cast<uintptr_t>(A) & 15) || ((lda * 2) & 15));
+    return tc_workspace_bytes(m, n, k, p, pack_a);
+  }
   return workspace_bytes(m, n, k, dtype, p);
 }
 
@@ -180,7 +186,7 @@ int run(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void*
     rc = plan_gemm(m, n, k, dtype, g_cfg.selector, s->info, g_cfg, &p);
     if (rc != COSMA_OK) return rc;
   }
-  const long long need = total_workspace(m, n, k, dtype, p);
+  const long long need = total_workspace(m, n, k, dtype, p, A, lda);
   void* ws = nullptr;
   long long have = 0;
   rc = workspace(s, need, st, &ws, &have);

@@ -1,8 +1,353 @@
-// K-BF16 (tcgen05) -- placeholder until the tensor-core kernel lands.
-#include "internal.h"
+// K-BF16: C (f32) = A (bf16) B (bf16) on the 5th-generation tensor cores.
+//
+// The paper's sequential schedule (Listing 1, Sec. 5.2) per CTA: a 128 x BN C
+// tile is held in tensor memory (the accumulator never leaves fast memory
+// until the tile is done), while A-column panels (128 x 64) and B-row panels
+// (64 x BN) stream through a STAGES-deep shared-memory ring filled by TMA --
+// Alg. 1's DistrData + Multiply with the double buffering of Sec. 7.3 (the
+// producer fetches round t+1 while the tensor cores multiply round t).
+//
+// Warp roles (192 threads): warp 0 issues TMA loads, warp 1 allocates tensor
+// memory and issues tcgen05.mma, warps 2-5 drain finished accumulators
+// (tcgen05.ld) to global memory.  Two accumulators alternate so the epilogue
+// of one tile overlaps the main loop of the next.  Work units come from the
+// plan's schedule (schedule.h); a k split writes f32 partials that the
+// Reduce kernel sums in a fixed order.
+//
+// B arrives row-major (k x n, n contiguous); it is first transposed into the
+// workspace so both operands are K-major for the MMA.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <mutex>
+
+#include "tc_common.cuh"
+
 namespace cosma {
-int launch_tc_bf16(const GemmArgs&, const Sched&, const cosma_plan&, void*, long long, int*,
-                   long long, cudaStream_t) {
-  return COSMA_ERR_UNSUPPORTED;
+
+// ---- host: tensor maps ---------------------------------------------------------
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
 }
+
+int encode_tmap_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
+                     int box_cols, int box_rows) {
+  auto fn = get_encode();
+  if (!fn) return COSMA_ERR_CUDA;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 2) & 15)) return COSMA_ERR_INVALID_ARG;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? COSMA_OK : COSMA_ERR_CUDA;
+}
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;
+
+// Bt[j][t] = B[t][j]: k x n (ldb) -> n x k (ldt).
+__global__ void transpose_bf16(const __nv_bfloat16* __restrict__ B, int64_t k, int64_t n,
+                               int64_t ldb, __nv_bfloat16* __restrict__ Bt, int64_t ldt) {
+  __shared__ __nv_bfloat16 tile[32][34];
+  const int64_t t0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t t = t0 + i, j = j0 + threadIdx.x;
+    if (t < k && j < n) tile[i][threadIdx.x] = B[t * ldb + j];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t j = j0 + i, t = t0 + threadIdx.x;
+    if (j < n && t < k) Bt[j * ldt + t] = tile[threadIdx.x][i];
+  }
+}
+
+struct TcArgs {
+  Sched s;
+  float* C;
+  int64_t ldc;
+  float* partial;
+  int* status;
+  long long wait_limit;
+  int vec_ok;  // C rows 16-byte aligned
+};
+
+template <int BN, int STAGES>
+struct Layout {
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int BAR_OFF = STAGES * STAGE_BYTES;
+  static constexpr int NBARS = 2 * STAGES + 5;  // full, empty, tfull[2], tempty[2], drain
+  static constexpr int TOTAL = BAR_OFF + NBARS * 8 + 16;
+  static constexpr int ALLOC = TOTAL + 1024;
+};
+
+__device__ __forceinline__ void store_row32(float* dst, int64_t col0, int64_t n, const uint32_t (&r)[32],
+                                            bool vec) {
+  if (vec && col0 + 32 <= n) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      d4[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                          __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (col0 + j < n) dst[j] = __uint_as_float(r[j]);
+  }
+}
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               TcArgs a) {
+  using L = Layout<BN, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&tfull[b], 1);
+      tc::mbar_init(&tempty[b], 4);
+    }
+    tc::mbar_init(drain, 1);
+    *abort_flag = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmA);
+    tc::prefetch_tmap(&tmB);
+  }
+  if (warp == 1) tc::tmem_alloc(tslot, 2 * BN);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem_base = *tslot;
+  const tc::WaitCtx w{a.wait_limit, a.status, abort_flag};
+  const int cta = blockIdx.x;
+  const int64_t nunits = units_of_cta(a.s, cta);
+
+  if (warp == 0) {
+    if (tc::elect_one()) {
+      int stage = 0;
+      uint32_t ph = 0;
+      uint32_t armed = 0;  // bit s: stage s armed at least once; last parity in armed_ph
+      uint32_t armed_ph = 0;
+      for (int64_t ui = 0; ui < nunits && !*abort_flag; ++ui) {
+        const Unit u = unit_of_cta(a.s, cta, ui);
+        bool ok = true;
+        for (int64_t kb = u.kb0; kb < u.kb1; ++kb) {
+          if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) { ok = false; break; }
+          tc::mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES);
+          uint8_t* sa = smem + stage * L::STAGE_BYTES;
+          tc::tma_load_2d(sa, &tmA, &full[stage], (int32_t)(kb * BK), (int32_t)(u.tile_row * BM));
+          tc::tma_load_2d(sa + L::A_BYTES, &tmB, &full[stage], (int32_t)(kb * BK),
+                          (int32_t)(u.tile_col * BN));
+          armed |= 1u << stage;
+          armed_ph = (armed_ph & ~(1u << stage)) | (ph << stage);
+          if (++stage == STAGES) { stage = 0; ph ^= 1; }
+        }
+        if (!ok) break;
+      }
+      if (*abort_flag) {
+        // Let every copy this thread started land before shared memory is released.
+        for (int s = 0; s < STAGES; ++s) {
+          if (!(armed >> s & 1)) continue;
+          const long long t0 = clock64();
+          while (!tc::mbar_try_wait(&full[s], (armed_ph >> s) & 1) &&
+                 clock64() - t0 < tc::kDrainCycles) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (tc::elect_one()) {
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+      int stage = 0;
+      uint32_t ph = 0, acc = 0;
+      uint32_t aph[2] = {0, 0};
+      for (int64_t ui = 0; ui < nunits && !*abort_flag; ++ui) {
+        const Unit u = unit_of_cta(a.s, cta, ui);
+        if (!tc::mbar_wait(&tempty[acc], aph[acc] ^ 1, w)) break;
+        tc::tc_fence_after();
+        const uint32_t d = tmem_base + acc * BN;
+        bool ok = true;
+        for (int64_t kb = u.kb0; kb < u.kb1; ++kb) {
+          if (!tc::mbar_wait(&full[stage], ph, w)) { ok = false; break; }
+          tc::tc_fence_after();
+          const uint32_t sa = tc::smem_u32(smem + stage * L::STAGE_BYTES);
+          const uint32_t sb = sa + L::A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            tc::mma_bf16(d, tc::smem_desc_sw128(sa + kk * 32), tc::smem_desc_sw128(sb + kk * 32),
+                         idesc, (kb > u.kb0 || kk > 0) ? 1u : 0u);
+          tc::mma_commit(&empty[stage]);
+          if (++stage == STAGES) { stage = 0; ph ^= 1; }
+        }
+        if (!ok) break;
+        tc::mma_commit(&tfull[acc]);
+        aph[acc] ^= 1;
+        acc ^= 1;
+      }
+      // All MMAs of this thread complete before tensor memory is released.
+      tc::mma_commit(drain);
+      const long long t0 = clock64();
+      while (!tc::mbar_try_wait(drain, 0) && clock64() - t0 < tc::kDrainCycles) {
+      }
+    }
+  } else {
+    const int q = warp & 3;  // tensor-memory lane quadrant this warp may access
+    uint32_t acc = 0;
+    uint32_t tph[2] = {0, 0};
+    for (int64_t ui = 0; ui < nunits; ++ui) {
+      const Unit u = unit_of_cta(a.s, cta, ui);
+      if (!tc::mbar_wait(&tfull[acc], tph[acc], w)) break;
+      tc::tc_fence_after();
+      const int64_t row = u.tile_row * BM + q * 32 + lane;
+      float* dst_row = nullptr;
+      if (row < a.s.m) {
+        dst_row = a.s.pk > 1 ? a.partial + (int64_t)u.ks * a.s.m * a.s.n + row * a.s.n
+                             : a.C + row * a.ldc;
+      }
+      const bool vec = a.s.pk > 1 ? ((a.s.n & 3) == 0) : (a.vec_ok != 0);
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 32) {
+        uint32_t r[32];
+        tc::tmem_ld_32x32(tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN + c, r);
+        tc::tmem_wait_ld();
+        const int64_t col0 = u.tile_col * BN + c;
+        if (dst_row && col0 < a.s.n) store_row32(dst_row + col0, col0, a.s.n, r, vec);
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&tempty[acc]);
+      tph[acc] ^= 1;
+      acc ^= 1;
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem_base, 2 * BN);
+  }
+}
+
+template <int BN, int STAGES>
+int launch_kernel(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& args,
+                  cudaStream_t st) {
+  using L = Layout<BN, STAGES>;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC);
+  });
+  if (attr != cudaSuccess) return (int)attr;
+  tc_gemm_kernel<BN, STAGES><<<args.s.ctas, 192, L::ALLOC, st>>>(ta, tb, args);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+inline int64_t round_up(int64_t x, int64_t r) { return (x + r - 1) / r * r; }
+
+}  // namespace
+
+int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void* ws,
+                   long long ws_bytes, int* status, long long wait_limit, cudaStream_t st) {
+  const int64_t kp = round_up(g.k, 8);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  long long off = 0;
+  float* partial = nullptr;
+  if (p.pk > 1) {
+    partial = reinterpret_cast<float*>(w + off);
+    off += round_up((long long)p.pk * g.m * g.n * 4, 256);
+  }
+  __nv_bfloat16* Bt = reinterpret_cast<__nv_bfloat16*>(w + off);
+  off += round_up(g.n * kp * 2, 256);
+  const __nv_bfloat16* Ause = static_cast<const __nv_bfloat16*>(g.A);
+  int64_t lda = g.lda;
+  const bool pack_a = (reinterpret_cast<uintptr_t>(g.A) & 15) || ((g.lda * 2) & 15);
+  if (pack_a) {
+    __nv_bfloat16* Ap = reinterpret_cast<__nv_bfloat16*>(w + off);
+    off += round_up(g.m * kp * 2, 256);
+    if (off > ws_bytes) return COSMA_ERR_NO_WORKSPACE;
+    if (cudaMemcpy2DAsync(Ap, kp * 2, g.A, g.lda * 2, g.k * 2, g.m, cudaMemcpyDeviceToDevice,
+                          st) != cudaSuccess)
+      return (int)cudaGetLastError();
+    Ause = Ap;
+    lda = kp;
+  }
+  if (off > ws_bytes) return COSMA_ERR_NO_WORKSPACE;
+  {
+    dim3 grid((unsigned)((g.n + 31) / 32), (unsigned)((g.k + 31) / 32));
+    if (grid.y > 65535) return COSMA_ERR_UNSUPPORTED;
+    transpose_bf16<<<grid, dim3(32, 8), 0, st>>>(static_cast<const __nv_bfloat16*>(g.B), g.k, g.n,
+                                                 g.ldb, Bt, kp);
+    count_launch();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return (int)e;
+  }
+  CUtensorMap ta, tb;
+  int rc = encode_tmap_bf16(&ta, Ause, g.m, g.k, lda, BK, BM);
+  if (rc != COSMA_OK) return rc;
+  rc = encode_tmap_bf16(&tb, Bt, g.n, g.k, kp, BK, p.tile_n);
+  if (rc != COSMA_OK) return rc;
+  TcArgs args;
+  args.s = s;
+  args.C = static_cast<float*>(g.C);
+  args.ldc = g.ldc;
+  args.partial = partial;
+  args.status = status;
+  args.wait_limit = wait_limit;
+  args.vec_ok = ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0 && (g.ldc & 3) == 0) ? 1 : 0;
+  int err;
+  if (p.tile_n == 256) err = launch_kernel<256, 4>(ta, tb, args, st);
+  else err = launch_kernel<128, 6>(ta, tb, args, st);
+  if (err) return err;
+  if (p.pk > 1) {
+    GemmArgs gr = g;
+    return launch_reduce(COSMA_F32, gr, p.pk, partial, st);
+  }
+  return 0;
+}
+
+long long tc_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_plan& p, bool pack_a) {
+  const int64_t kp = round_up(k, 8);
+  long long b = 0;
+  if (p.pk > 1) b += round_up((long long)p.pk * m * n * 4, 256);
+  b += round_up(n * kp * 2, 256);
+  if (pack_a) b += round_up(m * kp * 2, 256);
+  return b;
+}
+
 }  // namespace cosma
