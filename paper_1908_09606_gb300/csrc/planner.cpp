@@ -45,7 +45,7 @@ int tiles_for(int kernel, TileChoice* out) {
       out[0] = {128, 256, 64, 4}; out[1] = {128, 128, 64, 6};
       return 2;
     case COSMA_KERNEL_EMU_BF16:
-      out[0] = {128, 128, 64, 6};
+      out[0] = {128, 128, 64, 5};
       return 1;
   }
   return 0;
