@@ -36,8 +36,9 @@ WORKLOADS = {
     "emu8192": (8192, 8192, 8192),
     "4096": (4096, 4096, 4096),
     "512": (512, 512, 512),
+    "grouped512": None,   # 512 problems, dims log-uniform in [64, 4096], seed 1
 }
-DEFAULT_DTYPE = "f64"
+DEFAULT_DTYPE = "f64_emu_bf16"
 
 
 def parse():
@@ -51,6 +52,7 @@ def parse():
     ap.add_argument("--impl", default="cosma", choices=["cosma", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-native", action="store_true")
     return ap.parse_args()
 
 
@@ -149,22 +151,29 @@ def _smi_id(torch, dev):
 # oracle timing (CPU baseline leg and the reference arm)
 
 
-def oracle_sample(m, n, k, target_s, kind="uniform", gen="f64"):
+def oracle_sample(m, n, k, target_s, kind="uniform", gen="f64", seed=0, keep=False):
     """Time the oracle's plain product on an r x r corner of C (full k) sized
-    to about target_s seconds.  Returns (flop/s, seconds, rows)."""
+    to about target_s seconds.  Returns (flop/s, seconds, rows[, block])."""
     import numpy as np
     import cosma_inputs as ci
     from oracle import gemm as og
+
+    def operand(x):
+        if gen == "bf16":
+            x = x.float().numpy()
+        return np.asarray(x, dtype=np.float64)
+
     r = 32
     while True:
-        A = np.asarray(ci.rows(np.arange(r), k, kind, gen, 0, ci.STREAM_A), dtype=np.float64)
-        B = np.asarray(ci.cols(np.arange(r), k, n, kind, gen, 0, ci.STREAM_B), dtype=np.float64).T
-        B = np.ascontiguousarray(B)
+        A = operand(ci.rows(np.arange(r), k, kind, gen, seed, ci.STREAM_A))
+        B = np.ascontiguousarray(operand(ci.cols(np.arange(r), k, n, kind, gen, seed,
+                                                 ci.STREAM_B)).T)
         t0 = time.perf_counter()
-        og.gemm(A, B, "naive")
+        block = og.gemm(A, B, "naive")
         dt = time.perf_counter() - t0
         if dt >= target_s or r >= min(m, n):
-            return 2.0 * r * r * k / dt, dt, r
+            out = (2.0 * r * r * k / dt, dt, r)
+            return out + (block,) if keep else out
         grow = math.sqrt(max(target_s / max(dt, 1e-3), 1.0))
         r = int(min(min(m, n), max(r + 1, r * min(grow, 4.0))))
 
@@ -179,7 +188,7 @@ def run_reference(args):
     vals = []
     rows = None
     for i in range(args.warmup + args.steps):
-        fl, dt, rows = oracle_sample(m, n, k, 8.0 if i >= args.warmup else 2.0, gen=gen)
+        fl, dt, rows = oracle_sample(m, n, k, 8.0 if i >= args.warmup else 2.0, gen=gen)[:3]
         if i >= args.warmup:
             vals.append(fl)
     value = statistics.median(vals) / 1e12
@@ -201,10 +210,188 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 
 
+def run_grouped(args):
+    """512 independent products in one persistent grouped launch, replayed from a
+    CUDA graph; compared with one cosma_gemm launch per product."""
+    import numpy as np
+    import torch
+    from paper_1908_09606_gb300 import cosma
+    from cosma_inputs import device as cid
+    import cosma_inputs as ci
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    cosma.load()
+    dtype = "bf16" if args.dtype not in ("f32", "bf16") else args.dtype
+    g = "bf16" if dtype == "bf16" else "f32"
+    tdt = torch.bfloat16 if g == "bf16" else torch.float32
+    dims = ci.grouped_dims(512, seed=1)
+    As, Bs, Cs = [], [], []
+    for i, (m, n, k) in enumerate(dims):
+        A = torch.empty((m, k), dtype=tdt, device="cuda")
+        B = torch.empty((k, n), dtype=tdt, device="cuda")
+        cid.fill(A, "uniform", g, 1000 + i + 100000 * rank, ci.STREAM_A)
+        cid.fill(B, "uniform", g, 1000 + i + 100000 * rank, ci.STREAM_B)
+        As.append(A)
+        Bs.append(B)
+        Cs.append(torch.empty((m, n), dtype=torch.float32, device="cuda"))
+    flops = float((2 * dims.prod(axis=1)).sum())
+    stream = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        cosma.gemm_grouped(As, Bs, Cs, dtype)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        cosma.gemm_grouped(As, Bs, Cs, dtype)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(_smi_id(torch, local))
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    reps = 20  # graph replays per step: one replay is ~1 TFLOP
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    l0 = cosma.cosma_launch_count()
+    evs[0].record(stream)
+    for i in range(args.steps):
+        for _ in range(reps):
+            graph.replay()
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = sum(evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps))
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    replay_ms = total_ms / (args.steps * reps)
+    value = world * flops / (replay_ms * 1e-3) / 1e12
+    # library kernels per replay: the grouped prep (bf16) and the grouped GEMM
+    per_replay = 2 if dtype == "bf16" else 1
+    launches = per_replay * reps * args.steps
+    # dominant kernel time from an eager, profiled call
+    cosma.cosma_profile_read()
+    cosma.cosma_profile_enable(True)
+    for _ in range(3):
+        cosma.gemm_grouped(As, Bs, Cs, dtype)
+    torch.cuda.synchronize()
+    cosma.cosma_profile_enable(False)
+    kms, kn = cosma.cosma_profile_read()
+    kms /= max(kn, 1)
+    # one launch per product, same operands
+    code = cosma.DTYPES[dtype]
+    sh = stream.cuda_stream
+
+    def per_gemm():
+        for A, B, C in zip(As, Bs, Cs):
+            m, k = A.shape
+            n = B.shape[1]
+            rc = cosma.cosma_gemm(m, n, k, A.data_ptr(), k, B.data_ptr(), n, C.data_ptr(), n,
+                                  code, sh)
+            if rc != 0:
+                raise cosma.CosmaError(rc, "per-gemm baseline")
+    per_gemm()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        per_gemm()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pg_ms = e0.elapsed_time(e1) / 3
+    peaks, peak_src = _peaks()
+    if dtype == "bf16":
+        roof = {"kernel": "grouped_tc_kernel", "bound": "tensor",
+                "peak": peaks.get("bf16_tflops_sustained", 1700.0),
+                "peak_source": f"bf16_tflops_sustained of {peak_src} peaks"}
+    else:
+        roof = {"kernel": "grouped_simt_kernel", "bound": "alu",
+                "peak": _alu_peak_tflops("f32", torch.cuda.get_device_properties(local)
+                                         .multi_processor_count),
+                "peak_source": "derived: SMs x 128 FMA/clk x 2 x 2070 MHz"}
+    roof.update({"achieved": flops / (kms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                 "algorithmic": "sum of 2mnk over the 512 products per launch",
+                 "kernel_ms": kms, "traffic": None})
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    # e2e: operands copied in from pinned host memory, one result read back
+    Ah = [a.cpu().pin_memory() for a in As]
+    Bh = [b.cpu().pin_memory() for b in Bs]
+    Ch = [torch.empty(c.shape, dtype=c.dtype, pin_memory=True) for c in Cs]
+    e0.record(stream)
+    for A, B, a, b in zip(As, Bs, Ah, Bh):
+        A.copy_(a, non_blocking=True)
+        B.copy_(b, non_blocking=True)
+    graph.replay()
+    for C, c in zip(Cs, Ch):
+        c.copy_(C, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ems = e0.elapsed_time(e1)
+    esz = 2 if dtype == "bf16" else 4
+    e2e = {"value": world * flops / (ems * 1e-3) / 1e12, "unit": "TFLOP/s",
+           "h2d_bytes_per_step": int(sum(a.numel() + b.numel() for a, b in zip(As, Bs)) * esz),
+           "d2h_bytes_per_step": int(sum(c.numel() for c in Cs) * 4), "steps": 1}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        from oracle import gemm as og
+        t0 = time.perf_counter()
+        done = 0.0
+        i = 0
+        while time.perf_counter() - t0 < 12.0 and i < len(dims):
+            m, n, k = dims[i]
+            Ah_ = np.asarray(ci.matrix(m, k, "uniform", "f32", 1000 + i, ci.STREAM_A), np.float64)
+            Bh_ = np.asarray(ci.matrix(k, n, "uniform", "f32", 1000 + i, ci.STREAM_B), np.float64)
+            if m * n * k > 3e8:
+                Ah_, Bh_ = Ah_[:64], Bh_[:, :64]
+                m2, n2 = Ah_.shape[0], Bh_.shape[1]
+            else:
+                m2, n2 = m, n
+            og.gemm(Ah_, Bh_, "naive")
+            done += 2.0 * m2 * n2 * k
+            i += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": done / dt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle naive loop over the first {i} problems "
+                         f"(>3e8 MACs: 64x64 corner), {dt:.1f} s incl. input generation"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": dtype, "data": "synthetic",
+                "config": {"workload": "grouped: 512 independent products, m,n,k log-uniform "
+                                       "in [64,4096] seed 1, one persistent launch replayed "
+                                       f"from a CUDA graph ({reps} replays per step)",
+                           "flops_per_replay": flops, "replay_ms": replay_ms,
+                           "l2": "inputs larger than L2"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks,
+                "one_launch_per_gemm": {"value": flops / (pg_ms * 1e-3) / 1e12,
+                                        "unit": "TFLOP/s", "ms": pg_ms,
+                                        "grouped_speedup": pg_ms / replay_ms}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "grouped512":
+        return run_grouped(args)
 
     import torch
     import torch.distributed as dist
@@ -257,6 +444,8 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = cosma.cosma_launch_count()
+    cosma.cosma_profile_read()          # drop anything recorded before
+    cosma.cosma_profile_enable(True)
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     evs[0].record(stream)
     for i in range(args.steps):
@@ -266,6 +455,8 @@ def main():
     if world > 1:
         dist.barrier()
     launches = cosma.cosma_launch_count() - launches0
+    cosma.cosma_profile_enable(False)
+    kern_total_ms, kern_n = cosma.cosma_profile_read()
     clocks = sampler.stop()
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     total_ms = sum(step_ms)
@@ -279,21 +470,49 @@ def main():
     if st != 0:
         raise cosma.CosmaError(st, "device status after timed region")
 
-    # Roofline of the dominant kernel: one launch per step unless k is split.
+    # Roofline of the dominant kernel, timed by the library's event pair around it.
     peaks, peak_src = _peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    kern_ms = statistics.mean(step_ms)
+    kern_ms = kern_total_ms / max(kern_n, 1)
+    cfg_lib = cosma.cosma_get_config()
+    slices = cfg_lib.emu_slices or 6
+    pairs = slices * (slices + 1) // 2
     if dtype in ("f64", "f32"):
-        peak = _alu_peak_tflops(dtype, sms)
-        roof = {"bound": "alu", "achieved": flops / (kern_ms * 1e-3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "peak_source": "derived: SMs x FMA lanes x 2 x max clock"}
+        roof = {"kernel": f"simt_gemm_kernel<{dtype}>", "bound": "alu",
+                "achieved": flops / (kern_ms * 1e-3) / 1e12,
+                "peak": _alu_peak_tflops(dtype, sms), "unit": "TFLOP/s",
+                "peak_source": "derived: SMs x FMA lanes/clk x 2 x 2070 MHz",
+                "algorithmic": "2mnk flop per launch"}
     else:
-        peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        roof = {"bound": "tensor", "achieved": flops / (kern_ms * 1e-3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "peak_source": f"bf16 sustained, {peak_src}"}
+        work = flops * (pairs if dtype == "f64_emu_bf16" else 1)
+        roof = {"kernel": "emu_gemm_kernel" if dtype == "f64_emu_bf16" else "tc_gemm_kernel",
+                "bound": "tensor", "achieved": work / (kern_ms * 1e-3) / 1e12,
+                "peak": peaks.get("bf16_tflops_sustained", 1700.0), "unit": "TFLOP/s",
+                "peak_source": f"bf16_tflops_sustained of {peak_src} peaks",
+                "algorithmic": (f"{pairs} slice-pair products x 2mnk bf16 flop per launch"
+                                if dtype == "f64_emu_bf16" else "2mnk flop per launch")}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
-    roof["kernel_launches_per_step"] = 1 + (1 if plan.pk > 1 else 0)
+    roof["kernel_ms"] = kern_ms
+    roof["kernel_launches_timed"] = kern_n
+
+    # Native FP64 on the same operands, for "split-BF16 vs native FP64".
+    native = None
+    if dtype == "f64_emu_bf16" and not args.no_native:
+        Cn = torch.empty_like(C)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = cosma.cosma_gemm(m, n, k, A.data_ptr(), k, B.data_ptr(), n, Cn.data_ptr(), n,
+                              cosma.COSMA_F64, sh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rc != 0:
+            raise cosma.CosmaError(rc, "native f64")
+        nms = e0.elapsed_time(e1)
+        native = {"value": flops / (nms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms": nms,
+                  "speedup_of_emulated": (flops / (nms * 1e-3) / 1e12) and value /
+                  (flops / (nms * 1e-3) / 1e12)}
 
     # End-to-end through the public API from pinned host buffers.
     e2e = None
@@ -328,12 +547,24 @@ def main():
                "d2h_bytes_per_step": m * n * C.element_size(), "steps": e_steps}
         del Ah, Bh, Ch
 
+    # CPU baseline: the oracle on a bounded block of the same product; its values
+    # also give the error of the GPU results on that block.
     cpu = None
+    errors = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        fl, dt, rows = oracle_sample(m, n, k, 12.0, gen="f32" if dtype == "f32" else "f64")
+        import numpy as np
+        from oracle import gemm as og
+        gen_o = "f32" if dtype == "f32" else ("bf16" if dtype == "bf16" else "f64")
+        fl, dt, rows, ref = oracle_sample(m, n, k, 12.0, gen=gen_o, seed=rank, keep=True)
         cpu = {"value": fl / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
                "sample": f"oracle naive FP64 loop, {rows}x{rows} leading block of C, "
                          f"full k={k}, {dt:.1f} s"}
+        got = C[:rows, :rows].double().cpu().numpy()
+        errors = {"block": f"{rows}x{rows}", "this_path": og.normwise_rel_error(got, ref)}
+        if native is not None:
+            errors["native_f64"] = og.normwise_rel_error(
+                Cn[:rows, :rows].double().cpu().numpy(), ref)
+            errors["tolerance_emulated"] = 1e-12
 
     if rank == 0:
         cfg = workload_config(args.workload, m, n, k, dtype)
@@ -347,6 +578,7 @@ def main():
                           "f64_emu_bf16": "bf16 slices -> f64"}[dtype],
                 "data": "synthetic", "config": cfg, "roofline": roof, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+                "native_f64": native, "error_vs_oracle": errors,
                 "io": {"l2_to_sm_words_planned": plan.io_words,
                        "theorem1_words_at_S": plan.bound_words,
                        "ratio": plan.io_words / plan.bound_words,

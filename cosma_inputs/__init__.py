@@ -35,4 +35,5 @@ from .philox import (  # noqa: F401
     cols,
     STREAM_A,
     STREAM_B,
+    grouped_dims,
 )

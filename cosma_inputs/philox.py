@@ -102,3 +102,11 @@ def cols(col_idx, rows_total, cols_total, kind="uniform", dtype="f64", seed=0, s
     c = np.asarray(col_idx, dtype=np.uint64)[:, None]
     r = np.arange(rows_total, dtype=np.uint64)[None, :]
     return entries(r, c, cols_total, kind, dtype, seed, stream)
+
+
+def grouped_dims(count, seed=1, lo=64, hi=4096, stream=7):
+    """Sizes of a grouped workload: m, n, k of each problem are round(lo (hi/lo)^u),
+    u uniform in [0, 1) from this generator (seed, stream) -- log-uniform in [lo, hi]."""
+    u = (entries(np.arange(3 * count), np.zeros(3 * count), 1, "uniform", "f64", seed, stream)
+         + 1.0) / 2.0
+    return np.round(lo * (hi / lo) ** u).astype(np.int64).reshape(count, 3)

@@ -84,6 +84,8 @@ typedef struct cosma_config {
   int emu_slices;      /* slices per operand for F64_EMU_BF16; 0 = default (6) */
   int emu_slice_bits;  /* magnitude bits per slice, 1..8; 0 = default (7) */
   long long wait_limit;/* clock cycles before a device wait gives up; 0 = default (2^31, ~1 s) */
+  int grouped_tile;    /* C tile width of cosma_gemm_grouped: 0 = chosen by the library;
+                          bf16: 128 or 256 (tile 128 x N); f32: 64 or 128 (square tile) */
 } cosma_config;
 
 /* A schedule for one product: the outcome of Alg. 1's FindSeqSchedule
@@ -152,8 +154,14 @@ int cosma_gemm_planned(int64_t m, int64_t n, int64_t k, const void* A, int64_t l
                        const cosma_plan* plan, void* stream);
 
 /* `count` independent products in one persistent launch.  problems is a HOST
- * array (copied during the call; it may be reused once the call returns).
- * dtype: COSMA_F32 or COSMA_BF16. */
+ * array; it may be reused once the call returns.  dtype: COSMA_F32 or
+ * COSMA_BF16 (bf16 requires each A 16-byte aligned with lda a multiple of 8).
+ * The first call with a given set of problems builds a device table of the
+ * group (tensor maps, sizes, a cost-balanced assignment of tiles to CTAs) and
+ * caches it (8 groups per device, until cosma_finalize).  A repeated call
+ * with the same problems, pointers and workspace only launches kernels, so it
+ * may be captured in a CUDA graph; during capture a group that is not cached
+ * yet returns COSMA_ERR_NO_WORKSPACE. */
 int cosma_gemm_grouped(int count, const cosma_problem* problems, int dtype, void* stream);
 
 /* ---- allocation-free variant ------------------------------------------ */
@@ -206,6 +214,19 @@ int cosma_find_seq_schedule(long long S, int* a, int* b);
  * domain ceil(m/pm)ceil(k/pk) + ceil(k/pk)ceil(n/pn) + ceil(m/pm)ceil(n/pn)
  * (ties: more processors used, then the lexicographically smaller grid). */
 int cosma_fit_ranks(int64_t m, int64_t n, int64_t k, int p, double delta, int grid[3]);
+
+/* ---- measurement ------------------------------------------------------ */
+
+/* on != 0 enables timing of each call's dominant kernel (the main loop:
+ * K-F64, K-F32, K-BF16, K-EMU or the grouped kernel -- not the transposes,
+ * slice extraction or the Reduce).  While enabled the library records a CUDA
+ * event pair around that kernel on the call's stream.  Do not enable it while
+ * a stream is being captured into a graph. */
+int cosma_profile_enable(int on);
+
+/* Waits for the recorded event pairs, writes their summed elapsed time in
+ * milliseconds and their number, and clears them.  Either pointer may be NULL. */
+int cosma_profile_read(double* main_kernel_ms, long long* launches);
 
 /* ---- status ----------------------------------------------------------- */
 

@@ -28,7 +28,7 @@ KERNELS = {0: "simt_f64", 1: "simt_f32", 2: "tc_bf16", 3: "emu_bf16"}
 class cosma_config(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("selector", ctypes.c_int),
                 ("emu_slices", ctypes.c_int), ("emu_slice_bits", ctypes.c_int),
-                ("wait_limit", ctypes.c_longlong)]
+                ("wait_limit", ctypes.c_longlong), ("grouped_tile", ctypes.c_int)]
 
 
 class cosma_plan(ctypes.Structure):
@@ -79,6 +79,8 @@ SIGNATURES = [
     ("cosma_status_string", ctypes.c_char_p, [_INT]),
     ("cosma_device_sms", _INT, []),
     ("cosma_launch_count", _LL, []),
+    ("cosma_profile_enable", _INT, [_INT]),
+    ("cosma_profile_read", _INT, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_LL)]),
     ("cosma_gemm_splitk_static", _INT, [_I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64,
                                         _INT, _INT, _VP]),
 ]
@@ -120,8 +122,8 @@ def status_string(status):
 # ---- C-named wrappers (raw pointers and sizes) ---------------------------
 
 def cosma_init(delta=0.03, selector=COSMA_SELECT_ANALYTIC, emu_slices=0, emu_slice_bits=0,
-               wait_limit=0):
-    cfg = cosma_config(delta, selector, emu_slices, emu_slice_bits, wait_limit)
+               wait_limit=0, grouped_tile=0):
+    cfg = cosma_config(delta, selector, emu_slices, emu_slice_bits, wait_limit, grouped_tile)
     return load().cosma_init(ctypes.byref(cfg))
 
 
@@ -196,6 +198,17 @@ def cosma_device_sms():
 
 def cosma_launch_count():
     return load().cosma_launch_count()
+
+
+def cosma_profile_enable(on=True):
+    return load().cosma_profile_enable(1 if on else 0)
+
+
+def cosma_profile_read():
+    """(summed milliseconds of the dominant kernels, number of launches timed)."""
+    ms, n = ctypes.c_double(), ctypes.c_longlong()
+    _check(load().cosma_profile_read(ctypes.byref(ms), ctypes.byref(n)), "cosma_profile_read")
+    return ms.value, n.value
 
 
 # ---- torch convenience (marshalling only) --------------------------------

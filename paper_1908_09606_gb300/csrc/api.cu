@@ -5,6 +5,7 @@
 #include <string.h>
 #include <atomic>
 #include <mutex>
+#include <vector>
 
 #include "internal.h"
 
@@ -19,10 +20,29 @@ long long emu_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_confi
 long long tc_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_plan& p, bool pack_a);
 int grouped_gemm(int count, const cosma_problem* problems, int dtype, const DeviceInfo& dev,
                  void* ws, long long ws_bytes, int* status, long long wait_limit, cudaStream_t st,
-                 long long* needed);
+                 long long* needed, int requested_tile);
+void grouped_release(int dev);
 
 static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<cudaEvent_t> g_prof_ev;  // start, stop, start, stop, ...
+static size_t g_prof_used = 0;
+
+void prof_mark(cudaStream_t st, bool begin) {
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  if (!g_prof_on) return;
+  if (begin && (g_prof_used & 1)) return;   // unmatched begin: ignore
+  if (!begin && !(g_prof_used & 1)) return;
+  if (g_prof_used == g_prof_ev.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return; }
+    g_prof_ev.push_back(e);
+  }
+  cudaEventRecord(g_prof_ev[g_prof_used++], st);
+}
 
 namespace {
 
@@ -39,7 +59,7 @@ struct DeviceState {
 constexpr int kMaxDevices = 16;
 std::mutex g_mu;
 DeviceState g_dev[kMaxDevices];
-cosma_config g_cfg = {0.03, COSMA_SELECT_ANALYTIC, 0, 0, 0};
+cosma_config g_cfg = {0.03, COSMA_SELECT_ANALYTIC, 0, 0, 0, 0};
 
 const long long kDefaultWaitLimit = 1LL << 31;  // clock cycles (~1 s) before a device wait gives up
 
@@ -229,6 +249,9 @@ int cosma_init(const cosma_config* cfg) {
     if (cfg->emu_slices < 0 || cfg->emu_slices > 12) return COSMA_ERR_INVALID_ARG;
     if (cfg->emu_slice_bits < 0 || cfg->emu_slice_bits > 8) return COSMA_ERR_INVALID_ARG;
     if (cfg->wait_limit < 0) return COSMA_ERR_INVALID_ARG;
+    if (cfg->grouped_tile != 0 && cfg->grouped_tile != 64 && cfg->grouped_tile != 128 &&
+        cfg->grouped_tile != 256)
+      return COSMA_ERR_INVALID_ARG;
   }
   std::lock_guard<std::mutex> lock(g_mu);
   if (cfg) g_cfg = *cfg;
@@ -262,6 +285,7 @@ void cosma_finalize(void) {
   DeviceState& s = g_dev[d];
   if (!s.ready) return;
   cudaDeviceSynchronize();
+  grouped_release(d);
   if (s.arena) cudaFree(s.arena);
   if (s.d_status) cudaFree(s.d_status);
   s = DeviceState{};
@@ -294,14 +318,28 @@ int cosma_gemm_grouped(int count, const cosma_problem* problems, int dtype, void
   DeviceState* s = state(&rc);
   if (!s) return rc;
   long long need = 0;
-  rc = grouped_gemm(count, problems, dtype, s->info, nullptr, 0, s->d_status, 0, st, &need);
+  rc = grouped_gemm(count, problems, dtype, s->info, nullptr, 0, s->d_status, 0, st, &need,
+                    g_cfg.grouped_tile);
   if (rc != COSMA_OK) return rc;
   void* ws = nullptr;
   long long have = 0;
   rc = workspace(s, need, st, &ws, &have);
   if (rc != COSMA_OK) return rc;
+  // Problems with k == 0 get C = 0; empty ones need nothing.
+  const size_t w = (size_t)elem_bytes_out(dtype);
+  for (int i = 0; i < count; ++i) {
+    const cosma_problem& q = problems[i];
+    if (q.m > 0 && q.n > 0 && q.k == 0) {
+      if (cudaMemset2DAsync(q.C, (size_t)q.ldc * w, 0, (size_t)q.n * w, (size_t)q.m, st) !=
+          cudaSuccess)
+        return COSMA_ERR_CUDA;
+    }
+  }
   const long long wl = g_cfg.wait_limit > 0 ? g_cfg.wait_limit : kDefaultWaitLimit;
-  return grouped_gemm(count, problems, dtype, s->info, ws, have, s->d_status, wl, st, &need);
+  rc = grouped_gemm(count, problems, dtype, s->info, ws, have, s->d_status, wl, st, nullptr,
+                    g_cfg.grouped_tile);
+  if (rc < 0) return rc;
+  return rc == 0 ? COSMA_OK : COSMA_ERR_CUDA;
 }
 
 int cosma_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int selector, cosma_plan* out) {
@@ -377,6 +415,34 @@ const char* cosma_status_string(int status) {
 }
 
 long long cosma_launch_count(void) { return g_launches.load(); }
+
+int cosma_profile_enable(int on) {
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  g_prof_on = on != 0;
+  return COSMA_OK;
+}
+
+int cosma_profile_read(double* main_kernel_ms, long long* launches) {
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  double total = 0.0;
+  long long n = 0;
+  int rc = COSMA_OK;
+  for (size_t i = 0; i + 1 < g_prof_used; i += 2) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(g_prof_ev[i + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, g_prof_ev[i], g_prof_ev[i + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      rc = COSMA_ERR_CUDA;
+      continue;
+    }
+    total += ms;
+    ++n;
+  }
+  g_prof_used = 0;
+  if (main_kernel_ms) *main_kernel_ms = total;
+  if (launches) *launches = n;
+  return rc;
+}
 
 int cosma_device_sms(void) {
   int d = -1, sms = 0;

@@ -570,7 +570,9 @@ int launch_emu_bf16(const GemmArgs& g, const Sched& sch, const cosma_plan& p,
                                 ELayout::ALLOC);
   });
   if (attr != cudaSuccess) return (int)attr;
+  prof_mark(st, true);
   emu_gemm_kernel<<<sch.ctas, 320, ELayout::ALLOC, st>>>(ta, tb, args);
+  prof_mark(st, false);
   count_launch();
   return (int)cudaGetLastError();
 }

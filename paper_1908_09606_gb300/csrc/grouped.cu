@@ -1,9 +1,639 @@
-// K-GROUPED -- placeholder until the persistent grouped kernel lands.
-#include "internal.h"
+// K-GROUPED: many independent products C_i = A_i B_i in one persistent launch.
+//
+// Batching pattern (not in the paper).  The host builds, once per distinct
+// group, a device table: per problem its TMA tensor maps and sizes, and a
+// static assignment of all (problem, tile) work units to CTAs -- units sorted
+// by cost (k blocks) and handed to the least-loaded CTA (longest processing
+// time first), so no atomics or device queue are needed.  Each CTA then runs
+// the C-stationary schedule of Listing 1 on its units exactly as the
+// single-product kernels do: bf16 on tcgen05 (TMA ring, TMEM accumulators),
+// f32 on the FMA pipes.  B_i (k x n) is first transposed into the workspace
+// by one grouped prep launch so both MMA operands are K-major.
+//
+// The table is cached (by the problems' contents, the tile and the workspace
+// address): after one eager call the same call can be captured in a CUDA
+// graph, because a cache hit launches kernels only (no allocation, no host
+// copy).  Up to kCacheSlots groups stay cached per device until
+// cosma_finalize; a captured graph stays valid while its group is cached.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <mutex>
+#include <queue>
+#include <vector>
+
+#include "simt_f32.cuh"
+#include "simt_tile.cuh"
+#include "tc_common.cuh"
+
 namespace cosma {
-int grouped_gemm(int, const cosma_problem*, int, const DeviceInfo&, void*, long long, int*,
-                 long long, cudaStream_t, long long* needed) {
-  if (needed) *needed = 0;
-  return COSMA_ERR_UNSUPPORTED;
+
+namespace {
+
+constexpr int GBM = 128, GBK = 64;
+constexpr int kCacheSlots = 8;
+
+struct alignas(64) GMap {
+  CUtensorMap ta;
+  CUtensorMap tb;
+};
+
+struct GMeta {
+  int64_t m, n, k;
+  const void* A;
+  int64_t lda;
+  const void* B;
+  int64_t ldb;
+  void* C;
+  int64_t ldc;
+  __nv_bfloat16* Bt;  // bf16: B transposed (n x kp)
+  int64_t ldt;
+  __nv_bfloat16* Ap;  // bf16: A copied with a 16-byte row pitch when its own is not
+  int64_t ldap;
+  int vec_ok;
+  int f32_async;  // f32: A, B 16-byte aligned with pitches multiple of 4 floats
+};
+
+struct GUnit {
+  int p, tile_row, tile_col, pad;
+};
+
+struct Table {
+  unsigned long long key = 0;
+  int count = 0, dtype = -1, tile_n = 0, ctas = 0;
+  void* dev = nullptr;  // device copy
+  size_t bytes = 0;
+  // device views
+  const GMap* maps = nullptr;
+  const GMeta* meta = nullptr;
+  const GUnit* units = nullptr;
+  const int* cta_off = nullptr;
+  const int64_t* tprefix = nullptr;  // transpose-tile prefix, count + 1
+  const int64_t* aprefix = nullptr;  // A-copy-tile prefix, count + 1
+  int64_t ttiles = 0;
+  int64_t atiles = 0;
+  int64_t nunits = 0;
+};
+
+std::mutex g_tab_mu;
+Table g_cache[16][kCacheSlots];
+int g_next[16];
+
+inline int64_t rup(int64_t x, int64_t r) { return (x + r - 1) / r * r; }
+
+unsigned long long mix(unsigned long long h, unsigned long long v) {
+  h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+  return h;
 }
+
+// ---- kernels -------------------------------------------------------------------
+
+__device__ __forceinline__ int find_problem(const int64_t* prefix, int count, int64_t x) {
+  int lo = 0, hi = count;  // prefix[lo] <= x < prefix[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Transposes every B_i (k x n) into Bt_i (n x kp) and copies each A_i whose
+// row pitch is not a multiple of 16 bytes into Ap_i (m x kp); 32 x 32 tiles.
+__global__ void grouped_prep_kernel(const GMeta* __restrict__ meta, const int64_t* __restrict__ tprefix,
+                                    const int64_t* __restrict__ aprefix, int count, int64_t ttiles,
+                                    int64_t atiles) {
+  __shared__ __nv_bfloat16 tile[32][34];
+  for (int64_t x = blockIdx.x; x < ttiles + atiles; x += gridDim.x) {
+    if (x < ttiles) {
+      const int p = find_problem(tprefix, count, x);
+      const GMeta& g = meta[p];
+      const int64_t local = x - tprefix[p];
+      const int64_t tiles_j = (g.n + 31) / 32;
+      const int64_t tj = local % tiles_j, tt = local / tiles_j;
+      const int64_t t0 = tt * 32, j0 = tj * 32;
+      const __nv_bfloat16* B = static_cast<const __nv_bfloat16*>(g.B);
+      __syncthreads();
+      for (int i = threadIdx.y; i < 32; i += 8) {
+        const int64_t t = t0 + i, j = j0 + threadIdx.x;
+        if (t < g.k && j < g.n) tile[i][threadIdx.x] = B[t * g.ldb + j];
+      }
+      __syncthreads();
+      for (int i = threadIdx.y; i < 32; i += 8) {
+        const int64_t j = j0 + i, t = t0 + threadIdx.x;
+        if (j < g.n && t < g.k) g.Bt[j * g.ldt + t] = tile[threadIdx.x][i];
+      }
+    } else {
+      const int64_t y = x - ttiles;
+      const int p = find_problem(aprefix, count, y);
+      const GMeta& g = meta[p];
+      const int64_t local = y - aprefix[p];
+      const int64_t tiles_t = (g.k + 31) / 32;
+      const int64_t r0 = (local / tiles_t) * 32, t0 = (local % tiles_t) * 32;
+      const __nv_bfloat16* A = static_cast<const __nv_bfloat16*>(g.A);
+      for (int i = threadIdx.y; i < 32; i += 8) {
+        const int64_t r = r0 + i, t = t0 + threadIdx.x;
+        if (r < g.m && t < g.k) g.Ap[r * g.ldap + t] = A[r * g.lda + t];
+      }
+    }
+  }
+}
+
+struct GArgs {
+  const GMap* maps;
+  const GMeta* meta;
+  const GUnit* units;
+  const int* cta_off;
+  int* status;
+  long long wait_limit;
+};
+
+template <int BN, int STAGES>
+struct GLayout {
+  static constexpr int A_BYTES = GBM * GBK * 2;
+  static constexpr int B_BYTES = BN * GBK * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int BAR_OFF = STAGES * STAGE_BYTES;
+  static constexpr int NBARS = 2 * STAGES + 5;
+  static constexpr int TOTAL = BAR_OFF + NBARS * 8 + 16;
+  static constexpr int ALLOC = TOTAL + 1024;
+};
+
+__device__ __forceinline__ void acquire_tmap(const CUtensorMap* m) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(
+                   reinterpret_cast<uint64_t>(m))
+               : "memory");
+}
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(192, 1) grouped_tc_kernel(GArgs a) {
+  using L = GLayout<BN, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&tfull[b], 1);
+      tc::mbar_init(&tempty[b], 4);
+    }
+    tc::mbar_init(drain, 1);
+    *abort_flag = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) tc::tmem_alloc(tslot, 2 * BN);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem_base = *tslot;
+  const tc::WaitCtx w{a.wait_limit, a.status, abort_flag};
+  const int u0 = a.cta_off[blockIdx.x], u1 = a.cta_off[blockIdx.x + 1];
+
+  if (warp == 0) {
+    if (tc::elect_one()) {
+      int stage = 0;
+      uint32_t ph = 0, armed = 0, armed_ph = 0;
+      int last_p = -1;
+      for (int ui = u0; ui < u1 && !*abort_flag; ++ui) {
+        const GUnit u = a.units[ui];
+        const GMeta& g = a.meta[u.p];
+        const CUtensorMap* ta = &a.maps[u.p].ta;
+        const CUtensorMap* tb = &a.maps[u.p].tb;
+        if (u.p != last_p) {
+          acquire_tmap(ta);
+          acquire_tmap(tb);
+          last_p = u.p;
+        }
+        const int64_t kbt = (g.k + GBK - 1) / GBK;
+        bool ok = true;
+        for (int64_t kb = 0; kb < kbt; ++kb) {
+          if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) { ok = false; break; }
+          tc::mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES);
+          uint8_t* sa = smem + stage * L::STAGE_BYTES;
+          tc::tma_load_2d(sa, ta, &full[stage], (int32_t)(kb * GBK), u.tile_row * GBM);
+          tc::tma_load_2d(sa + L::A_BYTES, tb, &full[stage], (int32_t)(kb * GBK), u.tile_col * BN);
+          armed |= 1u << stage;
+          armed_ph = (armed_ph & ~(1u << stage)) | (ph << stage);
+          if (++stage == STAGES) { stage = 0; ph ^= 1; }
+        }
+        if (!ok) break;
+      }
+      if (*abort_flag) {
+        for (int s = 0; s < STAGES; ++s) {
+          if (!(armed >> s & 1)) continue;
+          const long long t0 = clock64();
+          while (!tc::mbar_try_wait(&full[s], (armed_ph >> s) & 1) &&
+                 clock64() - t0 < tc::kDrainCycles) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (tc::elect_one()) {
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(GBM, BN);
+      int stage = 0;
+      uint32_t ph = 0, acc = 0;
+      uint32_t aph[2] = {0, 0};
+      for (int ui = u0; ui < u1 && !*abort_flag; ++ui) {
+        const GUnit u = a.units[ui];
+        const int64_t kbt = (a.meta[u.p].k + GBK - 1) / GBK;
+        if (!tc::mbar_wait(&tempty[acc], aph[acc] ^ 1, w)) break;
+        tc::tc_fence_after();
+        const uint32_t d = tmem_base + acc * BN;
+        bool ok = true;
+        for (int64_t kb = 0; kb < kbt; ++kb) {
+          if (!tc::mbar_wait(&full[stage], ph, w)) { ok = false; break; }
+          tc::tc_fence_after();
+          const uint32_t sa = tc::smem_u32(smem + stage * L::STAGE_BYTES);
+          const uint32_t sb = sa + L::A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < GBK / 16; ++kk)
+            tc::mma_bf16(d, tc::smem_desc_sw128(sa + kk * 32), tc::smem_desc_sw128(sb + kk * 32),
+                         idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+          tc::mma_commit(&empty[stage]);
+          if (++stage == STAGES) { stage = 0; ph ^= 1; }
+        }
+        if (!ok) break;
+        tc::mma_commit(&tfull[acc]);
+        aph[acc] ^= 1;
+        acc ^= 1;
+      }
+      tc::mma_commit(drain);
+      const long long t0 = clock64();
+      while (!tc::mbar_try_wait(drain, 0) && clock64() - t0 < tc::kDrainCycles) {
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    uint32_t acc = 0;
+    uint32_t tph[2] = {0, 0};
+    for (int ui = u0; ui < u1; ++ui) {
+      const GUnit u = a.units[ui];
+      const GMeta& g = a.meta[u.p];
+      if (!tc::mbar_wait(&tfull[acc], tph[acc], w)) break;
+      tc::tc_fence_after();
+      const int64_t row = (int64_t)u.tile_row * GBM + q * 32 + lane;
+      float* dst_row = row < g.m ? static_cast<float*>(g.C) + row * g.ldc : nullptr;
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 32) {
+        uint32_t r[32];
+        tc::tmem_ld_32x32(tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN + c, r);
+        tc::tmem_wait_ld();
+        const int64_t col0 = (int64_t)u.tile_col * BN + c;
+        if (dst_row && col0 < g.n) {
+          float* dst = dst_row + col0;
+          if (g.vec_ok && col0 + 32 <= g.n) {
+            float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              d4[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                  __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (col0 + j < g.n) dst[j] = __uint_as_float(r[j]);
+          }
+        }
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&tempty[acc]);
+      tph[acc] ^= 1;
+      acc ^= 1;
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem_base, 2 * BN);
+  }
+}
+
+template <int BMN, int BK, int TMN>
+__global__ void __launch_bounds__(256) grouped_simt_kernel(GArgs a) {
+  __shared__ __align__(16) SimtSmem<float, BMN, BMN, BK> sm;
+  const int u0 = a.cta_off[blockIdx.x], u1 = a.cta_off[blockIdx.x + 1];
+  for (int ui = u0; ui < u1; ++ui) {
+    const GUnit u = a.units[ui];
+    const GMeta& g = a.meta[u.p];
+    simt_tile<float, BMN, BMN, BK, TMN, TMN>(
+        static_cast<const float*>(g.A), g.lda, static_cast<const float*>(g.B), g.ldb,
+        static_cast<float*>(g.C), g.ldc, g.m, g.n, (int64_t)u.tile_row * BMN,
+        (int64_t)u.tile_col * BMN, 0, g.k, sm);
+  }
+}
+
+// 128 x 128 tiles: the cp.async ring for aligned problems, the register-staged
+// tile otherwise (both layouts share the dynamic shared memory).
+__global__ void __launch_bounds__(256) grouped_f32_kernel(GArgs a) {
+  extern __shared__ __align__(16) uint8_t gsm[];
+  const int u0 = a.cta_off[blockIdx.x], u1 = a.cta_off[blockIdx.x + 1];
+  for (int ui = u0; ui < u1; ++ui) {
+    const GUnit u = a.units[ui];
+    const GMeta& g = a.meta[u.p];
+    const float* A = static_cast<const float*>(g.A);
+    const float* B = static_cast<const float*>(g.B);
+    float* C = static_cast<float*>(g.C);
+    const int64_t r0 = (int64_t)u.tile_row * 128, c0 = (int64_t)u.tile_col * 128;
+    if (g.f32_async)
+      f32_tile_async(A, g.lda, B, g.ldb, C, g.ldc, g.m, g.n, r0, c0, 0, g.k, g.vec_ok != 0,
+                     *reinterpret_cast<F32Smem*>(gsm));
+    else
+      simt_tile<float, 128, 128, 16, 8, 8>(A, g.lda, B, g.ldb, C, g.ldc, g.m, g.n, r0, c0, 0, g.k,
+                                           *reinterpret_cast<SimtSmem<float, 128, 128, 16>*>(gsm));
+  }
+}
+
+// ---- host -----------------------------------------------------------------------
+
+int encode(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
+           int box_rows) {
+  return encode_tmap_bf16(map, base, rows, cols, ld, GBK, box_rows);
+}
+
+int pick_tile(int count, const cosma_problem* pr, int dtype, int requested) {
+  if (dtype == COSMA_BF16) {
+    if (requested == 128 || requested == 256) return requested;
+    std::vector<int64_t> ns(count);
+    for (int i = 0; i < count; ++i) ns[i] = pr[i].n;
+    std::nth_element(ns.begin(), ns.begin() + count / 2, ns.end());
+    return ns[count / 2] >= 512 ? 256 : 128;
+  }
+  if (requested == 64 || requested == 128) return requested;
+  std::vector<int64_t> mn(count);
+  for (int i = 0; i < count; ++i) mn[i] = std::min(pr[i].m, pr[i].n);
+  std::nth_element(mn.begin(), mn.begin() + count / 2, mn.end());
+  return mn[count / 2] >= 256 ? 128 : 64;
+}
+
+bool needs_pack(const cosma_problem& q) {
+  return (reinterpret_cast<uintptr_t>(q.A) & 15) || ((q.lda * 2) & 15);
+}
+
+long long ws_need(int count, const cosma_problem* pr, int dtype) {
+  if (dtype != COSMA_BF16) return 0;
+  long long b = 0;
+  for (int i = 0; i < count; ++i) {
+    const cosma_problem& q = pr[i];
+    if (!(q.m > 0 && q.n > 0 && q.k > 0)) continue;
+    b += rup(q.n * rup(q.k, 8) * 2, 256);
+    if (needs_pack(q)) b += rup(q.m * rup(q.k, 8) * 2, 256);
+  }
+  return b;
+}
+
+// Builds (or finds) the device table of this group.
+int get_table(int dev, int count, const cosma_problem* pr, int dtype, int tile, int sms, void* ws,
+              bool capturing, Table** out) {
+  unsigned long long key = mix(0, (unsigned long long)count);
+  key = mix(key, (unsigned long long)dtype);
+  key = mix(key, (unsigned long long)tile);
+  key = mix(key, (unsigned long long)(uintptr_t)ws);
+  for (int i = 0; i < count; ++i) {
+    const cosma_problem& q = pr[i];
+    key = mix(key, (unsigned long long)q.m);
+    key = mix(key, (unsigned long long)q.n);
+    key = mix(key, (unsigned long long)q.k);
+    key = mix(key, (unsigned long long)(uintptr_t)q.A);
+    key = mix(key, (unsigned long long)q.lda);
+    key = mix(key, (unsigned long long)(uintptr_t)q.B);
+    key = mix(key, (unsigned long long)q.ldb);
+    key = mix(key, (unsigned long long)(uintptr_t)q.C);
+    key = mix(key, (unsigned long long)q.ldc);
+  }
+  for (int s = 0; s < kCacheSlots; ++s) {
+    Table& t = g_cache[dev][s];
+    if (t.dev && t.key == key && t.count == count && t.dtype == dtype && t.tile_n == tile) {
+      *out = &t;
+      return COSMA_OK;
+    }
+  }
+  if (capturing) return COSMA_ERR_NO_WORKSPACE;
+
+  // Host image of the table.
+  const int tm = GBM;
+  const int tn = tile;
+  const int tmm = dtype == COSMA_BF16 ? tm : tile;
+  std::vector<GMeta> meta(count);
+  std::vector<GMap> maps(dtype == COSMA_BF16 ? count : 0);
+  std::vector<int64_t> tpre(count + 1, 0);
+  std::vector<int64_t> apre(count + 1, 0);
+  std::vector<GUnit> units;
+  std::vector<int64_t> cost;
+  uint8_t* wsp = static_cast<uint8_t*>(ws);
+  for (int i = 0; i < count; ++i) {
+    const cosma_problem& q = pr[i];
+    GMeta& g = meta[i];
+    g.m = q.m; g.n = q.n; g.k = q.k;
+    g.A = q.A; g.lda = q.lda; g.B = q.B; g.ldb = q.ldb; g.C = q.C; g.ldc = q.ldc;
+    g.Bt = nullptr; g.ldt = 0; g.Ap = nullptr; g.ldap = 0;
+    g.f32_async = ((reinterpret_cast<uintptr_t>(q.A) & 15) == 0 && (q.lda & 3) == 0 &&
+                   (reinterpret_cast<uintptr_t>(q.B) & 15) == 0 && (q.ldb & 3) == 0)
+                      ? 1
+                      : 0;
+    apre[i + 1] = apre[i];
+    g.vec_ok = ((reinterpret_cast<uintptr_t>(q.C) & 15) == 0 && (q.ldc & 3) == 0) ? 1 : 0;
+    if (dtype == COSMA_BF16 && q.m > 0 && q.n > 0 && q.k > 0) {
+      const int64_t kp = rup(q.k, 8);
+      g.Bt = reinterpret_cast<__nv_bfloat16*>(wsp);
+      g.ldt = kp;
+      wsp += rup(q.n * kp * 2, 256);
+      const void* a_src = q.A;
+      int64_t a_ld = q.lda;
+      if (needs_pack(q)) {
+        g.Ap = reinterpret_cast<__nv_bfloat16*>(wsp);
+        g.ldap = kp;
+        wsp += rup(q.m * kp * 2, 256);
+        a_src = g.Ap;
+        a_ld = kp;
+        apre[i + 1] = apre[i] + ((q.m + 31) / 32) * ((q.k + 31) / 32);
+      }
+      int rc = encode(&maps[i].ta, a_src, q.m, q.k, a_ld, GBM);
+      if (rc != COSMA_OK) return rc;
+      rc = encode(&maps[i].tb, g.Bt, q.n, q.k, kp, tn);
+      if (rc != COSMA_OK) return rc;
+      tpre[i + 1] = tpre[i] + ((q.n + 31) / 32) * ((q.k + 31) / 32);
+    }
+    if (dtype == COSMA_BF16 && !(q.m > 0 && q.n > 0 && q.k > 0)) tpre[i + 1] = tpre[i];
+    if (q.m == 0 || q.n == 0 || q.k == 0) continue;
+    const int64_t mt = (q.m + tmm - 1) / tmm, nt = (q.n + tn - 1) / tn;
+    for (int64_t r = 0; r < mt; ++r)
+      for (int64_t c = 0; c < nt; ++c) {
+        units.push_back(GUnit{i, (int)r, (int)c, 0});
+        cost.push_back((q.k + 63) / 64 + 2);  // k blocks + epilogue
+      }
+  }
+  // Longest-processing-time-first assignment of units to CTAs.
+  const int64_t U = (int64_t)units.size();
+  const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>(sms, U));
+  std::vector<int64_t> order(U);
+  for (int64_t i = 0; i < U; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int64_t x, int64_t y) { return cost[x] > cost[y]; });
+  typedef std::pair<int64_t, int> Load;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+  for (int c = 0; c < ctas; ++c) heap.push(Load(0, c));
+  std::vector<std::vector<int64_t>> per(ctas);
+  for (int64_t oi = 0; oi < U; ++oi) {
+    Load l = heap.top();
+    heap.pop();
+    per[l.second].push_back(order[oi]);
+    l.first += cost[order[oi]];
+    heap.push(l);
+  }
+  std::vector<GUnit> flat;
+  flat.reserve(U);
+  std::vector<int> off(ctas + 1, 0);
+  for (int c = 0; c < ctas; ++c) {
+    // within a CTA keep problem / tile order so panels of one problem stay hot
+    std::sort(per[c].begin(), per[c].end());
+    for (int64_t id : per[c]) flat.push_back(units[id]);
+    off[c + 1] = (int)flat.size();
+  }
+
+  // Device image: [maps][meta][units][cta_off][tprefix]
+  size_t o_maps = 0;
+  size_t o_meta = rup((int64_t)(maps.size() * sizeof(GMap)), 256);
+  size_t o_units = o_meta + rup((int64_t)(meta.size() * sizeof(GMeta)), 256);
+  size_t o_off = o_units + rup((int64_t)(std::max<int64_t>(U, 1) * sizeof(GUnit)), 256);
+  size_t o_tp = o_off + rup((int64_t)((ctas + 1) * sizeof(int)), 256);
+  size_t o_ap = o_tp + rup((int64_t)((count + 1) * sizeof(int64_t)), 256);
+  size_t total = o_ap + rup((int64_t)((count + 1) * sizeof(int64_t)), 256);
+  std::vector<uint8_t> host(total, 0);
+  if (!maps.empty()) memcpy(host.data() + o_maps, maps.data(), maps.size() * sizeof(GMap));
+  memcpy(host.data() + o_meta, meta.data(), meta.size() * sizeof(GMeta));
+  if (U) memcpy(host.data() + o_units, flat.data(), flat.size() * sizeof(GUnit));
+  memcpy(host.data() + o_off, off.data(), off.size() * sizeof(int));
+  memcpy(host.data() + o_tp, tpre.data(), tpre.size() * sizeof(int64_t));
+  memcpy(host.data() + o_ap, apre.data(), apre.size() * sizeof(int64_t));
+
+  Table& t = g_cache[dev][g_next[dev]];
+  g_next[dev] = (g_next[dev] + 1) % kCacheSlots;
+  if (t.dev && t.bytes < total) {
+    cudaFree(t.dev);  // synchronising free of an older group's table
+    t.dev = nullptr;
+  }
+  if (!t.dev) {
+    if (cudaMalloc(&t.dev, total) != cudaSuccess) {
+      cudaGetLastError();
+      t = Table{};
+      return COSMA_ERR_NO_WORKSPACE;
+    }
+    t.bytes = total;
+  }
+  if (cudaMemcpy(t.dev, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return COSMA_ERR_CUDA;
+  }
+  uint8_t* d = static_cast<uint8_t*>(t.dev);
+  t.key = key;
+  t.count = count;
+  t.dtype = dtype;
+  t.tile_n = tile;
+  t.ctas = ctas;
+  t.maps = reinterpret_cast<const GMap*>(d + o_maps);
+  t.meta = reinterpret_cast<const GMeta*>(d + o_meta);
+  t.units = reinterpret_cast<const GUnit*>(d + o_units);
+  t.cta_off = reinterpret_cast<const int*>(d + o_off);
+  t.tprefix = reinterpret_cast<const int64_t*>(d + o_tp);
+  t.aprefix = reinterpret_cast<const int64_t*>(d + o_ap);
+  t.ttiles = tpre[count];
+  t.atiles = apre[count];
+  t.nunits = U;
+  *out = &t;
+  return COSMA_OK;
+}
+
+template <int BN, int STAGES>
+int launch_tc(const Table& t, const GArgs& args, cudaStream_t st) {
+  using L = GLayout<BN, STAGES>;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(grouped_tc_kernel<BN, STAGES>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC);
+  });
+  if (attr != cudaSuccess) return (int)attr;
+  prof_mark(st, true);
+  grouped_tc_kernel<BN, STAGES><<<t.ctas, 192, L::ALLOC, st>>>(args);
+  prof_mark(st, false);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+int grouped_gemm(int count, const cosma_problem* problems, int dtype, const DeviceInfo& dev,
+                 void* ws, long long ws_bytes, int* status, long long wait_limit,
+                 cudaStream_t st, long long* needed, int requested_tile) {
+  const long long need = ws_need(count, problems, dtype);
+  if (needed) {  // sizing pass: report the workspace, launch nothing
+    *needed = need;
+    return COSMA_OK;
+  }
+  if (need > ws_bytes) return COSMA_ERR_NO_WORKSPACE;
+  const int tile = pick_tile(count, problems, dtype, requested_tile);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusNone;
+  Table* t = nullptr;
+  int rc;
+  {
+    std::lock_guard<std::mutex> lock(g_tab_mu);
+    rc = get_table(dev.device, count, problems, dtype, tile, dev.sms > 0 ? dev.sms : 148, ws,
+                   cs != cudaStreamCaptureStatusNone, &t);
+  }
+  if (rc != COSMA_OK) return rc;
+  if (t->nunits == 0) return COSMA_OK;
+  GArgs args{t->maps, t->meta, t->units, t->cta_off, status, wait_limit};
+  if (dtype == COSMA_BF16) {
+    if (t->ttiles + t->atiles > 0) {
+      const int64_t blocks = std::min<int64_t>(t->ttiles + t->atiles,
+                                               (int64_t)(dev.sms > 0 ? dev.sms : 148) * 16);
+      grouped_prep_kernel<<<(unsigned)blocks, dim3(32, 8), 0, st>>>(
+          t->meta, t->tprefix, t->aprefix, count, t->ttiles, t->atiles);
+      count_launch();
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return (int)e;
+    }
+    return tile == 256 ? launch_tc<256, 4>(*t, args, st) : launch_tc<128, 6>(*t, args, st);
+  }
+  if (tile == 128) {
+    static cudaError_t attr = cudaFuncSetAttribute(
+        grouped_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(F32Smem));
+    if (attr != cudaSuccess) return (int)attr;
+    prof_mark(st, true);
+    grouped_f32_kernel<<<t->ctas, 256, sizeof(F32Smem), st>>>(args);
+  } else {
+    prof_mark(st, true);
+    grouped_simt_kernel<64, 16, 4><<<t->ctas, 256, 0, st>>>(args);
+  }
+  prof_mark(st, false);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+void grouped_release(int dev) {
+  std::lock_guard<std::mutex> lock(g_tab_mu);
+  if (dev < 0 || dev >= 16) return;
+  for (int s = 0; s < kCacheSlots; ++s) {
+    if (g_cache[dev][s].dev) cudaFree(g_cache[dev][s].dev);
+    g_cache[dev][s] = Table{};
+  }
+  g_next[dev] = 0;
+}
+
 }  // namespace cosma

@@ -54,6 +54,8 @@ int launch_reduce(int dtype, const GemmArgs& g, int pk, const void* partial, cud
 
 // Launch accounting (api.cu): every kernel launch the library makes calls this.
 void count_launch(int n = 1);
+// Event pair around the dominant kernel of a call when profiling is enabled.
+void prof_mark(cudaStream_t st, bool begin);
 
 // Bytes of workspace a plan needs (split-k partials, operand copies, slices).
 long long workspace_bytes(int64_t m, int64_t n, int64_t k, int dtype, const cosma_plan& p);

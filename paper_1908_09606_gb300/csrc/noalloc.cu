@@ -92,7 +92,7 @@ extern "C" int cosma_gemm_splitk_static(int64_t m, int64_t n, int64_t k, const v
     return COSMA_ERR_CUDA;
   cudaDeviceGetAttribute(&info.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&info.regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-  cosma_config cfg = {0.03, COSMA_SELECT_ANALYTIC, 0, 0, 0};
+  cosma_config cfg = {0.03, COSMA_SELECT_ANALYTIC, 0, 0, 0, 0};
   cosma_plan p;
   int rc = plan_gemm(m, n, k, dtype, COSMA_SELECT_ANALYTIC, info, cfg, &p);
   if (rc != COSMA_OK) return rc;

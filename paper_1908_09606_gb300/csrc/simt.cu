@@ -14,102 +14,22 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "simt_tile.cuh"
+#include "simt_f32.cuh"
 
 namespace cosma {
 namespace {
 
-template <typename T>
-struct VecW {
-  static constexpr int V = 16 / sizeof(T);  // elements per 16-byte shared-memory access
-};
-
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__(256)
 simt_gemm_kernel(GemmArgs g, Sched s, T* partial) {
-  static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
-  static_assert(BN / TN == 16 && BM / TM == 16, "16 x 16 thread grid");
-  constexpr int V = VecW<T>::V;
-  constexpr int A_PER = BM * BK / 256;
-  constexpr int B_PER = BK * BN / 256;
-  __shared__ __align__(16) T As[2][BK][BM];
-  __shared__ __align__(16) T Bs[2][BK][BN];
-
-  const T* __restrict__ A = static_cast<const T*>(g.A);
-  const T* __restrict__ B = static_cast<const T*>(g.B);
-  const int tid = threadIdx.x;
-  const int ty = tid / 16, tx = tid % 16;
+  __shared__ __align__(16) SimtSmem<T, BM, BN, BK> sm;
+  const T* A = static_cast<const T*>(g.A);
+  const T* B = static_cast<const T*>(g.B);
   const int cta = blockIdx.x;
   const int64_t nunits = units_of_cta(s, cta);
-
   for (int64_t ui = 0; ui < nunits; ++ui) {
     const Unit u = unit_of_cta(s, cta, ui);
-    const int64_t row0 = u.tile_row * BM, col0 = u.tile_col * BN;
-    const int64_t kbeg = u.kb0 * (int64_t)s.k_block;
-    const int64_t kend = min(u.kb1 * (int64_t)s.k_block, g.k);
-    const int64_t nsteps = (kend - kbeg + BK - 1) / BK;
-
-    T acc[TM][TN];
-#pragma unroll
-    for (int i = 0; i < TM; ++i)
-#pragma unroll
-      for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
-
-    T ra[A_PER], rb[B_PER];
-    auto fetch = [&](int64_t k0) {
-#pragma unroll
-      for (int e = 0; e < A_PER; ++e) {
-        const int idx = tid + e * 256;
-        const int r = idx / BK, kk = idx % BK;
-        const int64_t gr = row0 + r, gk = k0 + kk;
-        ra[e] = (gr < g.m && gk < kend) ? A[gr * g.lda + gk] : T(0);
-      }
-#pragma unroll
-      for (int e = 0; e < B_PER; ++e) {
-        const int idx = tid + e * 256;
-        const int kk = idx / BN, c = idx % BN;
-        const int64_t gk = k0 + kk, gc = col0 + c;
-        rb[e] = (gk < kend && gc < g.n) ? B[gk * g.ldb + gc] : T(0);
-      }
-    };
-    auto stash = [&](int buf) {
-#pragma unroll
-      for (int e = 0; e < A_PER; ++e) {
-        const int idx = tid + e * 256;
-        As[buf][idx % BK][idx / BK] = ra[e];
-      }
-#pragma unroll
-      for (int e = 0; e < B_PER; ++e) {
-        const int idx = tid + e * 256;
-        Bs[buf][idx / BN][idx % BN] = rb[e];
-      }
-    };
-
-    __syncthreads();  // previous unit's readers are done with the ring
-    if (nsteps > 0) {
-      fetch(kbeg);
-      stash(0);
-    }
-    __syncthreads();
-    for (int64_t st = 0; st < nsteps; ++st) {
-      const int buf = (int)(st & 1);
-      if (st + 1 < nsteps) fetch(kbeg + (st + 1) * BK);
-#pragma unroll
-      for (int kk = 0; kk < BK; ++kk) {
-        T a[TM], b[TN];
-#pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty * TM + i];
-#pragma unroll
-        for (int j = 0; j < TN; ++j) b[j] = Bs[buf][kk][(j / V) * (16 * V) + tx * V + (j % V)];
-#pragma unroll
-        for (int i = 0; i < TM; ++i)
-#pragma unroll
-          for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-      }
-      if (st + 1 < nsteps) stash(buf ^ 1);
-      __syncthreads();
-    }
-
-    // Epilogue: the C tile (or this k slice's partial) leaves fast memory.
     T* dst;
     int64_t ld;
     if (s.pk > 1) {
@@ -119,16 +39,37 @@ simt_gemm_kernel(GemmArgs g, Sched s, T* partial) {
       dst = static_cast<T*>(g.C);
       ld = g.ldc;
     }
-#pragma unroll
-    for (int i = 0; i < TM; ++i) {
-      const int64_t r = row0 + ty * TM + i;
-      if (r >= g.m) continue;
-#pragma unroll
-      for (int j = 0; j < TN; ++j) {
-        const int64_t c = col0 + (j / V) * (16 * V) + tx * V + (j % V);
-        if (c < g.n) dst[r * ld + c] = acc[i][j];
-      }
+    simt_tile<T, BM, BN, BK, TM, TN>(A, g.lda, B, g.ldb, dst, ld, g.m, g.n, u.tile_row * BM,
+                                     u.tile_col * BN, u.kb0 * (int64_t)s.k_block,
+                                     min(u.kb1 * (int64_t)s.k_block, g.k), sm);
+  }
+}
+
+// K-F32 fast path: the cp.async multi-stage tile (simt_f32.cuh).
+__global__ void __launch_bounds__(256)
+simt_f32_async_kernel(GemmArgs g, Sched s, float* partial, int vec_c) {
+  extern __shared__ __align__(16) uint8_t f32_smem[];
+  F32Smem& sm = *reinterpret_cast<F32Smem*>(f32_smem);
+  const float* A = static_cast<const float*>(g.A);
+  const float* B = static_cast<const float*>(g.B);
+  const int cta = blockIdx.x;
+  const int64_t nunits = units_of_cta(s, cta);
+  for (int64_t ui = 0; ui < nunits; ++ui) {
+    const Unit u = unit_of_cta(s, cta, ui);
+    float* dst;
+    int64_t ld;
+    bool vec;
+    if (s.pk > 1) {
+      dst = partial + (int64_t)u.ks * g.m * g.n;
+      ld = g.n;
+      vec = (g.n & 3) == 0;
+    } else {
+      dst = static_cast<float*>(g.C);
+      ld = g.ldc;
+      vec = vec_c != 0;
     }
+    f32_tile_async(A, g.lda, B, g.ldb, dst, ld, g.m, g.n, u.tile_row * F32_BM, u.tile_col * F32_BN,
+                   u.kb0 * (int64_t)s.k_block, min(u.kb1 * (int64_t)s.k_block, g.k), vec, sm);
   }
 }
 
@@ -149,8 +90,10 @@ __global__ void reduce_kernel(int64_t m, int64_t n, int pk, const T* __restrict_
 
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 int launch_tile(const GemmArgs& g, const Sched& s, void* partial, cudaStream_t st) {
+  prof_mark(st, true);
   simt_gemm_kernel<T, BM, BN, BK, TM, TN>
       <<<s.ctas, 256, 0, st>>>(g, s, static_cast<T*>(partial));
+  prof_mark(st, false);
   count_launch();
   return (int)cudaGetLastError();
 }
@@ -164,7 +107,23 @@ int launch_simt(int dtype, const GemmArgs& g, const Sched& s, void* partial, int
     if (s.tile_m == 128) return launch_tile<double, 128, 128, 8, 8, 8>(g, s, partial, st);
     return launch_tile<double, 64, 64, 8, 4, 4>(g, s, partial, st);
   }
-  if (s.tile_m == 128) return launch_tile<float, 128, 128, 16, 8, 8>(g, s, partial, st);
+  if (s.tile_m == 128) {
+    const bool aligned = (reinterpret_cast<uintptr_t>(g.A) & 15) == 0 && (g.lda & 3) == 0 &&
+                         (reinterpret_cast<uintptr_t>(g.B) & 15) == 0 && (g.ldb & 3) == 0;
+    if (aligned && s.k_block % F32_BK == 0) {
+      static cudaError_t attr = cudaFuncSetAttribute(
+          simt_f32_async_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(F32Smem));
+      if (attr != cudaSuccess) return (int)attr;
+      const int vec_c = (reinterpret_cast<uintptr_t>(g.C) & 15) == 0 && (g.ldc & 3) == 0;
+      prof_mark(st, true);
+      simt_f32_async_kernel<<<s.ctas, 256, sizeof(F32Smem), st>>>(
+          g, s, static_cast<float*>(partial), vec_c);
+      prof_mark(st, false);
+      count_launch();
+      return (int)cudaGetLastError();
+    }
+    return launch_tile<float, 128, 128, 16, 8, 8>(g, s, partial, st);
+  }
   return launch_tile<float, 64, 64, 16, 4, 4>(g, s, partial, st);
 }
 

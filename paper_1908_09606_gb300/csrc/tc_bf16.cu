@@ -273,7 +273,9 @@ int launch_kernel(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& ar
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC);
   });
   if (attr != cudaSuccess) return (int)attr;
+  prof_mark(st, true);
   tc_gemm_kernel<BN, STAGES><<<args.s.ctas, 192, L::ALLOC, st>>>(ta, tb, args);
+  prof_mark(st, false);
   count_launch();
   return (int)cudaGetLastError();
 }

@@ -1,0 +1,148 @@
+"""GPU parity of the grouped persistent launch (K-GROUPED) against the oracle,
+through the C ABI, and its capture in a CUDA graph.
+
+Problem sizes: m, n, k each round(64 * 64^u), u uniform in [0, 1) from the
+shared generator (seed 1, stream 7) -- log-uniform in [64, 4096].  Operands of
+problem i come from seed 1000 + i.  Each problem is checked on sampled
+entries (tile corners, ragged edges, random) against the Dot2 oracle within
+gamma_k |A||B| (u = 2^-23 for the tensor-core f32 accumulation, 2^-24 for FMA).
+"""
+import numpy as np
+import pytest
+
+import cosma_inputs as ci
+from oracle import gemm as og
+
+from gpu_util import lib
+
+pytestmark = pytest.mark.gpu
+
+
+def problem_dims(count, seed=1):
+    return ci.grouped_dims(count, seed)
+
+
+def make_group(dims, dtype):
+    import torch
+    from cosma_inputs import device as cid
+    g = "bf16" if dtype == "bf16" else "f32"
+    tdt = torch.bfloat16 if g == "bf16" else torch.float32
+    As, Bs, Cs = [], [], []
+    for i, (m, n, k) in enumerate(dims):
+        A = torch.empty((m, k), dtype=tdt, device="cuda")
+        B = torch.empty((k, n), dtype=tdt, device="cuda")
+        if m and k:
+            cid.fill(A, "uniform", g, 1000 + i, ci.STREAM_A)
+        if k and n:
+            cid.fill(B, "uniform", g, 1000 + i, ci.STREAM_B)
+        As.append(A)
+        Bs.append(B)
+        Cs.append(torch.full((m, n), float("nan"), dtype=torch.float32, device="cuda"))
+    return As, Bs, Cs
+
+
+def check_group(dims, Cs, dtype, per_problem=6, u=None):
+    u = u or (2.0 ** -23 if dtype == "bf16" else 2.0 ** -24)
+    g = "bf16" if dtype == "bf16" else "f32"
+    rng = np.random.default_rng(5)
+    for i, (m, n, k) in enumerate(dims):
+        if m == 0 or n == 0:
+            continue
+        C = Cs[i].double().cpu().numpy()
+        if k == 0:
+            assert not C.any()
+            continue
+        rr = np.array([0, m - 1, min(127, m - 1)] + list(rng.integers(0, m, per_problem)))
+        cc = np.array([0, n - 1, min(255, n - 1)] + list(rng.integers(0, n, per_problem)))
+        Ar = ci.rows(rr, k, "uniform", g, 1000 + i, ci.STREAM_A)
+        Bc = ci.cols(cc, k, n, "uniform", g, 1000 + i, ci.STREAM_B)
+        if g == "bf16":
+            Ar, Bc = Ar.float().numpy(), Bc.float().numpy()
+        Ar, Bc = np.asarray(Ar, np.float64), np.asarray(Bc, np.float64)
+        ref = og.dot2_pairs(Ar, Bc)
+        absr = np.einsum("ij,ij->i", np.abs(Ar), np.abs(Bc))
+        gam = k * u / (1 - k * u)
+        got = C[rr, cc]
+        assert np.all(np.abs(got - ref) <= gam * absr + 1e-300), (i, m, n, k)
+
+
+def run_group(As, Bs, Cs, dtype):
+    import torch
+    cosma = lib()
+    cosma.gemm_grouped(As, Bs, Cs, dtype)
+    torch.cuda.synchronize()
+    assert cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream) == 0
+
+
+@pytest.mark.parametrize("tile", [0, 128, 256])
+def test_grouped_bf16_512_problems(tile):
+    cosma = lib()
+    dims = problem_dims(512)
+    As, Bs, Cs = make_group(dims, "bf16")
+    try:
+        assert cosma.cosma_init(grouped_tile=tile) == 0
+        run_group(As, Bs, Cs, "bf16")
+    finally:
+        cosma.cosma_init()
+    check_group(dims, Cs, "bf16", per_problem=4 if tile else 8)
+
+
+@pytest.mark.parametrize("tile", [64, 128])
+def test_grouped_f32(tile):
+    cosma = lib()
+    dims = problem_dims(96)
+    As, Bs, Cs = make_group(dims, "f32")
+    try:
+        assert cosma.cosma_init(grouped_tile=tile) == 0
+        run_group(As, Bs, Cs, "f32")
+    finally:
+        cosma.cosma_init()
+    check_group(dims, Cs, "f32")
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f32"])
+def test_grouped_empty_and_k0_problems(dtype):
+    dims = np.array([[0, 5, 7], [9, 0, 3], [130, 70, 0], [1, 1, 1], [129, 257, 65], [7, 9, 3000]])
+    As, Bs, Cs = make_group(dims, dtype)
+    run_group(As, Bs, Cs, dtype)
+    check_group(dims, Cs, dtype)
+
+
+def test_grouped_bf16_unaligned_a_is_packed():
+    import torch
+    from cosma_inputs import device as cid
+    cosma = lib()
+    store = torch.zeros((100, 140), dtype=torch.bfloat16, device="cuda")
+    A = store[:, 1:131]  # base 2 bytes off a 16-byte boundary, pitch 280 bytes
+    cid.fill(A, "uniform", "bf16", 1000, ci.STREAM_A)
+    B = torch.empty((130, 90), dtype=torch.bfloat16, device="cuda")
+    cid.fill(B, "uniform", "bf16", 1000, ci.STREAM_B)
+    C = torch.full((100, 90), float("nan"), dtype=torch.float32, device="cuda")
+    cosma.gemm_grouped([A], [B], [C], "bf16")
+    torch.cuda.synchronize()
+    check_group(np.array([[100, 90, 130]]), [C], "bf16")
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f32"])
+def test_grouped_captured_in_cuda_graph(dtype):
+    import torch
+    cosma = lib()
+    dims = problem_dims(64, seed=3)
+    As, Bs, Cs = make_group(dims, dtype)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        cosma.gemm_grouped(As, Bs, Cs, dtype)      # eager: builds and caches the table
+    torch.cuda.synchronize()
+    eager = [c.clone() for c in Cs]
+    for c in Cs:
+        c.fill_(float("nan"))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        cosma.gemm_grouped(As, Bs, Cs, dtype)
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    for c, e in zip(Cs, eager):
+        assert torch.equal(c, e)
+    check_group(dims, Cs, dtype, per_problem=3)

@@ -168,3 +168,16 @@ def test_full_size_sampled(dtype, family):
     else:
         absref = np.einsum("ij,ij->i", np.abs(Ar[ri]), np.abs(Bc[cj]))
         assert np.all(np.abs(got - ref) <= _gamma(k, 2.0 ** -24) * absref)
+
+
+@pytest.mark.parametrize("shape,lda,ldb,ldc", [((129, 260, 1000), None, None, None),
+                                               ((300, 260, 1001), 1004, 264, 268),
+                                               ((1, 4, 3), 4, None, None)])
+def test_f32_aligned_ragged_async_path(shape, lda, ldb, ldc):
+    # 16-byte aligned rows take the cp.async ring; ragged m, n, k are zero-filled
+    m, n, k = shape
+    C = _run(m, n, k, "f32", lda=lda, ldb=ldb, ldc=ldc)
+    A, B = host_operands(m, n, k, "f32")
+    ref = og.gemm(A, B, "dot2")
+    absref = og.gemm(np.abs(A), np.abs(B), "naive")
+    assert np.all(np.abs(C - ref) <= _gamma(k, 2.0 ** -24) * absref * (1 + 1e-12) + 1e-300)
