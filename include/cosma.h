@@ -192,7 +192,9 @@ int cosma_gemm_splitk_static(int64_t m, int64_t n, int64_t k, const void* A, int
 /* ---- planning --------------------------------------------------------- */
 
 /* Plan for an m x n x k product of the given dtype with the given selector
- * (cosma_selector).  Host only, no GPU work.  Returns cosma_status. */
+ * (cosma_selector).  ANALYTIC is host only; LEARNED runs the selector's
+ * forward kernel once per new shape (synchronously) and caches the choice.
+ * Returns cosma_status. */
 int cosma_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int selector,
                      cosma_plan* out);
 
@@ -214,6 +216,60 @@ int cosma_find_seq_schedule(long long S, int* a, int* b);
  * domain ceil(m/pm)ceil(k/pk) + ceil(k/pk)ceil(n/pn) + ceil(m/pm)ceil(n/pn)
  * (ties: more processors used, then the lexicographically smaller grid). */
 int cosma_fit_ranks(int64_t m, int64_t n, int64_t k, int p, double delta, int grid[3]);
+
+/* ---- learned selector (MLP cost model) -------------------------------- */
+
+/* The selector is a 3-layer FP32 network IN -> 64 -> 64 -> OUT with ReLU that
+ * maps a product's features to the predicted log2-time of each of the OUT plan
+ * candidates.  Parameter vector layout: W1 (64 x IN, row-major), b1 (64),
+ * W2 (64 x 64), b2 (64), W3 (OUT x 64), b3 (OUT).  Not in the paper. */
+#define COSMA_MLP_IN 7
+#define COSMA_MLP_HIDDEN 64
+#define COSMA_MLP_OUT 16
+#define COSMA_MLP_PARAMS (COSMA_MLP_HIDDEN * COSMA_MLP_IN + COSMA_MLP_HIDDEN + \
+                          COSMA_MLP_HIDDEN * COSMA_MLP_HIDDEN + COSMA_MLP_HIDDEN + \
+                          COSMA_MLP_OUT * COSMA_MLP_HIDDEN + COSMA_MLP_OUT)
+
+/* Plan candidate c (0 <= c < COSMA_MLP_OUT) for an m x n x k product: tile
+ * class c / 8 (0: the kernel's largest C tile, 1: its smaller one), k split
+ * pk = {1, 2, 4, 8}[(c / 2) % 4] and assignment order c % 2 (0: the FitRanks
+ * grid of rectangular local domains, 1: balanced stripes).  Host only.
+ * Returns COSMA_ERR_UNSUPPORTED when the candidate does not apply (k too
+ * short for the split, a kernel without that tile or split). */
+int cosma_plan_candidate(int64_t m, int64_t n, int64_t k, int dtype, int c, cosma_plan* out);
+
+/* Selector input row x[COSMA_MLP_IN] (HOST) of a product: log2(m)/16,
+ * log2(n)/16, log2(k)/16 and a one-hot of the dtype (F64, F32, BF16,
+ * F64_EMU_BF16).  m, n, k >= 1. */
+int cosma_selector_features(int64_t m, int64_t n, int64_t k, int dtype, float* x);
+
+/* K-MLP-FWD: Y[b] = MLP(X[b]) for b < batch.  X (batch x IN), params, Y
+ * (batch x OUT) are DEVICE pointers; asynchronous on `stream`. */
+int cosma_mlp_forward(int batch, const float* X, const float* params, float* Y, void* stream);
+
+/* K-MLP-BWD: loss L = (1/batch) sum_b (Y[b][cand[b]] - target[b])^2 and its
+ * gradient with respect to params, summed over the batch in a fixed order
+ * (deterministic).  All pointers DEVICE (loss: one float, may be NULL; grad:
+ * COSMA_MLP_PARAMS floats).  Uses library workspace (grown outside capture). */
+int cosma_mlp_loss_grad(int batch, const float* X, const int* cand, const float* target,
+                        const float* params, float* grad, float* loss, void* stream);
+
+/* K-MLP-ADAM: one Adam step (Kingma and Ba) on n parameters, step counting
+ * from 1; m, v are the moment buffers.  DEVICE pointers. */
+int cosma_mlp_adam(int n, float* params, const float* grad, float* m, float* v, int step,
+                   float lr, float beta1, float beta2, float eps, void* stream);
+
+/* Installs a trained network (HOST parameter vector) for COSMA_SELECT_LEARNED
+ * on the current device, valid for sizes with log2 in [log2_lo, log2_hi];
+ * outside that range (or with no network) plans fall back to the analytic
+ * selector.  params == NULL removes the network. */
+int cosma_selector_set(const float* params, double log2_lo, double log2_hi);
+
+/* Runs K-MLP-FWD on `count` shapes (HOST array mnk of 3*count int64) and
+ * writes, per shape, the candidate with the smallest predicted time among
+ * those that apply (best, HOST, count ints) and optionally all predictions
+ * (pred, HOST, count x OUT floats, may be NULL).  Synchronous. */
+int cosma_selector_predict(int count, const int64_t* mnk, int dtype, int* best, float* pred);
 
 /* ---- measurement ------------------------------------------------------ */
 

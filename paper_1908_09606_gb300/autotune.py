@@ -1,0 +1,326 @@
+"""Autotuner, selector training and regret evaluation (a8 of the hot path).
+
+  collect()   times every applicable plan candidate (cosma_plan_candidate,
+              cosma_gemm_planned, CUDA events, best of `reps` after a warm-up)
+              on random shapes and appends (shape, dtype, candidate, seconds)
+              rows to a JSONL file; rows already present are skipped, so an
+              interrupted run resumes where it stopped.
+  train()     fits the MLP cost model on those rows with the library's own
+              kernels (cosma_mlp_loss_grad + cosma_mlp_adam on the GPU),
+              checkpointing parameters and Adam state after every epoch.
+  evaluate()  exhaustive timing on held-out shapes: regret of the learned
+              choice and of the analytic plan against the best candidate.
+
+Shapes: m, n, k log-uniform in [lo, hi] from the shared generator, rejecting
+shapes with an operand above `cap_bytes`.  Every compute step runs in the
+CUDA library; this module only orchestrates and keeps records.
+"""
+
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+from . import cosma
+
+DTYPE_BYTES = {cosma.COSMA_BF16: (2, 4), cosma.COSMA_F32: (4, 4), cosma.COSMA_F64: (8, 8),
+               cosma.COSMA_F64_EMU_BF16: (8, 8)}
+
+
+def random_shapes(count, seed, lo=256, hi=65536, cap_bytes=16e9, dtype=cosma.COSMA_BF16,
+                  max_flops=None):
+    import cosma_inputs as ci
+    win, wout = DTYPE_BYTES[dtype]
+    out, i = [], 0
+    while len(out) < count:
+        e = np.arange(3 * i, 3 * i + 3)
+        u = (ci.entries(e, np.zeros(3), 1, "uniform", "f64", seed, 11) + 1.0) / 2.0
+        m, n, k = (int(round(lo * (hi / lo) ** x)) for x in u)
+        i += 1
+        if max(m * k * win, k * n * win, m * n * wout) > cap_bytes:
+            continue
+        if max_flops and 2.0 * m * n * k > max_flops:
+            continue
+        out.append((m, n, k))
+    return out
+
+
+class Operands:
+    """Device buffers reused for every shape (views of their leading part)."""
+
+    def __init__(self, dtype, cap_bytes):
+        import torch
+        from cosma_inputs import device as cid
+        win, wout = DTYPE_BYTES[dtype]
+        tin = {2: torch.bfloat16, 4: torch.float32, 8: torch.float64}[win]
+        tout = {4: torch.float32, 8: torch.float64}[wout]
+        g = {2: "bf16", 4: "f32", 8: "f64"}[win]
+        self.A = torch.empty(int(cap_bytes // win), dtype=tin, device="cuda")
+        self.B = torch.empty(int(cap_bytes // win), dtype=tin, device="cuda")
+        self.C = torch.empty(int(cap_bytes // wout), dtype=tout, device="cuda")
+        cid.fill(self.A.view(1, -1), "uniform", g, 21, 0)
+        cid.fill(self.B.view(1, -1), "uniform", g, 21, 1)
+
+    def ptrs(self):
+        return self.A.data_ptr(), self.B.data_ptr(), self.C.data_ptr()
+
+
+def time_plan(m, n, k, dtype, plan, ops, reps=2):
+    """Best-of-reps seconds of one product with the given plan (None -> analytic)."""
+    import torch
+    a, b, c = ops.ptrs()
+    s = torch.cuda.current_stream()
+    sh = s.cuda_stream
+
+    def run():
+        if plan is None:
+            rc = cosma.cosma_gemm(m, n, k, a, k, b, n, c, n, dtype, sh)
+        else:
+            rc = cosma.cosma_gemm_planned(m, n, k, a, k, b, n, c, n, dtype, plan, sh)
+        if rc != 0:
+            raise cosma.CosmaError(rc, "time_plan")
+
+    run()
+    best = math.inf
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(reps):
+        e0.record(s)
+        run()
+        e1.record(s)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    return best
+
+
+def candidates(m, n, k, dtype, max_ws_bytes):
+    out = []
+    for c in range(cosma.COSMA_MLP_OUT):
+        p = cosma.cosma_plan_candidate(m, n, k, dtype, c)
+        if p is not None and p.workspace_bytes <= max_ws_bytes:
+            out.append((c, p))
+    return out
+
+
+def _load_rows(path):
+    rows = []
+    if path and os.path.exists(path):
+        with open(path) as f:
+            for line in f:
+                line = line.strip()
+                if line:
+                    rows.append(json.loads(line))
+    return rows
+
+
+def collect(path, shapes, dtype=cosma.COSMA_BF16, cap_bytes=16e9, max_ws_bytes=24e9, reps=2,
+            time_budget_s=None, log=None):
+    """Times all applicable candidates of each shape; returns the rows of `path`."""
+    done = {(r["m"], r["n"], r["k"], r["dtype"], r["cand"]) for r in _load_rows(path)}
+    ops = Operands(dtype, cap_bytes)
+    t0 = time.time()
+    with open(path, "a") as f:
+        for (m, n, k) in shapes:
+            if time_budget_s and time.time() - t0 > time_budget_s:
+                break
+            for c, p in candidates(m, n, k, dtype, max_ws_bytes):
+                key = (m, n, k, dtype, c)
+                if key in done:
+                    continue
+                sec = time_plan(m, n, k, dtype, p, ops, reps)
+                f.write(json.dumps({"m": m, "n": n, "k": k, "dtype": dtype, "cand": c,
+                                    "seconds": sec}) + "\n")
+                done.add(key)
+            f.flush()
+            if log:
+                log(f"collected {m}x{n}x{k}")
+    del ops
+    return _load_rows(path)
+
+
+def features(rows):
+    X = np.array([cosma.cosma_selector_features(r["m"], r["n"], r["k"], r["dtype"]) for r in rows],
+                 dtype=np.float32)
+    cand = np.array([r["cand"] for r in rows], dtype=np.int32)
+    y = np.log2(np.array([r["seconds"] for r in rows], dtype=np.float64))
+    return X, cand, y
+
+
+def init_params(seed):
+    """He-uniform initial weights from the shared generator, zero biases."""
+    import cosma_inputs as ci
+    IN, H, OUT = cosma.COSMA_MLP_IN, cosma.COSMA_MLP_HIDDEN, cosma.COSMA_MLP_OUT
+    parts = []
+    for j, (fo, fi) in enumerate([(H, IN), (H, H), (OUT, H)]):
+        lim = math.sqrt(6.0 / fi)
+        e = np.arange(fo * fi)
+        w = lim * ci.entries(e, np.zeros(fo * fi), 1, "uniform", "f64", seed, 30 + j)
+        parts += [w, np.zeros(fo)]
+    p = np.concatenate(parts).astype(np.float32)
+    assert p.size == cosma.COSMA_MLP_PARAMS
+    return p
+
+
+def train(X, cand, y, epochs=300, batch=256, lr=2e-3, seed=0, checkpoint=None, log=None):
+    """Adam on the library's MLP kernels.  Targets are standardised log2 times.
+    Returns (params, history of epoch losses, (mu, sigma))."""
+    import torch
+    mu, sigma = float(np.mean(y)), float(np.std(y) + 1e-9)
+    t = ((y - mu) / sigma).astype(np.float32)
+    N = X.shape[0]
+    dev = "cuda"
+    Xd = torch.from_numpy(X).to(dev)
+    cd = torch.from_numpy(cand).to(dev)
+    td = torch.from_numpy(t).to(dev)
+    start_epoch, step = 0, 0
+    p = torch.from_numpy(init_params(seed)).to(dev)
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    hist = []
+    if checkpoint and os.path.exists(checkpoint):
+        ck = np.load(checkpoint)
+        p.copy_(torch.from_numpy(ck["params"]))
+        m.copy_(torch.from_numpy(ck["m"]))
+        v.copy_(torch.from_numpy(ck["v"]))
+        start_epoch, step = int(ck["epoch"]) + 1, int(ck["step"])
+        hist = list(ck["hist"])
+    g = torch.zeros_like(p)
+    loss = torch.zeros(1, device=dev)
+    sh = torch.cuda.current_stream().cuda_stream
+    perm_rng = np.random.default_rng(seed)
+    for _ in range(start_epoch):  # replay the permutation stream for a resumed run
+        perm_rng.permutation(N)
+    for ep in range(start_epoch, epochs):
+        perm = torch.from_numpy(perm_rng.permutation(N).astype(np.int64)).to(dev)
+        Xs, cs, ts = Xd[perm].contiguous(), cd[perm].contiguous(), td[perm].contiguous()
+        tot = 0.0
+        nb = 0
+        for s0 in range(0, N, batch):
+            b = min(batch, N - s0)
+            rc = cosma.cosma_mlp_loss_grad(b, Xs[s0:].data_ptr(), cs[s0:].data_ptr(),
+                                           ts[s0:].data_ptr(), p.data_ptr(), g.data_ptr(),
+                                           loss.data_ptr(), sh)
+            if rc != 0:
+                raise cosma.CosmaError(rc, "cosma_mlp_loss_grad")
+            step += 1
+            rc = cosma.cosma_mlp_adam(p.numel(), p.data_ptr(), g.data_ptr(), m.data_ptr(),
+                                      v.data_ptr(), step, lr, 0.9, 0.999, 1e-8, sh)
+            if rc != 0:
+                raise cosma.CosmaError(rc, "cosma_mlp_adam")
+            tot += float(loss.item()) * b
+            nb += b
+        hist.append(tot / max(nb, 1))
+        if checkpoint:
+            np.savez(checkpoint, params=p.cpu().numpy(), m=m.cpu().numpy(), v=v.cpu().numpy(),
+                     epoch=ep, step=step, hist=np.array(hist))
+        if log and (ep % 50 == 0 or ep == epochs - 1):
+            log(f"epoch {ep} loss {hist[-1]:.4f}")
+    return p.cpu().numpy(), hist, (mu, sigma)
+
+
+def evaluate(shapes, dtype=cosma.COSMA_BF16, cap_bytes=16e9, max_ws_bytes=24e9, reps=2,
+             log=None):
+    """Exhaustive timing on shapes; returns per-shape records with the best
+    candidate, the learned pick (installed selector) and the analytic plan."""
+    best_l, _ = cosma.cosma_selector_predict(shapes, dtype)
+    ops = Operands(dtype, cap_bytes)
+    recs = []
+    for (m, n, k), pick in zip(shapes, best_l):
+        times = {}
+        for c, p in candidates(m, n, k, dtype, max_ws_bytes):
+            times[c] = time_plan(m, n, k, dtype, p, ops, reps)
+        if not times:
+            continue
+        t_best = min(times.values())
+        t_ana = time_plan(m, n, k, dtype, None, ops, reps)
+        t_sel = times.get(pick, t_ana)
+        recs.append({"m": m, "n": n, "k": k, "best": min(times, key=times.get), "pick": pick,
+                     "t_best": t_best, "t_sel": t_sel, "t_analytic": t_ana,
+                     "regret_sel": t_sel / t_best - 1.0, "regret_analytic": t_ana / t_best - 1.0})
+        if log:
+            log(f"eval {m}x{n}x{k} regret sel {recs[-1]['regret_sel']:.3f} "
+                f"analytic {recs[-1]['regret_analytic']:.3f}")
+    del ops
+    return recs
+
+
+def install(params_path, log2_lo=8.0, log2_hi=16.0):
+    """Installs trained selector weights saved by main() (an .npy vector)."""
+    p = np.load(params_path).astype(np.float32)
+    rc = cosma.cosma_selector_set(p, log2_lo, log2_hi)
+    if rc != 0:
+        raise cosma.CosmaError(rc, "cosma_selector_set")
+
+
+def main(argv=None):
+    import argparse
+    import torch
+    ap = argparse.ArgumentParser(description="collect timings, train the selector, report regret")
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--train-shapes", type=int, default=1250)
+    ap.add_argument("--test-shapes", type=int, default=500)
+    ap.add_argument("--epochs", type=int, default=400)
+    ap.add_argument("--collect-budget-s", type=float, default=900)
+    ap.add_argument("--eval-budget-s", type=float, default=600)
+    ap.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args(argv)
+    os.makedirs(a.out, exist_ok=True)
+    torch.cuda.set_device(0)
+    cosma.load()
+    log = lambda s: print(s, flush=True)  # noqa: E731
+    dt = cosma.COSMA_BF16
+    train_shapes = random_shapes(a.train_shapes, seed=100 + a.seed, dtype=dt)
+    test_shapes = random_shapes(a.test_shapes, seed=200 + a.seed, dtype=dt)
+    t0 = time.time()
+    rows = collect(os.path.join(a.out, "timings.jsonl"), train_shapes, dt,
+                   time_budget_s=a.collect_budget_s, reps=1)
+    t_collect = time.time() - t0
+    X, c, y = features(rows)
+    t0 = time.time()
+    p, hist, (mu, sigma) = train(X, c, y, epochs=a.epochs, seed=a.seed,
+                                 checkpoint=os.path.join(a.out, "checkpoint.npz"), log=log)
+    t_train = time.time() - t0
+    np.save(os.path.join(a.out, "selector_params.npy"), p)
+    lo = math.log2(256)
+    hi = math.log2(65536)
+    rc = cosma.cosma_selector_set(p, lo, hi)
+    if rc != 0:
+        raise cosma.CosmaError(rc, "cosma_selector_set")
+    t0 = time.time()
+    recs = []
+    for s in test_shapes:
+        if time.time() - t0 > a.eval_budget_s:
+            break
+        recs += evaluate([s], dt, reps=2)
+    t_eval = time.time() - t0
+    with open(os.path.join(a.out, "eval.jsonl"), "w") as f:
+        for r in recs:
+            f.write(json.dumps(r) + "\n")
+    rs = np.array([r["regret_sel"] for r in recs])
+    ra = np.array([r["regret_analytic"] for r in recs])
+    summary = {
+        "dtype": "bf16", "train_rows": len(rows), "train_shapes": len({(r["m"], r["n"], r["k"])
+                                                                      for r in rows}),
+        "test_shapes": len(recs), "epochs": a.epochs, "final_loss": hist[-1] if hist else None,
+        "median_regret_learned": float(np.median(rs)) if len(rs) else None,
+        "mean_regret_learned": float(np.mean(rs)) if len(rs) else None,
+        "p90_regret_learned": float(np.percentile(rs, 90)) if len(rs) else None,
+        "median_regret_analytic": float(np.median(ra)) if len(ra) else None,
+        "mean_regret_analytic": float(np.mean(ra)) if len(ra) else None,
+        "p90_regret_analytic": float(np.percentile(ra, 90)) if len(ra) else None,
+        "learned_exact_best_fraction": float(np.mean([r["pick"] == r["best"] for r in recs]))
+        if recs else None,
+        "seconds": {"collect": t_collect, "train": t_train, "eval": t_eval},
+        "target_standardisation": {"mu": mu, "sigma": sigma},
+    }
+    with open(os.path.join(a.out, "summary.json"), "w") as f:
+        json.dump(summary, f, indent=1)
+    print(json.dumps(summary), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    import sys
+    sys.exit(main())

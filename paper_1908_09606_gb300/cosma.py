@@ -81,10 +81,21 @@ SIGNATURES = [
     ("cosma_launch_count", _LL, []),
     ("cosma_profile_enable", _INT, [_INT]),
     ("cosma_profile_read", _INT, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_LL)]),
+    ("cosma_plan_candidate", _INT, [_I64, _I64, _I64, _INT, _INT, ctypes.POINTER(cosma_plan)]),
+    ("cosma_selector_features", _INT, [_I64, _I64, _I64, _INT, ctypes.POINTER(ctypes.c_float)]),
+    ("cosma_mlp_forward", _INT, [_INT, _VP, _VP, _VP, _VP]),
+    ("cosma_mlp_loss_grad", _INT, [_INT, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("cosma_mlp_adam", _INT, [_INT, _VP, _VP, _VP, _VP, _INT, ctypes.c_float, ctypes.c_float,
+                              ctypes.c_float, ctypes.c_float, _VP]),
+    ("cosma_selector_set", _INT, [ctypes.POINTER(ctypes.c_float), _D, _D]),
+    ("cosma_selector_predict", _INT, [_INT, ctypes.POINTER(ctypes.c_int64), _INT,
+                                      ctypes.POINTER(_INT), ctypes.POINTER(ctypes.c_float)]),
     ("cosma_gemm_splitk_static", _INT, [_I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64,
                                         _INT, _INT, _VP]),
 ]
 COSMA_STATIC_SCRATCH_BYTES = 32 << 20
+COSMA_MLP_IN, COSMA_MLP_HIDDEN, COSMA_MLP_OUT = 7, 64, 16
+COSMA_MLP_PARAMS = 64 * 7 + 64 + 64 * 64 + 64 + 16 * 64 + 16
 
 
 def load(path=None):
@@ -157,6 +168,52 @@ def cosma_gemm_grouped(problems, dtype, stream=0):
 
 def cosma_gemm_splitk_static(m, n, k, A, lda, B, ldb, C, ldc, dtype, pk, stream=0):
     return load().cosma_gemm_splitk_static(m, n, k, A, lda, B, ldb, C, ldc, dtype, pk, stream)
+
+
+def cosma_plan_candidate(m, n, k, dtype, c):
+    """Plan of candidate c, or None when it does not apply."""
+    p = cosma_plan()
+    rc = load().cosma_plan_candidate(m, n, k, dtype, c, ctypes.byref(p))
+    if rc == COSMA_ERR_UNSUPPORTED:
+        return None
+    _check(rc, "cosma_plan_candidate")
+    return p
+
+
+def cosma_selector_features(m, n, k, dtype):
+    x = (ctypes.c_float * COSMA_MLP_IN)()
+    _check(load().cosma_selector_features(m, n, k, dtype, x), "cosma_selector_features")
+    return list(x)
+
+
+def cosma_mlp_forward(batch, X, params, Y, stream=0):
+    return load().cosma_mlp_forward(batch, X, params, Y, stream)
+
+
+def cosma_mlp_loss_grad(batch, X, cand, target, params, grad, loss, stream=0):
+    return load().cosma_mlp_loss_grad(batch, X, cand, target, params, grad, loss, stream)
+
+
+def cosma_mlp_adam(n, params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=0):
+    return load().cosma_mlp_adam(n, params, grad, m, v, step, lr, beta1, beta2, eps, stream)
+
+
+def cosma_selector_set(params, log2_lo=0.0, log2_hi=64.0):
+    """params: sequence of COSMA_MLP_PARAMS floats, or None to remove the network."""
+    if params is None:
+        return load().cosma_selector_set(None, log2_lo, log2_hi)
+    arr = (ctypes.c_float * COSMA_MLP_PARAMS)(*[float(x) for x in params])
+    return load().cosma_selector_set(arr, log2_lo, log2_hi)
+
+
+def cosma_selector_predict(shapes, dtype):
+    """Best candidate (and all predictions) for a list of (m, n, k)."""
+    count = len(shapes)
+    mnk = (ctypes.c_int64 * (3 * count))(*[int(v) for s in shapes for v in s])
+    best = (ctypes.c_int * count)()
+    pred = (ctypes.c_float * (count * COSMA_MLP_OUT))()
+    _check(load().cosma_selector_predict(count, mnk, dtype, best, pred), "cosma_selector_predict")
+    return list(best), [list(pred[i * COSMA_MLP_OUT:(i + 1) * COSMA_MLP_OUT]) for i in range(count)]
 
 
 def cosma_plan_query(m, n, k, dtype, selector=COSMA_SELECT_ANALYTIC):

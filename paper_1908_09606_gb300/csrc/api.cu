@@ -203,7 +203,7 @@ int run(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void*
     rc = validate_plan(m, n, k, dtype, s->info, p);
     if (rc != COSMA_OK) return rc;
   } else {
-    rc = plan_gemm(m, n, k, dtype, g_cfg.selector, s->info, g_cfg, &p);
+    rc = plan_gemm(m, n, k, dtype, g_cfg.selector, s->info, g_cfg, &p, !capturing(st));
     if (rc != COSMA_OK) return rc;
   }
   const long long need = total_workspace(m, n, k, dtype, p, A, lda);
@@ -235,6 +235,25 @@ int run(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void*
 }
 
 }  // namespace
+
+int lib_scratch(long long bytes, cudaStream_t st, void** out) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  int rc;
+  DeviceState* s = state(&rc);
+  if (!s) return rc;
+  long long have = 0;
+  return workspace(s, bytes, st, out, &have);
+}
+
+int current_info(DeviceInfo* out) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  int rc;
+  DeviceState* s = state(&rc);
+  if (!s) return rc;
+  *out = s->info;
+  return COSMA_OK;
+}
+
 }  // namespace cosma
 
 using namespace cosma;

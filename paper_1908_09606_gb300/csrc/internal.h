@@ -31,7 +31,9 @@ struct KernelDesc {
 
 // Planner (planner.cpp).
 int plan_gemm(int64_t m, int64_t n, int64_t k, int dtype, int selector, const DeviceInfo& dev,
-              const cosma_config& cfg, cosma_plan* out);
+              const cosma_config& cfg, cosma_plan* out, bool may_sync = true);
+int plan_candidate(int64_t m, int64_t n, int64_t k, int dtype, int c, const DeviceInfo& dev,
+                   const cosma_config& cfg, cosma_plan* out);
 int validate_plan(int64_t m, int64_t n, int64_t k, int dtype, const DeviceInfo& dev,
                   const cosma_plan& p);
 Sched sched_from_plan(int64_t m, int64_t n, int64_t k, const cosma_plan& p);
@@ -39,7 +41,18 @@ int find_seq_schedule(long long S, int* a, int* b);
 int fit_ranks_weighted(int64_t m, int64_t n, int64_t k, int p, double delta, double wa, double wb,
                        double wc, int grid[3]);
 int learned_plan(int64_t m, int64_t n, int64_t k, int dtype, const DeviceInfo& dev,
-                 const cosma_config& cfg, cosma_plan* out);  // selector.cpp
+                 const cosma_config& cfg, cosma_plan* out, bool may_sync);  // selector.cu
+// MLP kernels (mlp.cu)
+int mlp_forward(int batch, const float* X, const float* params, float* Y, cudaStream_t st);
+int mlp_loss_grad(int batch, const float* X, const int* cand, const float* target,
+                  const float* params, float* grad, float* loss, float* partial, cudaStream_t st);
+long long mlp_partial_bytes(int batch);
+int mlp_adam(int n, float* params, const float* grad, float* m, float* v, int step, float lr,
+             float beta1, float beta2, float eps, cudaStream_t st);
+// Library workspace for internal users (api.cu); grows outside capture only.
+int lib_scratch(long long bytes, cudaStream_t st, void** out);
+// Device info of the current device (api.cu).
+int current_info(DeviceInfo* out);
 
 // Kernel launchers (return cudaError_t values).
 struct GemmArgs {

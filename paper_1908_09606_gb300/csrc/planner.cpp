@@ -165,13 +165,73 @@ static double estimate(const KernelDesc& d, int64_t m, int64_t n, const TileChoi
   return s;
 }
 
+static void finish_plan(int64_t m, int64_t n, int64_t k, int dtype, const KernelDesc& d, int P,
+                        cosma_plan& best) {
+  const int64_t mm = std::max<int64_t>(m, 1), nn = std::max<int64_t>(n, 1);
+  best.kernel = d.kernel;
+  best.sms = P;
+  best.fast_words = d.fast_bytes / d.w_in;
+  // Listing-1 I/O of the schedule: each tile streams k (h + w) input words and
+  // writes h w outputs; a k split adds pk partial stores + pk loads + 1 store.
+  const int64_t mt = cdiv(mm, best.tile_m), ntl = cdiv(nn, best.tile_n);
+  double io = (double)k * ((double)ntl * m + (double)mt * n);
+  io += (double)m * n * (best.pk > 1 ? 2.0 * best.pk + 1.0 : 1.0);
+  best.io_words = io;
+  best.bound_words = 2.0 * (double)m * n * k / sqrt(best.fast_words) + (double)m * n;
+  best.workspace_bytes = workspace_bytes(m, n, k, dtype, best);
+}
+
+int plan_candidate(int64_t m, int64_t n, int64_t k, int dtype, int c, const DeviceInfo& dev,
+                   const cosma_config& cfg, cosma_plan* out) {
+  if (!out || m < 1 || n < 1 || k < 1 || c < 0 || c >= COSMA_MLP_OUT) return COSMA_ERR_INVALID_ARG;
+  if (dtype < COSMA_F64 || dtype > COSMA_F64_EMU_BF16) return COSMA_ERR_INVALID_ARG;
+  const KernelDesc d = desc_for(dtype, dev);
+  const int P = dev.sms > 0 ? dev.sms : 148;
+  TileChoice tiles[4];
+  const int ntiles = tiles_for(d.kernel, tiles);
+  const int ti = (c / 8) % 2;
+  if (ti >= ntiles) return COSMA_ERR_UNSUPPORTED;
+  const int pks[4] = {1, 2, 4, 8};
+  const int pk = pks[(c / 2) % 4];
+  const int order = c % 2;
+  const TileChoice& t = tiles[ti];
+  const int64_t mt = cdiv(m, t.tile_m), ntl = cdiv(n, t.tile_n), kbt = cdiv(k, t.k_block);
+  if (pk > kbt) return COSMA_ERR_UNSUPPORTED;
+  if (d.kernel == COSMA_KERNEL_EMU_BF16 && (pk != 1 || order != 1)) return COSMA_ERR_UNSUPPORTED;
+  cosma_plan p{};
+  p.tile_m = t.tile_m; p.tile_n = t.tile_n; p.k_block = t.k_block; p.stages = t.stages;
+  p.pk = pk; p.order = order;
+  const int64_t kbu = cdiv(kbt, pk);
+  int64_t mu;
+  if (order == 1) {
+    const int64_t units = mt * ntl * pk;
+    p.pm = p.pn = 1;
+    p.ctas = (int)std::min<int64_t>(P, units);
+    mu = cdiv(units, p.ctas);
+  } else {
+    int g[3];
+    if (fit_ranks_weighted(mt, ntl, 1, std::max(1, P / pk), cfg.delta,
+                           (double)t.tile_m * t.k_block * kbu * d.w_in,
+                           (double)t.k_block * kbu * t.tile_n * d.w_in,
+                           (double)t.tile_m * t.tile_n * d.w_acc, g) != COSMA_OK)
+      return COSMA_ERR_UNSUPPORTED;
+    p.pm = g[0]; p.pn = g[1];
+    p.ctas = g[0] * g[1] * pk;
+    mu = cdiv(mt, g[0]) * cdiv(ntl, g[1]);
+  }
+  p.est_seconds = estimate(d, m, n, t, mu, kbu, pk);
+  finish_plan(m, n, k, dtype, d, P, p);
+  *out = p;
+  return COSMA_OK;
+}
+
 int plan_gemm(int64_t m, int64_t n, int64_t k, int dtype, int selector, const DeviceInfo& dev,
-              const cosma_config& cfg, cosma_plan* out) {
+              const cosma_config& cfg, cosma_plan* out, bool may_sync) {
   if (!out || m < 0 || n < 0 || k < 0) return COSMA_ERR_INVALID_ARG;
   if (dtype < COSMA_F64 || dtype > COSMA_F64_EMU_INT8) return COSMA_ERR_INVALID_ARG;
   if (dtype == COSMA_F64_EMU_INT8) return COSMA_ERR_UNSUPPORTED;
   if (selector == COSMA_SELECT_LEARNED) {
-    const int rc = learned_plan(m, n, k, dtype, dev, cfg, out);
+    const int rc = learned_plan(m, n, k, dtype, dev, cfg, out, may_sync);
     if (rc == COSMA_OK) return rc;  // otherwise fall back to the analytic plan
   }
   const KernelDesc d = desc_for(dtype, dev);
@@ -238,25 +298,8 @@ int plan_gemm(int64_t m, int64_t n, int64_t k, int dtype, int selector, const De
       }
     }
   }
-  best.kernel = d.kernel;
-  best.sms = P;
   best.est_seconds = best_s;
-  best.fast_words = d.fast_bytes / d.w_in;
-  // Listing-1 I/O of the schedule: each tile streams k (h + w) input words and
-  // writes h w outputs; a k split adds pk partial stores + pk loads + 1 store.
-  double io = 0.0;
-  {
-    const int64_t mt = cdiv(mm, best.tile_m), ntl = cdiv(nn, best.tile_n);
-    const int64_t full_m = m / best.tile_m, full_n = n / best.tile_n;
-    const double hm = (double)(m - full_m * best.tile_m), wn = (double)(n - full_n * best.tile_n);
-    // sum over tiles of (h + w) = (#cols of tiles) * m + (#rows of tiles) * n
-    io = (double)k * ((double)ntl * m + (double)mt * n);
-    (void)hm; (void)wn;
-    io += (double)m * n * (best.pk > 1 ? 2.0 * best.pk + 1.0 : 1.0);
-  }
-  best.io_words = io;
-  best.bound_words = 2.0 * (double)m * n * k / sqrt(best.fast_words) + (double)m * n;
-  best.workspace_bytes = workspace_bytes(m, n, k, dtype, best);
+  finish_plan(m, n, k, dtype, d, P, best);
   *out = best;
   return COSMA_OK;
 }

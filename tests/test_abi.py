@@ -164,3 +164,27 @@ def test_plan_io_accounting_matches_units(lib):
         io += (k1 - k0) * ((r1 - r0) + (c1 - c0))
     io += m * n * (2 * p.pk + 1 if p.pk > 1 else 1)
     assert io == pytest.approx(p.io_words)
+
+
+def test_plan_candidates_host_only(lib):
+    for dt in (lib.COSMA_F64, lib.COSMA_F32, lib.COSMA_BF16, lib.COSMA_F64_EMU_BF16):
+        for shape in [(4096, 4096, 4096), (300, 260, 70), (65536, 256, 1 << 16)]:
+            valid = [c for c in range(lib.COSMA_MLP_OUT)
+                     if lib.cosma_plan_candidate(*shape, dt, c) is not None]
+            assert valid, (dt, shape)
+            for c in valid:
+                p = lib.cosma_plan_candidate(*shape, dt, c)
+                assert p.pk == [1, 2, 4, 8][(c // 2) % 4] and p.order == c % 2
+                assert 1 <= p.ctas <= p.sms
+                if p.order == 0:
+                    assert p.pm * p.pn * p.pk == p.ctas
+            if dt == lib.COSMA_F64_EMU_BF16:
+                assert valid == [1]
+
+
+def test_selector_features_match_oracle(lib):
+    from oracle import mlp as om
+    import numpy as np
+    for (m, n, k, dt) in [(256, 65536, 1024, 2), (3, 5, 7, 0), (4096, 1, 2, 3)]:
+        got = np.array(lib.cosma_selector_features(m, n, k, dt))
+        assert np.allclose(got, om.features(m, n, k, dt), rtol=1e-6, atol=1e-7)
