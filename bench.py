@@ -80,6 +80,17 @@ def workload_config(name, m, n, k, dtype):
             "l2": "inputs larger than L2" if (m * k + k * n) * 2 > 130e6 else "inputs fit in L2"}
 
 
+def combine_ranks(local_ms, flops_per_step, steps, world, dist=None, device=None):
+    """Whole-job throughput: the slowest rank's timed region (max over ranks)
+    against all ranks' work.  Returns (max_ms, TFLOP/s)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1 and dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    return max_ms, world * flops_per_step * steps / (max_ms * 1e-3) / 1e12
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 
@@ -270,13 +281,10 @@ def run_grouped(args):
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    total_ms = sum(evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps))
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms, value = combine_ranks(sum(evs[i].elapsed_time(evs[i + 1])
+                                        for i in range(args.steps)),
+                                    flops * reps, args.steps, world, dist, "cuda")
     replay_ms = total_ms / (args.steps * reps)
-    value = world * flops / (replay_ms * 1e-3) / 1e12
     # library kernels per replay: the grouped prep (bf16) and the grouped GEMM
     per_replay = 2 if dtype == "bf16" else 1
     launches = per_replay * reps * args.steps
@@ -459,13 +467,8 @@ def main():
     kern_total_ms, kern_n = cosma.cosma_profile_read()
     clocks = sampler.stop()
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
     flops = 2.0 * m * n * k
-    value = world * flops * args.steps / (total_ms * 1e-3) / 1e12
+    total_ms, value = combine_ranks(sum(step_ms), flops, args.steps, world, dist, dev)
     st = cosma.cosma_stream_status(sh)
     if st != 0:
         raise cosma.CosmaError(st, "device status after timed region")
