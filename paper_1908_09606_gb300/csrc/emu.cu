@@ -33,6 +33,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cmath>
 #include <mutex>
 
 #include "tc_common.cuh"
@@ -199,7 +200,7 @@ struct ELayout {
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int T_OFF = ESTAGES * STAGE_BYTES;           // running total, high parts
   static constexpr int BAR_OFF = T_OFF + EBM * TPITCH * 4;
-  static constexpr int NBARS = 2 * ESTAGES + 5;
+  static constexpr int NBARS = 2 * ESTAGES + 9;  // full, empty, tfull[4], tempty[4], drain
   static constexpr int TOTAL = BAR_OFF + NBARS * 8 + 16;
   static constexpr int ALLOC = TOTAL + 1024;
 };
@@ -238,18 +239,196 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
   e = b - (s - a);
 }
 
+// Epilogue warps (2..9) of K-EMU / K-RECOMB for the units of one CTA (or CTA
+// pair): warp -> tensor-memory lane quadrant q4 = warp % 4 and column half h.
+// Drains every exact group into the float-float level sum in tensor memory,
+// merges finished levels into the running total (high parts in shared memory
+// at Tsm, low parts in registers) and stores the FP64 tile.  Rows of this CTA
+// start at tile_row * tile_rows + row_off.  tempty_addr: cluster addresses of
+// the accumulator-free barriers of the MMA-issuing CTA.
+template <bool IL>
+__device__ __forceinline__ void emu_epilogue(const EmuArgs& a, int unit_cta, int64_t nunits,
+                                             int64_t row_off, int64_t tile_rows,
+                                             uint32_t tmem_base, uint8_t* Tsm,
+                                             uint64_t* tfull, const uint32_t* tempty_addr,
+                                             const tc::WaitCtx& w, int warp, int lane) {
+  constexpr int NACC = IL ? 3 : 2;
+  const int64_t kbt = a.sch.kbt;
+  const int top = a.s + 1;
+  const int q4 = warp & 3;
+  const int h = (warp - 2) >> 2;
+  const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
+  const uint32_t col_lo = (uint32_t)(64 * h);
+  const uint32_t lvl_hi_col = 256 + col_lo, lvl_lo_col = 384 + col_lo;
+  const float down = 1.0f / (float)(1 << a.beta);
+  float* Th = reinterpret_cast<float*>(Tsm) + (q4 * 32 + lane) * TPITCH + col_lo;
+  uint32_t acc = 0;
+  uint32_t tph[NACC];
+#pragma unroll
+  for (int b = 0; b < NACC; ++b) tph[b] = 0;
+  bool ok = true;
+  for (int64_t ui = 0; ui < nunits && ok; ++ui) {
+    const Unit u = unit_of_cta(a.sch, unit_cta, ui);
+    // Running total T = Th + Tl: Th in shared memory; Tl in registers (float-float
+    // level sums) or, with int32 level sums, in tensor memory columns 384.. .
+    float Tl[IL ? 1 : 64];
+    int Lv[IL ? 64 : 1];  // exact level sum (int32 path)
+    const uint32_t tl_col = 384 + col_lo;
+#pragma unroll
+    for (int j = 0; j < 64; ++j) {
+      Th[j] = 0.f;
+      if constexpr (!IL) Tl[j] = 0.f;
+    }
+    if constexpr (IL) {
+      uint32_t z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+      for (int c = 0; c < 64; c += 8) tc::tmem_st_32x8(tmem_base + lane_off + tl_col + c, z);
+      tc::tmem_wait_st();
+    }
+    for (int lvl = top; lvl >= 2 && ok; --lvl) {
+      const int p = lvl - 1;
+      const int gk = group_blocks(a.group_kb, p);
+      const int64_t ngroups = (kbt + gk - 1) / gk;
+      for (int64_t g = 0; g < ngroups; ++g) {
+        if (!tc::mbar_wait(&tfull[acc], tph[acc], w)) { ok = false; break; }
+        tc::tc_fence_after();
+        const bool first = (g == 0), last = (g == ngroups - 1);
+        if constexpr (IL) {
+          // Drain: the group's exact integer sums join the int32 level sum.
+#pragma unroll
+          for (int c = 0; c < 64; c += 8) {
+            uint32_t v[8];
+            tc::tmem_ld_32x8(tmem_base + lane_off + acc * EBN + col_lo + c, v);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int iv = __float2int_rn(__uint_as_float(v[j]));
+              Lv[IL ? c + j : 0] = first ? iv : Lv[IL ? c + j : 0] + iv;
+            }
+          }
+          tc::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive_remote(tempty_addr[acc]);
+          tph[acc] ^= 1;
+          acc = (acc + 1) % NACC;
+          if (last) {
+            // K-RECOMB: T = T * 2^-beta + level, the level split exactly into two floats.
+#pragma unroll
+            for (int c = 0; c < 64; c += 8) {
+              uint32_t tl[8];
+              tc::tmem_ld_32x8(tmem_base + lane_off + tl_col + c, tl);
+              tc::tmem_wait_ld();
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int li = Lv[IL ? c + j : 0];
+                const float lh = (float)li;
+                const float ll = (float)(li - (int)lh);
+                float s, e, nh, nl;
+                two_sum(Th[c + j] * down, lh, s, e);
+                e += __uint_as_float(tl[j]) * down + ll;
+                fast_two_sum(s, e, nh, nl);
+                Th[c + j] = nh;
+                tl[j] = __float_as_uint(nl);
+              }
+              tc::tmem_st_32x8(tmem_base + lane_off + tl_col + c, tl);
+            }
+            tc::tmem_wait_st();
+          }
+        } else {
+#pragma unroll
+        for (int c = 0; c < 64; c += 8) {
+          uint32_t v[8], hi[8], lo[8];
+          tc::tmem_ld_32x8(tmem_base + lane_off + acc * EBN + col_lo + c, v);
+          if (!first) {
+            tc::tmem_ld_32x8(tmem_base + lane_off + lvl_hi_col + c, hi);
+            tc::tmem_ld_32x8(tmem_base + lane_off + lvl_lo_col + c, lo);
+          }
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float x = __uint_as_float(v[j]);  // exact integer
+            float fh = x, fl = 0.f;
+            if (!first) {
+              float s, e;
+              two_sum(__uint_as_float(hi[j]), x, s, e);
+              fast_two_sum(s, __uint_as_float(lo[j]) + e, fh, fl);
+            }
+            if (last) {
+              // K-RECOMB: T = T * 2^-beta + level (the first level processed starts T).
+              float s, e, nh;
+              two_sum(Th[c + j] * down, fh, s, e);
+              e += Tl[IL ? 0 : c + j] * down + fl;
+              fast_two_sum(s, e, nh, Tl[IL ? 0 : c + j]);
+              Th[c + j] = nh;
+            } else {
+              hi[j] = __float_as_uint(fh);
+              lo[j] = __float_as_uint(fl);
+            }
+          }
+          if (!last) {
+            tc::tmem_st_32x8(tmem_base + lane_off + lvl_hi_col + c, hi);
+            tc::tmem_st_32x8(tmem_base + lane_off + lvl_lo_col + c, lo);
+          }
+        }
+        tc::tmem_wait_st();
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive_remote(tempty_addr[acc]);
+        tph[acc] ^= 1;
+        acc = (acc + 1) % NACC;
+        }
+      }
+    }
+    if (!ok) break;
+    // Final FP64 store of this thread's 64 columns of one row.
+    const int64_t row = u.tile_row * tile_rows + row_off + q4 * 32 + lane;
+    const int64_t cbase = u.tile_col * EBN + col_lo;
+    const int ea = row < a.sch.m ? a.eA[row] : kExpNone;
+    double* dst = a.C + row * a.ldc;
+#pragma unroll
+    for (int c = 0; c < 64; c += 8) {
+      float tl[8];
+      if constexpr (IL) {
+        uint32_t t[8];
+        tc::tmem_ld_32x8(tmem_base + lane_off + tl_col + c, t);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) tl[j] = __uint_as_float(t[j]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) tl[j] = Tl[IL ? 0 : c + j];
+      }
+      if (row < a.sch.m) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int64_t col = cbase + c + j;
+          if (col < a.sch.n) {
+            const int eb = a.eB[col];
+            const double val = (double)Th[c + j] + (double)tl[j];
+            dst[col] = (ea == kExpNone || eb == kExpNone)
+                           ? 0.0
+                           : scale_pow2(val, ea + eb + 2 - 2 * a.beta);
+          }
+        }
+      }
+    }
+  }
+}
+
+template <bool IL>
 __global__ void __launch_bounds__(320, 1)
 emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 EmuArgs a) {
   using L = ELayout;
+  constexpr int NACC = IL ? 3 : 2;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
   uint64_t* empty = full + ESTAGES;
   uint64_t* tfull = empty + ESTAGES;
-  uint64_t* tempty = tfull + 2;
-  uint64_t* drain = tempty + 2;
+  uint64_t* tempty = tfull + 4;
+  uint64_t* drain = tempty + 4;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
@@ -259,7 +438,7 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NACC; ++b) {
       tc::mbar_init(&tfull[b], 1);
       tc::mbar_init(&tempty[b], 8);
     }
@@ -327,7 +506,9 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       constexpr uint32_t idesc = tc::idesc_bf16_f32(EBM, EBN);
       int stage = 0;
       uint32_t ph = 0, acc = 0;
-      uint32_t aph[2] = {0, 0};
+      uint32_t aph[NACC];
+#pragma unroll
+      for (int b = 0; b < NACC; ++b) aph[b] = 0;
       bool ok = true;
       for (int64_t ui = 0; ui < nunits && ok && !*abort_flag; ++ui) {
         for (int lvl = top; lvl >= 2 && ok; --lvl) {
@@ -358,7 +539,7 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             if (!ok) break;
             tc::mma_commit(&tfull[acc]);
             aph[acc] ^= 1;
-            acc ^= 1;
+            acc = (acc + 1) % NACC;
           }
         }
       }
@@ -368,93 +549,10 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       }
     }
   } else {
-    // Epilogue: 8 warps; warp (2..9) -> lane quadrant q4 = warp % 4, column half h.
-    const int q4 = warp & 3;
-    const int h = (warp - 2) >> 2;
-    const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
-    const uint32_t col_lo = (uint32_t)(64 * h);
-    const uint32_t lvl_hi_col = 256 + col_lo, lvl_lo_col = 384 + col_lo;
-    const float down = 1.0f / (float)(1 << a.beta);
-    float* Th = reinterpret_cast<float*>(smem + L::T_OFF) + (q4 * 32 + lane) * TPITCH + col_lo;
-    uint32_t acc = 0;
-    uint32_t tph[2] = {0, 0};
-    bool ok = true;
-    for (int64_t ui = 0; ui < nunits && ok; ++ui) {
-      const Unit u = unit_of_cta(a.sch, cta, ui);
-      float Tl[64];
+    uint32_t te[NACC];
 #pragma unroll
-      for (int j = 0; j < 64; ++j) { Th[j] = 0.f; Tl[j] = 0.f; }
-      for (int lvl = top; lvl >= 2 && ok; --lvl) {
-        const int p = lvl - 1;
-        const int gk = group_blocks(a.group_kb, p);
-        const int64_t ngroups = (kbt + gk - 1) / gk;
-        for (int64_t g = 0; g < ngroups; ++g) {
-          if (!tc::mbar_wait(&tfull[acc], tph[acc], w)) { ok = false; break; }
-          tc::tc_fence_after();
-          const bool first = (g == 0), last = (g == ngroups - 1);
-#pragma unroll
-          for (int c = 0; c < 64; c += 8) {
-            uint32_t v[8], hi[8], lo[8];
-            tc::tmem_ld_32x8(tmem_base + lane_off + acc * EBN + col_lo + c, v);
-            if (!first) {
-              tc::tmem_ld_32x8(tmem_base + lane_off + lvl_hi_col + c, hi);
-              tc::tmem_ld_32x8(tmem_base + lane_off + lvl_lo_col + c, lo);
-            }
-            tc::tmem_wait_ld();
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float x = __uint_as_float(v[j]);  // exact integer
-              float fh = x, fl = 0.f;
-              if (!first) {
-                float s, e;
-                two_sum(__uint_as_float(hi[j]), x, s, e);
-                fast_two_sum(s, __uint_as_float(lo[j]) + e, fh, fl);
-              }
-              if (last) {
-                // K-RECOMB: T = T * 2^-beta + level (the first level processed starts T).
-                float s, e, nh;
-                two_sum(Th[c + j] * down, fh, s, e);
-                e += Tl[c + j] * down + fl;
-                fast_two_sum(s, e, nh, Tl[c + j]);
-                Th[c + j] = nh;
-              } else {
-                hi[j] = __float_as_uint(fh);
-                lo[j] = __float_as_uint(fl);
-              }
-            }
-            if (!last) {
-              tc::tmem_st_32x8(tmem_base + lane_off + lvl_hi_col + c, hi);
-              tc::tmem_st_32x8(tmem_base + lane_off + lvl_lo_col + c, lo);
-            }
-          }
-          tc::tmem_wait_st();
-          tc::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive(&tempty[acc]);
-          tph[acc] ^= 1;
-          acc ^= 1;
-        }
-      }
-      if (!ok) break;
-      // Final FP64 store of this thread's 64 columns of one row.
-      const int64_t row = u.tile_row * EBM + q4 * 32 + lane;
-      if (row < a.sch.m) {
-        const int ea = a.eA[row];
-        double* dst = a.C + row * a.ldc;
-        const int64_t cbase = u.tile_col * EBN + col_lo;
-#pragma unroll
-        for (int j = 0; j < 64; ++j) {
-          const int64_t col = cbase + j;
-          if (col < a.sch.n) {
-            const int eb = a.eB[col];
-            const double val = (double)Th[j] + (double)Tl[j];
-            dst[col] = (ea == kExpNone || eb == kExpNone)
-                           ? 0.0
-                           : scale_pow2(val, ea + eb + 2 - 2 * a.beta);
-          }
-        }
-      }
-    }
+    for (int b = 0; b < NACC; ++b) te[b] = tc::mapa_shared(&tempty[b], 0);
+    emu_epilogue<IL>(a, cta, nunits, 0, EBM, tmem_base, smem + L::T_OFF, tfull, te, w, warp, lane);
   }
   __syncthreads();
   if (warp == 1) {
@@ -463,8 +561,186 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   }
 }
 
+
+// ---- 2-SM variant ------------------------------------------------------------------
+//
+// A cluster of two CTAs computes a 256 x 128 tile with tcgen05.mma.cta_group::2
+// (M = 256): each CTA loads its own 128 rows of the A slice and its own 64 of
+// the 128 columns of the B slice (no multicast), the even CTA issues the MMAs
+// and commits to the barriers of both, and each CTA drains its own 128 x 128
+// accumulator exactly as the single-SM kernel does.  Per SM an MMA step then
+// reads 6 KB of operands instead of 8 KB, and the ring is 6 stages deep.
+constexpr int E2_STAGES = 6;
+
+struct E2Layout {
+  static constexpr int A_BYTES = EBM * EBK * 2;        // own 128 rows
+  static constexpr int B_BYTES = (EBN / 2) * EBK * 2;  // own 64 columns
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int T_OFF = E2_STAGES * STAGE_BYTES;
+  static constexpr int BAR_OFF = T_OFF + EBM * TPITCH * 4;
+  static constexpr int NBARS = 2 * E2_STAGES + 9;
+  static constexpr int TOTAL = BAR_OFF + NBARS * 8 + 16;
+  static constexpr int ALLOC = TOTAL + 1024;
+};
+
+__device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* map,
+                                                 uint32_t bar_cluster, int32_t x, int32_t y,
+                                                 int32_t z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];\n" ::"r"(tc::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+template <bool IL>
+__global__ void __launch_bounds__(320, 1)
+emu_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
+                     const __grid_constant__ CUtensorMap tmB, EmuArgs a) {
+  using L = E2Layout;
+  constexpr int NACC = IL ? 3 : 2;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+  uint64_t* empty = full + E2_STAGES;
+  uint64_t* tfull = empty + E2_STAGES;
+  uint64_t* tempty = tfull + 4;
+  uint64_t* drain = tempty + 4;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const uint32_t rank = tc::cluster_ctarank();
+  const bool leader = rank == 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < E2_STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);   // leader: its producer's arrival + both CTAs' bytes
+      tc::mbar_init(&empty[s], 1);  // the leader's commit, multicast to both CTAs
+    }
+    for (int b = 0; b < NACC; ++b) {
+      tc::mbar_init(&tfull[b], 1);
+      tc::mbar_init(&tempty[b], 16);  // leader: 8 epilogue warps of each CTA
+    }
+    tc::mbar_init(drain, 1);
+    *abort_flag = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) tc::tmem_alloc_pair(tslot, 512);
+  tc::tc_fence_before();
+  tc::cluster_sync();  // barriers of both CTAs initialised, tensor memory allocated
+  tc::tc_fence_after();
+  const uint32_t tmem_base = *tslot;
+  const tc::WaitCtx w{a.wait_limit, a.status, abort_flag};
+  const int pair = blockIdx.x >> 1;
+  const int64_t nunits = units_of_cta(a.sch, pair);
+  const int64_t kbt = a.sch.kbt;
+  const int top = a.s + 1;
+
+  if (warp == 0) {
+    if (tc::elect_one()) {
+      int stage = 0;
+      uint32_t ph = 0;
+      bool issued = false;
+      uint32_t full_cl[E2_STAGES];
+#pragma unroll
+      for (int s = 0; s < E2_STAGES; ++s) full_cl[s] = tc::mapa_shared(&full[s], 0);
+      for (int64_t ui = 0; ui < nunits && !*abort_flag; ++ui) {
+        const Unit u = unit_of_cta(a.sch, pair, ui);
+        bool ok = true;
+        for (int lvl = top; lvl >= 2 && ok; --lvl) {
+          const int p = lvl - 1;
+          const int gk = group_blocks(a.group_kb, p);
+          for (int64_t c0 = 0; c0 < kbt && ok; c0 += gk) {
+            const int64_t c1 = min(c0 + gk, kbt);
+            for (int q = 1; q <= p && ok; ++q) {
+              for (int64_t kb = c0; kb < c1; ++kb) {
+                if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) { ok = false; break; }
+                if (leader) tc::mbar_arrive_expect_tx(&full[stage], 2 * L::STAGE_BYTES);
+                uint8_t* sa = smem + stage * L::STAGE_BYTES;
+                tma_load_3d_pair(sa, &tmA, full_cl[stage], (int32_t)(kb * EBK),
+                                 (int32_t)(u.tile_row * (2 * EBM) + rank * EBM), q - 1);
+                tma_load_3d_pair(sa + L::A_BYTES, &tmB, full_cl[stage], (int32_t)(kb * EBK),
+                                 (int32_t)(u.tile_col * EBN + rank * (EBN / 2)), lvl - q - 1);
+                issued = true;
+                if (++stage == E2_STAGES) { stage = 0; ph ^= 1; }
+              }
+            }
+          }
+        }
+        if (!ok) break;
+      }
+      if (*abort_flag && issued) {
+        // Copies of this CTA signal the leader's barriers: give any still in
+        // flight time to land before the pair leaves.
+        const long long t0 = clock64();
+        while (clock64() - t0 < (1LL << 22)) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (leader && tc::elect_one()) {
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(2 * EBM, EBN);
+      int stage = 0;
+      uint32_t ph = 0, acc = 0;
+      uint32_t aph[NACC];
+#pragma unroll
+      for (int b = 0; b < NACC; ++b) aph[b] = 0;
+      bool ok = true;
+      for (int64_t ui = 0; ui < nunits && ok && !*abort_flag; ++ui) {
+        for (int lvl = top; lvl >= 2 && ok; --lvl) {
+          const int p = lvl - 1;
+          const int gk = group_blocks(a.group_kb, p);
+          for (int64_t c0 = 0; c0 < kbt && ok; c0 += gk) {
+            const int64_t c1 = min(c0 + gk, kbt);
+            if (!tc::mbar_wait(&tempty[acc], aph[acc] ^ 1, w)) { ok = false; break; }
+            tc::tc_fence_after();
+            const uint32_t d = tmem_base + acc * EBN;
+            bool first = true;
+            for (int q = 1; q <= p && ok; ++q) {
+              for (int64_t kb = c0; kb < c1; ++kb) {
+                if (!tc::mbar_wait(&full[stage], ph, w)) { ok = false; break; }
+                tc::tc_fence_after();
+                const uint32_t sa = tc::smem_u32(smem + stage * L::STAGE_BYTES);
+                const uint32_t sb = sa + L::A_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < EBK / 16; ++kk) {
+                  tc::mma_bf16_pair(d, tc::smem_desc_sw128(sa + kk * 32),
+                                    tc::smem_desc_sw128(sb + kk * 32), idesc, first ? 0u : 1u);
+                  first = false;
+                }
+                tc::mma_commit_pair(&empty[stage]);
+                if (++stage == E2_STAGES) { stage = 0; ph ^= 1; }
+              }
+            }
+            if (!ok) break;
+            tc::mma_commit_pair(&tfull[acc]);
+            aph[acc] ^= 1;
+            acc = (acc + 1) % NACC;
+          }
+        }
+      }
+      tc::mma_commit_pair(drain);  // every MMA of the pair done (both CTAs' drain barriers)
+      const long long t0 = clock64();
+      while (!tc::mbar_try_wait(drain, 0) && clock64() - t0 < tc::kDrainCycles) {
+      }
+    }
+  } else {
+    uint32_t te[NACC];
+#pragma unroll
+    for (int b = 0; b < NACC; ++b) te[b] = tc::mapa_shared(&tempty[b], 0);
+    emu_epilogue<IL>(a, pair, nunits, (int64_t)rank * EBM, 2 * EBM, tmem_base, smem + L::T_OFF,
+                     tfull, te, w, warp, lane);
+  }
+  __syncthreads();
+  tc::tc_fence_before();
+  tc::cluster_sync();  // no CTA leaves while its peer may still signal its barriers
+  tc::tc_fence_after();
+  if (warp == 1) tc::tmem_dealloc_pair(tmem_base, 512);
+}
+
 int encode_tmap_slices(CUtensorMap* map, const void* base, int64_t rows, int64_t k, int64_t kp,
-                       int s) {
+                       int s, int box_rows = EBM) {
   static std::once_flag once;
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   std::call_once(once, [] {
@@ -478,7 +754,7 @@ int encode_tmap_slices(CUtensorMap* map, const void* base, int64_t rows, int64_t
   if (!fn) return COSMA_ERR_CUDA;
   cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)s};
   cuuint64_t strides[2] = {(cuuint64_t)(kp * 2), (cuuint64_t)(rows * kp * 2)};
-  cuuint32_t box[3] = {(cuuint32_t)EBK, (cuuint32_t)EBM, 1};
+  cuuint32_t box[3] = {(cuuint32_t)EBK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -503,7 +779,8 @@ int launch_emu_bf16(const GemmArgs& g, const Sched& sch, const cosma_plan& p,
   const int s = emu_slices(cfg), beta = emu_bits(cfg);
   if (s < 2 || s > EMU_MAX_SLICES || beta < 2 || beta > 8 || beta * s - 1 > 62)
     return COSMA_ERR_INVALID_ARG;
-  if (sch.tile_m != EBM || sch.tile_n != EBN || sch.k_block != EBK || sch.pk != 1)
+  const bool pairs = sch.tile_m == 2 * EBM;
+  if ((sch.tile_m != EBM && !pairs) || sch.tile_n != EBN || sch.k_block != EBK || sch.pk != 1)
     return COSMA_ERR_INVALID_ARG;
   const int64_t m = g.m, n = g.n, k = g.k, kp = rup(k, 8);
   if (emu_workspace_bytes(m, n, k, cfg) > ws_bytes) return COSMA_ERR_NO_WORKSPACE;
@@ -547,7 +824,7 @@ int launch_emu_bf16(const GemmArgs& g, const Sched& sch, const cosma_plan& p,
   CUtensorMap ta, tb;
   int rc = encode_tmap_slices(&ta, SA, m, k, kp, s);
   if (rc != COSMA_OK) return rc;
-  rc = encode_tmap_slices(&tb, SB, n, k, kp, s);
+  rc = encode_tmap_slices(&tb, SB, n, k, kp, s, pairs ? EBN / 2 : EBN);
   if (rc != COSMA_OK) return rc;
 
   EmuArgs args;
@@ -563,16 +840,43 @@ int launch_emu_bf16(const GemmArgs& g, const Sched& sch, const cosma_plan& p,
   args.ldc = g.ldc;
   args.status = status;
   args.wait_limit = wait_limit;
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(emu_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                ELayout::ALLOC);
-  });
-  if (attr != cudaSuccess) return (int)attr;
-  prof_mark(st, true);
-  emu_gemm_kernel<<<sch.ctas, 320, ELayout::ALLOC, st>>>(ta, tb, args);
-  prof_mark(st, false);
+  // Level sums fit in int32 when every level's products do: at most s pairs of
+  // k products of magnitude <= 2^(2 beta - 2).
+  const bool il = (double)s * (double)k * std::ldexp(1.0, 2 * beta - 2) < 2147483647.0;
+  cudaError_t le;
+  if (pairs) {
+    void (*kern)(const CUtensorMap, const CUtensorMap, EmuArgs) =
+        il ? emu_gemm_pair_kernel<true> : emu_gemm_pair_kernel<false>;
+    const cudaError_t attr2 =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, E2Layout::ALLOC);
+    if (attr2 != cudaSuccess) return (int)attr2;
+    cudaLaunchConfig_t cfgl = {};
+    cfgl.gridDim = dim3((unsigned)(2 * sch.ctas));
+    cfgl.blockDim = dim3(320);
+    cfgl.dynamicSmemBytes = E2Layout::ALLOC;
+    cfgl.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfgl.attrs = at;
+    cfgl.numAttrs = 1;
+    prof_mark(st, true);
+    le = cudaLaunchKernelEx(&cfgl, kern, ta, tb, args);
+    prof_mark(st, false);
+  } else {
+    void (*kern)(const CUtensorMap, const CUtensorMap, EmuArgs) =
+        il ? emu_gemm_kernel<true> : emu_gemm_kernel<false>;
+    const cudaError_t attr =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, ELayout::ALLOC);
+    if (attr != cudaSuccess) return (int)attr;
+    prof_mark(st, true);
+    kern<<<sch.ctas, 320, ELayout::ALLOC, st>>>(ta, tb, args);
+    prof_mark(st, false);
+    le = cudaGetLastError();
+  }
+  if (le != cudaSuccess) return (int)le;
   count_launch();
   return (int)cudaGetLastError();
 }

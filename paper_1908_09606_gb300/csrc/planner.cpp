@@ -44,9 +44,9 @@ int tiles_for(int kernel, TileChoice* out) {
     case COSMA_KERNEL_TC_BF16:
       out[0] = {128, 256, 64, 4}; out[1] = {128, 128, 64, 6};
       return 2;
-    case COSMA_KERNEL_EMU_BF16:
-      out[0] = {128, 128, 64, 5};
-      return 1;
+    case COSMA_KERNEL_EMU_BF16:  // 256-row tiles run on CTA pairs (2 SMs per tile)
+      out[0] = {256, 128, 64, 6}; out[1] = {128, 128, 64, 5};
+      return 2;
   }
   return 0;
 }
@@ -203,10 +203,11 @@ int plan_candidate(int64_t m, int64_t n, int64_t k, int dtype, int c, const Devi
   p.pk = pk; p.order = order;
   const int64_t kbu = cdiv(kbt, pk);
   int64_t mu;
+  const bool pair = d.kernel == COSMA_KERNEL_EMU_BF16 && t.tile_m == 256;
   if (order == 1) {
     const int64_t units = mt * ntl * pk;
     p.pm = p.pn = 1;
-    p.ctas = (int)std::min<int64_t>(P, units);
+    p.ctas = (int)std::min<int64_t>(pair ? std::max(1, P / 2) : P, units);
     mu = cdiv(units, p.ctas);
   } else {
     int g[3];
@@ -219,7 +220,9 @@ int plan_candidate(int64_t m, int64_t n, int64_t k, int dtype, int c, const Devi
     p.ctas = g[0] * g[1] * pk;
     mu = cdiv(mt, g[0]) * cdiv(ntl, g[1]);
   }
-  p.est_seconds = estimate(d, m, n, t, mu, kbu, pk);
+  TileChoice per_sm = t;
+  if (pair) per_sm.tile_m = 128;
+  p.est_seconds = estimate(d, m, n, per_sm, mu, kbu, pk) * (pair ? 0.8 : 1.0);
   finish_plan(m, n, k, dtype, d, P, p);
   *out = p;
   return COSMA_OK;
@@ -263,12 +266,15 @@ int plan_gemm(int64_t m, int64_t n, int64_t k, int dtype, int selector, const De
     for (int pi = 0; pi < npk; ++pi) {
       const int pk = pks[pi];
       const int64_t kbu = cdiv(kbt, pk);
-      // order 1: balanced stripes
+      // order 1: balanced stripes (a 256-row emulation tile occupies a pair of SMs)
       {
+        const bool pair = d.kernel == COSMA_KERNEL_EMU_BF16 && t.tile_m == 256;
         const int64_t units = tiles_total * pk;
-        const int ctas = (int)std::min<int64_t>(P, units);
+        const int ctas = (int)std::min<int64_t>(pair ? std::max(1, P / 2) : P, units);
         const int64_t mu = cdiv(units, ctas);
-        const double s = estimate(d, m, n, t, mu, kbu, pk);
+        TileChoice per_sm = t;
+        if (pair) per_sm.tile_m = 128;
+        const double s = estimate(d, m, n, per_sm, mu, kbu, pk) * (pair ? 0.8 : 1.0);
         if (best_s < 0 || s < best_s) {
           best_s = s;
           best = cosma_plan{};

@@ -113,3 +113,37 @@ def test_emu_full_size_sampled(size, kind):
     got = C[torch.as_tensor(rr, device="cuda"), torch.as_tensor(cc, device="cuda")].cpu().numpy()
     err = og.normwise_rel_error(got, ref)
     assert err <= 1e-12, err
+
+
+@pytest.mark.parametrize("cand", [1, 9])
+@pytest.mark.parametrize("shape", [(128, 128, 64), (300, 257, 999), (513, 129, 2048)])
+def test_emu_pair_and_single_sm_tiles(cand, shape):
+    # candidate 1: 256 x 128 tiles on CTA pairs; candidate 9: 128 x 128 on one SM
+    import torch
+    cosma = lib()
+    m, n, k = shape
+    p = cosma.cosma_plan_candidate(m, n, k, cosma.COSMA_F64_EMU_BF16, cand)
+    assert p.tile_m == (256 if cand == 1 else 128)
+    A, B = device_operands(m, n, k, DT, seed=4)
+    C, _ = out_tensor(m, n, DT)
+    cosma.gemm(A, B, C, DT, plan=p)
+    torch.cuda.synchronize()
+    assert cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream) == 0
+    Ah, Bh = host_operands(m, n, k, DT, seed=4)
+    assert og.normwise_rel_error(C.cpu().numpy(), og.gemm(Ah, Bh, "dot2")) <= 1e-12
+
+
+@pytest.mark.parametrize("cand", [1, 9])
+def test_emu_long_k_float_float_level_sums(cand):
+    # k > 21845: level sums no longer fit int32, the float-float path runs
+    import torch
+    cosma = lib()
+    m, n, k = 130, 129, 22001
+    p = cosma.cosma_plan_candidate(m, n, k, cosma.COSMA_F64_EMU_BF16, cand)
+    A, B = device_operands(m, n, k, DT, seed=8)
+    C, _ = out_tensor(m, n, DT)
+    cosma.gemm(A, B, C, DT, plan=p)
+    torch.cuda.synchronize()
+    assert cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream) == 0
+    Ah, Bh = host_operands(m, n, k, DT, seed=8)
+    assert og.normwise_rel_error(C.cpu().numpy(), og.gemm(Ah, Bh, "dot2")) <= 1e-12
