@@ -181,11 +181,24 @@ __global__ void split_b_kernel(const double* __restrict__ B, int64_t k, int64_t 
 }
 
 // ---- K-EMU / K-RECOMB -------------------------------------------------------------
+//
+// Iteration order of one C tile (all roles walk it identically):
+//   for each k super-chunk [sc0, sc1) of kcb k-blocks
+//     for each level l = s+1 down to 2 (p = l - 1 slice pairs)
+//       for each exact group [c0, c1) of gk(p) k-blocks inside the super-chunk
+//         for each pair q = 1..p:  for each k-block kb in [c0, c1):
+//           D[acc] (+)= A_q[tile rows, kb] * B_{l-q}[tile cols, kb]
+//       (the group's f32 sums are exact integers: drained into an int32 level sum)
+//     (end of level in the super-chunk: the exact level sum L joins the float-float
+//      running total T += 2^(-beta (l - 2)) L)
+// Super-chunks keep the slice panels a wave of tiles touches small enough to stay in
+// L2 across all levels (each level re-reads the same panels).
 
 struct EmuArgs {
-  Sched sch;           // tiles of 128 x 128, order 1, pk = 1
+  Sched sch;           // tiles (128 or 256 rows x 128 columns), order 1, pk = 1
   int s, beta;
-  int group_kb;        // k blocks of one pair per exact group at level 2 (2^(24-2beta+2)/64)
+  int group_kb;        // k blocks of one pair per exact group (2^(24 - 2 beta + 2) / 64)
+  int chunk_kb;        // k blocks per super-chunk
   const int* eA;
   const int* eB;
   double* C;
@@ -194,16 +207,8 @@ struct EmuArgs {
   long long wait_limit;
 };
 
-struct ELayout {
-  static constexpr int A_BYTES = EBM * EBK * 2;
-  static constexpr int B_BYTES = EBN * EBK * 2;
-  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int T_OFF = ESTAGES * STAGE_BYTES;           // running total, high parts
-  static constexpr int BAR_OFF = T_OFF + EBM * TPITCH * 4;
-  static constexpr int NBARS = 2 * ESTAGES + 9;  // full, empty, tfull[4], tempty[4], drain
-  static constexpr int TOTAL = BAR_OFF + NBARS * 8 + 16;
-  static constexpr int ALLOC = TOTAL + 1024;
-};
+constexpr int NACC = 3;            // accumulator buffers in tensor memory (columns 0..383)
+constexpr uint32_t TL_COL = 384;   // low parts of the running total (columns 384..511)
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int32_t x, int32_t y, int32_t z) {
@@ -241,60 +246,47 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
 
 // Epilogue warps (2..9) of K-EMU / K-RECOMB for the units of one CTA (or CTA
 // pair): warp -> tensor-memory lane quadrant q4 = warp % 4 and column half h.
-// Drains every exact group into the float-float level sum in tensor memory,
-// merges finished levels into the running total (high parts in shared memory
-// at Tsm, low parts in registers) and stores the FP64 tile.  Rows of this CTA
-// start at tile_row * tile_rows + row_off.  tempty_addr: cluster addresses of
-// the accumulator-free barriers of the MMA-issuing CTA.
-template <bool IL>
+// Rows of this CTA start at tile_row * tile_rows + row_off.  tempty_addr: cluster
+// addresses of the accumulator-free barriers of the MMA-issuing CTA.  The
+// running total T = Th + Tl keeps Th in shared memory (Tsm) and Tl in tensor
+// memory.
 __device__ __forceinline__ void emu_epilogue(const EmuArgs& a, int unit_cta, int64_t nunits,
                                              int64_t row_off, int64_t tile_rows,
-                                             uint32_t tmem_base, uint8_t* Tsm,
-                                             uint64_t* tfull, const uint32_t* tempty_addr,
-                                             const tc::WaitCtx& w, int warp, int lane) {
-  constexpr int NACC = IL ? 3 : 2;
+                                             uint32_t tmem_base, uint8_t* Tsm, uint64_t* tfull,
+                                             const uint32_t* tempty_addr, const tc::WaitCtx& w,
+                                             int warp, int lane) {
   const int64_t kbt = a.sch.kbt;
   const int top = a.s + 1;
   const int q4 = warp & 3;
   const int h = (warp - 2) >> 2;
   const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
   const uint32_t col_lo = (uint32_t)(64 * h);
-  const uint32_t lvl_hi_col = 256 + col_lo, lvl_lo_col = 384 + col_lo;
-  const float down = 1.0f / (float)(1 << a.beta);
+  const uint32_t tl = tmem_base + lane_off + TL_COL + col_lo;
   float* Th = reinterpret_cast<float*>(Tsm) + (q4 * 32 + lane) * TPITCH + col_lo;
   uint32_t acc = 0;
-  uint32_t tph[NACC];
-#pragma unroll
-  for (int b = 0; b < NACC; ++b) tph[b] = 0;
+  uint32_t tph[NACC] = {0, 0, 0};
   bool ok = true;
   for (int64_t ui = 0; ui < nunits && ok; ++ui) {
     const Unit u = unit_of_cta(a.sch, unit_cta, ui);
-    // Running total T = Th + Tl: Th in shared memory; Tl in registers (float-float
-    // level sums) or, with int32 level sums, in tensor memory columns 384.. .
-    float Tl[IL ? 1 : 64];
-    int Lv[IL ? 64 : 1];  // exact level sum (int32 path)
-    const uint32_t tl_col = 384 + col_lo;
-#pragma unroll
-    for (int j = 0; j < 64; ++j) {
-      Th[j] = 0.f;
-      if constexpr (!IL) Tl[j] = 0.f;
-    }
-    if constexpr (IL) {
+    int Lv[64];  // exact level sum of the current super-chunk
+    {
       uint32_t z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
-      for (int c = 0; c < 64; c += 8) tc::tmem_st_32x8(tmem_base + lane_off + tl_col + c, z);
+      for (int j = 0; j < 64; ++j) Th[j] = 0.f;
+#pragma unroll
+      for (int c = 0; c < 64; c += 8) tc::tmem_st_32x8(tl + c, z);
       tc::tmem_wait_st();
     }
-    for (int lvl = top; lvl >= 2 && ok; --lvl) {
-      const int p = lvl - 1;
-      const int gk = group_blocks(a.group_kb, p);
-      const int64_t ngroups = (kbt + gk - 1) / gk;
-      for (int64_t g = 0; g < ngroups; ++g) {
-        if (!tc::mbar_wait(&tfull[acc], tph[acc], w)) { ok = false; break; }
-        tc::tc_fence_after();
-        const bool first = (g == 0), last = (g == ngroups - 1);
-        if constexpr (IL) {
-          // Drain: the group's exact integer sums join the int32 level sum.
+    for (int64_t sc0 = 0; sc0 < kbt && ok; sc0 += a.chunk_kb) {
+      const int64_t sc1 = min(sc0 + (int64_t)a.chunk_kb, kbt);
+      for (int lvl = top; lvl >= 2 && ok; --lvl) {
+        const int gk = group_blocks(a.group_kb, lvl - 1);
+        // 2^(-beta (lvl - 2)): exact power of two
+        const float scale = __int_as_float((127 - a.beta * (lvl - 2)) << 23);
+        for (int64_t c0 = sc0; c0 < sc1; c0 += gk) {
+          if (!tc::mbar_wait(&tfull[acc], tph[acc], w)) { ok = false; break; }
+          tc::tc_fence_after();
+          const bool first = (c0 == sc0), last = (c0 + gk >= sc1);
 #pragma unroll
           for (int c = 0; c < 64; c += 8) {
             uint32_t v[8];
@@ -302,109 +294,60 @@ __device__ __forceinline__ void emu_epilogue(const EmuArgs& a, int unit_cta, int
             tc::tmem_wait_ld();
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              const int iv = __float2int_rn(__uint_as_float(v[j]));
-              Lv[IL ? c + j : 0] = first ? iv : Lv[IL ? c + j : 0] + iv;
+              const int iv = __float2int_rn(__uint_as_float(v[j]));  // exact integer
+              Lv[c + j] = first ? iv : Lv[c + j] + iv;
             }
           }
           tc::tc_fence_before();
           __syncwarp();
           if (lane == 0) tc::mbar_arrive_remote(tempty_addr[acc]);
           tph[acc] ^= 1;
-          acc = (acc + 1) % NACC;
+          acc = (acc + 1) == NACC ? 0 : acc + 1;
           if (last) {
-            // K-RECOMB: T = T * 2^-beta + level, the level split exactly into two floats.
+            // K-RECOMB: T += 2^(-beta (lvl - 2)) L, L split exactly into two floats.
 #pragma unroll
             for (int c = 0; c < 64; c += 8) {
-              uint32_t tl[8];
-              tc::tmem_ld_32x8(tmem_base + lane_off + tl_col + c, tl);
+              uint32_t t[8];
+              tc::tmem_ld_32x8(tl + c, t);
               tc::tmem_wait_ld();
 #pragma unroll
               for (int j = 0; j < 8; ++j) {
-                const int li = Lv[IL ? c + j : 0];
+                const int li = Lv[c + j];
                 const float lh = (float)li;
                 const float ll = (float)(li - (int)lh);
                 float s, e, nh, nl;
-                two_sum(Th[c + j] * down, lh, s, e);
-                e += __uint_as_float(tl[j]) * down + ll;
+                two_sum(Th[c + j], lh * scale, s, e);
+                e += __uint_as_float(t[j]) + ll * scale;
                 fast_two_sum(s, e, nh, nl);
                 Th[c + j] = nh;
-                tl[j] = __float_as_uint(nl);
+                t[j] = __float_as_uint(nl);
               }
-              tc::tmem_st_32x8(tmem_base + lane_off + tl_col + c, tl);
+              tc::tmem_st_32x8(tl + c, t);
             }
             tc::tmem_wait_st();
           }
-        } else {
-#pragma unroll
-        for (int c = 0; c < 64; c += 8) {
-          uint32_t v[8], hi[8], lo[8];
-          tc::tmem_ld_32x8(tmem_base + lane_off + acc * EBN + col_lo + c, v);
-          if (!first) {
-            tc::tmem_ld_32x8(tmem_base + lane_off + lvl_hi_col + c, hi);
-            tc::tmem_ld_32x8(tmem_base + lane_off + lvl_lo_col + c, lo);
-          }
-          tc::tmem_wait_ld();
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float x = __uint_as_float(v[j]);  // exact integer
-            float fh = x, fl = 0.f;
-            if (!first) {
-              float s, e;
-              two_sum(__uint_as_float(hi[j]), x, s, e);
-              fast_two_sum(s, __uint_as_float(lo[j]) + e, fh, fl);
-            }
-            if (last) {
-              // K-RECOMB: T = T * 2^-beta + level (the first level processed starts T).
-              float s, e, nh;
-              two_sum(Th[c + j] * down, fh, s, e);
-              e += Tl[IL ? 0 : c + j] * down + fl;
-              fast_two_sum(s, e, nh, Tl[IL ? 0 : c + j]);
-              Th[c + j] = nh;
-            } else {
-              hi[j] = __float_as_uint(fh);
-              lo[j] = __float_as_uint(fl);
-            }
-          }
-          if (!last) {
-            tc::tmem_st_32x8(tmem_base + lane_off + lvl_hi_col + c, hi);
-            tc::tmem_st_32x8(tmem_base + lane_off + lvl_lo_col + c, lo);
-          }
-        }
-        tc::tmem_wait_st();
-        tc::tc_fence_before();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive_remote(tempty_addr[acc]);
-        tph[acc] ^= 1;
-        acc = (acc + 1) % NACC;
         }
       }
     }
     if (!ok) break;
-    // Final FP64 store of this thread's 64 columns of one row.
+    // Final FP64 store of this thread's 64 columns of one row:
+    // C = (Th + Tl) 2^(sigma_i + tau_j + 2 - 2 beta).
     const int64_t row = u.tile_row * tile_rows + row_off + q4 * 32 + lane;
     const int64_t cbase = u.tile_col * EBN + col_lo;
     const int ea = row < a.sch.m ? a.eA[row] : kExpNone;
     double* dst = a.C + row * a.ldc;
 #pragma unroll
     for (int c = 0; c < 64; c += 8) {
-      float tl[8];
-      if constexpr (IL) {
-        uint32_t t[8];
-        tc::tmem_ld_32x8(tmem_base + lane_off + tl_col + c, t);
-        tc::tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 8; ++j) tl[j] = __uint_as_float(t[j]);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) tl[j] = Tl[IL ? 0 : c + j];
-      }
+      uint32_t t[8];
+      tc::tmem_ld_32x8(tl + c, t);
+      tc::tmem_wait_ld();
       if (row < a.sch.m) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int64_t col = cbase + c + j;
           if (col < a.sch.n) {
             const int eb = a.eB[col];
-            const double val = (double)Th[c + j] + (double)tl[j];
+            const double val = (double)Th[c + j] + (double)__uint_as_float(t[j]);
             dst[col] = (ea == kExpNone || eb == kExpNone)
                            ? 0.0
                            : scale_pow2(val, ea + eb + 2 - 2 * a.beta);
@@ -415,20 +358,58 @@ __device__ __forceinline__ void emu_epilogue(const EmuArgs& a, int unit_cta, int
   }
 }
 
-template <bool IL>
+// Same iteration order for the producer and the MMA issuer: calls body(q, lvl,
+// kb) for every k-block of every pair, and group_begin / group_end around the
+// exact groups.  Returns false as soon as a callback does (abort).
+template <class GroupBegin, class Body, class GroupEnd>
+__device__ __forceinline__ bool emu_walk(const EmuArgs& a, GroupBegin group_begin, Body body,
+                                         GroupEnd group_end) {
+  const int64_t kbt = a.sch.kbt;
+  const int top = a.s + 1;
+  for (int64_t sc0 = 0; sc0 < kbt; sc0 += a.chunk_kb) {
+    const int64_t sc1 = min(sc0 + (int64_t)a.chunk_kb, kbt);
+    for (int lvl = top; lvl >= 2; --lvl) {
+      const int p = lvl - 1;
+      const int gk = group_blocks(a.group_kb, p);
+      for (int64_t c0 = sc0; c0 < sc1; c0 += gk) {
+        const int64_t c1 = min(c0 + (int64_t)gk, sc1);
+        if (!group_begin()) return false;
+        bool first = true;
+        for (int q = 1; q <= p; ++q)
+          for (int64_t kb = c0; kb < c1; ++kb) {
+            if (!body(q, lvl, kb, first)) return false;
+            first = false;
+          }
+        group_end();
+      }
+    }
+  }
+  return true;
+}
+
+struct ELayout {
+  static constexpr int A_BYTES = EBM * EBK * 2;
+  static constexpr int B_BYTES = EBN * EBK * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int T_OFF = ESTAGES * STAGE_BYTES;           // running total, high parts
+  static constexpr int BAR_OFF = T_OFF + EBM * TPITCH * 4;
+  static constexpr int NBARS = 2 * ESTAGES + 2 * NACC + 1;      // full, empty, tfull, tempty, drain
+  static constexpr int TOTAL = BAR_OFF + NBARS * 8 + 16;
+  static constexpr int ALLOC = TOTAL + 1024;
+};
+
 __global__ void __launch_bounds__(320, 1)
 emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 EmuArgs a) {
   using L = ELayout;
-  constexpr int NACC = IL ? 3 : 2;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
   uint64_t* empty = full + ESTAGES;
   uint64_t* tfull = empty + ESTAGES;
-  uint64_t* tempty = tfull + 4;
-  uint64_t* drain = tempty + 4;
+  uint64_t* tempty = tfull + NACC;
+  uint64_t* drain = tempty + NACC;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
@@ -458,8 +439,6 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   const tc::WaitCtx w{a.wait_limit, a.status, abort_flag};
   const int cta = blockIdx.x;
   const int64_t nunits = units_of_cta(a.sch, cta);
-  const int64_t kbt = a.sch.kbt;
-  const int top = a.s + 1;
 
   if (warp == 0) {
     if (tc::elect_one()) {
@@ -467,28 +446,22 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       uint32_t ph = 0, armed = 0, armed_ph = 0;
       for (int64_t ui = 0; ui < nunits && !*abort_flag; ++ui) {
         const Unit u = unit_of_cta(a.sch, cta, ui);
-        bool ok = true;
-        for (int lvl = top; lvl >= 2 && ok; --lvl) {
-          const int p = lvl - 1;
-          const int gk = group_blocks(a.group_kb, p);
-          for (int64_t c0 = 0; c0 < kbt && ok; c0 += gk) {
-            const int64_t c1 = min(c0 + gk, kbt);
-            for (int q = 1; q <= p && ok; ++q) {
-              for (int64_t kb = c0; kb < c1; ++kb) {
-                if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) { ok = false; break; }
-                tc::mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES);
-                uint8_t* sa = smem + stage * L::STAGE_BYTES;
-                tma_load_3d(sa, &tmA, &full[stage], (int32_t)(kb * EBK),
-                            (int32_t)(u.tile_row * EBM), q - 1);
-                tma_load_3d(sa + L::A_BYTES, &tmB, &full[stage], (int32_t)(kb * EBK),
-                            (int32_t)(u.tile_col * EBN), lvl - q - 1);
-                armed |= 1u << stage;
-                armed_ph = (armed_ph & ~(1u << stage)) | (ph << stage);
-                if (++stage == ESTAGES) { stage = 0; ph ^= 1; }
-              }
-            }
-          }
-        }
+        const bool ok = emu_walk(
+            a, [] { return true; },
+            [&](int q, int lvl, int64_t kb, bool) {
+              if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) return false;
+              tc::mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES);
+              uint8_t* sa = smem + stage * L::STAGE_BYTES;
+              tma_load_3d(sa, &tmA, &full[stage], (int32_t)(kb * EBK),
+                          (int32_t)(u.tile_row * EBM), q - 1);
+              tma_load_3d(sa + L::A_BYTES, &tmB, &full[stage], (int32_t)(kb * EBK),
+                          (int32_t)(u.tile_col * EBN), lvl - q - 1);
+              armed |= 1u << stage;
+              armed_ph = (armed_ph & ~(1u << stage)) | (ph << stage);
+              if (++stage == ESTAGES) { stage = 0; ph ^= 1; }
+              return true;
+            },
+            [] {});
         if (!ok) break;
       }
       if (*abort_flag) {
@@ -506,42 +479,36 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       constexpr uint32_t idesc = tc::idesc_bf16_f32(EBM, EBN);
       int stage = 0;
       uint32_t ph = 0, acc = 0;
-      uint32_t aph[NACC];
+      uint32_t aph[NACC] = {0, 0, 0};
+      for (int64_t ui = 0; ui < nunits && !*abort_flag; ++ui) {
+        const bool ok = emu_walk(
+            a,
+            [&] {
+              if (!tc::mbar_wait(&tempty[acc], aph[acc] ^ 1, w)) return false;
+              tc::tc_fence_after();
+              return true;
+            },
+            [&](int, int, int64_t, bool first) {
+              if (!tc::mbar_wait(&full[stage], ph, w)) return false;
+              tc::tc_fence_after();
+              const uint32_t sa = tc::smem_u32(smem + stage * L::STAGE_BYTES);
+              const uint32_t sb = sa + L::A_BYTES;
+              const uint32_t d = tmem_base + acc * EBN;
 #pragma unroll
-      for (int b = 0; b < NACC; ++b) aph[b] = 0;
-      bool ok = true;
-      for (int64_t ui = 0; ui < nunits && ok && !*abort_flag; ++ui) {
-        for (int lvl = top; lvl >= 2 && ok; --lvl) {
-          const int p = lvl - 1;
-          const int gk = group_blocks(a.group_kb, p);
-          for (int64_t c0 = 0; c0 < kbt && ok; c0 += gk) {
-            const int64_t c1 = min(c0 + gk, kbt);
-            if (!tc::mbar_wait(&tempty[acc], aph[acc] ^ 1, w)) { ok = false; break; }
-            tc::tc_fence_after();
-            const uint32_t d = tmem_base + acc * EBN;
-            bool first = true;
-            for (int q = 1; q <= p && ok; ++q) {
-              for (int64_t kb = c0; kb < c1; ++kb) {
-                if (!tc::mbar_wait(&full[stage], ph, w)) { ok = false; break; }
-                tc::tc_fence_after();
-                const uint32_t sa = tc::smem_u32(smem + stage * L::STAGE_BYTES);
-                const uint32_t sb = sa + L::A_BYTES;
-#pragma unroll
-                for (int kk = 0; kk < EBK / 16; ++kk) {
-                  tc::mma_bf16(d, tc::smem_desc_sw128(sa + kk * 32),
-                               tc::smem_desc_sw128(sb + kk * 32), idesc, first ? 0u : 1u);
-                  first = false;
-                }
-                tc::mma_commit(&empty[stage]);
-                if (++stage == ESTAGES) { stage = 0; ph ^= 1; }
-              }
-            }
-            if (!ok) break;
-            tc::mma_commit(&tfull[acc]);
-            aph[acc] ^= 1;
-            acc = (acc + 1) % NACC;
-          }
-        }
+              for (int kk = 0; kk < EBK / 16; ++kk)
+                tc::mma_bf16(d, tc::smem_desc_sw128(sa + kk * 32),
+                             tc::smem_desc_sw128(sb + kk * 32), idesc,
+                             (first && kk == 0) ? 0u : 1u);
+              tc::mma_commit(&empty[stage]);
+              if (++stage == ESTAGES) { stage = 0; ph ^= 1; }
+              return true;
+            },
+            [&] {
+              tc::mma_commit(&tfull[acc]);
+              aph[acc] ^= 1;
+              acc = (acc + 1) == NACC ? 0 : acc + 1;
+            });
+        if (!ok) break;
       }
       tc::mma_commit(drain);
       const long long t0 = clock64();
@@ -552,7 +519,7 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     uint32_t te[NACC];
 #pragma unroll
     for (int b = 0; b < NACC; ++b) te[b] = tc::mapa_shared(&tempty[b], 0);
-    emu_epilogue<IL>(a, cta, nunits, 0, EBM, tmem_base, smem + L::T_OFF, tfull, te, w, warp, lane);
+    emu_epilogue(a, cta, nunits, 0, EBM, tmem_base, smem + L::T_OFF, tfull, te, w, warp, lane);
   }
   __syncthreads();
   if (warp == 1) {
@@ -560,7 +527,6 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     tc::tmem_dealloc(tmem_base, 512);
   }
 }
-
 
 // ---- 2-SM variant ------------------------------------------------------------------
 //
@@ -578,7 +544,7 @@ struct E2Layout {
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int T_OFF = E2_STAGES * STAGE_BYTES;
   static constexpr int BAR_OFF = T_OFF + EBM * TPITCH * 4;
-  static constexpr int NBARS = 2 * E2_STAGES + 9;
+  static constexpr int NBARS = 2 * E2_STAGES + 2 * NACC + 1;
   static constexpr int TOTAL = BAR_OFF + NBARS * 8 + 16;
   static constexpr int ALLOC = TOTAL + 1024;
 };
@@ -593,20 +559,18 @@ __device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* m
       : "memory");
 }
 
-template <bool IL>
 __global__ void __launch_bounds__(320, 1)
 emu_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB, EmuArgs a) {
   using L = E2Layout;
-  constexpr int NACC = IL ? 3 : 2;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
   uint64_t* empty = full + E2_STAGES;
   uint64_t* tfull = empty + E2_STAGES;
-  uint64_t* tempty = tfull + 4;
-  uint64_t* drain = tempty + 4;
+  uint64_t* tempty = tfull + NACC;
+  uint64_t* drain = tempty + NACC;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
@@ -634,8 +598,6 @@ emu_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
   const tc::WaitCtx w{a.wait_limit, a.status, abort_flag};
   const int pair = blockIdx.x >> 1;
   const int64_t nunits = units_of_cta(a.sch, pair);
-  const int64_t kbt = a.sch.kbt;
-  const int top = a.s + 1;
 
   if (warp == 0) {
     if (tc::elect_one()) {
@@ -647,27 +609,21 @@ emu_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
       for (int s = 0; s < E2_STAGES; ++s) full_cl[s] = tc::mapa_shared(&full[s], 0);
       for (int64_t ui = 0; ui < nunits && !*abort_flag; ++ui) {
         const Unit u = unit_of_cta(a.sch, pair, ui);
-        bool ok = true;
-        for (int lvl = top; lvl >= 2 && ok; --lvl) {
-          const int p = lvl - 1;
-          const int gk = group_blocks(a.group_kb, p);
-          for (int64_t c0 = 0; c0 < kbt && ok; c0 += gk) {
-            const int64_t c1 = min(c0 + gk, kbt);
-            for (int q = 1; q <= p && ok; ++q) {
-              for (int64_t kb = c0; kb < c1; ++kb) {
-                if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) { ok = false; break; }
-                if (leader) tc::mbar_arrive_expect_tx(&full[stage], 2 * L::STAGE_BYTES);
-                uint8_t* sa = smem + stage * L::STAGE_BYTES;
-                tma_load_3d_pair(sa, &tmA, full_cl[stage], (int32_t)(kb * EBK),
-                                 (int32_t)(u.tile_row * (2 * EBM) + rank * EBM), q - 1);
-                tma_load_3d_pair(sa + L::A_BYTES, &tmB, full_cl[stage], (int32_t)(kb * EBK),
-                                 (int32_t)(u.tile_col * EBN + rank * (EBN / 2)), lvl - q - 1);
-                issued = true;
-                if (++stage == E2_STAGES) { stage = 0; ph ^= 1; }
-              }
-            }
-          }
-        }
+        const bool ok = emu_walk(
+            a, [] { return true; },
+            [&](int q, int lvl, int64_t kb, bool) {
+              if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) return false;
+              if (leader) tc::mbar_arrive_expect_tx(&full[stage], 2 * L::STAGE_BYTES);
+              uint8_t* sa = smem + stage * L::STAGE_BYTES;
+              tma_load_3d_pair(sa, &tmA, full_cl[stage], (int32_t)(kb * EBK),
+                               (int32_t)(u.tile_row * (2 * EBM) + rank * EBM), q - 1);
+              tma_load_3d_pair(sa + L::A_BYTES, &tmB, full_cl[stage], (int32_t)(kb * EBK),
+                               (int32_t)(u.tile_col * EBN + rank * (EBN / 2)), lvl - q - 1);
+              issued = true;
+              if (++stage == E2_STAGES) { stage = 0; ph ^= 1; }
+              return true;
+            },
+            [] {});
         if (!ok) break;
       }
       if (*abort_flag && issued) {
@@ -683,42 +639,36 @@ emu_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
       constexpr uint32_t idesc = tc::idesc_bf16_f32(2 * EBM, EBN);
       int stage = 0;
       uint32_t ph = 0, acc = 0;
-      uint32_t aph[NACC];
+      uint32_t aph[NACC] = {0, 0, 0};
+      for (int64_t ui = 0; ui < nunits && !*abort_flag; ++ui) {
+        const bool ok = emu_walk(
+            a,
+            [&] {
+              if (!tc::mbar_wait(&tempty[acc], aph[acc] ^ 1, w)) return false;
+              tc::tc_fence_after();
+              return true;
+            },
+            [&](int, int, int64_t, bool first) {
+              if (!tc::mbar_wait(&full[stage], ph, w)) return false;
+              tc::tc_fence_after();
+              const uint32_t sa = tc::smem_u32(smem + stage * L::STAGE_BYTES);
+              const uint32_t sb = sa + L::A_BYTES;
+              const uint32_t d = tmem_base + acc * EBN;
 #pragma unroll
-      for (int b = 0; b < NACC; ++b) aph[b] = 0;
-      bool ok = true;
-      for (int64_t ui = 0; ui < nunits && ok && !*abort_flag; ++ui) {
-        for (int lvl = top; lvl >= 2 && ok; --lvl) {
-          const int p = lvl - 1;
-          const int gk = group_blocks(a.group_kb, p);
-          for (int64_t c0 = 0; c0 < kbt && ok; c0 += gk) {
-            const int64_t c1 = min(c0 + gk, kbt);
-            if (!tc::mbar_wait(&tempty[acc], aph[acc] ^ 1, w)) { ok = false; break; }
-            tc::tc_fence_after();
-            const uint32_t d = tmem_base + acc * EBN;
-            bool first = true;
-            for (int q = 1; q <= p && ok; ++q) {
-              for (int64_t kb = c0; kb < c1; ++kb) {
-                if (!tc::mbar_wait(&full[stage], ph, w)) { ok = false; break; }
-                tc::tc_fence_after();
-                const uint32_t sa = tc::smem_u32(smem + stage * L::STAGE_BYTES);
-                const uint32_t sb = sa + L::A_BYTES;
-#pragma unroll
-                for (int kk = 0; kk < EBK / 16; ++kk) {
-                  tc::mma_bf16_pair(d, tc::smem_desc_sw128(sa + kk * 32),
-                                    tc::smem_desc_sw128(sb + kk * 32), idesc, first ? 0u : 1u);
-                  first = false;
-                }
-                tc::mma_commit_pair(&empty[stage]);
-                if (++stage == E2_STAGES) { stage = 0; ph ^= 1; }
-              }
-            }
-            if (!ok) break;
-            tc::mma_commit_pair(&tfull[acc]);
-            aph[acc] ^= 1;
-            acc = (acc + 1) % NACC;
-          }
-        }
+              for (int kk = 0; kk < EBK / 16; ++kk)
+                tc::mma_bf16_pair(d, tc::smem_desc_sw128(sa + kk * 32),
+                                  tc::smem_desc_sw128(sb + kk * 32), idesc,
+                                  (first && kk == 0) ? 0u : 1u);
+              tc::mma_commit_pair(&empty[stage]);
+              if (++stage == E2_STAGES) { stage = 0; ph ^= 1; }
+              return true;
+            },
+            [&] {
+              tc::mma_commit_pair(&tfull[acc]);
+              aph[acc] ^= 1;
+              acc = (acc + 1) == NACC ? 0 : acc + 1;
+            });
+        if (!ok) break;
       }
       tc::mma_commit_pair(drain);  // every MMA of the pair done (both CTAs' drain barriers)
       const long long t0 = clock64();
@@ -729,8 +679,8 @@ emu_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
     uint32_t te[NACC];
 #pragma unroll
     for (int b = 0; b < NACC; ++b) te[b] = tc::mapa_shared(&tempty[b], 0);
-    emu_epilogue<IL>(a, pair, nunits, (int64_t)rank * EBM, 2 * EBM, tmem_base, smem + L::T_OFF,
-                     tfull, te, w, warp, lane);
+    emu_epilogue(a, pair, nunits, (int64_t)rank * EBM, 2 * EBM, tmem_base, smem + L::T_OFF,
+                 tfull, te, w, warp, lane);
   }
   __syncthreads();
   tc::tc_fence_before();
@@ -840,15 +790,19 @@ int launch_emu_bf16(const GemmArgs& g, const Sched& sch, const cosma_plan& p,
   args.ldc = g.ldc;
   args.status = status;
   args.wait_limit = wait_limit;
-  // Level sums fit in int32 when every level's products do: at most s pairs of
-  // k products of magnitude <= 2^(2 beta - 2).
-  const bool il = (double)s * (double)k * std::ldexp(1.0, 2 * beta - 2) < 2147483647.0;
+  // Super-chunk: short enough for the slice panels of a wave of tiles to stay in
+  // L2 (2048 k), and for every level sum of a chunk to fit in int32 exactly
+  // (at most s pairs x chunk x 2^(2 beta - 2)).
+  {
+    const double lim = 2147483647.0 / ((double)s * std::ldexp(1.0, 2 * beta - 2));
+    int64_t ck = 2048 / EBK;
+    while (ck > 1 && (double)ck * EBK > lim) --ck;
+    args.chunk_kb = (int)ck;
+  }
   cudaError_t le;
   if (pairs) {
-    void (*kern)(const CUtensorMap, const CUtensorMap, EmuArgs) =
-        il ? emu_gemm_pair_kernel<true> : emu_gemm_pair_kernel<false>;
-    const cudaError_t attr2 =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, E2Layout::ALLOC);
+    const cudaError_t attr2 = cudaFuncSetAttribute(
+        emu_gemm_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, E2Layout::ALLOC);
     if (attr2 != cudaSuccess) return (int)attr2;
     cudaLaunchConfig_t cfgl = {};
     cfgl.gridDim = dim3((unsigned)(2 * sch.ctas));
@@ -863,16 +817,14 @@ int launch_emu_bf16(const GemmArgs& g, const Sched& sch, const cosma_plan& p,
     cfgl.attrs = at;
     cfgl.numAttrs = 1;
     prof_mark(st, true);
-    le = cudaLaunchKernelEx(&cfgl, kern, ta, tb, args);
+    le = cudaLaunchKernelEx(&cfgl, emu_gemm_pair_kernel, ta, tb, args);
     prof_mark(st, false);
   } else {
-    void (*kern)(const CUtensorMap, const CUtensorMap, EmuArgs) =
-        il ? emu_gemm_kernel<true> : emu_gemm_kernel<false>;
-    const cudaError_t attr =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, ELayout::ALLOC);
+    const cudaError_t attr = cudaFuncSetAttribute(
+        emu_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ELayout::ALLOC);
     if (attr != cudaSuccess) return (int)attr;
     prof_mark(st, true);
-    kern<<<sch.ctas, 320, ELayout::ALLOC, st>>>(ta, tb, args);
+    emu_gemm_kernel<<<sch.ctas, 320, ELayout::ALLOC, st>>>(ta, tb, args);
     prof_mark(st, false);
     le = cudaGetLastError();
   }

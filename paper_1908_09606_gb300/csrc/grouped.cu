@@ -101,41 +101,67 @@ __device__ __forceinline__ int find_problem(const int64_t* prefix, int count, in
 }
 
 // Transposes every B_i (k x n) into Bt_i (n x kp) and copies each A_i whose
-// row pitch is not a multiple of 16 bytes into Ap_i (m x kp); 32 x 32 tiles.
-__global__ void grouped_prep_kernel(const GMeta* __restrict__ meta, const int64_t* __restrict__ tprefix,
-                                    const int64_t* __restrict__ aprefix, int count, int64_t ttiles,
-                                    int64_t atiles) {
-  __shared__ __nv_bfloat16 tile[32][34];
+// row pitch is not a multiple of 16 bytes into Ap_i (m x kp).  64 x 64 tiles,
+// 256 threads: each warp moves rows of 64 elements as 32 pairs (4 bytes per
+// lane) when the pitch allows, single elements otherwise.
+constexpr int PT = 64;
+
+__global__ void __launch_bounds__(256)
+grouped_prep_kernel(const GMeta* __restrict__ meta, const int64_t* __restrict__ tprefix,
+                    const int64_t* __restrict__ aprefix, int count, int64_t ttiles,
+                    int64_t atiles) {
+  __shared__ __nv_bfloat16 tile[PT][PT + 2];
+  const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;
   for (int64_t x = blockIdx.x; x < ttiles + atiles; x += gridDim.x) {
     if (x < ttiles) {
       const int p = find_problem(tprefix, count, x);
       const GMeta& g = meta[p];
       const int64_t local = x - tprefix[p];
-      const int64_t tiles_j = (g.n + 31) / 32;
-      const int64_t tj = local % tiles_j, tt = local / tiles_j;
-      const int64_t t0 = tt * 32, j0 = tj * 32;
+      const int64_t tiles_j = (g.n + PT - 1) / PT;
+      const int64_t t0 = (local / tiles_j) * PT, j0 = (local % tiles_j) * PT;
       const __nv_bfloat16* B = static_cast<const __nv_bfloat16*>(g.B);
+      const bool pairs_in = ((g.ldb & 1) == 0) && ((reinterpret_cast<uintptr_t>(B) & 3) == 0);
       __syncthreads();
-      for (int i = threadIdx.y; i < 32; i += 8) {
-        const int64_t t = t0 + i, j = j0 + threadIdx.x;
-        if (t < g.k && j < g.n) tile[i][threadIdx.x] = B[t * g.ldb + j];
+      for (int r = wrp; r < PT; r += 8) {  // rows t of B, columns j
+        const int64_t t = t0 + r, j = j0 + 2 * lane;
+        if (t >= g.k) continue;
+        if (pairs_in && j + 1 < g.n) {
+          const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(B + t * g.ldb + j);
+          tile[r][2 * lane] = v.x;
+          tile[r][2 * lane + 1] = v.y;
+        } else {
+          if (j < g.n) tile[r][2 * lane] = B[t * g.ldb + j];
+          if (j + 1 < g.n) tile[r][2 * lane + 1] = B[t * g.ldb + j + 1];
+        }
       }
       __syncthreads();
-      for (int i = threadIdx.y; i < 32; i += 8) {
-        const int64_t j = j0 + i, t = t0 + threadIdx.x;
-        if (j < g.n && t < g.k) g.Bt[j * g.ldt + t] = tile[threadIdx.x][i];
+      for (int r = wrp; r < PT; r += 8) {  // rows j of Bt, columns t (ldt is even)
+        const int64_t j = j0 + r, t = t0 + 2 * lane;
+        if (j >= g.n) continue;
+        if (t + 1 < g.k) {
+          __nv_bfloat162 v;
+          v.x = tile[2 * lane][r];
+          v.y = tile[2 * lane + 1][r];
+          *reinterpret_cast<__nv_bfloat162*>(g.Bt + j * g.ldt + t) = v;
+        } else if (t < g.k) {
+          g.Bt[j * g.ldt + t] = tile[2 * lane][r];
+        }
       }
     } else {
       const int64_t y = x - ttiles;
       const int p = find_problem(aprefix, count, y);
       const GMeta& g = meta[p];
       const int64_t local = y - aprefix[p];
-      const int64_t tiles_t = (g.k + 31) / 32;
-      const int64_t r0 = (local / tiles_t) * 32, t0 = (local % tiles_t) * 32;
+      const int64_t tiles_t = (g.k + PT - 1) / PT;
+      const int64_t r0 = (local / tiles_t) * PT, t0 = (local % tiles_t) * PT;
       const __nv_bfloat16* A = static_cast<const __nv_bfloat16*>(g.A);
-      for (int i = threadIdx.y; i < 32; i += 8) {
-        const int64_t r = r0 + i, t = t0 + threadIdx.x;
-        if (r < g.m && t < g.k) g.Ap[r * g.ldap + t] = A[r * g.lda + t];
+      for (int i = wrp; i < PT; i += 8) {
+        const int64_t r = r0 + i;
+        if (r >= g.m) continue;
+        for (int c = lane; c < PT; c += 32) {
+          const int64_t t = t0 + c;
+          if (t < g.k) g.Ap[r * g.ldap + t] = A[r * g.lda + t];
+        }
       }
     }
   }
@@ -337,8 +363,8 @@ __global__ void __launch_bounds__(256) grouped_simt_kernel(GArgs a) {
   }
 }
 
-// 128 x 128 tiles: the cp.async ring for aligned problems, the register-staged
-// tile otherwise (both layouts share the dynamic shared memory).
+// 128 x 128 tiles: the cp.async ring, 16-byte copies for problems whose rows
+// allow them and 4-byte copies otherwise.
 __global__ void __launch_bounds__(256) grouped_f32_kernel(GArgs a) {
   extern __shared__ __align__(16) uint8_t gsm[];
   const int u0 = a.cta_off[blockIdx.x], u1 = a.cta_off[blockIdx.x + 1];
@@ -350,11 +376,11 @@ __global__ void __launch_bounds__(256) grouped_f32_kernel(GArgs a) {
     float* C = static_cast<float*>(g.C);
     const int64_t r0 = (int64_t)u.tile_row * 128, c0 = (int64_t)u.tile_col * 128;
     if (g.f32_async)
-      f32_tile_async(A, g.lda, B, g.ldb, C, g.ldc, g.m, g.n, r0, c0, 0, g.k, g.vec_ok != 0,
-                     *reinterpret_cast<F32Smem*>(gsm));
+      f32_tile_async<4>(A, g.lda, B, g.ldb, C, g.ldc, g.m, g.n, r0, c0, 0, g.k, g.vec_ok != 0,
+                        *reinterpret_cast<F32Smem*>(gsm));
     else
-      simt_tile<float, 128, 128, 16, 8, 8>(A, g.lda, B, g.ldb, C, g.ldc, g.m, g.n, r0, c0, 0, g.k,
-                                           *reinterpret_cast<SimtSmem<float, 128, 128, 16>*>(gsm));
+      f32_tile_async<1>(A, g.lda, B, g.ldb, C, g.ldc, g.m, g.n, r0, c0, 0, g.k, g.vec_ok != 0,
+                        *reinterpret_cast<F32Smem*>(gsm));
   }
 }
 
@@ -460,13 +486,13 @@ int get_table(int dev, int count, const cosma_problem* pr, int dtype, int tile, 
         wsp += rup(q.m * kp * 2, 256);
         a_src = g.Ap;
         a_ld = kp;
-        apre[i + 1] = apre[i] + ((q.m + 31) / 32) * ((q.k + 31) / 32);
+        apre[i + 1] = apre[i] + ((q.m + PT - 1) / PT) * ((q.k + PT - 1) / PT);
       }
       int rc = encode(&maps[i].ta, a_src, q.m, q.k, a_ld, GBM);
       if (rc != COSMA_OK) return rc;
       rc = encode(&maps[i].tb, g.Bt, q.n, q.k, kp, tn);
       if (rc != COSMA_OK) return rc;
-      tpre[i + 1] = tpre[i] + ((q.n + 31) / 32) * ((q.k + 31) / 32);
+      tpre[i + 1] = tpre[i] + ((q.n + PT - 1) / PT) * ((q.k + PT - 1) / PT);
     }
     if (dtype == COSMA_BF16 && !(q.m > 0 && q.n > 0 && q.k > 0)) tpre[i + 1] = tpre[i];
     if (q.m == 0 || q.n == 0 || q.k == 0) continue;
@@ -603,7 +629,7 @@ int grouped_gemm(int count, const cosma_problem* problems, int dtype, const Devi
     if (t->ttiles + t->atiles > 0) {
       const int64_t blocks = std::min<int64_t>(t->ttiles + t->atiles,
                                                (int64_t)(dev.sms > 0 ? dev.sms : 148) * 16);
-      grouped_prep_kernel<<<(unsigned)blocks, dim3(32, 8), 0, st>>>(
+      grouped_prep_kernel<<<(unsigned)blocks, 256, 0, st>>>(
           t->meta, t->tprefix, t->aprefix, count, t->ttiles, t->atiles);
       count_launch();
       const cudaError_t e = cudaGetLastError();

@@ -46,6 +46,7 @@ simt_gemm_kernel(GemmArgs g, Sched s, T* partial) {
 }
 
 // K-F32 fast path: the cp.async multi-stage tile (simt_f32.cuh).
+template <int VEC>
 __global__ void __launch_bounds__(256)
 simt_f32_async_kernel(GemmArgs g, Sched s, float* partial, int vec_c) {
   extern __shared__ __align__(16) uint8_t f32_smem[];
@@ -68,7 +69,7 @@ simt_f32_async_kernel(GemmArgs g, Sched s, float* partial, int vec_c) {
       ld = g.ldc;
       vec = vec_c != 0;
     }
-    f32_tile_async(A, g.lda, B, g.ldb, dst, ld, g.m, g.n, u.tile_row * F32_BM, u.tile_col * F32_BN,
+    f32_tile_async<VEC>(A, g.lda, B, g.ldb, dst, ld, g.m, g.n, u.tile_row * F32_BM, u.tile_col * F32_BN,
                    u.kb0 * (int64_t)s.k_block, min(u.kb1 * (int64_t)s.k_block, g.k), vec, sm);
   }
 }
@@ -107,22 +108,20 @@ int launch_simt(int dtype, const GemmArgs& g, const Sched& s, void* partial, int
     if (s.tile_m == 128) return launch_tile<double, 128, 128, 8, 8, 8>(g, s, partial, st);
     return launch_tile<double, 64, 64, 8, 4, 4>(g, s, partial, st);
   }
-  if (s.tile_m == 128) {
+  if (s.tile_m == 128 && s.k_block % F32_BK == 0) {
     const bool aligned = (reinterpret_cast<uintptr_t>(g.A) & 15) == 0 && (g.lda & 3) == 0 &&
                          (reinterpret_cast<uintptr_t>(g.B) & 15) == 0 && (g.ldb & 3) == 0;
-    if (aligned && s.k_block % F32_BK == 0) {
-      static cudaError_t attr = cudaFuncSetAttribute(
-          simt_f32_async_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(F32Smem));
-      if (attr != cudaSuccess) return (int)attr;
-      const int vec_c = (reinterpret_cast<uintptr_t>(g.C) & 15) == 0 && (g.ldc & 3) == 0;
-      prof_mark(st, true);
-      simt_f32_async_kernel<<<s.ctas, 256, sizeof(F32Smem), st>>>(
-          g, s, static_cast<float*>(partial), vec_c);
-      prof_mark(st, false);
-      count_launch();
-      return (int)cudaGetLastError();
-    }
-    return launch_tile<float, 128, 128, 16, 8, 8>(g, s, partial, st);
+    void (*kern)(GemmArgs, Sched, float*, int) =
+        aligned ? simt_f32_async_kernel<4> : simt_f32_async_kernel<1>;
+    const cudaError_t attr =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(F32Smem));
+    if (attr != cudaSuccess) return (int)attr;
+    const int vec_c = (reinterpret_cast<uintptr_t>(g.C) & 15) == 0 && (g.ldc & 3) == 0;
+    prof_mark(st, true);
+    kern<<<s.ctas, 256, sizeof(F32Smem), st>>>(g, s, static_cast<float*>(partial), vec_c);
+    prof_mark(st, false);
+    count_launch();
+    return (int)cudaGetLastError();
   }
   return launch_tile<float, 64, 64, 16, 4, 4>(g, s, partial, st);
 }

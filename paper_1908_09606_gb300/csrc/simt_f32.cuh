@@ -6,7 +6,8 @@
 // (row-major) streamed through STAGES shared-memory buffers by cp.async --
 // the panels of round t + STAGES - 1 are in flight while round t is
 // multiplied (the overlap of Sec. 7.3).  Ragged edges are zero-filled by the
-// copy itself.  Requires 16-byte aligned A and B with lda, ldb multiples of 4.
+// copy itself.  VEC = 4: 16-byte copies (A and B 16-byte aligned, lda and ldb
+// multiples of 4); VEC = 1: 4-byte copies for any pitch.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -30,11 +31,17 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_b
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes)
+               : "memory");
+}
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+template <int VEC>
 __device__ __forceinline__ void f32_tile_async(const float* __restrict__ A, int64_t lda,
                                                const float* __restrict__ B, int64_t ldb,
                                                float* dst, int64_t ld, int64_t m, int64_t n,
@@ -52,33 +59,52 @@ __device__ __forceinline__ void f32_tile_async(const float* __restrict__ A, int6
 
   auto issue = [&](int64_t step, int buf) {
     const int64_t k0 = kbeg + step * F32_BK;
+    if constexpr (VEC == 4) {
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {  // A: 128 rows x 4 chunks of 4 floats
-      const int idx = tid + e * 256;
-      const int r = idx >> 2, c4 = idx & 3;
-      const int64_t gr = row0 + r, gk = k0 + c4 * 4;
-      int bytes = 0;
-      const float* src = A;
-      if (gr < m && gk < kend) {
-        const int64_t left = kend - gk;
-        bytes = left >= 4 ? 16 : (int)left * 4;
-        src = A + gr * lda + gk;
+      for (int e = 0; e < 2; ++e) {  // A: 128 rows x 4 chunks of 4 floats
+        const int idx = tid + e * 256;
+        const int r = idx >> 2, c4 = idx & 3;
+        const int64_t gr = row0 + r, gk = k0 + c4 * 4;
+        int bytes = 0;
+        const float* src = A;
+        if (gr < m && gk < kend) {
+          const int64_t left = kend - gk;
+          bytes = left >= 4 ? 16 : (int)left * 4;
+          src = A + gr * lda + gk;
+        }
+        cp_async16(&sm.As[buf][r][c4 * 4], src, bytes);
       }
-      cp_async16(&sm.As[buf][r][c4 * 4], src, bytes);
-    }
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {  // B: 16 rows x 32 chunks of 4 floats
-      const int idx = tid + e * 256;
-      const int kr = idx >> 5, c4 = idx & 31;
-      const int64_t gk = k0 + kr, gc = col0 + c4 * 4;
-      int bytes = 0;
-      const float* src = B;
-      if (gk < kend && gc < n) {
-        const int64_t left = n - gc;
-        bytes = left >= 4 ? 16 : (int)left * 4;
-        src = B + gk * ldb + gc;
+      for (int e = 0; e < 2; ++e) {  // B: 16 rows x 32 chunks of 4 floats
+        const int idx = tid + e * 256;
+        const int kr = idx >> 5, c4 = idx & 31;
+        const int64_t gk = k0 + kr, gc = col0 + c4 * 4;
+        int bytes = 0;
+        const float* src = B;
+        if (gk < kend && gc < n) {
+          const int64_t left = n - gc;
+          bytes = left >= 4 ? 16 : (int)left * 4;
+          src = B + gk * ldb + gc;
+        }
+        cp_async16(&sm.Bs[buf][kr][c4 * 4], src, bytes);
       }
-      cp_async16(&sm.Bs[buf][kr][c4 * 4], src, bytes);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {  // A: 128 rows x 16 floats
+        const int idx = tid + e * 256;
+        const int r = idx >> 4, c = idx & 15;
+        const int64_t gr = row0 + r, gk = k0 + c;
+        const bool in = gr < m && gk < kend;
+        cp_async4(&sm.As[buf][r][c], in ? A + gr * lda + gk : A, in ? 4 : 0);
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {  // B: 16 rows x 128 floats
+        const int idx = tid + e * 256;
+        const int kr = idx >> 7, c = idx & 127;
+        const int64_t gk = k0 + kr, gc = col0 + c;
+        const bool in = gk < kend && gc < n;
+        cp_async4(&sm.Bs[buf][kr][c], in ? B + gk * ldb + gc : B, in ? 4 : 0);
+      }
     }
   };
 
