@@ -74,10 +74,46 @@ def _alu_peak_tflops(dtype, sms):
     return sms * 2070e6 * lanes * 2 / 1e12
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant kernel, from one single-pass ncu capture of exactly this workload and
+# kernel version; absent entries are reported as null.
+DRAM_TRAFFIC = {}
+
+
+def io_report(m, n, k, dtype, plan, traffic, l2_bytes, sms, smem_per_sm):
+    """Planned L2->SM words against Theorem 1 at one SM's S, and DRAM bytes
+    against Theorem 1 at the chip's fast memory (L2 + all SMs) and against the
+    compulsory bytes."""
+    w_in = {"f64": 8, "f32": 4, "bf16": 2, "f64_emu_bf16": 2}[dtype]
+    w_out = {"f64": 8, "f32": 4, "bf16": 4, "f64_emu_bf16": 8}[dtype]
+    reg_or_tmem = 262144
+    s_chip = (l2_bytes + sms * (smem_per_sm + reg_or_tmem)) / w_in
+    products = 1
+    compulsory = w_in * (m * k + k * n) + w_out * m * n
+    if dtype == "f64_emu_bf16":
+        slices = 6
+        products = slices * (slices + 1) // 2
+        compulsory = w_in * slices * (m * k + k * n) + w_out * m * n
+    thm1_chip_words = products * 2.0 * m * n * k / math.sqrt(s_chip) + m * n
+    out = {"S_sm_words": plan.fast_words, "S_chip_words": s_chip,
+           "l2_to_sm_words_planned": plan.io_words * products,
+           "theorem1_words_at_S_sm": products * (plan.bound_words - m * n) + m * n,
+           "dram_bytes_per_launch": traffic,
+           "theorem1_bytes_at_S_chip": thm1_chip_words * w_in,
+           "compulsory_bytes": compulsory,
+           "products_per_call": products}
+    out["ratio_l2_sm"] = out["l2_to_sm_words_planned"] / out["theorem1_words_at_S_sm"]
+    if traffic:
+        out["ratio_dram_vs_theorem1_chip"] = traffic / out["theorem1_bytes_at_S_chip"]
+        out["ratio_dram_vs_compulsory"] = traffic / compulsory
+    return out
+
+
 def workload_config(name, m, n, k, dtype):
+    w = {"f64": 8, "f32": 4, "bf16": 2, "f64_emu_bf16": 8}[dtype]
     return {"workload": f"{name} m={m} n={n} k={k} {dtype} uniform[-1,1) seed 0",
             "m": m, "n": n, "k": k, "operands": "row-major, device-generated (Philox4x32-10)",
-            "l2": "inputs larger than L2" if (m * k + k * n) * 2 > 130e6 else "inputs fit in L2"}
+            "l2": "inputs larger than L2" if (m * k + k * n) * w > 130e6 else "inputs fit in L2"}
 
 
 def combine_ranks(local_ms, flops_per_step, steps, world, dist=None, device=None):
@@ -495,7 +531,7 @@ def main():
                 "algorithmic": (f"{pairs} slice-pair products x 2mnk bf16 flop per launch"
                                 if dtype == "f64_emu_bf16" else "2mnk flop per launch")}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = DRAM_TRAFFIC.get((args.workload, dtype))
     roof["kernel_ms"] = kern_ms
     roof["kernel_launches_timed"] = kern_n
 
@@ -569,6 +605,8 @@ def main():
                 Cn[:rows, :rows].double().cpu().numpy(), ref)
             errors["tolerance_emulated"] = 1e-12
 
+    props = torch.cuda.get_device_properties(local)
+    smem_sm = getattr(props, "shared_memory_per_multiprocessor", 233472)
     if rank == 0:
         cfg = workload_config(args.workload, m, n, k, dtype)
         cfg["plan"] = {kk: (round(v, 6) if isinstance(v, float) else v)
@@ -582,10 +620,9 @@ def main():
                 "data": "synthetic", "config": cfg, "roofline": roof, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
                 "native_f64": native, "error_vs_oracle": errors,
-                "io": {"l2_to_sm_words_planned": plan.io_words,
-                       "theorem1_words_at_S": plan.bound_words,
-                       "ratio": plan.io_words / plan.bound_words,
-                       "S_words": plan.fast_words}}
+                "io": io_report(m, n, k, dtype, plan, roof["traffic"],
+                                props.L2_cache_size, props.multi_processor_count,
+                                smem_sm)}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

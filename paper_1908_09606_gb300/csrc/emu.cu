@@ -205,6 +205,7 @@ struct EmuArgs {
   int64_t ldc;
   int* status;
   long long wait_limit;
+  unsigned int* lockstep;  // cooperative launches: per-unit progress counter (zeroed), else null
 };
 
 constexpr int NACC = 3;            // accumulator buffers in tensor memory (columns 0..383)
@@ -607,7 +608,33 @@ emu_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
       uint32_t full_cl[E2_STAGES];
 #pragma unroll
       for (int s = 0; s < E2_STAGES; ++s) full_cl[s] = tc::mapa_shared(&full[s], 0);
-      for (int64_t ui = 0; ui < nunits && !*abort_flag; ++ui) {
+      // Lock-step rounds (cooperative launches only): the leader's producer of
+      // every pair announces each issued unit on a global counter and does not
+      // start round r + 1 before all pairs have issued round r, so concurrent
+      // pairs stream the same slice panels through L2.
+      const int npairs = (int)(gridDim.x >> 1);
+      const int64_t total = a.sch.mt * a.sch.nt;
+      const int64_t rounds = a.lockstep ? (total + npairs - 1) / npairs : nunits;
+      for (int64_t ui = 0; ui < rounds && !*abort_flag; ++ui) {
+        if (a.lockstep && leader && ui > 0) {
+          const unsigned int want = (unsigned int)(ui * npairs);
+          const long long t0 = clock64();
+          while (*reinterpret_cast<volatile unsigned int*>(a.lockstep) < want) {
+            if (*abort_flag) break;
+            if (clock64() - t0 > w.limit) {
+              atomicCAS(a.status, 0, (int)COSMA_ERR_TIMEOUT);
+              *abort_flag = 1;
+              break;
+            }
+            __nanosleep(256);
+          }
+          __threadfence();
+          if (*abort_flag) break;
+        }
+        if (ui >= nunits) {
+          if (a.lockstep && leader) atomicAdd(a.lockstep, 1u);
+          continue;
+        }
         const Unit u = unit_of_cta(a.sch, pair, ui);
         const bool ok = emu_walk(
             a, [] { return true; },
@@ -624,6 +651,7 @@ emu_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
               return true;
             },
             [] {});
+        if (a.lockstep && leader) atomicAdd(a.lockstep, 1u);
         if (!ok) break;
       }
       if (*abort_flag && issued) {
@@ -719,13 +747,12 @@ long long emu_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_confi
   const int s = emu_slices(cfg);
   const int64_t kp = rup(k, 8);
   return rup(m * 4, 256) + rup(n * 4, 256) + rup((int64_t)s * m * kp * 2, 256) +
-         rup((int64_t)s * n * kp * 2, 256);
+         rup((int64_t)s * n * kp * 2, 256) + 256;
 }
 
 int launch_emu_bf16(const GemmArgs& g, const Sched& sch, const cosma_plan& p,
                     const cosma_config& cfg, void* ws, long long ws_bytes, int* status,
                     long long wait_limit, cudaStream_t st) {
-  (void)p;
   const int s = emu_slices(cfg), beta = emu_bits(cfg);
   if (s < 2 || s > EMU_MAX_SLICES || beta < 2 || beta > 8 || beta * s - 1 > 62)
     return COSMA_ERR_INVALID_ARG;
@@ -745,6 +772,9 @@ int launch_emu_bf16(const GemmArgs& g, const Sched& sch, const cosma_plan& p,
   __nv_bfloat16* SA = reinterpret_cast<__nv_bfloat16*>(w);
   w += rup((int64_t)s * m * kp * 2, 256);
   __nv_bfloat16* SB = reinterpret_cast<__nv_bfloat16*>(w);
+  w += rup((int64_t)s * n * kp * 2, 256);
+  unsigned int* lockstep_counter =
+      2 * sch.ctas <= p.sms ? reinterpret_cast<unsigned int*>(w) : nullptr;
 
   if (cudaMemsetAsync(eB, 0x80, (size_t)n * 4, st) != cudaSuccess) return (int)cudaGetLastError();
   const double* A = static_cast<const double*>(g.A);
@@ -790,6 +820,7 @@ int launch_emu_bf16(const GemmArgs& g, const Sched& sch, const cosma_plan& p,
   args.ldc = g.ldc;
   args.status = status;
   args.wait_limit = wait_limit;
+  args.lockstep = nullptr;
   // Super-chunk: short enough for the slice panels of a wave of tiles to stay in
   // L2 (2048 k), and for every level sum of a chunk to fit in int32 exactly
   // (at most s pairs x chunk x 2^(2 beta - 2)).
@@ -809,15 +840,29 @@ int launch_emu_bf16(const GemmArgs& g, const Sched& sch, const cosma_plan& p,
     cfgl.blockDim = dim3(320);
     cfgl.dynamicSmemBytes = E2Layout::ALLOC;
     cfgl.stream = st;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = 2;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeCooperative;
+    at[1].val.cooperative = 1;
     cfgl.attrs = at;
-    cfgl.numAttrs = 1;
+    // Lock-step rounds need every pair resident at once: launch cooperatively
+    // (at most one CTA per SM here); without that guarantee run free.
+    cfgl.numAttrs = lockstep_counter ? 2 : 1;
+    args.lockstep = lockstep_counter;
+    if (lockstep_counter &&
+        cudaMemsetAsync(lockstep_counter, 0, sizeof(unsigned int), st) != cudaSuccess)
+      return (int)cudaGetLastError();
     prof_mark(st, true);
     le = cudaLaunchKernelEx(&cfgl, emu_gemm_pair_kernel, ta, tb, args);
+    if (le != cudaSuccess && lockstep_counter) {
+      cudaGetLastError();
+      cfgl.numAttrs = 1;
+      args.lockstep = nullptr;
+      le = cudaLaunchKernelEx(&cfgl, emu_gemm_pair_kernel, ta, tb, args);
+    }
     prof_mark(st, false);
   } else {
     const cudaError_t attr = cudaFuncSetAttribute(
