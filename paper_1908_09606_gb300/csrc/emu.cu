@@ -34,6 +34,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 
 #include "tc_common.cuh"
@@ -773,8 +774,14 @@ int launch_emu_bf16(const GemmArgs& g, const Sched& sch, const cosma_plan& p,
   w += rup((int64_t)s * m * kp * 2, 256);
   __nv_bfloat16* SB = reinterpret_cast<__nv_bfloat16*>(w);
   w += rup((int64_t)s * n * kp * 2, 256);
+  // COSMA_EMU_LOCKSTEP=0 in the environment (read once) runs the pairs free:
+  // profilers that cannot launch cooperative cluster kernels need it.
+  static const bool lockstep_on = [] {
+    const char* e = getenv("COSMA_EMU_LOCKSTEP");
+    return !(e && e[0] == '0');
+  }();
   unsigned int* lockstep_counter =
-      2 * sch.ctas <= p.sms ? reinterpret_cast<unsigned int*>(w) : nullptr;
+      lockstep_on && 2 * sch.ctas <= p.sms ? reinterpret_cast<unsigned int*>(w) : nullptr;
 
   if (cudaMemsetAsync(eB, 0x80, (size_t)n * 4, st) != cudaSuccess) return (int)cudaGetLastError();
   const double* A = static_cast<const double*>(g.A);
