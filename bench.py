@@ -524,7 +524,11 @@ def main():
                 "algorithmic": "2mnk flop per launch"}
     else:
         work = flops * (pairs if dtype == "f64_emu_bf16" else 1)
-        roof = {"kernel": "emu_gemm_kernel" if dtype == "f64_emu_bf16" else "tc_gemm_kernel",
+        if dtype == "f64_emu_bf16":
+            kname = "emu_gemm_pair_kernel" if plan.tile_m == 256 else "emu_gemm_kernel"
+        else:
+            kname = "tc_gemm_kernel"
+        roof = {"kernel": kname,
                 "bound": "tensor", "achieved": work / (kern_ms * 1e-3) / 1e12,
                 "peak": peaks.get("bf16_tflops_sustained", 1700.0), "unit": "TFLOP/s",
                 "peak_source": f"bf16_tflops_sustained of {peak_src} peaks",
@@ -532,6 +536,9 @@ def main():
                                 if dtype == "f64_emu_bf16" else "2mnk flop per launch")}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = DRAM_TRAFFIC.get((args.workload, dtype))
+    if roof["traffic"] is None and roof["kernel"] == "emu_gemm_pair_kernel":
+        roof["traffic_note"] = ("null: ncu cannot launch the cooperative (lock-step) cluster "
+                                "kernel; captures with the pairs free are under profiles/")
     roof["kernel_ms"] = kern_ms
     roof["kernel_launches_timed"] = kern_n
 
