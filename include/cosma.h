@@ -164,6 +164,28 @@ int cosma_gemm_planned(int64_t m, int64_t n, int64_t k, const void* A, int64_t l
  * yet returns COSMA_ERR_NO_WORKSPACE. */
 int cosma_gemm_grouped(int count, const cosma_problem* problems, int dtype, void* stream);
 
+/* C = A B with A, B and C in HOST memory: the call copies the operands in and
+ * the product out itself.  Arguments and dtypes as cosma_gemm, except that A,
+ * B and C must be host pointers (device pointers: COSMA_ERR_INVALID_ARG).
+ * Page-locked memory (cudaHostAlloc / cudaHostRegister) lets the copies
+ * overlap the kernels; pageable memory works outside stream capture but
+ * serialises them.  The call is asynchronous on `stream`: C holds the product
+ * once the stream has reached the call (e.g. cudaStreamSynchronize), and A, B,
+ * C must stay alive (A and B unchanged) until then.
+ * The product is cut into at most 2 x 2 blocks (rows of A x columns of B, each
+ * cut only when it is at least 8192 long); the host-to-device copies of the
+ * next blocks, the kernels of the current block and the device-to-host copy of
+ * the finished C block run concurrently, on two library-owned copy streams
+ * that fork from and join back to `stream` through events (capturable).
+ * Device staging -- the m x k and k x n inputs and the m x n result, rows
+ * padded to a multiple of 8 elements -- is a library-owned buffer grown with
+ * cudaMalloc outside capture; inside capture a call that needs more returns
+ * COSMA_ERR_NO_WORKSPACE.  Calls whose work overlaps on the GPU (other streams
+ * or threads) share that buffer and must be serialised.  The paper has no
+ * counterpart: its operands start in the processors' memories. */
+int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void* B,
+                    int64_t ldb, void* C, int64_t ldc, int dtype, void* stream);
+
 /* ---- allocation-free variant ------------------------------------------ */
 
 /* Size of the device array cosma_gemm_splitk_static uses for its partial sums

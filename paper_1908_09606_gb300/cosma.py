@@ -70,6 +70,7 @@ SIGNATURES = [
     ("cosma_gemm_planned", _INT, [_I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _INT,
                                   ctypes.POINTER(cosma_plan), _VP]),
     ("cosma_gemm_grouped", _INT, [_INT, ctypes.POINTER(cosma_problem), _INT, _VP]),
+    ("cosma_gemm_host", _INT, [_I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _INT, _VP]),
     ("cosma_plan_query", _INT, [_I64, _I64, _I64, _INT, _INT, ctypes.POINTER(cosma_plan)]),
     ("cosma_plan_units", _LL, [_I64, _I64, _I64, ctypes.POINTER(cosma_plan),
                                ctypes.POINTER(ctypes.c_int64), _LL]),
@@ -164,6 +165,10 @@ def cosma_gemm_planned(m, n, k, A, lda, B, ldb, C, ldc, dtype, plan, stream=0):
 def cosma_gemm_grouped(problems, dtype, stream=0):
     arr = (cosma_problem * len(problems))(*problems)
     return load().cosma_gemm_grouped(len(problems), arr, dtype, stream)
+
+
+def cosma_gemm_host(m, n, k, A, lda, B, ldb, C, ldc, dtype, stream=0):
+    return load().cosma_gemm_host(m, n, k, A, lda, B, ldb, C, ldc, dtype, stream)
 
 
 def cosma_gemm_splitk_static(m, n, k, A, lda, B, ldb, C, ldc, dtype, pk, stream=0):
@@ -294,6 +299,22 @@ def gemm(A, B, C, dtype, stream=None, plan=None):
         rc = cosma_gemm_planned(m, n, k, A.data_ptr(), lda, B.data_ptr(), ldb, C.data_ptr(),
                                 ldc, dtype, plan, s)
     return _check(rc, "cosma_gemm")
+
+
+def gemm_host(A, B, C, dtype, stream=None):
+    """C = A B for row-major torch CPU tensors (page-locked for overlap), C
+    preallocated; asynchronous on `stream` (synchronise before reading C)."""
+    m, k = A.shape
+    k2, n = B.shape
+    assert k == k2 and tuple(C.shape) == (m, n)
+    for t in (A, B, C):
+        assert not t.is_cuda and t.stride(1) == 1, "row-major CPU tensors with unit column stride"
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    s = _stream_handle(stream)
+    lda, ldb, ldc = max(A.stride(0), 1), max(B.stride(0), 1), max(C.stride(0), 1)
+    rc = cosma_gemm_host(m, n, k, A.data_ptr(), lda, B.data_ptr(), ldb, C.data_ptr(), ldc, dtype, s)
+    return _check(rc, "cosma_gemm_host")
 
 
 def gemm_grouped(As, Bs, Cs, dtype, stream=None):

@@ -13,15 +13,12 @@ namespace cosma {
 
 int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void* ws,
                    long long ws_bytes, int* status, long long wait_limit, cudaStream_t st);
-int launch_emu_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, const cosma_config& cfg,
-                    void* ws, long long ws_bytes, int* status, long long wait_limit,
-                    cudaStream_t st);
-long long emu_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_config& cfg);
 long long tc_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_plan& p, bool pack_a);
 int grouped_gemm(int count, const cosma_problem* problems, int dtype, const DeviceInfo& dev,
                  void* ws, long long ws_bytes, int* status, long long wait_limit, cudaStream_t st,
                  long long* needed, int requested_tile);
 void grouped_release(int dev);
+void host_release(int dev);
 
 static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -225,7 +222,7 @@ int run(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void*
       err = launch_tc_bf16(g, sc, p, ws, have, s->d_status, wl, st);
       break;
     case COSMA_KERNEL_EMU_BF16:
-      err = launch_emu_bf16(g, sc, p, g_cfg, ws, have, s->d_status, wl, st);
+      err = launch_emu_bf16(g, p, g_cfg, ws, have, s->d_status, wl, st);
       break;
     default:
       return COSMA_ERR_INVALID_ARG;
@@ -252,6 +249,23 @@ int current_info(DeviceInfo* out) {
   if (!s) return rc;
   *out = s->info;
   return COSMA_OK;
+}
+
+int lib_context(LibContext* out) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  int rc;
+  DeviceState* s = state(&rc);
+  if (!s) return rc;
+  out->info = s->info;
+  out->cfg = g_cfg;
+  out->status = s->d_status;
+  out->wait_limit = g_cfg.wait_limit > 0 ? g_cfg.wait_limit : kDefaultWaitLimit;
+  return COSMA_OK;
+}
+
+int run_device(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void* B,
+               int64_t ldb, void* C, int64_t ldc, int dtype, void* stream) {
+  return run(m, n, k, A, lda, B, ldb, C, ldc, dtype, nullptr, stream);
 }
 
 }  // namespace cosma
@@ -298,9 +312,10 @@ int cosma_set_workspace(void* dptr, size_t bytes) {
 }
 
 void cosma_finalize(void) {
-  std::lock_guard<std::mutex> lock(g_mu);
   const int d = current_device();
   if (d < 0) return;
+  host_release(d);  // takes its own lock, never while holding g_mu
+  std::lock_guard<std::mutex> lock(g_mu);
   DeviceState& s = g_dev[d];
   if (!s.ready) return;
   cudaDeviceSynchronize();

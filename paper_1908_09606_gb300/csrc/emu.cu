@@ -138,10 +138,11 @@ __global__ void col_exp_kernel(const double* __restrict__ B, int64_t k, int64_t 
   if (e != kExpNone) atomicMax(&eB[j], e);
 }
 
-// Slices of A: S[q][i][t] (ld kp), one thread per element.
+// Slices of A: S[q][i][t] (ld kp, slice_rows rows between slices), one thread
+// per element.
 __global__ void split_a_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda,
                                const int* __restrict__ eA, __nv_bfloat16* __restrict__ S,
-                               int64_t kp, int s, int beta) {
+                               int64_t kp, int64_t slice_rows, int s, int beta) {
   const int L = beta * s - 1;
   const int64_t total = m * k;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -151,14 +152,15 @@ __global__ void split_a_kernel(const double* __restrict__ A, int64_t m, int64_t 
     split_digits(A[i * lda + t], eA[i], L, beta, s, d);
 #pragma unroll
     for (int q = 0; q < EMU_MAX_SLICES; ++q)
-      if (q < s) S[((int64_t)q * m + i) * kp + t] = __float2bfloat16_rn((float)d[q]);
+      if (q < s) S[((int64_t)q * slice_rows + i) * kp + t] = __float2bfloat16_rn((float)d[q]);
   }
 }
 
-// Slices of B, transposed to K-major: S[q][j][t] (ld kp).  32 x 32 tiles.
+// Slices of B, transposed to K-major: S[q][j][t] (ld kp, slice_rows rows
+// between slices).  32 x 32 tiles.
 __global__ void split_b_kernel(const double* __restrict__ B, int64_t k, int64_t n, int64_t ldb,
                                const int* __restrict__ eB, __nv_bfloat16* __restrict__ S,
-                               int64_t kp, int s, int beta) {
+                               int64_t kp, int64_t slice_rows, int s, int beta) {
   __shared__ __nv_bfloat16 tile[EMU_MAX_SLICES][32][34];
   const int L = beta * s - 1;
   const int64_t t0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
@@ -177,7 +179,7 @@ __global__ void split_b_kernel(const double* __restrict__ B, int64_t k, int64_t 
   for (int r = threadIdx.y; r < 32; r += 8) {
     const int64_t j = j0 + r, t = t0 + threadIdx.x;
     if (j < n && t < k)
-      for (int q = 0; q < s; ++q) S[((int64_t)q * n + j) * kp + t] = tile[q][r][threadIdx.x];
+      for (int q = 0; q < s; ++q) S[((int64_t)q * slice_rows + j) * kp + t] = tile[q][r][threadIdx.x];
   }
 }
 
@@ -719,7 +721,7 @@ emu_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
 }
 
 int encode_tmap_slices(CUtensorMap* map, const void* base, int64_t rows, int64_t k, int64_t kp,
-                       int s, int box_rows = EBM) {
+                       int s, int64_t slice_rows, int box_rows) {
   static std::once_flag once;
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   std::call_once(once, [] {
@@ -732,7 +734,7 @@ int encode_tmap_slices(CUtensorMap* map, const void* base, int64_t rows, int64_t
   });
   if (!fn) return COSMA_ERR_CUDA;
   cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)s};
-  cuuint64_t strides[2] = {(cuuint64_t)(kp * 2), (cuuint64_t)(rows * kp * 2)};
+  cuuint64_t strides[2] = {(cuuint64_t)(kp * 2), (cuuint64_t)(slice_rows * kp * 2)};
   cuuint32_t box[3] = {(cuuint32_t)EBK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims,
@@ -751,67 +753,88 @@ long long emu_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_confi
          rup((int64_t)s * n * kp * 2, 256) + 256;
 }
 
-int launch_emu_bf16(const GemmArgs& g, const Sched& sch, const cosma_plan& p,
-                    const cosma_config& cfg, void* ws, long long ws_bytes, int* status,
-                    long long wait_limit, cudaStream_t st) {
+EmuWorkspace emu_carve(void* ws, int64_t m, int64_t n, int64_t k, const cosma_config& cfg) {
+  const int s = emu_slices(cfg);
+  const int64_t kp = rup(k, 8);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  EmuWorkspace e;
+  e.eA = reinterpret_cast<int*>(w);
+  w += rup(m * 4, 256);
+  e.eB = reinterpret_cast<int*>(w);
+  w += rup(n * 4, 256);
+  e.SA = w;
+  w += rup((int64_t)s * m * kp * 2, 256);
+  e.SB = w;
+  w += rup((int64_t)s * n * kp * 2, 256);
+  e.lockstep = reinterpret_cast<unsigned int*>(w);
+  e.kp = kp;
+  return e;
+}
+
+int emu_check_config(const cosma_config& cfg) {
   const int s = emu_slices(cfg), beta = emu_bits(cfg);
   if (s < 2 || s > EMU_MAX_SLICES || beta < 2 || beta > 8 || beta * s - 1 > 62)
     return COSMA_ERR_INVALID_ARG;
+  return COSMA_OK;
+}
+
+int emu_prepare_a(const double* A, int64_t m, int64_t k, int64_t lda, int* eA, void* SA,
+                  int64_t slice_rows, int* status, const cosma_config& cfg, cudaStream_t st) {
+  const int s = emu_slices(cfg), beta = emu_bits(cfg);
+  const int64_t kp = rup(k, 8);
+  if (m <= 0) return COSMA_OK;
+  const int64_t rb = m < 65535LL * 16 ? m : 65535LL * 16;
+  row_exp_kernel<<<(unsigned)rb, 256, 0, st>>>(A, m, k, lda, eA, status);
+  count_launch();
+  int64_t blocks = (m * k + 255) / 256;
+  if (blocks > 152LL * 64) blocks = 152LL * 64;
+  split_a_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, m, k, lda, eA,
+                                                   static_cast<__nv_bfloat16*>(SA), kp,
+                                                   slice_rows, s, beta);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+int emu_prepare_b(const double* B, int64_t k, int64_t n, int64_t ldb, int* eB, void* SB,
+                  int64_t slice_rows, int* status, const cosma_config& cfg, cudaStream_t st) {
+  const int s = emu_slices(cfg), beta = emu_bits(cfg);
+  const int64_t kp = rup(k, 8);
+  if (n <= 0) return COSMA_OK;
+  if ((k + 31) / 32 > 65535) return COSMA_ERR_UNSUPPORTED;
+  if (cudaMemsetAsync(eB, 0x80, (size_t)n * 4, st) != cudaSuccess) return (int)cudaGetLastError();
+  dim3 g1((unsigned)((n + 255) / 256), (unsigned)((k + 255) / 256));
+  col_exp_kernel<<<g1, 256, 0, st>>>(B, k, n, ldb, eB, status);
+  count_launch();
+  dim3 g2((unsigned)((n + 31) / 32), (unsigned)((k + 31) / 32));
+  split_b_kernel<<<g2, dim3(32, 8), 0, st>>>(B, k, n, ldb, eB, static_cast<__nv_bfloat16*>(SB),
+                                             kp, slice_rows, s, beta);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cosma_config& cfg,
+                 const int* eA, const void* SA, int64_t a_slice_rows, const int* eB,
+                 const void* SB, int64_t b_slice_rows, double* C, int64_t ldc,
+                 unsigned int* lockstep, int* status, long long wait_limit, cudaStream_t st) {
+  const int s = emu_slices(cfg), beta = emu_bits(cfg);
+  const Sched sch = sched_from_plan(m, n, k, p);
   const bool pairs = sch.tile_m == 2 * EBM;
   if ((sch.tile_m != EBM && !pairs) || sch.tile_n != EBN || sch.k_block != EBK || sch.pk != 1)
     return COSMA_ERR_INVALID_ARG;
-  const int64_t m = g.m, n = g.n, k = g.k, kp = rup(k, 8);
-  if (emu_workspace_bytes(m, n, k, cfg) > ws_bytes) return COSMA_ERR_NO_WORKSPACE;
-  if ((reinterpret_cast<uintptr_t>(g.A) & 7) || (reinterpret_cast<uintptr_t>(g.B) & 7) ||
-      (reinterpret_cast<uintptr_t>(g.C) & 7))
-    return COSMA_ERR_INVALID_ARG;
-  uint8_t* w = static_cast<uint8_t*>(ws);
-  int* eA = reinterpret_cast<int*>(w);
-  w += rup(m * 4, 256);
-  int* eB = reinterpret_cast<int*>(w);
-  w += rup(n * 4, 256);
-  __nv_bfloat16* SA = reinterpret_cast<__nv_bfloat16*>(w);
-  w += rup((int64_t)s * m * kp * 2, 256);
-  __nv_bfloat16* SB = reinterpret_cast<__nv_bfloat16*>(w);
-  w += rup((int64_t)s * n * kp * 2, 256);
+  if (reinterpret_cast<uintptr_t>(C) & 7) return COSMA_ERR_INVALID_ARG;
+  const int64_t kp = rup(k, 8);
   // COSMA_EMU_LOCKSTEP=0 in the environment (read once) runs the pairs free:
   // profilers that cannot launch cooperative cluster kernels need it.
   static const bool lockstep_on = [] {
     const char* e = getenv("COSMA_EMU_LOCKSTEP");
     return !(e && e[0] == '0');
   }();
-  unsigned int* lockstep_counter =
-      lockstep_on && 2 * sch.ctas <= p.sms ? reinterpret_cast<unsigned int*>(w) : nullptr;
-
-  if (cudaMemsetAsync(eB, 0x80, (size_t)n * 4, st) != cudaSuccess) return (int)cudaGetLastError();
-  const double* A = static_cast<const double*>(g.A);
-  const double* B = static_cast<const double*>(g.B);
-  {
-    const int64_t blocks = m < 65535LL * 16 ? m : 65535LL * 16;
-    row_exp_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, m, k, g.lda, eA, status);
-    count_launch();
-    dim3 grid((unsigned)((n + 255) / 256), (unsigned)((k + 255) / 256));
-    if (grid.y > 65535) return COSMA_ERR_UNSUPPORTED;
-    col_exp_kernel<<<grid, 256, 0, st>>>(B, k, n, g.ldb, eB, status);
-    count_launch();
-  }
-  {
-    int64_t blocks = (m * k + 255) / 256;
-    if (blocks > 152LL * 64) blocks = 152LL * 64;
-    split_a_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, m, k, g.lda, eA, SA, kp, s, beta);
-    count_launch();
-    dim3 grid((unsigned)((n + 31) / 32), (unsigned)((k + 31) / 32));
-    if (grid.y > 65535) return COSMA_ERR_UNSUPPORTED;
-    split_b_kernel<<<grid, dim3(32, 8), 0, st>>>(B, k, n, g.ldb, eB, SB, kp, s, beta);
-    count_launch();
-  }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return (int)e;
+  unsigned int* lockstep_counter = lockstep_on && 2 * sch.ctas <= p.sms ? lockstep : nullptr;
 
   CUtensorMap ta, tb;
-  int rc = encode_tmap_slices(&ta, SA, m, k, kp, s);
+  int rc = encode_tmap_slices(&ta, SA, m, k, kp, s, a_slice_rows, EBM);
   if (rc != COSMA_OK) return rc;
-  rc = encode_tmap_slices(&tb, SB, n, k, kp, s, pairs ? EBN / 2 : EBN);
+  rc = encode_tmap_slices(&tb, SB, n, k, kp, s, b_slice_rows, pairs ? EBN / 2 : EBN);
   if (rc != COSMA_OK) return rc;
 
   EmuArgs args;
@@ -823,8 +846,8 @@ int launch_emu_bf16(const GemmArgs& g, const Sched& sch, const cosma_plan& p,
   if (args.group_kb < 1) args.group_kb = 1;
   args.eA = eA;
   args.eB = eB;
-  args.C = static_cast<double*>(g.C);
-  args.ldc = g.ldc;
+  args.C = C;
+  args.ldc = ldc;
   args.status = status;
   args.wait_limit = wait_limit;
   args.lockstep = nullptr;
@@ -883,6 +906,25 @@ int launch_emu_bf16(const GemmArgs& g, const Sched& sch, const cosma_plan& p,
   if (le != cudaSuccess) return (int)le;
   count_launch();
   return (int)cudaGetLastError();
+}
+
+int launch_emu_bf16(const GemmArgs& g, const cosma_plan& p, const cosma_config& cfg, void* ws,
+                    long long ws_bytes, int* status, long long wait_limit, cudaStream_t st) {
+  int rc = emu_check_config(cfg);
+  if (rc != COSMA_OK) return rc;
+  const int64_t m = g.m, n = g.n, k = g.k;
+  if (emu_workspace_bytes(m, n, k, cfg) > ws_bytes) return COSMA_ERR_NO_WORKSPACE;
+  if ((k + 31) / 32 > 65535) return COSMA_ERR_UNSUPPORTED;
+  if ((reinterpret_cast<uintptr_t>(g.A) & 7) || (reinterpret_cast<uintptr_t>(g.B) & 7) ||
+      (reinterpret_cast<uintptr_t>(g.C) & 7))
+    return COSMA_ERR_INVALID_ARG;
+  const EmuWorkspace e = emu_carve(ws, m, n, k, cfg);
+  rc = emu_prepare_a(static_cast<const double*>(g.A), m, k, g.lda, e.eA, e.SA, m, status, cfg, st);
+  if (rc != 0) return rc;
+  rc = emu_prepare_b(static_cast<const double*>(g.B), k, n, g.ldb, e.eB, e.SB, n, status, cfg, st);
+  if (rc != 0) return rc;
+  return emu_multiply(m, n, k, p, cfg, e.eA, e.SA, m, e.eB, e.SB, n, static_cast<double*>(g.C),
+                      g.ldc, e.lockstep, status, wait_limit, st);
 }
 
 }  // namespace cosma

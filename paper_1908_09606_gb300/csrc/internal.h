@@ -53,6 +53,17 @@ int mlp_adam(int n, float* params, const float* grad, float* m, float* v, int st
 int lib_scratch(long long bytes, cudaStream_t st, void** out);
 // Device info of the current device (api.cu).
 int current_info(DeviceInfo* out);
+// What a launcher outside api.cu needs of the current device (api.cu).
+struct LibContext {
+  DeviceInfo info;
+  cosma_config cfg;
+  int* status;           // device status word
+  long long wait_limit;  // clock cycles before a device wait gives up
+};
+int lib_context(LibContext* out);
+// cosma_gemm on device operands, planned by the configured selector (api.cu).
+int run_device(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void* B,
+               int64_t ldb, void* C, int64_t ldc, int dtype, void* stream);
 
 // Kernel launchers (return cudaError_t values).
 struct GemmArgs {
@@ -64,6 +75,32 @@ struct GemmArgs {
 int launch_simt(int dtype, const GemmArgs& g, const Sched& s, void* partial, int* status,
                 cudaStream_t st);
 int launch_reduce(int dtype, const GemmArgs& g, int pk, const void* partial, cudaStream_t st);
+
+// Emulated FP64 (emu.cu): workspace layout and the three phases of a product.
+struct EmuWorkspace {
+  int* eA;                 // row exponents of A [m]
+  int* eB;                 // column exponents of B [n]
+  void* SA;                // bf16 slices of A [s][m][kp]
+  void* SB;                // bf16 slices of B^T [s][n][kp]
+  unsigned int* lockstep;  // one counter for lock-step rounds
+  int64_t kp;              // k rounded up to 8
+};
+long long emu_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_config& cfg);
+EmuWorkspace emu_carve(void* ws, int64_t m, int64_t n, int64_t k, const cosma_config& cfg);
+int emu_check_config(const cosma_config& cfg);
+// Exponents and slices of rows [0, m) of A into eA[0..m) and SA (slice_rows
+// rows between slices); of columns [0, n) of B likewise.
+int emu_prepare_a(const double* A, int64_t m, int64_t k, int64_t lda, int* eA, void* SA,
+                  int64_t slice_rows, int* status, const cosma_config& cfg, cudaStream_t st);
+int emu_prepare_b(const double* B, int64_t k, int64_t n, int64_t ldb, int* eB, void* SB,
+                  int64_t slice_rows, int* status, const cosma_config& cfg, cudaStream_t st);
+// C[m x n] from prepared slices, under plan p (an F64_EMU_BF16 plan for m x n x k).
+int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cosma_config& cfg,
+                 const int* eA, const void* SA, int64_t a_slice_rows, const int* eB,
+                 const void* SB, int64_t b_slice_rows, double* C, int64_t ldc,
+                 unsigned int* lockstep, int* status, long long wait_limit, cudaStream_t st);
+int launch_emu_bf16(const GemmArgs& g, const cosma_plan& p, const cosma_config& cfg, void* ws,
+                    long long ws_bytes, int* status, long long wait_limit, cudaStream_t st);
 
 // Launch accounting (api.cu): every kernel launch the library makes calls this.
 void count_launch(int n = 1);

@@ -67,6 +67,16 @@ def test_rejects_bad_arguments_without_launch(lib):
     assert lib.cosma_gemm_grouped([], lib.COSMA_F64) == lib.COSMA_ERR_UNSUPPORTED
 
 
+def test_host_entry_rejects_bad_arguments(lib):
+    bad = lib.COSMA_ERR_INVALID_ARG
+    assert lib.cosma_gemm_host(-1, 4, 4, 0, 4, 0, 4, 0, 4, lib.COSMA_F64) == bad
+    assert lib.cosma_gemm_host(4, 4, 4, 0, 3, 0, 4, 0, 4, lib.COSMA_F64) == bad   # lda < k
+    assert lib.cosma_gemm_host(4, 4, 4, 0, 4, 0, 4, 0, 2, lib.COSMA_F64) == bad   # ldc < n
+    assert lib.cosma_gemm_host(4, 4, 4, 0, 4, 0, 4, 0, 4, lib.COSMA_F64) == bad   # null C
+    assert lib.cosma_gemm_host(4, 4, 4, 8, 4, 8, 4, 8, 4, 9) == bad                 # dtype
+    assert lib.cosma_gemm_host(0, 4, 4, 0, 4, 0, 4, 0, 4, lib.COSMA_F64) == lib.COSMA_OK
+
+
 def test_init_validates_config(lib):
     assert lib.cosma_init(delta=1.5) == lib.COSMA_ERR_INVALID_ARG
     assert lib.cosma_init(selector=7) == lib.COSMA_ERR_INVALID_ARG
