@@ -13,22 +13,25 @@
 //           COSMA_ERR_NONFINITE.
 //  K-EMU    C_ij ~ 2^(sigma_i + tau_j - 2L) sum_{q,r} 2^(beta(2s - q - r)) (D^A_q D^B_r)_ij
 //           over the truncated triangle q + r <= s + 1.  Pairs of one level
-//           l = q + r share a scale, so a level is one product with an
-//           extended k loop over its l-1 pairs.  Digit products are at most
-//           2^(2 beta - 2), so an f32 tensor-memory accumulator is exact for
-//           2^24 / 2^(2 beta - 2) products; the k loop is cut into groups of
-//           that size and each group's exact integer sum is drained by the
-//           epilogue warps into an exact float-float level sum kept in tensor
-//           memory.  Two accumulators alternate so the MMAs of the next
-//           group overlap the drain of this one.
-//  K-RECOMB At the end of each level its exact sum is merged into a
-//           float-float running total (high parts in shared memory, low parts
-//           in registers: ten warps leave at most 168 registers a thread) (Horner, smallest
-//           level first: T = T 2^-beta + L_l); after level 2 the tile is
-//           converted to FP64 and scaled by 2^(sigma_i + tau_j + 2 - 2 beta).
+//           l = q + r share a scale.  Digit products are at most 2^(2 beta - 2),
+//           so an f32 tensor-memory accumulator is exact for 2^24 / 2^(2 beta - 2)
+//           products; the k loop is cut into groups of that size, and each
+//           group's exact integer sum is drained by the epilogue warps into an
+//           int32 level sum held in registers.  k is walked in super-chunks of
+//           2048 (all levels per chunk), so a level sum stays below 2^31 for any
+//           k and the slice panels a wave of tiles touches stay in L2.  Three
+//           accumulator buffers let the MMAs of the next groups overlap a drain.
+//  K-RECOMB At the end of each (chunk, level) the exact level sum joins a
+//           float-float running total T += 2^(-beta (l - 2)) L (high parts in
+//           shared memory, low parts in tensor memory); after the last chunk
+//           the tile is converted to FP64 and scaled by
+//           2^(sigma_i + tau_j + 2 - 2 beta).
 //
-// The C tile (128 x 128) is the paper's resident a x b tile (Listing 1); the
-// slices of A and B stream through a 5-stage TMA ring exactly as in K-BF16.
+// The C tile (128 x 128 on one SM, or 256 x 128 on a CTA pair with
+// tcgen05.mma.cta_group::2) is the paper's resident a x b tile (Listing 1); the
+// slices of A and B stream through a TMA ring (5 stages single, 6 per CTA of a
+// pair).  Pairs launched cooperatively advance in lock-step rounds (bounded
+// waits) so concurrent tiles read the same slice panels from L2.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
