@@ -376,11 +376,11 @@ __global__ void __launch_bounds__(256) grouped_f32_kernel(GArgs a) {
     float* C = static_cast<float*>(g.C);
     const int64_t r0 = (int64_t)u.tile_row * 128, c0 = (int64_t)u.tile_col * 128;
     if (g.f32_async)
-      f32_tile_async<4>(A, g.lda, B, g.ldb, C, g.ldc, g.m, g.n, r0, c0, 0, g.k, g.vec_ok != 0,
-                        *reinterpret_cast<F32Smem*>(gsm));
+      f32_tile<128, 4>(A, g.lda, B, g.ldb, C, g.ldc, g.m, g.n, r0, c0, 0, g.k, g.vec_ok != 0,
+                       *reinterpret_cast<F32Smem<128>*>(gsm));
     else
-      f32_tile_async<1>(A, g.lda, B, g.ldb, C, g.ldc, g.m, g.n, r0, c0, 0, g.k, g.vec_ok != 0,
-                        *reinterpret_cast<F32Smem*>(gsm));
+      f32_tile<128, 1>(A, g.lda, B, g.ldb, C, g.ldc, g.m, g.n, r0, c0, 0, g.k, g.vec_ok != 0,
+                       *reinterpret_cast<F32Smem<128>*>(gsm));
   }
 }
 
@@ -639,10 +639,10 @@ int grouped_gemm(int count, const cosma_problem* problems, int dtype, const Devi
   }
   if (tile == 128) {
     static cudaError_t attr = cudaFuncSetAttribute(
-        grouped_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(F32Smem));
+        grouped_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(F32Smem<128>));
     if (attr != cudaSuccess) return (int)attr;
     prof_mark(st, true);
-    grouped_f32_kernel<<<t->ctas, 256, sizeof(F32Smem), st>>>(args);
+    grouped_f32_kernel<<<t->ctas, 256, sizeof(F32Smem<128>), st>>>(args);
   } else {
     prof_mark(st, true);
     grouped_simt_kernel<64, 16, 4><<<t->ctas, 256, 0, st>>>(args);

@@ -30,6 +30,7 @@ const double kLaunchS = 4e-6;         // one kernel launch + tail
 
 struct TileChoice {
   int tile_m, tile_n, k_block, stages;
+  double eff = 1.0;  // main-loop efficiency of this tile relative to its family's
 };
 
 // Tiles each kernel family implements.
@@ -38,8 +39,8 @@ int tiles_for(int kernel, TileChoice* out) {
     case COSMA_KERNEL_SIMT_F64:
       out[0] = {128, 128, 8, 2}; out[1] = {64, 64, 8, 2};
       return 2;
-    case COSMA_KERNEL_SIMT_F32:
-      out[0] = {128, 128, 16, 2}; out[1] = {64, 64, 16, 2};
+    case COSMA_KERNEL_SIMT_F32:  // 256 x 128 runs 512 threads at a 128-register cap
+      out[0] = {128, 128, 16, 4, 1.0}; out[1] = {256, 128, 16, 4, 0.95};
       return 2;
     case COSMA_KERNEL_TC_BF16:
       out[0] = {128, 256, 64, 4}; out[1] = {128, 128, 64, 6};
@@ -63,7 +64,7 @@ KernelDesc desc_for(int dtype, const DeviceInfo& dev) {
       break;
     case COSMA_F32:
       d.kernel = COSMA_KERNEL_SIMT_F32; d.w_in = 4; d.w_acc = 4; d.w_out = 4;
-      d.fast_bytes = smem + rf; d.flops_per_clk_sm = 256.0; d.efficiency = 0.7;
+      d.fast_bytes = smem + rf; d.flops_per_clk_sm = 256.0; d.efficiency = 0.6;
       break;
     case COSMA_BF16:
       d.kernel = COSMA_KERNEL_TC_BF16; d.w_in = 2; d.w_acc = 4; d.w_out = 4;
@@ -154,7 +155,7 @@ Sched sched_from_plan(int64_t m, int64_t n, int64_t k, const cosma_plan& p) {
 static double estimate(const KernelDesc& d, int64_t m, int64_t n, const TileChoice& t,
                        int64_t max_units, int64_t kblocks_per_unit, int pk) {
   const double flops_kb = 2.0 * t.tile_m * t.tile_n * t.k_block;
-  const double t_compute = flops_kb / (d.flops_per_clk_sm * d.efficiency * kClockHz);
+  const double t_compute = flops_kb / (d.flops_per_clk_sm * d.efficiency * t.eff * kClockHz);
   const double t_io = (double)(t.tile_m + t.tile_n) * t.k_block * d.w_in /
                       (kL2BytesPerClkSm * kClockHz);
   const double t_kb = std::max(t_compute, t_io);

@@ -4,10 +4,11 @@
 // Each CTA is one processor of the schedule: it walks the work units of its
 // local domain (schedule.h).  For one unit the tile_m x tile_n C tile stays in
 // registers (8 x 8 or 4 x 4 per thread) while A-column and B-row panels of
-// k_block outer products stream through a double-buffered shared-memory ring
-// -- the rank-1-update order of Listing 1 with a k_block-deep step (Alg. 1's
-// step size s).  The next panel pair is fetched into registers while the
-// current one is multiplied (the overlap of Sec. 7.3).
+// k_block outer products stream through a shared-memory ring -- the
+// rank-1-update order of Listing 1 with a k_block-deep step (Alg. 1's step
+// size s).  K-F64 fetches the next panel pair into registers while the current
+// one is multiplied; K-F32 keeps four panels in flight with cp.async
+// (simt_f32.cuh); both overlap loads with multiplies as in Sec. 7.3.
 //
 // GB300 has a narrow FP64 pipe, so K-F64 is bound by FP64 FMA issue; its
 // global loads are plain (any alignment / leading dimension is accepted).
@@ -45,12 +46,12 @@ simt_gemm_kernel(GemmArgs g, Sched s, T* partial) {
   }
 }
 
-// K-F32 fast path: the cp.async multi-stage tile (simt_f32.cuh).
-template <int VEC>
-__global__ void __launch_bounds__(256)
-simt_f32_async_kernel(GemmArgs g, Sched s, float* partial, int vec_c) {
+// K-F32: the cp.async multi-stage tile of simt_f32.cuh (BM x 128, 2 BM threads).
+template <int BM, int VEC>
+__global__ void __launch_bounds__(f32_threads<BM>(), 1)
+simt_f32_kernel(GemmArgs g, Sched s, float* partial, int vec_c) {
   extern __shared__ __align__(16) uint8_t f32_smem[];
-  F32Smem& sm = *reinterpret_cast<F32Smem*>(f32_smem);
+  F32Smem<BM>& sm = *reinterpret_cast<F32Smem<BM>*>(f32_smem);
   const float* A = static_cast<const float*>(g.A);
   const float* B = static_cast<const float*>(g.B);
   const int cta = blockIdx.x;
@@ -69,8 +70,9 @@ simt_f32_async_kernel(GemmArgs g, Sched s, float* partial, int vec_c) {
       ld = g.ldc;
       vec = vec_c != 0;
     }
-    f32_tile_async<VEC>(A, g.lda, B, g.ldb, dst, ld, g.m, g.n, u.tile_row * F32_BM, u.tile_col * F32_BN,
-                   u.kb0 * (int64_t)s.k_block, min(u.kb1 * (int64_t)s.k_block, g.k), vec, sm);
+    f32_tile<BM, VEC>(A, g.lda, B, g.ldb, dst, ld, g.m, g.n, u.tile_row * BM,
+                      u.tile_col * F32_BN, u.kb0 * (int64_t)s.k_block,
+                      min(u.kb1 * (int64_t)s.k_block, g.k), vec, sm);
   }
 }
 
@@ -108,22 +110,30 @@ int launch_simt(int dtype, const GemmArgs& g, const Sched& s, void* partial, int
     if (s.tile_m == 128) return launch_tile<double, 128, 128, 8, 8, 8>(g, s, partial, st);
     return launch_tile<double, 64, 64, 8, 4, 4>(g, s, partial, st);
   }
-  if (s.tile_m == 128 && s.k_block % F32_BK == 0) {
-    const bool aligned = (reinterpret_cast<uintptr_t>(g.A) & 15) == 0 && (g.lda & 3) == 0 &&
-                         (reinterpret_cast<uintptr_t>(g.B) & 15) == 0 && (g.ldb & 3) == 0;
-    void (*kern)(GemmArgs, Sched, float*, int) =
-        aligned ? simt_f32_async_kernel<4> : simt_f32_async_kernel<1>;
-    const cudaError_t attr =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(F32Smem));
-    if (attr != cudaSuccess) return (int)attr;
-    const int vec_c = (reinterpret_cast<uintptr_t>(g.C) & 15) == 0 && (g.ldc & 3) == 0;
-    prof_mark(st, true);
-    kern<<<s.ctas, 256, sizeof(F32Smem), st>>>(g, s, static_cast<float*>(partial), vec_c);
-    prof_mark(st, false);
-    count_launch();
-    return (int)cudaGetLastError();
+  if ((s.tile_m != 128 && s.tile_m != 256) || s.tile_n != F32_BN || s.k_block % F32_BK)
+    return COSMA_ERR_INVALID_ARG;
+  const bool vec_ab = (reinterpret_cast<uintptr_t>(g.A) & 15) == 0 && (g.lda & 3) == 0 &&
+                     (reinterpret_cast<uintptr_t>(g.B) & 15) == 0 && (g.ldb & 3) == 0;
+  const int vec_c = (reinterpret_cast<uintptr_t>(g.C) & 15) == 0 && (g.ldc & 3) == 0;
+  void (*kern)(GemmArgs, Sched, float*, int);
+  int threads, smem;
+  if (s.tile_m == 256) {
+    kern = vec_ab ? simt_f32_kernel<256, 4> : simt_f32_kernel<256, 1>;
+    threads = f32_threads<256>();
+    smem = (int)sizeof(F32Smem<256>);
+  } else {
+    kern = vec_ab ? simt_f32_kernel<128, 4> : simt_f32_kernel<128, 1>;
+    threads = f32_threads<128>();
+    smem = (int)sizeof(F32Smem<128>);
   }
-  return launch_tile<float, 64, 64, 16, 4, 4>(g, s, partial, st);
+  const cudaError_t attr =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (attr != cudaSuccess) return (int)attr;
+  prof_mark(st, true);
+  kern<<<s.ctas, threads, smem, st>>>(g, s, static_cast<float*>(partial), vec_c);
+  prof_mark(st, false);
+  count_launch();
+  return (int)cudaGetLastError();
 }
 
 int launch_reduce(int dtype, const GemmArgs& g, int pk, const void* partial, cudaStream_t st) {

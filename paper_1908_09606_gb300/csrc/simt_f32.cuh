@@ -1,26 +1,39 @@
-// FP32 C-stationary tile with a multi-stage cp.async ring (K-F32 fast path).
+// FP32 C-stationary tile on the FFMA pipe (K-F32).
 //
-// 128 x 128 C tile in registers (8 x 8 per thread: rows ty + 16 i, columns
-// 4 tx + j and 64 + 4 tx + j), 16-deep k panels of A (row-major, pitch 20
-// floats so the 16-byte fragment loads of a warp hit distinct banks) and B
-// (row-major) streamed through STAGES shared-memory buffers by cp.async --
-// the panels of round t + STAGES - 1 are in flight while round t is
-// multiplied (the overlap of Sec. 7.3).  Ragged edges are zero-filled by the
-// copy itself.  VEC = 4: 16-byte copies (A and B 16-byte aligned, lda and ldb
-// multiples of 4); VEC = 1: 4-byte copies for any pitch.
+// A BM x 128 C tile stays in registers, 8 x 8 per thread.  Warps own 64 x 32
+// sub-tiles (BM = 128: 2 x 4 warps, 256 threads; BM = 256: 4 x 4 warps, 512
+// threads, four warps per SM quarter to hide shared-memory latency).  The 32
+// lanes of a warp form an 8 x 4 grid: lane (y, x) owns rows y, y + 8, ..., y + 56
+// of the warp tile and columns 4x..4x+3, 16+4x..16+4x+3.
+//
+// Both panels keep their global layout in shared memory: A row-major with a
+// 20-float pitch (k contiguous), so one 16-byte read gives a thread four k
+// steps of one row and the 8 rows a warp reads at once fall in distinct bank
+// quads; B row-major, two 16-byte reads per k step (4 distinct per warp).  Per
+// 4 k steps a thread issues 8 + 8 shared loads for 256 FFMAs.  16-deep k panels
+// stream through F32_STAGES buffers by cp.async (16-byte copies when A and B
+// are 16-byte aligned with pitches a multiple of 4 floats, else 4-byte): the
+// panels of round t + STAGES - 1 are in flight while round t is multiplied
+// (the overlap of Sec. 7.3).  Ragged edges are zero-filled by the copies.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace cosma {
 
-constexpr int F32_BM = 128, F32_BN = 128, F32_BK = 16, F32_STAGES = 4;
-constexpr int F32_APITCH = F32_BK + 4;
+constexpr int F32_BN = 128, F32_BK = 16, F32_STAGES = 4, F32_APITCH = F32_BK + 4;
 
+template <int BM>
 struct F32Smem {
-  float As[F32_STAGES][F32_BM][F32_APITCH];
-  float Bs[F32_STAGES][F32_BK][F32_BN];
+  float As[F32_STAGES][BM][F32_APITCH];  // row-major A panel
+  float Bs[F32_STAGES][F32_BK][F32_BN];  // row-major B panel
 };
+
+// Threads of a CTA running f32_tile<BM>.
+template <int BM>
+__host__ __device__ constexpr int f32_threads() {
+  return 2 * BM;
+}
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
   const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
@@ -28,28 +41,50 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_b
                "r"(src_bytes)
                : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
 __device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
   const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes)
                : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-template <int VEC>
-__device__ __forceinline__ void f32_tile_async(const float* __restrict__ A, int64_t lda,
-                                               const float* __restrict__ B, int64_t ldb,
-                                               float* dst, int64_t ld, int64_t m, int64_t n,
-                                               int64_t row0, int64_t col0, int64_t kbeg,
-                                               int64_t kend, bool vec_out, F32Smem& sm) {
+// C[row0 : row0 + BM, col0 : col0 + 128] (clipped to m x n) = A[rows, kbeg:kend] B[kbeg:kend, cols],
+// written to dst (leading dimension ld).  Every thread of the CTA calls it.
+template <int BM, int VEC>
+__device__ __forceinline__ void f32_tile(const float* __restrict__ A, int64_t lda,
+                                         const float* __restrict__ B, int64_t ldb, float* dst,
+                                         int64_t ld, int64_t m, int64_t n, int64_t row0,
+                                         int64_t col0, int64_t kbeg, int64_t kend, bool vec_out,
+                                         F32Smem<BM>& sm) {
+  constexpr int NT = f32_threads<BM>();
   const int tid = threadIdx.x;
-  const int ty = tid / 16, tx = tid % 16;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int ar = (warp >> 2) * 64 + (lane >> 2);   // rows ar + 8 i, i = 0..7
+  const int bc = (warp & 3) * 32 + (lane & 3) * 4;  // cols bc..bc+3, bc+16..bc+19
   const int64_t nsteps = (kend - kbeg + F32_BK - 1) / F32_BK;
+
+  // A copies: VEC-float chunks; this thread's chunk column a_c and rows
+  // a_r + e * A_STEP.  A zero-fill copy reads nothing; its source is any valid
+  // address.
+  constexpr int A_COLS = F32_BK / VEC;       // chunks per A row
+  constexpr int A_STEP = NT / A_COLS;        // A rows per pass of the CTA
+  constexpr int A_PER = BM / A_STEP;
+  const int a_r = tid / A_COLS, a_c = (tid % A_COLS) * VEC;
+  const float* a_src = A + (kbeg + a_c);
+  // B copies: a fixed chunk column per thread, rows b_k0 + e * B_STEP.
+  constexpr int B_COLS = F32_BN / VEC;
+  constexpr int B_STEP = NT / B_COLS;
+  constexpr int B_PER = F32_BK / B_STEP;
+  const int b_k0 = tid / B_COLS, b_c = (tid % B_COLS) * VEC;
+  const int64_t b_gc = col0 + b_c;
+  const int b_bytes = b_gc >= n ? 0 : (n - b_gc >= VEC ? 4 * VEC : (int)(n - b_gc) * 4);
+  const float* b_src = B + (b_bytes ? b_gc : 0) + (kbeg + b_k0) * ldb;
 
   float acc[8][8];
 #pragma unroll
@@ -58,53 +93,28 @@ __device__ __forceinline__ void f32_tile_async(const float* __restrict__ A, int6
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
   auto issue = [&](int64_t step, int buf) {
-    const int64_t k0 = kbeg + step * F32_BK;
-    if constexpr (VEC == 4) {
+    const int64_t kk0 = step * F32_BK;  // offset from kbeg
+    const int64_t kleft = kend - (kbeg + kk0 + a_c);
+    const int a_bytes = kleft >= VEC ? 4 * VEC : (kleft > 0 ? (int)kleft * 4 : 0);
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {  // A: 128 rows x 4 chunks of 4 floats
-        const int idx = tid + e * 256;
-        const int r = idx >> 2, c4 = idx & 3;
-        const int64_t gr = row0 + r, gk = k0 + c4 * 4;
-        int bytes = 0;
-        const float* src = A;
-        if (gr < m && gk < kend) {
-          const int64_t left = kend - gk;
-          bytes = left >= 4 ? 16 : (int)left * 4;
-          src = A + gr * lda + gk;
-        }
-        cp_async16(&sm.As[buf][r][c4 * 4], src, bytes);
-      }
+    for (int e = 0; e < A_PER; ++e) {
+      const int r = a_r + e * A_STEP;
+      const int bytes = row0 + r < m ? a_bytes : 0;
+      const float* src = bytes ? a_src + (row0 + r) * lda + kk0 : A;
+      if constexpr (VEC == 4)
+        cp_async16(&sm.As[buf][r][a_c], src, bytes);
+      else
+        cp_async4(&sm.As[buf][r][a_c], src, bytes);
+    }
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {  // B: 16 rows x 32 chunks of 4 floats
-        const int idx = tid + e * 256;
-        const int kr = idx >> 5, c4 = idx & 31;
-        const int64_t gk = k0 + kr, gc = col0 + c4 * 4;
-        int bytes = 0;
-        const float* src = B;
-        if (gk < kend && gc < n) {
-          const int64_t left = n - gc;
-          bytes = left >= 4 ? 16 : (int)left * 4;
-          src = B + gk * ldb + gc;
-        }
-        cp_async16(&sm.Bs[buf][kr][c4 * 4], src, bytes);
-      }
-    } else {
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {  // A: 128 rows x 16 floats
-        const int idx = tid + e * 256;
-        const int r = idx >> 4, c = idx & 15;
-        const int64_t gr = row0 + r, gk = k0 + c;
-        const bool in = gr < m && gk < kend;
-        cp_async4(&sm.As[buf][r][c], in ? A + gr * lda + gk : A, in ? 4 : 0);
-      }
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {  // B: 16 rows x 128 floats
-        const int idx = tid + e * 256;
-        const int kr = idx >> 7, c = idx & 127;
-        const int64_t gk = k0 + kr, gc = col0 + c;
-        const bool in = gk < kend && gc < n;
-        cp_async4(&sm.Bs[buf][kr][c], in ? B + gk * ldb + gc : B, in ? 4 : 0);
-      }
+    for (int e = 0; e < B_PER; ++e) {
+      const int kr = b_k0 + e * B_STEP;
+      const int bytes = kbeg + kk0 + kr < kend ? b_bytes : 0;
+      const float* src = bytes ? b_src + (kk0 + e * B_STEP) * ldb : B;
+      if constexpr (VEC == 4)
+        cp_async16(&sm.Bs[buf][kr][b_c], src, bytes);
+      else
+        cp_async4(&sm.Bs[buf][kr][b_c], src, bytes);
     }
   };
 
@@ -128,12 +138,12 @@ __device__ __forceinline__ void f32_tile_async(const float* __restrict__ A, int6
       float4 a4[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i)
-        a4[i] = *reinterpret_cast<const float4*>(&sm.As[buf][ty + 16 * i][kq]);
+        a4[i] = *reinterpret_cast<const float4*>(&sm.As[buf][ar + 8 * i][kq]);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
-        const float4 b0 = *reinterpret_cast<const float4*>(&sm.Bs[buf][kq + kk][tx * 4]);
-        const float4 b1 = *reinterpret_cast<const float4*>(&sm.Bs[buf][kq + kk][64 + tx * 4]);
-        const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        const float4 u = *reinterpret_cast<const float4*>(&sm.Bs[buf][kq + kk][bc]);
+        const float4 v = *reinterpret_cast<const float4*>(&sm.Bs[buf][kq + kk][bc + 16]);
+        const float b[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const float a = kk == 0 ? a4[i].x : kk == 1 ? a4[i].y : kk == 2 ? a4[i].z : a4[i].w;
@@ -147,12 +157,12 @@ __device__ __forceinline__ void f32_tile_async(const float* __restrict__ A, int6
 
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const int64_t r = row0 + ty + 16 * i;
+    const int64_t r = row0 + ar + 8 * i;
     if (r >= m) continue;
     float* drow = dst + r * ld;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int64_t c = col0 + h * 64 + tx * 4;
+      const int64_t c = col0 + bc + 16 * h;
       if (vec_out && c + 4 <= n) {
         *reinterpret_cast<float4*>(drow + c) =
             make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);

@@ -90,19 +90,23 @@ def _forced_plan(m, n, k, dtype, tile, pk, order, ctas, pm=1, pn=1):
     cosma = lib()
     p = cosma.cosma_plan_query(m, n, k, cosma.DTYPES[dtype])
     kb = p.k_block
-    p.tile_m = p.tile_n = tile
+    p.tile_m, p.tile_n = tile
     p.pk, p.order, p.ctas, p.pm, p.pn = pk, order, ctas, pm, pn
     p.k_block = kb
     return p
 
 
+# the two tiles of each family: FP64 128 x 128 / 64 x 64, FP32 128 x 128 / 256 x 128
+TILES = {"f64": [(128, 128), (64, 64)], "f32": [(128, 128), (256, 128)]}
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("tile,pk,order,ctas,pm,pn", [
-    (128, 1, 1, 7, 1, 1), (128, 3, 1, 20, 1, 1), (64, 2, 0, 2 * 2 * 3, 2, 3),
-    (64, 5, 1, 148, 1, 1), (128, 2, 0, 2 * 1 * 2, 2, 1)])
-def test_forced_plans_split_k_and_orders(dtype, tile, pk, order, ctas, pm, pn):
+@pytest.mark.parametrize("ti,pk,order,ctas,pm,pn", [
+    (0, 1, 1, 7, 1, 1), (0, 3, 1, 20, 1, 1), (1, 2, 0, 2 * 2 * 2, 2, 2),
+    (1, 5, 1, 148, 1, 1), (0, 2, 0, 2 * 1 * 2, 2, 1)])
+def test_forced_plans_split_k_and_orders(dtype, ti, pk, order, ctas, pm, pn):
     m, n, k = 300, 260, 515
-    p = _forced_plan(m, n, k, dtype, tile, pk, order, ctas, pm, pn)
+    p = _forced_plan(m, n, k, dtype, TILES[dtype][ti], pk, order, ctas, pm, pn)
     C = _run(m, n, k, dtype, plan=p)
     A, B = host_operands(m, n, k, dtype)
     ref = og.gemm(A, B, "dot2")
