@@ -13,7 +13,9 @@ namespace cosma {
 
 int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void* ws,
                    long long ws_bytes, int* status, long long wait_limit, cudaStream_t st);
-long long tc_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_plan& p, bool pack_a);
+long long tc_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_plan& p, bool pack_a,
+                             bool transpose_b);
+bool tc_b_direct(const void* B, int64_t ldb);
 int grouped_gemm(int count, const cosma_problem* problems, int dtype, const DeviceInfo& dev,
                  void* ws, long long ws_bytes, int* status, long long wait_limit, cudaStream_t st,
                  long long* needed, int requested_tile);
@@ -168,12 +170,14 @@ int check_args(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, cons
   return COSMA_OK;
 }
 
+// Workspace of a plan; without operand pointers, the most any operands need.
 long long total_workspace(int64_t m, int64_t n, int64_t k, int dtype, const cosma_plan& p,
-                          const void* A = nullptr, int64_t lda = 0) {
+                          const void* A = nullptr, int64_t lda = 0, const void* B = nullptr,
+                          int64_t ldb = 0) {
   if (dtype == COSMA_F64_EMU_BF16) return emu_workspace_bytes(m, n, k, g_cfg);
   if (dtype == COSMA_BF16) {
-    const bool pack_a = A && ((reinterpret_cast<uintptr_t>(A) & 15) || ((lda * 2) & 15));
-    return tc_workspace_bytes(m, n, k, p, pack_a);
+    const bool pack_a = !A || (reinterpret_cast<uintptr_t>(A) & 15) || ((lda * 2) & 15);
+    return tc_workspace_bytes(m, n, k, p, pack_a, !B || !tc_b_direct(B, ldb));
   }
   return workspace_bytes(m, n, k, dtype, p);
 }
@@ -203,7 +207,7 @@ int run(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void*
     rc = plan_gemm(m, n, k, dtype, g_cfg.selector, s->info, g_cfg, &p, !capturing(st));
     if (rc != COSMA_OK) return rc;
   }
-  const long long need = total_workspace(m, n, k, dtype, p, A, lda);
+  const long long need = total_workspace(m, n, k, dtype, p, A, lda, B, ldb);
   void* ws = nullptr;
   long long have = 0;
   rc = workspace(s, need, st, &ws, &have);

@@ -14,8 +14,10 @@
 // plan's schedule (schedule.h); a k split writes f32 partials that the
 // Reduce kernel sums in a fixed order.
 //
-// B arrives row-major (k x n, n contiguous); it is first transposed into the
-// workspace so both operands are K-major for the MMA.
+// B arrives row-major (k x n, n contiguous).  When its rows are 16-byte aligned
+// it is loaded as it is -- 64 x 64 TMA boxes (64 n by 64 k, 128-byte swizzle) --
+// and multiplied as an MN-major operand; otherwise it is first transposed into
+// the workspace so both operands are K-major.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -114,7 +116,7 @@ __device__ __forceinline__ void store_row32(float* dst, int64_t col0, int64_t n,
   }
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool B_MN>
 __global__ void __launch_bounds__(192, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                TcArgs a) {
@@ -171,8 +173,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           tc::mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES);
           uint8_t* sa = smem + stage * L::STAGE_BYTES;
           tc::tma_load_2d(sa, &tmA, &full[stage], (int32_t)(kb * BK), (int32_t)(u.tile_row * BM));
-          tc::tma_load_2d(sa + L::A_BYTES, &tmB, &full[stage], (int32_t)(kb * BK),
-                          (int32_t)(u.tile_col * BN));
+          if constexpr (B_MN) {
+#pragma unroll
+            for (int j = 0; j < BN / 64; ++j)  // box j: columns j*64.., k rows kb*64..
+              tc::tma_load_2d(sa + L::A_BYTES + j * (64 * BK * 2), &tmB, &full[stage],
+                              (int32_t)(u.tile_col * BN + j * 64), (int32_t)(kb * BK));
+          } else {
+            tc::tma_load_2d(sa + L::A_BYTES, &tmB, &full[stage], (int32_t)(kb * BK),
+                            (int32_t)(u.tile_col * BN));
+          }
           armed |= 1u << stage;
           armed_ph = (armed_ph & ~(1u << stage)) | (ph << stage);
           if (++stage == STAGES) { stage = 0; ph ^= 1; }
@@ -192,7 +201,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
   } else if (warp == 1) {
     if (tc::elect_one()) {
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+      constexpr uint32_t idesc = B_MN ? tc::idesc_bf16_f32_bmn(BM, BN) : tc::idesc_bf16_f32(BM, BN);
       int stage = 0;
       uint32_t ph = 0, acc = 0;
       uint32_t aph[2] = {0, 0};
@@ -208,9 +217,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           const uint32_t sa = tc::smem_u32(smem + stage * L::STAGE_BYTES);
           const uint32_t sb = sa + L::A_BYTES;
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk)
-            tc::mma_bf16(d, tc::smem_desc_sw128(sa + kk * 32), tc::smem_desc_sw128(sb + kk * 32),
-                         idesc, (kb > u.kb0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            // B MN-major: 16 k rows of 128 bytes per step; boxes 64 x BK apart
+            const uint64_t db = B_MN ? tc::smem_desc_mn_sw128(sb + kk * 16 * 128, 64 * BK * 2, 1024)
+                                     : tc::smem_desc_sw128(sb + kk * 32);
+            tc::mma_bf16(d, tc::smem_desc_sw128(sa + kk * 32), db, idesc,
+                         (kb > u.kb0 || kk > 0) ? 1u : 0u);
+          }
           tc::mma_commit(&empty[stage]);
           if (++stage == STAGES) { stage = 0; ph ^= 1; }
         }
@@ -262,19 +275,19 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   }
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool B_MN>
 int launch_kernel(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& args,
                   cudaStream_t st) {
   using L = Layout<BN, STAGES>;
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>,
+    attr = cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES, B_MN>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC);
   });
   if (attr != cudaSuccess) return (int)attr;
   prof_mark(st, true);
-  tc_gemm_kernel<BN, STAGES><<<args.s.ctas, 192, L::ALLOC, st>>>(ta, tb, args);
+  tc_gemm_kernel<BN, STAGES, B_MN><<<args.s.ctas, 192, L::ALLOC, st>>>(ta, tb, args);
   prof_mark(st, false);
   count_launch();
   return (int)cudaGetLastError();
@@ -283,6 +296,8 @@ int launch_kernel(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& ar
 inline int64_t round_up(int64_t x, int64_t r) { return (x + r - 1) / r * r; }
 
 }  // namespace
+
+bool tc_b_direct(const void* B, int64_t ldb);
 
 int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void* ws,
                    long long ws_bytes, int* status, long long wait_limit, cudaStream_t st) {
@@ -294,8 +309,12 @@ int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void*
     partial = reinterpret_cast<float*>(w + off);
     off += round_up((long long)p.pk * g.m * g.n * 4, 256);
   }
-  __nv_bfloat16* Bt = reinterpret_cast<__nv_bfloat16*>(w + off);
-  off += round_up(g.n * kp * 2, 256);
+  const bool b_mn = tc_b_direct(g.B, g.ldb);
+  __nv_bfloat16* Bt = nullptr;
+  if (!b_mn) {
+    Bt = reinterpret_cast<__nv_bfloat16*>(w + off);
+    off += round_up(g.n * kp * 2, 256);
+  }
   const __nv_bfloat16* Ause = static_cast<const __nv_bfloat16*>(g.A);
   int64_t lda = g.lda;
   const bool pack_a = (reinterpret_cast<uintptr_t>(g.A) & 15) || ((g.lda * 2) & 15);
@@ -310,7 +329,7 @@ int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void*
     lda = kp;
   }
   if (off > ws_bytes) return COSMA_ERR_NO_WORKSPACE;
-  {
+  if (!b_mn) {
     dim3 grid((unsigned)((g.n + 31) / 32), (unsigned)((g.k + 31) / 32));
     if (grid.y > 65535) return COSMA_ERR_UNSUPPORTED;
     transpose_bf16<<<grid, dim3(32, 8), 0, st>>>(static_cast<const __nv_bfloat16*>(g.B), g.k, g.n,
@@ -322,7 +341,10 @@ int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void*
   CUtensorMap ta, tb;
   int rc = encode_tmap_bf16(&ta, Ause, g.m, g.k, lda, BK, BM);
   if (rc != COSMA_OK) return rc;
-  rc = encode_tmap_bf16(&tb, Bt, g.n, g.k, kp, BK, p.tile_n);
+  if (b_mn)  // B itself: k rows of n, 64 x 64 boxes
+    rc = encode_tmap_bf16(&tb, g.B, g.k, g.n, g.ldb, 64, BK);
+  else
+    rc = encode_tmap_bf16(&tb, Bt, g.n, g.k, kp, BK, p.tile_n);
   if (rc != COSMA_OK) return rc;
   TcArgs args;
   args.s = s;
@@ -333,8 +355,12 @@ int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void*
   args.wait_limit = wait_limit;
   args.vec_ok = ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0 && (g.ldc & 3) == 0) ? 1 : 0;
   int err;
-  if (p.tile_n == 256) err = launch_kernel<256, 4>(ta, tb, args, st);
-  else err = launch_kernel<128, 6>(ta, tb, args, st);
+  if (b_mn)
+    err = p.tile_n == 256 ? launch_kernel<256, 4, true>(ta, tb, args, st)
+                          : launch_kernel<128, 6, true>(ta, tb, args, st);
+  else
+    err = p.tile_n == 256 ? launch_kernel<256, 4, false>(ta, tb, args, st)
+                          : launch_kernel<128, 6, false>(ta, tb, args, st);
   if (err) return err;
   if (p.pk > 1) {
     GemmArgs gr = g;
@@ -343,11 +369,16 @@ int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void*
   return 0;
 }
 
-long long tc_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_plan& p, bool pack_a) {
+bool tc_b_direct(const void* B, int64_t ldb) {
+  return (reinterpret_cast<uintptr_t>(B) & 15) == 0 && ((ldb * 2) & 15) == 0;
+}
+
+long long tc_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_plan& p, bool pack_a,
+                             bool transpose_b) {
   const int64_t kp = round_up(k, 8);
   long long b = 0;
   if (p.pk > 1) b += round_up((long long)p.pk * m * n * 4, 256);
-  b += round_up(n * kp * 2, 256);
+  if (transpose_b) b += round_up(n * kp * 2, 256);
   if (pack_a) b += round_up(m * kp * 2, 256);
   return b;
 }

@@ -224,6 +224,20 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// Shared-memory descriptor of an MN-major operand with 128-byte swizzle: rows of
+// 64 bf16 along M/N (128 bytes) for 8 consecutive k form a 1024-byte atom; the
+// next 8 k are sbo bytes further, the next 64 elements along M/N lbo bytes.
+__device__ __forceinline__ uint64_t smem_desc_mn_sw128(uint32_t saddr, uint32_t lbo,
+                                                       uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);        // start address
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;    // leading byte offset: next 64 along M/N
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;    // stride byte offset: next 8 along k
+  d |= (uint64_t)1 << 46;                        // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                        // swizzle: 128B
+  return d;
+}
+
 // Instruction descriptor, kind::f16: A, B bf16 (K-major), D f32, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4)                 // D format f32
@@ -231,6 +245,10 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
          | (1u << 10)              // B format bf16
          | ((uint32_t)(N >> 3) << 17)
          | ((uint32_t)(M >> 4) << 24);
+}
+// Same with B MN-major (the B operand's "transpose" bit).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_bmn(int M, int N) {
+  return idesc_bf16_f32(M, N) | (1u << 16);
 }
 
 // ---- CTA pairs (cta_group::2) --------------------------------------------------

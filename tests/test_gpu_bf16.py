@@ -109,3 +109,17 @@ def test_bounded_wait_reports_timeout_and_context_survives():
         assert cosma.cosma_init(wait_limit=0) == 0
     m, n, k = 256, 384, 320
     _check(_run(m, n, k, seed=9), m, n, k, seed=9)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "integer"])
+def test_bf16_b_loaded_directly_or_transposed(kind):
+    """ldb % 8 == 0 loads B as it is (MN-major operand); an odd ldb transposes it
+    into the workspace first (K-major).  Both meet the bound; integer inputs agree
+    bit for bit."""
+    m, n, k = 300, 520, 700
+    Cd = _run(m, n, k, kind=kind, seed=6)              # ldb = 520: direct
+    Ct = _run(m, n, k, kind=kind, seed=6, ldb=521)     # transposed
+    _check(Cd, m, n, k, kind=kind, seed=6)
+    _check(Ct, m, n, k, kind=kind, seed=6)
+    if kind == "integer":
+        assert np.array_equal(Cd, Ct)
