@@ -277,15 +277,18 @@ def run_grouped(args):
     g = "bf16" if dtype == "bf16" else "f32"
     tdt = torch.bfloat16 if g == "bf16" else torch.float32
     dims = ci.grouped_dims(512, seed=1)
+    # Row pitches padded to 16 bytes (B loaded as it is, C written by tensor stores).
+    pad = 8 if g == "bf16" else 4
+    rup = lambda x, r: -(-int(x) // r) * r
     As, Bs, Cs = [], [], []
     for i, (m, n, k) in enumerate(dims):
-        A = torch.empty((m, k), dtype=tdt, device="cuda")
-        B = torch.empty((k, n), dtype=tdt, device="cuda")
+        A = torch.empty((m, rup(k, pad)), dtype=tdt, device="cuda")[:, :k]
+        B = torch.empty((k, rup(n, pad)), dtype=tdt, device="cuda")[:, :n]
         cid.fill(A, "uniform", g, 1000 + i + 100000 * rank, ci.STREAM_A)
         cid.fill(B, "uniform", g, 1000 + i + 100000 * rank, ci.STREAM_B)
         As.append(A)
         Bs.append(B)
-        Cs.append(torch.empty((m, n), dtype=torch.float32, device="cuda"))
+        Cs.append(torch.empty((m, rup(n, 4)), dtype=torch.float32, device="cuda")[:, :n])
     flops = float((2 * dims.prod(axis=1)).sum())
     stream = torch.cuda.current_stream()
     side = torch.cuda.Stream()
@@ -341,8 +344,8 @@ def run_grouped(args):
         for A, B, C in zip(As, Bs, Cs):
             m, k = A.shape
             n = B.shape[1]
-            rc = cosma.cosma_gemm(m, n, k, A.data_ptr(), k, B.data_ptr(), n, C.data_ptr(), n,
-                                  code, sh)
+            rc = cosma.cosma_gemm(m, n, k, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
+                                  C.data_ptr(), C.stride(0), code, sh)
             if rc != 0:
                 raise cosma.CosmaError(rc, "per-gemm baseline")
     per_gemm()
@@ -361,7 +364,7 @@ def run_grouped(args):
                 "peak": peaks.get("bf16_tflops_sustained", 1700.0),
                 "peak_source": f"bf16_tflops_sustained of {peak_src} peaks"}
     else:
-        roof = {"kernel": "grouped_simt_kernel", "bound": "alu",
+        roof = {"kernel": "grouped_f32_kernel", "bound": "alu",
                 "peak": _alu_peak_tflops("f32", torch.cuda.get_device_properties(local)
                                          .multi_processor_count),
                 "peak_source": "derived: SMs x 128 FMA/clk x 2 x 2070 MHz"}
@@ -418,6 +421,7 @@ def run_grouped(args):
                                        "in [64,4096] seed 1, one persistent launch replayed "
                                        f"from a CUDA graph ({reps} replays per step)",
                            "flops_per_replay": flops, "replay_ms": replay_ms,
+                           "pitches": "rows padded to 16 bytes",
                            "l2": "inputs larger than L2"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks,

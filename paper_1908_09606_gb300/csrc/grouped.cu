@@ -35,9 +35,10 @@ namespace {
 constexpr int GBM = 128, GBK = 64;
 constexpr int kCacheSlots = 8;
 
-struct alignas(64) GMap {
+struct alignas(128) GMap {
   CUtensorMap ta;
   CUtensorMap tb;
+  CUtensorMap tc;  // f32 C, 32 x 32 boxes (stores), when c_tma
 };
 
 struct GMeta {
@@ -54,6 +55,8 @@ struct GMeta {
   int64_t ldap;
   int vec_ok;
   int f32_async;  // f32: A, B 16-byte aligned with pitches multiple of 4 floats
+  int b_mn;       // bf16: B loaded as it is (MN-major operand), no transposed copy
+  int c_tma;      // bf16: C written by tensor stores (16-byte aligned rows)
 };
 
 struct GUnit {
@@ -181,7 +184,10 @@ struct GLayout {
   static constexpr int A_BYTES = GBM * GBK * 2;
   static constexpr int B_BYTES = BN * GBK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int BAR_OFF = STAGES * STAGE_BYTES;
+  // epilogue staging: per epilogue warp two 32 x 32 f32 boxes (128-byte swizzle)
+  static constexpr int EPI_OFF = STAGES * STAGE_BYTES;
+  static constexpr int EPI_BYTES = 4 * 2 * 4096;
+  static constexpr int BAR_OFF = EPI_OFF + EPI_BYTES;
   static constexpr int NBARS = 2 * STAGES + 5;
   static constexpr int TOTAL = BAR_OFF + NBARS * 8 + 16;
   static constexpr int ALLOC = TOTAL + 1024;
@@ -245,13 +251,22 @@ __global__ void __launch_bounds__(192, 1) grouped_tc_kernel(GArgs a) {
           last_p = u.p;
         }
         const int64_t kbt = (g.k + GBK - 1) / GBK;
+        const bool bmn = g.b_mn != 0;
         bool ok = true;
         for (int64_t kb = 0; kb < kbt; ++kb) {
           if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) { ok = false; break; }
           tc::mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES);
           uint8_t* sa = smem + stage * L::STAGE_BYTES;
           tc::tma_load_2d(sa, ta, &full[stage], (int32_t)(kb * GBK), u.tile_row * GBM);
-          tc::tma_load_2d(sa + L::A_BYTES, tb, &full[stage], (int32_t)(kb * GBK), u.tile_col * BN);
+          if (bmn) {
+#pragma unroll
+            for (int j = 0; j < BN / 64; ++j)  // box j: columns j*64.., k rows kb*64..
+              tc::tma_load_2d(sa + L::A_BYTES + j * (64 * GBK * 2), tb, &full[stage],
+                              u.tile_col * BN + j * 64, (int32_t)(kb * GBK));
+          } else {
+            tc::tma_load_2d(sa + L::A_BYTES, tb, &full[stage], (int32_t)(kb * GBK),
+                            u.tile_col * BN);
+          }
           armed |= 1u << stage;
           armed_ph = (armed_ph & ~(1u << stage)) | (ph << stage);
           if (++stage == STAGES) { stage = 0; ph ^= 1; }
@@ -270,13 +285,15 @@ __global__ void __launch_bounds__(192, 1) grouped_tc_kernel(GArgs a) {
     }
   } else if (warp == 1) {
     if (tc::elect_one()) {
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(GBM, BN);
       int stage = 0;
       uint32_t ph = 0, acc = 0;
       uint32_t aph[2] = {0, 0};
       for (int ui = u0; ui < u1 && !*abort_flag; ++ui) {
         const GUnit u = a.units[ui];
         const int64_t kbt = (a.meta[u.p].k + GBK - 1) / GBK;
+        const bool bmn = a.meta[u.p].b_mn != 0;
+        const uint32_t idesc =
+            bmn ? tc::idesc_bf16_f32_bmn(GBM, BN) : tc::idesc_bf16_f32(GBM, BN);
         if (!tc::mbar_wait(&tempty[acc], aph[acc] ^ 1, w)) break;
         tc::tc_fence_after();
         const uint32_t d = tmem_base + acc * BN;
@@ -287,9 +304,12 @@ __global__ void __launch_bounds__(192, 1) grouped_tc_kernel(GArgs a) {
           const uint32_t sa = tc::smem_u32(smem + stage * L::STAGE_BYTES);
           const uint32_t sb = sa + L::A_BYTES;
 #pragma unroll
-          for (int kk = 0; kk < GBK / 16; ++kk)
-            tc::mma_bf16(d, tc::smem_desc_sw128(sa + kk * 32), tc::smem_desc_sw128(sb + kk * 32),
-                         idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < GBK / 16; ++kk) {
+            const uint64_t db = bmn ? tc::smem_desc_mn_sw128(sb + kk * 16 * 128, 64 * GBK * 2, 1024)
+                                    : tc::smem_desc_sw128(sb + kk * 32);
+            tc::mma_bf16(d, tc::smem_desc_sw128(sa + kk * 32), db, idesc,
+                         (kb > 0 || kk > 0) ? 1u : 0u);
+          }
           tc::mma_commit(&empty[stage]);
           if (++stage == STAGES) { stage = 0; ph ^= 1; }
         }
@@ -307,12 +327,15 @@ __global__ void __launch_bounds__(192, 1) grouped_tc_kernel(GArgs a) {
     const int q = warp & 3;
     uint32_t acc = 0;
     uint32_t tph[2] = {0, 0};
+    uint8_t* stage_c = smem + L::EPI_OFF + q * 8192;  // this warp's two staging boxes
+    uint32_t stores = 0;                               // tensor stores committed so far
     for (int ui = u0; ui < u1; ++ui) {
       const GUnit u = a.units[ui];
       const GMeta& g = a.meta[u.p];
       if (!tc::mbar_wait(&tfull[acc], tph[acc], w)) break;
       tc::tc_fence_after();
-      const int64_t row = (int64_t)u.tile_row * GBM + q * 32 + lane;
+      const int64_t row0 = (int64_t)u.tile_row * GBM + q * 32;
+      const int64_t row = row0 + lane;
       float* dst_row = row < g.m ? static_cast<float*>(g.C) + row * g.ldc : nullptr;
 #pragma unroll 1
       for (int c = 0; c < BN; c += 32) {
@@ -320,6 +343,38 @@ __global__ void __launch_bounds__(192, 1) grouped_tc_kernel(GArgs a) {
         tc::tmem_ld_32x32(tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN + c, r);
         tc::tmem_wait_ld();
         const int64_t col0 = (int64_t)u.tile_col * BN + c;
+        if (g.c_tma) {
+          // Columns below n4 = n rounded down to 4: rows of this warp -> one 32 x 32
+          // box in shared memory (16-byte chunk j of row l at chunk j ^ (l % 8): the
+          // 128-byte swizzle), then one tensor store, which clips at m and n4 (the C
+          // map is n4 wide: a store clips in whole 16-byte units).  Columns n4..n-1
+          // are written by the lanes themselves.
+          if (row0 >= g.m || col0 >= g.n) continue;
+          const int64_t n4 = g.n & ~(int64_t)3;
+          if (col0 < n4) {
+            uint8_t* box = stage_c + (stores & 1) * 4096;
+            if (lane == 0) tc::bulk_wait_read<1>();  // the box's previous store has read it
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              *reinterpret_cast<float4*>(box + lane * 128 + ((j ^ (lane & 7)) * 16)) =
+                  make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                              __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+              tc::tma_store_2d(&a.maps[u.p].tc, box, (int32_t)col0, (int32_t)row0);
+              tc::bulk_commit();
+            }
+            ++stores;
+          }
+          if (dst_row && col0 + 32 > n4) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (col0 + j >= n4 && col0 + j < g.n) dst_row[col0 + j] = __uint_as_float(r[j]);
+          }
+          continue;
+        }
         if (dst_row && col0 < g.n) {
           float* dst = dst_row + col0;
           if (g.vec_ok && col0 + 32 <= g.n) {
@@ -341,6 +396,8 @@ __global__ void __launch_bounds__(192, 1) grouped_tc_kernel(GArgs a) {
       tph[acc] ^= 1;
       acc ^= 1;
     }
+    if (lane == 0) tc::bulk_wait_all();  // stores done before shared memory goes away
+    __syncwarp();
   }
   __syncthreads();
   if (warp == 1) {
@@ -399,15 +456,43 @@ int pick_tile(int count, const cosma_problem* pr, int dtype, int requested) {
     std::nth_element(ns.begin(), ns.begin() + count / 2, ns.end());
     return ns[count / 2] >= 512 ? 256 : 128;
   }
+  // f32: the 128 x 128 cp.async tile (about three times the FFMA rate of the
+  // 64 x 64 one even on small problems); 64 only on request.
   if (requested == 64 || requested == 128) return requested;
-  std::vector<int64_t> mn(count);
-  for (int i = 0; i < count; ++i) mn[i] = std::min(pr[i].m, pr[i].n);
-  std::nth_element(mn.begin(), mn.begin() + count / 2, mn.end());
-  return mn[count / 2] >= 256 ? 128 : 64;
+  return 128;
 }
 
 bool needs_pack(const cosma_problem& q) {
   return (reinterpret_cast<uintptr_t>(q.A) & 15) || ((q.lda * 2) & 15);
+}
+bool b_direct(const cosma_problem& q) {
+  return (reinterpret_cast<uintptr_t>(q.B) & 15) == 0 && ((q.ldb * 2) & 15) == 0;
+}
+bool c_tensor_store(const cosma_problem& q) {
+  return (reinterpret_cast<uintptr_t>(q.C) & 15) == 0 && ((q.ldc * 4) & 15) == 0;
+}
+
+// f32 C map for tensor stores: 32 x 32 boxes, 128-byte swizzle.
+int encode_c(CUtensorMap* map, void* base, int64_t rows, int64_t cols, int64_t ld) {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  if (!fn) return COSMA_ERR_CUDA;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? COSMA_OK : COSMA_ERR_CUDA;
 }
 
 long long ws_need(int count, const cosma_problem* pr, int dtype) {
@@ -416,7 +501,7 @@ long long ws_need(int count, const cosma_problem* pr, int dtype) {
   for (int i = 0; i < count; ++i) {
     const cosma_problem& q = pr[i];
     if (!(q.m > 0 && q.n > 0 && q.k > 0)) continue;
-    b += rup(q.n * rup(q.k, 8) * 2, 256);
+    if (!b_direct(q)) b += rup(q.n * rup(q.k, 8) * 2, 256);
     if (needs_pack(q)) b += rup(q.m * rup(q.k, 8) * 2, 256);
   }
   return b;
@@ -467,6 +552,7 @@ int get_table(int dev, int count, const cosma_problem* pr, int dtype, int tile, 
     g.m = q.m; g.n = q.n; g.k = q.k;
     g.A = q.A; g.lda = q.lda; g.B = q.B; g.ldb = q.ldb; g.C = q.C; g.ldc = q.ldc;
     g.Bt = nullptr; g.ldt = 0; g.Ap = nullptr; g.ldap = 0;
+    g.b_mn = 0; g.c_tma = 0;
     g.f32_async = ((reinterpret_cast<uintptr_t>(q.A) & 15) == 0 && (q.lda & 3) == 0 &&
                    (reinterpret_cast<uintptr_t>(q.B) & 15) == 0 && (q.ldb & 3) == 0)
                       ? 1
@@ -475,9 +561,12 @@ int get_table(int dev, int count, const cosma_problem* pr, int dtype, int tile, 
     g.vec_ok = ((reinterpret_cast<uintptr_t>(q.C) & 15) == 0 && (q.ldc & 3) == 0) ? 1 : 0;
     if (dtype == COSMA_BF16 && q.m > 0 && q.n > 0 && q.k > 0) {
       const int64_t kp = rup(q.k, 8);
-      g.Bt = reinterpret_cast<__nv_bfloat16*>(wsp);
-      g.ldt = kp;
-      wsp += rup(q.n * kp * 2, 256);
+      g.b_mn = b_direct(q) ? 1 : 0;
+      if (!g.b_mn) {
+        g.Bt = reinterpret_cast<__nv_bfloat16*>(wsp);
+        g.ldt = kp;
+        wsp += rup(q.n * kp * 2, 256);
+      }
       const void* a_src = q.A;
       int64_t a_ld = q.lda;
       if (needs_pack(q)) {
@@ -490,9 +579,19 @@ int get_table(int dev, int count, const cosma_problem* pr, int dtype, int tile, 
       }
       int rc = encode(&maps[i].ta, a_src, q.m, q.k, a_ld, GBM);
       if (rc != COSMA_OK) return rc;
-      rc = encode(&maps[i].tb, g.Bt, q.n, q.k, kp, tn);
+      if (g.b_mn) {  // B itself: k rows of n, 64 x 64 boxes
+        rc = encode_tmap_bf16(&maps[i].tb, q.B, q.k, q.n, q.ldb, 64, GBK);
+        tpre[i + 1] = tpre[i];
+      } else {
+        rc = encode(&maps[i].tb, g.Bt, q.n, q.k, kp, tn);
+        tpre[i + 1] = tpre[i] + ((q.n + PT - 1) / PT) * ((q.k + PT - 1) / PT);
+      }
       if (rc != COSMA_OK) return rc;
-      tpre[i + 1] = tpre[i] + ((q.n + PT - 1) / PT) * ((q.k + PT - 1) / PT);
+      if (c_tensor_store(q) && q.n >= 4) {
+        rc = encode_c(&maps[i].tc, q.C, q.m, q.n & ~(int64_t)3, q.ldc);
+        if (rc != COSMA_OK) return rc;
+        g.c_tma = 1;
+      }
     }
     if (dtype == COSMA_BF16 && !(q.m > 0 && q.n > 0 && q.k > 0)) tpre[i + 1] = tpre[i];
     if (q.m == 0 || q.n == 0 || q.k == 0) continue;

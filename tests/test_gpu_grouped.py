@@ -22,22 +22,32 @@ def problem_dims(count, seed=1):
     return ci.grouped_dims(count, seed)
 
 
-def make_group(dims, dtype):
+def _pad(x, r):
+    return max(1, -(-int(x) // r) * r)
+
+
+def make_group(dims, dtype, pad=False):
+    """Operands of each problem; pad=True gives every row a 16-byte-multiple pitch
+    (B loaded as it is, C written by tensor stores), else pitches equal the
+    widths (most B transposed first, most C stored row by row)."""
     import torch
     from cosma_inputs import device as cid
     g = "bf16" if dtype == "bf16" else "f32"
     tdt = torch.bfloat16 if g == "bf16" else torch.float32
+    r = 8 if g == "bf16" else 4
     As, Bs, Cs = [], [], []
     for i, (m, n, k) in enumerate(dims):
-        A = torch.empty((m, k), dtype=tdt, device="cuda")
-        B = torch.empty((k, n), dtype=tdt, device="cuda")
+        lda, ldb, ldc = (_pad(k, r), _pad(n, r), _pad(n, 4)) if pad else (k, n, n)
+        A = torch.empty((m, max(lda, 1)), dtype=tdt, device="cuda")[:, :k]
+        B = torch.empty((k, max(ldb, 1)), dtype=tdt, device="cuda")[:, :n]
         if m and k:
             cid.fill(A, "uniform", g, 1000 + i, ci.STREAM_A)
         if k and n:
             cid.fill(B, "uniform", g, 1000 + i, ci.STREAM_B)
         As.append(A)
         Bs.append(B)
-        Cs.append(torch.full((m, n), float("nan"), dtype=torch.float32, device="cuda"))
+        Cs.append(torch.full((m, max(ldc, 1)), float("nan"), dtype=torch.float32,
+                             device="cuda")[:, :n])
     return As, Bs, Cs
 
 
@@ -146,3 +156,19 @@ def test_grouped_captured_in_cuda_graph(dtype):
     for c, e in zip(Cs, eager):
         assert torch.equal(c, e)
     check_group(dims, Cs, dtype, per_problem=3)
+
+
+def test_grouped_bf16_padded_pitches_direct_b_and_tensor_stores():
+    """Every B loaded as it is (MN-major) and every C written by tensor stores;
+    the padding columns of C stay untouched."""
+    import torch
+    dims = problem_dims(96, seed=4)
+    As, Bs, Cs = make_group(dims, "bf16", pad=True)
+    stores = [c.as_strided((c.shape[0], c.stride(0)), (c.stride(0), 1)) for c in Cs]
+    for st in stores:
+        st.fill_(-3.0)
+    run_group(As, Bs, Cs, "bf16")
+    check_group(dims, Cs, "bf16", per_problem=6)
+    for (m, n, k), st in zip(dims, stores):
+        if st.shape[1] > n:
+            assert torch.all(st[:, n:] == -3.0)
