@@ -77,7 +77,12 @@ def _alu_peak_tflops(dtype, sms):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # dominant kernel, from one single-pass ncu capture of exactly this workload and
 # kernel version; absent entries are reported as null.
-DRAM_TRAFFIC = {}
+DRAM_TRAFFIC = {
+    ("square", "bf16"): 10.91e9 + 1.06e9,    # tc_gemm_kernel<256,4,B MN-major>, 1-pass capture
+    ("4096", "f32"): 0.306e9 + 0.054e9,      # simt_f32_kernel<128,4>
+    ("4096", "f64"): 1.240e9 + 0.130e9,      # simt_gemm_kernel<double,64,64,8,4,4>
+    ("grouped512", "bf16"): 4.718e9 + 2.027e9,  # grouped_tc_kernel<256,4>
+}
 
 
 def io_report(m, n, k, dtype, plan, traffic, l2_bytes, sms, smem_per_sm):
@@ -370,7 +375,7 @@ def run_grouped(args):
                 "peak_source": "derived: SMs x 128 FMA/clk x 2 x 2070 MHz"}
     roof.update({"achieved": flops / (kms * 1e-3) / 1e12, "unit": "TFLOP/s",
                  "algorithmic": "sum of 2mnk over the 512 products per launch",
-                 "kernel_ms": kms, "traffic": None})
+                 "kernel_ms": kms, "traffic": DRAM_TRAFFIC.get(("grouped512", dtype))})
     roof["frac"] = roof["achieved"] / roof["peak"]
     # e2e: operands copied in from pinned host memory, one result read back
     Ah = [a.cpu().pin_memory() for a in As]
