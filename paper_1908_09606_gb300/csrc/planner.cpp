@@ -147,7 +147,18 @@ Sched sched_from_plan(int64_t m, int64_t n, int64_t k, const cosma_plan& p) {
   s.tile_m = p.tile_m; s.tile_n = p.tile_n; s.k_block = p.k_block;
   s.mt = cdiv(m, p.tile_m); s.nt = cdiv(n, p.tile_n); s.kbt = cdiv(k, p.k_block);
   s.pm = p.pm; s.pn = p.pn; s.pk = p.pk; s.order = p.order; s.ctas = p.ctas;
-  s.group = 8;
+  // Raster group of order 1 (rows of tiles per group): the ctas / pk tiles in flight
+  // at once form a G x W block.  One k step of that wave reads G tile_m rows of A and
+  // W tile_n columns of B through L2; with G W fixed the sum is smallest at
+  // G tile_m = W tile_n -- the square-tile rule of eq. optTileShape one level up,
+  // L2 being the fast memory of the whole wave.
+  {
+    const double wave = std::max(1.0, (double)p.ctas / std::max(1, p.pk));
+    int g = (int)std::lround(std::sqrt(wave * p.tile_n / std::max(1, p.tile_m)));
+    if (g < 1) g = 1;
+    if (g > s.mt) g = (int)std::max<int64_t>(1, s.mt);
+    s.group = g;
+  }
   return s;
 }
 
