@@ -147,6 +147,23 @@ void cosma_finalize(void);
 int cosma_gemm(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void* B,
                int64_t ldb, void* C, int64_t ldc, int dtype, void* stream);
 
+/* C = alpha op(A) op(B) + beta C: the BLAS / ScaLAPACK GEMM surface over the same
+ * schedule (the paper's integration target; op only changes how a panel is read,
+ * alpha and beta only the epilogue and the Reduce).
+ *   trans_a = 0: A is m x k row-major (lda >= k); 1: A holds op(A)^T, k x m
+ *   row-major (lda >= m).  trans_b = 0: B is k x n (ldb >= n); 1: B holds
+ *   op(B)^T, n x k (ldb >= k).  C is m x n row-major (ldc >= n).
+ *   beta == 0: C is not read (NaN or Inf there do not propagate).  k == 0 or
+ *   alpha == 0: C = beta C and A, B are not read.  alpha and beta are applied
+ *   in the output precision (f32 for COSMA_F32 / COSMA_BF16).
+ *   COSMA_BF16 reads transposed operands in place (MN-major A, K-major B);
+ *   COSMA_F64_EMU_BF16 splits them directly; COSMA_F64 / COSMA_F32 first copy a
+ *   transposed operand untransposed into the workspace (one extra pass over it).
+ * Other arguments, ownership and errors as cosma_gemm. */
+int cosma_gemm_ex(int trans_a, int trans_b, int64_t m, int64_t n, int64_t k, double alpha,
+                  const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C,
+                  int64_t ldc, int dtype, void* stream);
+
 /* Same as cosma_gemm but runs the given plan (e.g. from cosma_plan_query or an
  * autotuner).  The plan is validated against the kernel's limits first. */
 int cosma_gemm_planned(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda,

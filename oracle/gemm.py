@@ -7,7 +7,10 @@ contraction, no fast-math) and calls it through ctypes.
 Pins (tests/test_oracle_gemm.py): exact integer products against Python
 integers, identity / diagonal / rank-1 closed forms, exact rational arithmetic
 (fractions) on tiny inputs for Dot2, the classical bound |C_naive - C| <= gamma_k
-|A||B| for the naive loop, and Freivalds catching a planted error.
+|A||B| for the naive loop, and Freivalds catching a planted error; for gemm_ex,
+integer alpha op(A) op(B) + beta C0 against Python integer loops in all four
+transpose cases, alpha = 0 giving exactly beta C0, and NaN in C0 ignored when
+beta = 0.
 """
 
 import ctypes
@@ -75,6 +78,25 @@ def gemm(A, B, method="dot2"):
         fn = {"naive": _load().oracle_gemm_naive, "dot2": _load().oracle_gemm_dot2}[method]
         fn(m, n, k, _ptr(A), max(k, 1), _ptr(B), max(n, 1), _ptr(C), max(n, 1))
     return C
+
+
+def gemm_ex(A, B, C0, alpha, beta, trans_a=False, trans_b=False, method="dot2"):
+    """C = alpha op(A) op(B) + beta C0 in FP64: the BLAS GEMM definition that the
+    ScaLAPACK interface of the paper's implementation follows.  op(X) is X, or the
+    transpose of the stored X when its flag is set (A stored k x m, B n x k).  As
+    in BLAS, beta == 0 does not read C0 and alpha == 0 or k == 0 does not read A, B."""
+    A, B = _f64(A), _f64(B)
+    opA = A.T if trans_a else A
+    opB = B.T if trans_b else B
+    m, k = opA.shape
+    k2, n = opB.shape
+    assert k == k2
+    out = np.zeros((m, n), dtype=np.float64)
+    if alpha != 0.0 and k > 0:
+        out = alpha * gemm(opA, opB, method)
+    if beta != 0.0:
+        out = out + beta * _f64(C0)
+    return out
 
 
 def dot2_pairs(arows, bcols):

@@ -69,6 +69,8 @@ SIGNATURES = [
     ("cosma_gemm", _INT, [_I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _INT, _VP]),
     ("cosma_gemm_planned", _INT, [_I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _INT,
                                   ctypes.POINTER(cosma_plan), _VP]),
+    ("cosma_gemm_ex", _INT, [_INT, _INT, _I64, _I64, _I64, _D, _VP, _I64, _VP, _I64, _D, _VP,
+                             _I64, _INT, _VP]),
     ("cosma_gemm_grouped", _INT, [_INT, ctypes.POINTER(cosma_problem), _INT, _VP]),
     ("cosma_gemm_host", _INT, [_I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _INT, _VP]),
     ("cosma_plan_query", _INT, [_I64, _I64, _I64, _INT, _INT, ctypes.POINTER(cosma_plan)]),
@@ -165,6 +167,12 @@ def cosma_gemm_planned(m, n, k, A, lda, B, ldb, C, ldc, dtype, plan, stream=0):
 def cosma_gemm_grouped(problems, dtype, stream=0):
     arr = (cosma_problem * len(problems))(*problems)
     return load().cosma_gemm_grouped(len(problems), arr, dtype, stream)
+
+
+def cosma_gemm_ex(trans_a, trans_b, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, dtype,
+                  stream=0):
+    return load().cosma_gemm_ex(trans_a, trans_b, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                                dtype, stream)
 
 
 def cosma_gemm_host(m, n, k, A, lda, B, ldb, C, ldc, dtype, stream=0):
@@ -299,6 +307,25 @@ def gemm(A, B, C, dtype, stream=None, plan=None):
         rc = cosma_gemm_planned(m, n, k, A.data_ptr(), lda, B.data_ptr(), ldb, C.data_ptr(),
                                 ldc, dtype, plan, s)
     return _check(rc, "cosma_gemm")
+
+
+def gemm_ex(A, B, C, dtype, alpha=1.0, beta=0.0, trans_a=False, trans_b=False, stream=None):
+    """C = alpha op(A) op(B) + beta C for row-major torch CUDA tensors; A (B) holds
+    op(A)^T (op(B)^T) when trans_a (trans_b).  Raises on error."""
+    m, n = C.shape
+    k = A.shape[0] if trans_a else A.shape[1]
+    assert (A.shape[1] if trans_a else A.shape[0]) == m
+    assert (B.shape[1] if trans_b else B.shape[0]) == k
+    assert (B.shape[0] if trans_b else B.shape[1]) == n
+    for t in (A, B, C):
+        assert t.is_cuda and t.stride(1) == 1, "row-major CUDA tensors with unit column stride"
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    s = _stream_handle(stream)
+    rc = cosma_gemm_ex(int(trans_a), int(trans_b), m, n, k, float(alpha), A.data_ptr(),
+                       max(A.stride(0), 1), B.data_ptr(), max(B.stride(0), 1), float(beta),
+                       C.data_ptr(), max(C.stride(0), 1), dtype, s)
+    return _check(rc, "cosma_gemm_ex")
 
 
 def gemm_host(A, B, C, dtype, stream=None):

@@ -13,9 +13,8 @@ namespace cosma {
 
 int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void* ws,
                    long long ws_bytes, int* status, long long wait_limit, cudaStream_t st);
-long long tc_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_plan& p, bool pack_a,
-                             bool transpose_b);
-bool tc_b_direct(const void* B, int64_t ldb);
+long long tc_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const void* A,
+                             int64_t lda, int trans_a, const void* B, int64_t ldb, int trans_b);
 int grouped_gemm(int count, const cosma_problem* problems, int dtype, const DeviceInfo& dev,
                  void* ws, long long ws_bytes, int* status, long long wait_limit, cudaStream_t st,
                  long long* needed, int requested_tile);
@@ -153,10 +152,12 @@ int elem_bytes_in(int dtype) {
 int elem_bytes_out(int dtype) { return dtype == COSMA_F32 || dtype == COSMA_BF16 ? 4 : 8; }
 
 int check_args(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void* B,
-               int64_t ldb, const void* C, int64_t ldc, int dtype) {
+               int64_t ldb, const void* C, int64_t ldc, int dtype, int ta = 0, int tb = 0) {
   if (dtype < COSMA_F64 || dtype > COSMA_F64_EMU_INT8) return COSMA_ERR_INVALID_ARG;
   if (m < 0 || n < 0 || k < 0) return COSMA_ERR_INVALID_ARG;
-  if (lda < (k > 1 ? k : 1) || ldb < (n > 1 ? n : 1) || ldc < (n > 1 ? n : 1))
+  if ((ta != 0 && ta != 1) || (tb != 0 && tb != 1)) return COSMA_ERR_INVALID_ARG;
+  const int64_t a_cols = ta ? m : k, b_cols = tb ? k : n;
+  if (lda < (a_cols > 1 ? a_cols : 1) || ldb < (b_cols > 1 ? b_cols : 1) || ldc < (n > 1 ? n : 1))
     return COSMA_ERR_INVALID_ARG;
   if (m == 0 || n == 0) return COSMA_OK;
   if (!C) return COSMA_ERR_INVALID_ARG;
@@ -173,30 +174,48 @@ int check_args(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, cons
 // Workspace of a plan; without operand pointers, the most any operands need.
 long long total_workspace(int64_t m, int64_t n, int64_t k, int dtype, const cosma_plan& p,
                           const void* A = nullptr, int64_t lda = 0, const void* B = nullptr,
-                          int64_t ldb = 0) {
+                          int64_t ldb = 0, int ta = 0, int tb = 0) {
   if (dtype == COSMA_F64_EMU_BF16) return emu_workspace_bytes(m, n, k, g_cfg);
-  if (dtype == COSMA_BF16) {
-    const bool pack_a = !A || (reinterpret_cast<uintptr_t>(A) & 15) || ((lda * 2) & 15);
-    return tc_workspace_bytes(m, n, k, p, pack_a, !B || !tc_b_direct(B, ldb));
-  }
-  return workspace_bytes(m, n, k, dtype, p);
+  if (dtype == COSMA_BF16) return tc_workspace_bytes(m, n, k, p, A, lda, ta, B, ldb, tb);
+  // FMA paths: split-k partials, then untransposed copies of transposed operands
+  const int w = dtype == COSMA_F32 ? 4 : 8;
+  long long b = workspace_bytes(m, n, k, dtype, p);
+  if (ta) b += (m * k * w + 255) / 256 * 256;
+  if (tb) b += (k * n * w + 255) / 256 * 256;
+  return b;
 }
 
+// C = alpha op(A) op(B) + beta C (op: transposed storage when ta / tb is 1).
 int run(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void* B, int64_t ldb,
-        void* C, int64_t ldc, int dtype, const cosma_plan* given, void* stream) {
-  int rc = check_args(m, n, k, A, lda, B, ldb, C, ldc, dtype);
+        void* C, int64_t ldc, int dtype, const cosma_plan* given, void* stream,
+        double alpha = 1.0, double beta = 0.0, int ta = 0, int tb = 0) {
+  const bool no_ab = k == 0 || alpha == 0.0;  // A and B are not read
+  int rc = check_args(m, n, no_ab ? 0 : k, no_ab ? nullptr : A, lda, no_ab ? nullptr : B, ldb, C,
+                      ldc, dtype, ta, tb);
+  if (rc == COSMA_OK && no_ab) {  // the leading dimensions still have to be valid
+    const int64_t a_cols = ta ? m : k, b_cols = tb ? k : n;
+    if (lda < (a_cols > 1 ? a_cols : 1) || ldb < (b_cols > 1 ? b_cols : 1))
+      rc = COSMA_ERR_INVALID_ARG;
+  }
   if (rc != COSMA_OK) return rc;
   if (m == 0 || n == 0) return COSMA_OK;
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lock(g_mu);
   DeviceState* s = state(&rc);
   if (!s) return rc;
-  if (k == 0) {
-    const size_t w = (size_t)elem_bytes_out(dtype);
-    count_launch();
-    return cudaMemset2DAsync(C, (size_t)ldc * w, 0, (size_t)n * w, (size_t)m, st) == cudaSuccess
-               ? COSMA_OK
-               : COSMA_ERR_CUDA;
+  if (no_ab) {  // C = beta C
+    GemmArgs gs{m, n, k, A, lda, B, ldb, C, ldc};
+    gs.beta = beta;
+    if (beta == 0.0) {
+      const size_t w = (size_t)elem_bytes_out(dtype);
+      count_launch();
+      return cudaMemset2DAsync(C, (size_t)ldc * w, 0, (size_t)n * w, (size_t)m, st) ==
+                     cudaSuccess
+                 ? COSMA_OK
+                 : COSMA_ERR_CUDA;
+    }
+    if (beta == 1.0) return COSMA_OK;
+    return launch_scale(dtype, gs, st) == 0 ? COSMA_OK : COSMA_ERR_CUDA;
   }
   cosma_plan p;
   if (given) {
@@ -207,21 +226,42 @@ int run(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void*
     rc = plan_gemm(m, n, k, dtype, g_cfg.selector, s->info, g_cfg, &p, !capturing(st));
     if (rc != COSMA_OK) return rc;
   }
-  const long long need = total_workspace(m, n, k, dtype, p, A, lda, B, ldb);
+  const long long need = total_workspace(m, n, k, dtype, p, A, lda, B, ldb, ta, tb);
   void* ws = nullptr;
   long long have = 0;
   rc = workspace(s, need, st, &ws, &have);
   if (rc != COSMA_OK) return rc;
-  const GemmArgs g{m, n, k, A, lda, B, ldb, C, ldc};
+  GemmArgs g{m, n, k, A, lda, B, ldb, C, ldc};
+  g.alpha = alpha;
+  g.beta = beta;
+  g.trans_a = ta;
+  g.trans_b = tb;
   const Sched sc = sched_from_plan(m, n, k, p);
   const long long wl = g_cfg.wait_limit > 0 ? g_cfg.wait_limit : kDefaultWaitLimit;
   int err = 0;
   switch (p.kernel) {
     case COSMA_KERNEL_SIMT_F64:
-    case COSMA_KERNEL_SIMT_F32:
-      err = launch_simt(dtype, g, sc, ws, s->d_status, st);
+    case COSMA_KERNEL_SIMT_F32: {
+      // Transposed operands are first copied untransposed after the partials.
+      const int w = dtype == COSMA_F32 ? 4 : 8;
+      uint8_t* extra = static_cast<uint8_t*>(ws) + workspace_bytes(m, n, k, dtype, p);
+      if (ta) {
+        err = launch_transpose(w, A, k, m, lda, extra, k, st);
+        g.A = extra;
+        g.lda = k;
+        g.trans_a = 0;
+        extra += (m * k * w + 255) / 256 * 256;
+      }
+      if (!err && tb) {
+        err = launch_transpose(w, B, n, k, ldb, extra, n, st);
+        g.B = extra;
+        g.ldb = n;
+        g.trans_b = 0;
+      }
+      if (!err) err = launch_simt(dtype, g, sc, ws, s->d_status, st);
       if (!err && p.pk > 1) err = launch_reduce(dtype, g, p.pk, ws, st);
       break;
+    }
     case COSMA_KERNEL_TC_BF16:
       err = launch_tc_bf16(g, sc, p, ws, have, s->d_status, wl, st);
       break;
@@ -332,6 +372,13 @@ void cosma_finalize(void) {
 int cosma_gemm(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void* B,
                int64_t ldb, void* C, int64_t ldc, int dtype, void* stream) {
   return run(m, n, k, A, lda, B, ldb, C, ldc, dtype, nullptr, stream);
+}
+
+int cosma_gemm_ex(int trans_a, int trans_b, int64_t m, int64_t n, int64_t k, double alpha,
+                  const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C,
+                  int64_t ldc, int dtype, void* stream) {
+  return run(m, n, k, A, lda, B, ldb, C, ldc, dtype, nullptr, stream, alpha, beta, trans_a,
+             trans_b);
 }
 
 int cosma_gemm_planned(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda,

@@ -212,6 +212,7 @@ struct EmuArgs {
   int* status;
   long long wait_limit;
   unsigned int* lockstep;  // cooperative launches: per-unit progress counter (zeroed), else null
+  double alpha, beta_c;    // C = alpha A B + beta_c C (C read only when beta_c != 0)
 };
 
 constexpr int NACC = 3;            // accumulator buffers in tensor memory (columns 0..383)
@@ -355,9 +356,12 @@ __device__ __forceinline__ void emu_epilogue(const EmuArgs& a, int unit_cta, int
           if (col < a.sch.n) {
             const int eb = a.eB[col];
             const double val = (double)Th[c + j] + (double)__uint_as_float(t[j]);
-            dst[col] = (ea == kExpNone || eb == kExpNone)
+            double v = (ea == kExpNone || eb == kExpNone)
                            ? 0.0
                            : scale_pow2(val, ea + eb + 2 - 2 * a.beta);
+            if (a.alpha != 1.0) v *= a.alpha;
+            if (a.beta_c != 0.0) v = fma(a.beta_c, dst[col], v);
+            dst[col] = v;
           }
         }
       }
@@ -781,11 +785,25 @@ int emu_check_config(const cosma_config& cfg) {
   return COSMA_OK;
 }
 
-int emu_prepare_a(const double* A, int64_t m, int64_t k, int64_t lda, int* eA, void* SA,
-                  int64_t slice_rows, int* status, const cosma_config& cfg, cudaStream_t st) {
+int emu_prepare_a(const double* A, int64_t m, int64_t k, int64_t lda, int trans, int* eA,
+                  void* SA, int64_t slice_rows, int* status, const cosma_config& cfg,
+                  cudaStream_t st) {
   const int s = emu_slices(cfg), beta = emu_bits(cfg);
   const int64_t kp = rup(k, 8);
   if (m <= 0) return COSMA_OK;
+  if (trans) {  // A stored as k x m: its rows are columns of the stored matrix
+    if ((k + 31) / 32 > 65535) return COSMA_ERR_UNSUPPORTED;
+    if (cudaMemsetAsync(eA, 0x80, (size_t)m * 4, st) != cudaSuccess)
+      return (int)cudaGetLastError();
+    dim3 g1((unsigned)((m + 255) / 256), (unsigned)((k + 255) / 256));
+    col_exp_kernel<<<g1, 256, 0, st>>>(A, k, m, lda, eA, status);
+    count_launch();
+    dim3 g2((unsigned)((m + 31) / 32), (unsigned)((k + 31) / 32));
+    split_b_kernel<<<g2, dim3(32, 8), 0, st>>>(A, k, m, lda, eA, static_cast<__nv_bfloat16*>(SA),
+                                               kp, slice_rows, s, beta);
+    count_launch();
+    return (int)cudaGetLastError();
+  }
   const int64_t rb = m < 65535LL * 16 ? m : 65535LL * 16;
   row_exp_kernel<<<(unsigned)rb, 256, 0, st>>>(A, m, k, lda, eA, status);
   count_launch();
@@ -798,11 +816,24 @@ int emu_prepare_a(const double* A, int64_t m, int64_t k, int64_t lda, int* eA, v
   return (int)cudaGetLastError();
 }
 
-int emu_prepare_b(const double* B, int64_t k, int64_t n, int64_t ldb, int* eB, void* SB,
-                  int64_t slice_rows, int* status, const cosma_config& cfg, cudaStream_t st) {
+int emu_prepare_b(const double* B, int64_t k, int64_t n, int64_t ldb, int trans, int* eB,
+                  void* SB, int64_t slice_rows, int* status, const cosma_config& cfg,
+                  cudaStream_t st) {
   const int s = emu_slices(cfg), beta = emu_bits(cfg);
   const int64_t kp = rup(k, 8);
   if (n <= 0) return COSMA_OK;
+  if (trans) {  // B stored as n x k: its columns are rows of the stored matrix
+    const int64_t rb = n < 65535LL * 16 ? n : 65535LL * 16;
+    row_exp_kernel<<<(unsigned)rb, 256, 0, st>>>(B, n, k, ldb, eB, status);
+    count_launch();
+    int64_t blocks = (n * k + 255) / 256;
+    if (blocks > 152LL * 64) blocks = 152LL * 64;
+    split_a_kernel<<<(unsigned)blocks, 256, 0, st>>>(B, n, k, ldb, eB,
+                                                     static_cast<__nv_bfloat16*>(SB), kp,
+                                                     slice_rows, s, beta);
+    count_launch();
+    return (int)cudaGetLastError();
+  }
   if ((k + 31) / 32 > 65535) return COSMA_ERR_UNSUPPORTED;
   if (cudaMemsetAsync(eB, 0x80, (size_t)n * 4, st) != cudaSuccess) return (int)cudaGetLastError();
   dim3 g1((unsigned)((n + 255) / 256), (unsigned)((k + 255) / 256));
@@ -817,8 +848,9 @@ int emu_prepare_b(const double* B, int64_t k, int64_t n, int64_t ldb, int* eB, v
 
 int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cosma_config& cfg,
                  const int* eA, const void* SA, int64_t a_slice_rows, const int* eB,
-                 const void* SB, int64_t b_slice_rows, double* C, int64_t ldc,
-                 unsigned int* lockstep, int* status, long long wait_limit, cudaStream_t st) {
+                 const void* SB, int64_t b_slice_rows, double* C, int64_t ldc, double alpha,
+                 double beta_c, unsigned int* lockstep, int* status, long long wait_limit,
+                 cudaStream_t st) {
   const int s = emu_slices(cfg), beta = emu_bits(cfg);
   const Sched sch = sched_from_plan(m, n, k, p);
   const bool pairs = sch.tile_m == 2 * EBM;
@@ -854,6 +886,8 @@ int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cos
   args.status = status;
   args.wait_limit = wait_limit;
   args.lockstep = nullptr;
+  args.alpha = alpha;
+  args.beta_c = beta_c;
   // Super-chunk: short enough for the slice panels of a wave of tiles to stay in
   // L2 (2048 k), and for every level sum of a chunk to fit in int32 exactly
   // (at most s pairs x chunk x 2^(2 beta - 2)).
@@ -922,12 +956,14 @@ int launch_emu_bf16(const GemmArgs& g, const cosma_plan& p, const cosma_config& 
       (reinterpret_cast<uintptr_t>(g.C) & 7))
     return COSMA_ERR_INVALID_ARG;
   const EmuWorkspace e = emu_carve(ws, m, n, k, cfg);
-  rc = emu_prepare_a(static_cast<const double*>(g.A), m, k, g.lda, e.eA, e.SA, m, status, cfg, st);
+  rc = emu_prepare_a(static_cast<const double*>(g.A), m, k, g.lda, g.trans_a, e.eA, e.SA, m,
+                     status, cfg, st);
   if (rc != 0) return rc;
-  rc = emu_prepare_b(static_cast<const double*>(g.B), k, n, g.ldb, e.eB, e.SB, n, status, cfg, st);
+  rc = emu_prepare_b(static_cast<const double*>(g.B), k, n, g.ldb, g.trans_b, e.eB, e.SB, n,
+                     status, cfg, st);
   if (rc != 0) return rc;
   return emu_multiply(m, n, k, p, cfg, e.eA, e.SA, m, e.eB, e.SB, n, static_cast<double*>(g.C),
-                      g.ldc, e.lockstep, status, wait_limit, st);
+                      g.ldc, g.alpha, g.beta, e.lockstep, status, wait_limit, st);
 }
 
 }  // namespace cosma

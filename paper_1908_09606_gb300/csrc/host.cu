@@ -215,8 +215,8 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
       if ((rc = ok(cudaStreamWaitEvent(st, ev_a[i], 0))) != COSMA_OK) return rc;
       if (emu) {
         rc = emu_prepare_a(reinterpret_cast<const double*>(Ad) + r0 * lda_d, r1 - r0, k, lda_d,
-                           ew.eA + r0, static_cast<uint8_t*>(ew.SA) + (size_t)r0 * ew.kp * 2, m,
-                           ctx.status, ctx.cfg, st);
+                           0, ew.eA + r0, static_cast<uint8_t*>(ew.SA) + (size_t)r0 * ew.kp * 2,
+                           m, ctx.status, ctx.cfg, st);
         if (rc > 0) return COSMA_ERR_CUDA;
         if (rc < 0) return rc;
       }
@@ -226,9 +226,9 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
         if (i == 0) {
           if ((rc = ok(cudaStreamWaitEvent(st, ev_b[j], 0))) != COSMA_OK) return rc;
           if (emu) {
-            rc = emu_prepare_b(reinterpret_cast<const double*>(Bd) + c0, k, nb, ldb_d, ew.eB + c0,
-                               static_cast<uint8_t*>(ew.SB) + (size_t)c0 * ew.kp * 2, n,
-                               ctx.status, ctx.cfg, st);
+            rc = emu_prepare_b(reinterpret_cast<const double*>(Bd) + c0, k, nb, ldb_d, 0,
+                               ew.eB + c0, static_cast<uint8_t*>(ew.SB) + (size_t)c0 * ew.kp * 2,
+                               n, ctx.status, ctx.cfg, st);
             if (rc > 0) return COSMA_ERR_CUDA;
             if (rc < 0) return rc;
           }
@@ -241,8 +241,8 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
           rc = emu_multiply(mb, nb, k, p, ctx.cfg, ew.eA + r0,
                             static_cast<uint8_t*>(ew.SA) + (size_t)r0 * ew.kp * 2, m, ew.eB + c0,
                             static_cast<uint8_t*>(ew.SB) + (size_t)c0 * ew.kp * 2, n,
-                            reinterpret_cast<double*>(Cblk), ldc_d, ew.lockstep, ctx.status,
-                            ctx.wait_limit, st);
+                            reinterpret_cast<double*>(Cblk), ldc_d, 1.0, 0.0, ew.lockstep,
+                            ctx.status, ctx.wait_limit, st);
           if (rc > 0) return COSMA_ERR_CUDA;
           if (rc < 0) return rc;
         } else {

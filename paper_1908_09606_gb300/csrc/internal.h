@@ -71,10 +71,19 @@ struct GemmArgs {
   const void* A; int64_t lda;
   const void* B; int64_t ldb;
   void* C; int64_t ldc;
+  double alpha = 1.0, beta = 0.0;  // C = alpha A B + beta C (beta == 0: C is not read)
+  // 1: the operand is stored transposed (A as k x m with lda >= m, B as n x k with
+  // ldb >= k).  Only the bf16 and emulated launchers take transposed operands.
+  int trans_a = 0, trans_b = 0;
 };
 int launch_simt(int dtype, const GemmArgs& g, const Sched& s, void* partial, int* status,
                 cudaStream_t st);
 int launch_reduce(int dtype, const GemmArgs& g, int pk, const void* partial, cudaStream_t st);
+// C = beta C (beta == 0: C = 0 without reading it), for k == 0 or alpha == 0.
+int launch_scale(int dtype, const GemmArgs& g, cudaStream_t st);
+// dst (cols x rows, ld_dst) = transpose of src (rows x cols, ld_src), 4- or 8-byte elements.
+int launch_transpose(int elem_bytes, const void* src, int64_t rows, int64_t cols,
+                     int64_t ld_src, void* dst, int64_t ld_dst, cudaStream_t st);
 
 // Emulated FP64 (emu.cu): workspace layout and the three phases of a product.
 struct EmuWorkspace {
@@ -90,15 +99,20 @@ EmuWorkspace emu_carve(void* ws, int64_t m, int64_t n, int64_t k, const cosma_co
 int emu_check_config(const cosma_config& cfg);
 // Exponents and slices of rows [0, m) of A into eA[0..m) and SA (slice_rows
 // rows between slices); of columns [0, n) of B likewise.
-int emu_prepare_a(const double* A, int64_t m, int64_t k, int64_t lda, int* eA, void* SA,
-                  int64_t slice_rows, int* status, const cosma_config& cfg, cudaStream_t st);
-int emu_prepare_b(const double* B, int64_t k, int64_t n, int64_t ldb, int* eB, void* SB,
-                  int64_t slice_rows, int* status, const cosma_config& cfg, cudaStream_t st);
-// C[m x n] from prepared slices, under plan p (an F64_EMU_BF16 plan for m x n x k).
+// trans = 1: the operand is stored transposed (A as k x m, B as n x k).
+int emu_prepare_a(const double* A, int64_t m, int64_t k, int64_t lda, int trans, int* eA,
+                  void* SA, int64_t slice_rows, int* status, const cosma_config& cfg,
+                  cudaStream_t st);
+int emu_prepare_b(const double* B, int64_t k, int64_t n, int64_t ldb, int trans, int* eB,
+                  void* SB, int64_t slice_rows, int* status, const cosma_config& cfg,
+                  cudaStream_t st);
+// C[m x n] = alpha (product of the prepared slices) + beta C, under plan p (an
+// F64_EMU_BF16 plan for m x n x k).
 int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cosma_config& cfg,
                  const int* eA, const void* SA, int64_t a_slice_rows, const int* eB,
-                 const void* SB, int64_t b_slice_rows, double* C, int64_t ldc,
-                 unsigned int* lockstep, int* status, long long wait_limit, cudaStream_t st);
+                 const void* SB, int64_t b_slice_rows, double* C, int64_t ldc, double alpha,
+                 double beta, unsigned int* lockstep, int* status, long long wait_limit,
+                 cudaStream_t st);
 int launch_emu_bf16(const GemmArgs& g, const cosma_plan& p, const cosma_config& cfg, void* ws,
                     long long ws_bytes, int* status, long long wait_limit, cudaStream_t st);
 

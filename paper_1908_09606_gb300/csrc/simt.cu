@@ -40,9 +40,11 @@ simt_gemm_kernel(GemmArgs g, Sched s, T* partial) {
       dst = static_cast<T*>(g.C);
       ld = g.ldc;
     }
+    // split-k partials are raw sums; the Reduce applies alpha and beta
+    const T al = s.pk > 1 ? T(1) : (T)g.alpha, be = s.pk > 1 ? T(0) : (T)g.beta;
     simt_tile<T, BM, BN, BK, TM, TN>(A, g.lda, B, g.ldb, dst, ld, g.m, g.n, u.tile_row * BM,
                                      u.tile_col * BN, u.kb0 * (int64_t)s.k_block,
-                                     min(u.kb1 * (int64_t)s.k_block, g.k), sm);
+                                     min(u.kb1 * (int64_t)s.k_block, g.k), sm, al, be);
   }
 }
 
@@ -70,24 +72,26 @@ simt_f32_kernel(GemmArgs g, Sched s, float* partial, int vec_c) {
       ld = g.ldc;
       vec = vec_c != 0;
     }
+    const float al = s.pk > 1 ? 1.f : (float)g.alpha, be = s.pk > 1 ? 0.f : (float)g.beta;
     f32_tile<BM, VEC>(A, g.lda, B, g.ldb, dst, ld, g.m, g.n, u.tile_row * BM,
                       u.tile_col * F32_BN, u.kb0 * (int64_t)s.k_block,
-                      min(u.kb1 * (int64_t)s.k_block, g.k), vec, sm);
+                      min(u.kb1 * (int64_t)s.k_block, g.k), vec, sm, al, be);
   }
 }
 
-// Reduce over the k dimension of the grid: C = sum_{ks = 0}^{pk-1} P[ks], in
-// that fixed order, so the result does not depend on scheduling.
+// Reduce over the k dimension of the grid: C = alpha sum_{ks = 0}^{pk-1} P[ks]
+// (+ beta C), the sum in that fixed order, so the result does not depend on
+// scheduling.
 template <typename T>
 __global__ void reduce_kernel(int64_t m, int64_t n, int pk, const T* __restrict__ partial,
-                              T* __restrict__ C, int64_t ldc) {
+                              T* __restrict__ C, int64_t ldc, T alpha, T beta) {
   const int64_t total = m * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     T acc = partial[e];
     for (int q = 1; q < pk; ++q) acc += partial[(int64_t)q * total + e];
     const int64_t r = e / n, c = e - r * n;
-    C[r * ldc + c] = acc;
+    store_ab(&C[r * ldc + c], acc, alpha, beta);
   }
 }
 
@@ -101,7 +105,67 @@ int launch_tile(const GemmArgs& g, const Sched& s, void* partial, cudaStream_t s
   return (int)cudaGetLastError();
 }
 
+// C = beta C over m x n (beta == 0: zeros, C not read).
+template <typename T>
+__global__ void scale_kernel(int64_t m, int64_t n, T* __restrict__ C, int64_t ldc, T beta) {
+  const int64_t total = m * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / n, c = e - r * n;
+    T* p = C + r * ldc + c;
+    *p = beta == T(0) ? T(0) : beta * *p;
+  }
+}
+
+// dst[j][i] = src[i][j] for a rows x cols src; 32 x 32 tiles through shared memory.
+template <typename T>
+__global__ void transpose_kernel(const T* __restrict__ src, int64_t rows, int64_t cols,
+                                 int64_t ld_src, T* __restrict__ dst, int64_t ld_dst) {
+  __shared__ T tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[i][threadIdx.x] = src[r * ld_src + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t c = c0 + i, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) dst[c * ld_dst + r] = tile[threadIdx.x][i];
+  }
+}
+
 }  // namespace
+
+int launch_scale(int dtype, const GemmArgs& g, cudaStream_t st) {
+  const int64_t total = g.m * g.n;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks < 1) return 0;
+  if (dtype == COSMA_F32 || dtype == COSMA_BF16)
+    scale_kernel<float><<<(unsigned)blocks, 256, 0, st>>>(g.m, g.n, static_cast<float*>(g.C),
+                                                          g.ldc, (float)g.beta);
+  else
+    scale_kernel<double><<<(unsigned)blocks, 256, 0, st>>>(g.m, g.n, static_cast<double*>(g.C),
+                                                           g.ldc, g.beta);
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
+int launch_transpose(int elem_bytes, const void* src, int64_t rows, int64_t cols, int64_t ld_src,
+                     void* dst, int64_t ld_dst, cudaStream_t st) {
+  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+  if ((rows + 31) / 32 > 65535) return COSMA_ERR_UNSUPPORTED;
+  if (elem_bytes == 8)
+    transpose_kernel<double><<<grid, dim3(32, 8), 0, st>>>(static_cast<const double*>(src), rows,
+                                                           cols, ld_src, static_cast<double*>(dst),
+                                                           ld_dst);
+  else
+    transpose_kernel<float><<<grid, dim3(32, 8), 0, st>>>(static_cast<const float*>(src), rows,
+                                                          cols, ld_src, static_cast<float*>(dst),
+                                                          ld_dst);
+  count_launch();
+  return (int)cudaGetLastError();
+}
 
 int launch_simt(int dtype, const GemmArgs& g, const Sched& s, void* partial, int* status,
                 cudaStream_t st) {
@@ -139,13 +203,15 @@ int launch_simt(int dtype, const GemmArgs& g, const Sched& s, void* partial, int
 int launch_reduce(int dtype, const GemmArgs& g, int pk, const void* partial, cudaStream_t st) {
   const int64_t total = g.m * g.n;
   int64_t blocks = (total + 255) / 256;
-  if (blocks > 148 * 32) blocks = 148 * 32;
+  if (blocks > 152 * 32) blocks = 152 * 32;
   if (dtype == COSMA_F64)
     reduce_kernel<double><<<(unsigned)blocks, 256, 0, st>>>(
-        g.m, g.n, pk, static_cast<const double*>(partial), static_cast<double*>(g.C), g.ldc);
+        g.m, g.n, pk, static_cast<const double*>(partial), static_cast<double*>(g.C), g.ldc,
+        g.alpha, g.beta);
   else
     reduce_kernel<float><<<(unsigned)blocks, 256, 0, st>>>(
-        g.m, g.n, pk, static_cast<const float*>(partial), static_cast<float*>(g.C), g.ldc);
+        g.m, g.n, pk, static_cast<const float*>(partial), static_cast<float*>(g.C), g.ldc,
+        (float)g.alpha, (float)g.beta);
   count_launch();
   return (int)cudaGetLastError();
 }

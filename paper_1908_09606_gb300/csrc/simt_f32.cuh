@@ -61,7 +61,7 @@ __device__ __forceinline__ void f32_tile(const float* __restrict__ A, int64_t ld
                                          const float* __restrict__ B, int64_t ldb, float* dst,
                                          int64_t ld, int64_t m, int64_t n, int64_t row0,
                                          int64_t col0, int64_t kbeg, int64_t kend, bool vec_out,
-                                         F32Smem<BM>& sm) {
+                                         F32Smem<BM>& sm, float alpha = 1.f, float beta = 0.f) {
   constexpr int NT = f32_threads<BM>();
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -155,6 +155,8 @@ __device__ __forceinline__ void f32_tile(const float* __restrict__ A, int64_t ld
   }
   cp_async_wait<0>();
 
+  // C = alpha acc + beta C (C read only when beta != 0)
+  const bool plain = alpha == 1.f && beta == 0.f;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int64_t r = row0 + ar + 8 * i;
@@ -163,7 +165,15 @@ __device__ __forceinline__ void f32_tile(const float* __restrict__ A, int64_t ld
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int64_t c = col0 + bc + 16 * h;
-      if (vec_out && c + 4 <= n) {
+      if (!plain) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (c + j >= n) continue;
+          float v = alpha * acc[i][4 * h + j];
+          if (beta != 0.f) v = fmaf(beta, drow[c + j], v);
+          drow[c + j] = v;
+        }
+      } else if (vec_out && c + 4 <= n) {
         *reinterpret_cast<float4*>(drow + c) =
             make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
       } else {

@@ -19,13 +19,23 @@ struct SimtSmem {
   T Bs[2][BK][BN];
 };
 
-// dst[(row0 + i) * ld + col0 + j] = sum_{t in [kbeg, kend)} A[row0+i][t] B[t][col0+j]
+// Value stored for one C entry: alpha acc + beta c, with c read only when beta != 0.
+template <typename T>
+__device__ __forceinline__ void store_ab(T* p, T acc, T alpha, T beta) {
+  T v = alpha == T(1) ? acc : alpha * acc;
+  if (beta != T(0)) v = fma(beta, *p, v);
+  *p = v;
+}
+
+// dst[(row0 + i) * ld + col0 + j] = alpha sum_{t in [kbeg, kend)} A[row0+i][t] B[t][col0+j]
+//                                   (+ beta dst[...] when beta != 0)
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 __device__ __forceinline__ void simt_tile(const T* __restrict__ A, int64_t lda,
                                           const T* __restrict__ B, int64_t ldb, T* dst, int64_t ld,
                                           int64_t m, int64_t n, int64_t row0, int64_t col0,
                                           int64_t kbeg, int64_t kend,
-                                          SimtSmem<T, BM, BN, BK>& sm) {
+                                          SimtSmem<T, BM, BN, BK>& sm, T alpha = T(1),
+                                          T beta = T(0)) {
   static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
   static_assert(BN / TN == 16 && BM / TM == 16, "16 x 16 thread grid");
   constexpr int V = VecW<T>::V;
@@ -104,7 +114,7 @@ __device__ __forceinline__ void simt_tile(const T* __restrict__ A, int64_t lda,
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int64_t c = col0 + (j / V) * (16 * V) + tx * V + (j % V);
-      if (c < n) dst[r * ld + c] = acc[i][j];
+      if (c < n) store_ab(&dst[r * ld + c], acc[i][j], alpha, beta);
     }
   }
 }

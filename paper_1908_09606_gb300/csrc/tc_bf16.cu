@@ -88,6 +88,7 @@ struct TcArgs {
   int* status;
   long long wait_limit;
   int vec_ok;  // C rows 16-byte aligned
+  float alpha, beta;  // C = alpha A B + beta C (C read only when beta != 0)
 };
 
 template <int BN, int STAGES>
@@ -102,7 +103,17 @@ struct Layout {
 };
 
 __device__ __forceinline__ void store_row32(float* dst, int64_t col0, int64_t n, const uint32_t (&r)[32],
-                                            bool vec) {
+                                            bool vec, float alpha = 1.f, float beta = 0.f) {
+  if (alpha != 1.f || beta != 0.f) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (col0 + j >= n) continue;
+      float v = alpha * __uint_as_float(r[j]);
+      if (beta != 0.f) v = fmaf(beta, dst[j], v);
+      dst[j] = v;
+    }
+    return;
+  }
   if (vec && col0 + 32 <= n) {
     float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
@@ -116,7 +127,7 @@ __device__ __forceinline__ void store_row32(float* dst, int64_t col0, int64_t n,
   }
 }
 
-template <int BN, int STAGES, bool B_MN>
+template <int BN, int STAGES, bool A_MN, bool B_MN>
 __global__ void __launch_bounds__(192, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                TcArgs a) {
@@ -172,7 +183,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) { ok = false; break; }
           tc::mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES);
           uint8_t* sa = smem + stage * L::STAGE_BYTES;
-          tc::tma_load_2d(sa, &tmA, &full[stage], (int32_t)(kb * BK), (int32_t)(u.tile_row * BM));
+          if constexpr (A_MN) {
+#pragma unroll
+            for (int j = 0; j < BM / 64; ++j)  // box j: rows j*64.. of the tile, k rows kb*64..
+              tc::tma_load_2d(sa + j * (64 * BK * 2), &tmA, &full[stage],
+                              (int32_t)(u.tile_row * BM + j * 64), (int32_t)(kb * BK));
+          } else {
+            tc::tma_load_2d(sa, &tmA, &full[stage], (int32_t)(kb * BK),
+                            (int32_t)(u.tile_row * BM));
+          }
           if constexpr (B_MN) {
 #pragma unroll
             for (int j = 0; j < BN / 64; ++j)  // box j: columns j*64.., k rows kb*64..
@@ -201,7 +220,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
   } else if (warp == 1) {
     if (tc::elect_one()) {
-      constexpr uint32_t idesc = B_MN ? tc::idesc_bf16_f32_bmn(BM, BN) : tc::idesc_bf16_f32(BM, BN);
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN) | (A_MN ? (1u << 15) : 0u) |
+                                 (B_MN ? (1u << 16) : 0u);
       int stage = 0;
       uint32_t ph = 0, acc = 0;
       uint32_t aph[2] = {0, 0};
@@ -221,8 +241,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             // B MN-major: 16 k rows of 128 bytes per step; boxes 64 x BK apart
             const uint64_t db = B_MN ? tc::smem_desc_mn_sw128(sb + kk * 16 * 128, 64 * BK * 2, 1024)
                                      : tc::smem_desc_sw128(sb + kk * 32);
-            tc::mma_bf16(d, tc::smem_desc_sw128(sa + kk * 32), db, idesc,
-                         (kb > u.kb0 || kk > 0) ? 1u : 0u);
+            const uint64_t da = A_MN ? tc::smem_desc_mn_sw128(sa + kk * 16 * 128, 64 * BK * 2, 1024)
+                                     : tc::smem_desc_sw128(sa + kk * 32);
+            tc::mma_bf16(d, da, db, idesc, (kb > u.kb0 || kk > 0) ? 1u : 0u);
           }
           tc::mma_commit(&empty[stage]);
           if (++stage == STAGES) { stage = 0; ph ^= 1; }
@@ -259,7 +280,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         tc::tmem_ld_32x32(tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN + c, r);
         tc::tmem_wait_ld();
         const int64_t col0 = u.tile_col * BN + c;
-        if (dst_row && col0 < a.s.n) store_row32(dst_row + col0, col0, a.s.n, r, vec);
+        if (dst_row && col0 < a.s.n) {
+          if (a.s.pk > 1) store_row32(dst_row + col0, col0, a.s.n, r, vec);
+          else store_row32(dst_row + col0, col0, a.s.n, r, vec, a.alpha, a.beta);
+        }
       }
       tc::tc_fence_before();
       __syncwarp();
@@ -275,19 +299,19 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   }
 }
 
-template <int BN, int STAGES, bool B_MN>
+template <int BN, int STAGES, bool A_MN, bool B_MN>
 int launch_kernel(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& args,
                   cudaStream_t st) {
   using L = Layout<BN, STAGES>;
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES, B_MN>,
+    attr = cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES, A_MN, B_MN>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC);
   });
   if (attr != cudaSuccess) return (int)attr;
   prof_mark(st, true);
-  tc_gemm_kernel<BN, STAGES, B_MN><<<args.s.ctas, 192, L::ALLOC, st>>>(ta, tb, args);
+  tc_gemm_kernel<BN, STAGES, A_MN, B_MN><<<args.s.ctas, 192, L::ALLOC, st>>>(ta, tb, args);
   prof_mark(st, false);
   count_launch();
   return (int)cudaGetLastError();
@@ -299,9 +323,30 @@ inline int64_t round_up(int64_t x, int64_t r) { return (x + r - 1) / r * r; }
 
 bool tc_b_direct(const void* B, int64_t ldb);
 
+// Bytes of the operand copies launch_tc_bf16 makes (see there).
+struct TcCopies {
+  bool a_mn, b_mn;      // operands multiplied MN-major
+  bool pack_a, copy_b;  // A copied to the workspace; B copied (transposed or packed)
+  bool b_transpose;     // the B copy is a transpose (else a packed copy of B^T)
+};
+
+static TcCopies tc_copies(const void* A, int64_t lda, int trans_a, const void* B, int64_t ldb,
+                          int trans_b) {
+  TcCopies c;
+  const bool a_ok = A && (reinterpret_cast<uintptr_t>(A) & 15) == 0 && ((lda * 2) & 15) == 0;
+  const bool b_ok = B && (reinterpret_cast<uintptr_t>(B) & 15) == 0 && ((ldb * 2) & 15) == 0;
+  c.a_mn = trans_a != 0;
+  c.pack_a = !a_ok;
+  c.b_mn = !trans_b && b_ok;
+  c.copy_b = !c.b_mn && !(trans_b && b_ok);
+  c.b_transpose = !trans_b;
+  return c;
+}
+
 int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void* ws,
                    long long ws_bytes, int* status, long long wait_limit, cudaStream_t st) {
-  const int64_t kp = round_up(g.k, 8);
+  const int64_t kp = round_up(g.k, 8), mp = round_up(g.m, 8);
+  const TcCopies cp = tc_copies(g.A, g.lda, g.trans_a, g.B, g.ldb, g.trans_b);
   uint8_t* w = static_cast<uint8_t*>(ws);
   long long off = 0;
   float* partial = nullptr;
@@ -309,42 +354,52 @@ int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void*
     partial = reinterpret_cast<float*>(w + off);
     off += round_up((long long)p.pk * g.m * g.n * 4, 256);
   }
-  const bool b_mn = tc_b_direct(g.B, g.ldb);
-  __nv_bfloat16* Bt = nullptr;
-  if (!b_mn) {
-    Bt = reinterpret_cast<__nv_bfloat16*>(w + off);
+  // B operand: in place (MN-major when stored k x n, K-major when stored n x k),
+  // else a K-major n x kp copy (a transpose of k x n, or a pitch-padded copy of n x k).
+  const __nv_bfloat16* Buse = static_cast<const __nv_bfloat16*>(g.B);
+  int64_t ldb = g.ldb;
+  if (cp.copy_b) {
+    __nv_bfloat16* Bt = reinterpret_cast<__nv_bfloat16*>(w + off);
     off += round_up(g.n * kp * 2, 256);
+    if (off > ws_bytes) return COSMA_ERR_NO_WORKSPACE;
+    if (cp.b_transpose) {
+      dim3 grid((unsigned)((g.n + 31) / 32), (unsigned)((g.k + 31) / 32));
+      if (grid.y > 65535) return COSMA_ERR_UNSUPPORTED;
+      transpose_bf16<<<grid, dim3(32, 8), 0, st>>>(static_cast<const __nv_bfloat16*>(g.B), g.k,
+                                                   g.n, g.ldb, Bt, kp);
+      count_launch();
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return (int)e;
+    } else if (cudaMemcpy2DAsync(Bt, kp * 2, g.B, g.ldb * 2, g.k * 2, g.n,
+                                 cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+      return (int)cudaGetLastError();
+    }
+    Buse = Bt;
+    ldb = kp;
   }
+  // A operand: in place, else a copy with a 16-byte pitch (m x kp, or k x mp when
+  // stored transposed).
   const __nv_bfloat16* Ause = static_cast<const __nv_bfloat16*>(g.A);
   int64_t lda = g.lda;
-  const bool pack_a = (reinterpret_cast<uintptr_t>(g.A) & 15) || ((g.lda * 2) & 15);
-  if (pack_a) {
+  if (cp.pack_a) {
     __nv_bfloat16* Ap = reinterpret_cast<__nv_bfloat16*>(w + off);
-    off += round_up(g.m * kp * 2, 256);
+    const int64_t rows = cp.a_mn ? g.k : g.m, cols = cp.a_mn ? g.m : g.k;
+    const int64_t pitch = cp.a_mn ? mp : kp;
+    off += round_up(rows * pitch * 2, 256);
     if (off > ws_bytes) return COSMA_ERR_NO_WORKSPACE;
-    if (cudaMemcpy2DAsync(Ap, kp * 2, g.A, g.lda * 2, g.k * 2, g.m, cudaMemcpyDeviceToDevice,
+    if (cudaMemcpy2DAsync(Ap, pitch * 2, g.A, g.lda * 2, cols * 2, rows, cudaMemcpyDeviceToDevice,
                           st) != cudaSuccess)
       return (int)cudaGetLastError();
     Ause = Ap;
-    lda = kp;
+    lda = pitch;
   }
   if (off > ws_bytes) return COSMA_ERR_NO_WORKSPACE;
-  if (!b_mn) {
-    dim3 grid((unsigned)((g.n + 31) / 32), (unsigned)((g.k + 31) / 32));
-    if (grid.y > 65535) return COSMA_ERR_UNSUPPORTED;
-    transpose_bf16<<<grid, dim3(32, 8), 0, st>>>(static_cast<const __nv_bfloat16*>(g.B), g.k, g.n,
-                                                 g.ldb, Bt, kp);
-    count_launch();
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return (int)e;
-  }
   CUtensorMap ta, tb;
-  int rc = encode_tmap_bf16(&ta, Ause, g.m, g.k, lda, BK, BM);
+  int rc = cp.a_mn ? encode_tmap_bf16(&ta, Ause, g.k, g.m, lda, 64, BK)   // k rows of m
+                   : encode_tmap_bf16(&ta, Ause, g.m, g.k, lda, BK, BM);  // m rows of k
   if (rc != COSMA_OK) return rc;
-  if (b_mn)  // B itself: k rows of n, 64 x 64 boxes
-    rc = encode_tmap_bf16(&tb, g.B, g.k, g.n, g.ldb, 64, BK);
-  else
-    rc = encode_tmap_bf16(&tb, Bt, g.n, g.k, kp, BK, p.tile_n);
+  rc = cp.b_mn ? encode_tmap_bf16(&tb, Buse, g.k, g.n, ldb, 64, BK)        // k rows of n
+               : encode_tmap_bf16(&tb, Buse, g.n, g.k, ldb, BK, p.tile_n);  // n rows of k
   if (rc != COSMA_OK) return rc;
   TcArgs args;
   args.s = s;
@@ -354,18 +409,24 @@ int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void*
   args.status = status;
   args.wait_limit = wait_limit;
   args.vec_ok = ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0 && (g.ldc & 3) == 0) ? 1 : 0;
+  args.alpha = (float)g.alpha;
+  args.beta = (float)g.beta;
+  const bool wide = p.tile_n == 256;
   int err;
-  if (b_mn)
-    err = p.tile_n == 256 ? launch_kernel<256, 4, true>(ta, tb, args, st)
-                          : launch_kernel<128, 6, true>(ta, tb, args, st);
+  if (cp.a_mn && cp.b_mn)
+    err = wide ? launch_kernel<256, 4, true, true>(ta, tb, args, st)
+               : launch_kernel<128, 6, true, true>(ta, tb, args, st);
+  else if (cp.a_mn)
+    err = wide ? launch_kernel<256, 4, true, false>(ta, tb, args, st)
+               : launch_kernel<128, 6, true, false>(ta, tb, args, st);
+  else if (cp.b_mn)
+    err = wide ? launch_kernel<256, 4, false, true>(ta, tb, args, st)
+               : launch_kernel<128, 6, false, true>(ta, tb, args, st);
   else
-    err = p.tile_n == 256 ? launch_kernel<256, 4, false>(ta, tb, args, st)
-                          : launch_kernel<128, 6, false>(ta, tb, args, st);
+    err = wide ? launch_kernel<256, 4, false, false>(ta, tb, args, st)
+               : launch_kernel<128, 6, false, false>(ta, tb, args, st);
   if (err) return err;
-  if (p.pk > 1) {
-    GemmArgs gr = g;
-    return launch_reduce(COSMA_F32, gr, p.pk, partial, st);
-  }
+  if (p.pk > 1) return launch_reduce(COSMA_F32, g, p.pk, partial, st);
   return 0;
 }
 
@@ -373,13 +434,14 @@ bool tc_b_direct(const void* B, int64_t ldb) {
   return (reinterpret_cast<uintptr_t>(B) & 15) == 0 && ((ldb * 2) & 15) == 0;
 }
 
-long long tc_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_plan& p, bool pack_a,
-                             bool transpose_b) {
-  const int64_t kp = round_up(k, 8);
+long long tc_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const void* A,
+                             int64_t lda, int trans_a, const void* B, int64_t ldb, int trans_b) {
+  const int64_t kp = round_up(k, 8), mp = round_up(m, 8);
+  const TcCopies cp = tc_copies(A, lda, trans_a, B, ldb, trans_b);
   long long b = 0;
   if (p.pk > 1) b += round_up((long long)p.pk * m * n * 4, 256);
-  if (transpose_b) b += round_up(n * kp * 2, 256);
-  if (pack_a) b += round_up(m * kp * 2, 256);
+  if (cp.copy_b) b += round_up(n * kp * 2, 256);
+  if (cp.pack_a) b += round_up((cp.a_mn ? k * mp : m * kp) * 2, 256);
   return b;
 }
 

@@ -200,3 +200,14 @@ def test_selector_features_match_oracle(lib):
     for (m, n, k, dt) in [(256, 65536, 1024, 2), (3, 5, 7, 0), (4096, 1, 2, 3)]:
         got = np.array(lib.cosma_selector_features(m, n, k, dt))
         assert np.allclose(got, om.features(m, n, k, dt), rtol=1e-6, atol=1e-7)
+
+
+def test_gemm_ex_rejects_short_leading_dimensions(lib):
+    cosma = lib
+    # trans_a: A is k x m, so lda >= m; trans_b: B is n x k, so ldb >= k
+    assert cosma.cosma_gemm_ex(1, 0, 8, 4, 16, 1.0, 1, 7, 1, 4, 0.0, 1, 4,
+                               cosma.COSMA_F64, 0) == cosma.COSMA_ERR_INVALID_ARG
+    assert cosma.cosma_gemm_ex(0, 1, 8, 4, 16, 1.0, 1, 16, 1, 15, 0.0, 1, 4,
+                               cosma.COSMA_F64, 0) == cosma.COSMA_ERR_INVALID_ARG
+    assert cosma.cosma_gemm_ex(2, 0, 8, 4, 16, 1.0, 1, 16, 1, 4, 0.0, 1, 4,
+                               cosma.COSMA_F64, 0) == cosma.COSMA_ERR_INVALID_ARG

@@ -126,3 +126,58 @@ def test_empty_and_k0():
     assert og.gemm(np.zeros((0, 3)), np.zeros((3, 4))).shape == (0, 4)
     C = og.gemm(np.zeros((3, 0)), np.zeros((0, 4)))
     assert C.shape == (3, 4) and not C.any()
+
+
+# ---- gemm_ex: alpha op(A) op(B) + beta C0 -------------------------------------
+
+def _int_loops(Astore, Bstore, C0, alpha, beta, ta, tb):
+    """Brute force with Python integers, indexing the stored arrays directly."""
+    m = len(Astore[0]) if ta else len(Astore)
+    k = len(Astore) if ta else len(Astore[0])
+    n = len(Bstore) if tb else len(Bstore[0])
+    out = [[0] * n for _ in range(m)]
+    for i in range(m):
+        for j in range(n):
+            acc = 0
+            for t in range(k):
+                a = Astore[t][i] if ta else Astore[i][t]
+                b = Bstore[j][t] if tb else Bstore[t][j]
+                acc += int(a) * int(b)
+            out[i][j] = alpha * acc + beta * int(C0[i][j])
+    return out
+
+
+@pytest.mark.parametrize("ta", [False, True])
+@pytest.mark.parametrize("tb", [False, True])
+def test_gemm_ex_integer_all_transposes(ta, tb):
+    rng = np.random.default_rng(11)
+    m, n, k = 5, 7, 6
+    Ast = rng.integers(-8, 9, (k, m) if ta else (m, k))
+    Bst = rng.integers(-8, 9, (n, k) if tb else (k, n))
+    C0 = rng.integers(-50, 51, (m, n))
+    for alpha, beta in [(1, 0), (3, -2), (-1, 1), (0, 5)]:
+        got = og.gemm_ex(Ast, Bst, C0, alpha, beta, ta, tb)
+        want = np.array(_int_loops(Ast.tolist(), Bst.tolist(), C0.tolist(), alpha, beta, ta, tb),
+                        dtype=np.float64)
+        assert np.array_equal(got, want), (alpha, beta)
+
+
+def test_gemm_ex_alpha_zero_and_beta_zero():
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((4, 3))
+    B = rng.standard_normal((3, 5))
+    C0 = rng.standard_normal((4, 5))
+    assert np.array_equal(og.gemm_ex(A, B, C0, 0.0, 0.625), 0.625 * C0)
+    A[0, 0] = np.nan  # not read when alpha == 0
+    assert np.array_equal(og.gemm_ex(A, B, C0, 0.0, 2.0), 2.0 * C0)
+    C0[:] = np.nan    # not read when beta == 0
+    A[0, 0] = 1.0
+    assert np.isfinite(og.gemm_ex(A, B, C0, 1.5, 0.0)).all()
+
+
+def test_gemm_ex_identity_closed_form():
+    rng = np.random.default_rng(13)
+    Bst = rng.standard_normal((6, 4))   # stored n x k: op(B) = Bst^T (k = 4, n = 6)
+    C0 = rng.standard_normal((4, 6))
+    got = og.gemm_ex(np.eye(4), Bst, C0, 2.0, -1.0, False, True)
+    assert np.array_equal(got, 2.0 * Bst.T + (-1.0) * C0)
