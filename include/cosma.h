@@ -164,6 +164,22 @@ int cosma_gemm_ex(int trans_a, int trans_b, int64_t m, int64_t n, int64_t k, dou
                   const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C,
                   int64_t ldc, int dtype, void* stream);
 
+/* Complex double: C = alpha op(A) op(B) + beta C over interleaved (re, im) pairs
+ * (C99 double complex / std::complex<double> layout, 16-byte aligned), run as
+ * four real products on `engine` (COSMA_F64 or COSMA_F64_EMU_BF16; else
+ * COSMA_ERR_UNSUPPORTED): Tr = Ar Br - Ai Bi, Ti = Ar Bi + Ai Br.
+ *   op_a / op_b: 0 none, 1 transpose, 2 conjugate transpose; a transposed operand
+ *   is stored transposed (A as k x m with lda >= m, B as n x k with ldb >= k).
+ *   alpha, beta: HOST arrays {re, im}.  Leading dimensions count complex
+ *   elements.  beta == 0 does not read C; alpha == 0 or k == 0 does not read A, B.
+ * The planar parts and Tr, Ti (2 (mk + kn + mn) doubles) live in a library-owned
+ * buffer grown with cudaMalloc outside capture (COSMA_ERR_NO_WORKSPACE inside
+ * capture when too small); calls overlapping on the GPU must be serialised.  The
+ * paper has no counterpart beyond the ScaLAPACK interface it targets. */
+int cosma_zgemm(int op_a, int op_b, int64_t m, int64_t n, int64_t k, const double* alpha,
+                const void* A, int64_t lda, const void* B, int64_t ldb, const double* beta,
+                void* C, int64_t ldc, int engine, void* stream);
+
 /* Same as cosma_gemm but runs the given plan (e.g. from cosma_plan_query or an
  * autotuner).  The plan is validated against the kernel's limits first. */
 int cosma_gemm_planned(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda,

@@ -10,7 +10,8 @@ integers, identity / diagonal / rank-1 closed forms, exact rational arithmetic
 |A||B| for the naive loop, and Freivalds catching a planted error; for gemm_ex,
 integer alpha op(A) op(B) + beta C0 against Python integer loops in all four
 transpose cases, alpha = 0 giving exactly beta C0, and NaN in C0 ignored when
-beta = 0.
+beta = 0; for zgemm, Gaussian-integer products against Python complex loops for
+all nine op cases.
 """
 
 import ctypes
@@ -96,6 +97,25 @@ def gemm_ex(A, B, C0, alpha, beta, trans_a=False, trans_b=False, method="dot2"):
         out = alpha * gemm(opA, opB, method)
     if beta != 0.0:
         out = out + beta * _f64(C0)
+    return out
+
+
+def zgemm(A, B, C0, alpha, beta, op_a=0, op_b=0):
+    """Complex C = alpha op(A) op(B) + beta C0 in complex128 (BLAS ZGEMM definition);
+    op 0: X, 1: transpose of the stored X, 2: conjugate transpose.  The product is
+    numpy's complex matmul (a library primitive).  beta == 0 does not read C0;
+    alpha == 0 or k == 0 does not read A, B."""
+    def op(X, o):
+        X = np.asarray(X, dtype=np.complex128)
+        return X if o == 0 else (X.T if o == 1 else X.conj().T)
+    opA, opB = op(A, op_a), op(B, op_b)
+    m, k = opA.shape
+    assert opB.shape[0] == k
+    out = np.zeros((m, opB.shape[1]), dtype=np.complex128)
+    if alpha != 0 and k > 0:
+        out = alpha * np.matmul(opA, opB)
+    if beta != 0:
+        out = out + beta * np.asarray(C0, dtype=np.complex128)
     return out
 
 

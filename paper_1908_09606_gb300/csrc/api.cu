@@ -20,6 +20,7 @@ int grouped_gemm(int count, const cosma_problem* problems, int dtype, const Devi
                  long long* needed, int requested_tile);
 void grouped_release(int dev);
 void host_release(int dev);
+void complex_release(int dev);
 
 static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -312,6 +313,13 @@ int run_device(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, cons
   return run(m, n, k, A, lda, B, ldb, C, ldc, dtype, nullptr, stream);
 }
 
+int run_device_ex(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void* B,
+                  int64_t ldb, void* C, int64_t ldc, int dtype, double alpha, double beta,
+                  int trans_a, int trans_b, void* stream) {
+  return run(m, n, k, A, lda, B, ldb, C, ldc, dtype, nullptr, stream, alpha, beta, trans_a,
+             trans_b);
+}
+
 }  // namespace cosma
 
 using namespace cosma;
@@ -358,7 +366,8 @@ int cosma_set_workspace(void* dptr, size_t bytes) {
 void cosma_finalize(void) {
   const int d = current_device();
   if (d < 0) return;
-  host_release(d);  // takes its own lock, never while holding g_mu
+  host_release(d);  // these take their own locks, never while holding g_mu
+  complex_release(d);
   std::lock_guard<std::mutex> lock(g_mu);
   DeviceState& s = g_dev[d];
   if (!s.ready) return;

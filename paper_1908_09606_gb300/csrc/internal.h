@@ -64,6 +64,10 @@ int lib_context(LibContext* out);
 // cosma_gemm on device operands, planned by the configured selector (api.cu).
 int run_device(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void* B,
                int64_t ldb, void* C, int64_t ldc, int dtype, void* stream);
+// cosma_gemm_ex on device operands (api.cu).
+int run_device_ex(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void* B,
+                  int64_t ldb, void* C, int64_t ldc, int dtype, double alpha, double beta,
+                  int trans_a, int trans_b, void* stream);
 
 // Kernel launchers (return cudaError_t values).
 struct GemmArgs {

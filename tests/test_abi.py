@@ -211,3 +211,14 @@ def test_gemm_ex_rejects_short_leading_dimensions(lib):
                                cosma.COSMA_F64, 0) == cosma.COSMA_ERR_INVALID_ARG
     assert cosma.cosma_gemm_ex(2, 0, 8, 4, 16, 1.0, 1, 16, 1, 4, 0.0, 1, 4,
                                cosma.COSMA_F64, 0) == cosma.COSMA_ERR_INVALID_ARG
+
+
+def test_zgemm_rejects_other_engines_and_bad_ops(lib):
+    cosma = lib
+    al = 1.0 + 0j
+    assert cosma.cosma_zgemm(0, 0, 4, 4, 4, al, 0, 4, 0, 4, al, 0, 4,
+                             cosma.COSMA_BF16, 0) == cosma.COSMA_ERR_UNSUPPORTED
+    assert cosma.cosma_zgemm(3, 0, 4, 4, 4, al, 0, 4, 0, 4, al, 0, 4,
+                             cosma.COSMA_F64, 0) == cosma.COSMA_ERR_INVALID_ARG
+    assert cosma.cosma_zgemm(1, 0, 8, 4, 4, al, 0, 7, 0, 4, al, 0, 4,
+                             cosma.COSMA_F64, 0) == cosma.COSMA_ERR_INVALID_ARG  # lda < m

@@ -181,3 +181,38 @@ def test_gemm_ex_identity_closed_form():
     C0 = rng.standard_normal((4, 6))
     got = og.gemm_ex(np.eye(4), Bst, C0, 2.0, -1.0, False, True)
     assert np.array_equal(got, 2.0 * Bst.T + (-1.0) * C0)
+
+
+# ---- zgemm: complex alpha op(A) op(B) + beta C0 -----------------------------------
+
+@pytest.mark.parametrize("op_a", [0, 1, 2])
+@pytest.mark.parametrize("op_b", [0, 1, 2])
+def test_zgemm_gaussian_integers_all_ops(op_a, op_b):
+    rng = np.random.default_rng(21)
+    m, n, k = 4, 5, 3
+    def mk(r, c):
+        return rng.integers(-6, 7, (r, c)) + 1j * rng.integers(-6, 7, (r, c))
+    Ast = mk(k, m) if op_a else mk(m, k)
+    Bst = mk(n, k) if op_b else mk(k, n)
+    C0 = mk(m, n)
+    alpha, beta = 2 - 1j, -1 + 3j
+    got = og.zgemm(Ast, Bst, C0, alpha, beta, op_a, op_b)
+    def el(X, o, i, j):  # element (i, j) of op(X) from the stored X
+        if o == 0:
+            return complex(X[i][j])
+        v = complex(X[j][i])
+        return v.conjugate() if o == 2 else v
+    for i in range(m):
+        for j in range(n):
+            acc = sum(el(Ast, op_a, i, t) * el(Bst, op_b, t, j) for t in range(k))
+            assert got[i, j] == alpha * acc + beta * complex(C0[i][j])
+
+
+def test_zgemm_alpha_zero_beta_zero():
+    rng = np.random.default_rng(22)
+    A = rng.standard_normal((3, 4)) + 1j * rng.standard_normal((3, 4))
+    B = rng.standard_normal((4, 2)) + 1j * rng.standard_normal((4, 2))
+    C0 = rng.standard_normal((3, 2)) + 1j * rng.standard_normal((3, 2))
+    assert np.array_equal(og.zgemm(A, B, C0, 0, 1j), 1j * C0)
+    C0[:] = np.nan
+    assert np.isfinite(og.zgemm(A, B, C0, 1, 0)).all()
