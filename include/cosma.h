@@ -77,12 +77,17 @@ typedef enum {
   COSMA_KERNEL_EMU_BF16 = 3   /* tcgen05 bf16 slices, FP64 recombination */
 } cosma_kernel;
 
-/* Library configuration (all fields have defaults; see cosma_init). */
+/* Library configuration (all fields have defaults; see cosma_init).  The
+ * defaults can be changed by environment variables read once when the library
+ * is loaded -- COSMA_DELTA, COSMA_SELECTOR (analytic | learned), COSMA_EMU_SLICES,
+ * COSMA_EMU_SLICE_BITS, COSMA_WAIT_LIMIT, COSMA_GROUPED_TILE -- a malformed or
+ * out-of-range value leaving its field at the built-in default; cosma_init
+ * replaces the whole configuration. */
 typedef struct cosma_config {
   double delta;        /* FitRanks: max fraction of SMs left idle (Sec. 7.1); default 0.03 */
   int selector;        /* default cosma_selector for cosma_gemm; default ANALYTIC */
   int emu_slices;      /* slices per operand for F64_EMU_BF16; 0 = default (6) */
-  int emu_slice_bits;  /* magnitude bits per slice, 1..8; 0 = default (7) */
+  int emu_slice_bits;  /* digit width beta in bits, 2..8; 0 = default (8) */
   long long wait_limit;/* clock cycles before a device wait gives up; 0 = default (2^31, ~1 s) */
   int grouped_tile;    /* C tile width of cosma_gemm_grouped: 0 = chosen by the library;
                           bf16: 128 or 256 (tile 128 x N); f32: 64 or 128 (square tile) */

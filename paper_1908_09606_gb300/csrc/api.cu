@@ -2,6 +2,7 @@
 // dispatch to the kernels, device status word.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 #include <atomic>
 #include <mutex>
@@ -58,7 +59,52 @@ struct DeviceState {
 constexpr int kMaxDevices = 16;
 std::mutex g_mu;
 DeviceState g_dev[kMaxDevices];
-cosma_config g_cfg = {0.03, COSMA_SELECT_ANALYTIC, 0, 0, 0, 0};
+bool config_valid(const cosma_config& c) {
+  if (!(c.delta >= 0.0 && c.delta < 1.0)) return false;
+  if (c.selector < COSMA_SELECT_ANALYTIC || c.selector > COSMA_SELECT_LEARNED) return false;
+  if (c.emu_slices < 0 || c.emu_slices > 12) return false;
+  if (c.emu_slice_bits < 0 || c.emu_slice_bits > 8) return false;
+  if (c.wait_limit < 0) return false;
+  if (c.grouped_tile != 0 && c.grouped_tile != 64 && c.grouped_tile != 128 &&
+      c.grouped_tile != 256)
+    return false;
+  return true;
+}
+
+// Defaults, then COSMA_* environment variables (read once, when the library is
+// loaded); a malformed or out-of-range value leaves its field at the default.
+cosma_config env_config() {
+  cosma_config c = {0.03, COSMA_SELECT_ANALYTIC, 0, 0, 0, 0};
+  auto num = [](const char* name, double* out) {
+    const char* v = getenv(name);
+    if (!v || !*v) return false;
+    char* end = nullptr;
+    const double x = strtod(v, &end);
+    if (!end || *end) return false;
+    *out = x;
+    return true;
+  };
+  auto apply = [&c](const cosma_config& trial) {
+    if (config_valid(trial)) c = trial;
+  };
+  double x;
+  cosma_config t;
+  if (num("COSMA_DELTA", &x)) { t = c; t.delta = x; apply(t); }
+  if (const char* v = getenv("COSMA_SELECTOR")) {
+    t = c;
+    if (!strcmp(v, "analytic") || !strcmp(v, "0")) t.selector = COSMA_SELECT_ANALYTIC;
+    else if (!strcmp(v, "learned") || !strcmp(v, "1")) t.selector = COSMA_SELECT_LEARNED;
+    else t.selector = -1;
+    apply(t);
+  }
+  if (num("COSMA_EMU_SLICES", &x) && x == (int)x) { t = c; t.emu_slices = (int)x; apply(t); }
+  if (num("COSMA_EMU_SLICE_BITS", &x) && x == (int)x) { t = c; t.emu_slice_bits = (int)x; apply(t); }
+  if (num("COSMA_WAIT_LIMIT", &x) && x == (long long)x) { t = c; t.wait_limit = (long long)x; apply(t); }
+  if (num("COSMA_GROUPED_TILE", &x) && x == (int)x) { t = c; t.grouped_tile = (int)x; apply(t); }
+  return c;
+}
+
+cosma_config g_cfg = env_config();
 
 const long long kDefaultWaitLimit = 1LL << 31;  // clock cycles (~1 s) before a device wait gives up
 
@@ -327,17 +373,7 @@ using namespace cosma;
 extern "C" {
 
 int cosma_init(const cosma_config* cfg) {
-  if (cfg) {
-    if (!(cfg->delta >= 0.0 && cfg->delta < 1.0)) return COSMA_ERR_INVALID_ARG;
-    if (cfg->selector < COSMA_SELECT_ANALYTIC || cfg->selector > COSMA_SELECT_LEARNED)
-      return COSMA_ERR_INVALID_ARG;
-    if (cfg->emu_slices < 0 || cfg->emu_slices > 12) return COSMA_ERR_INVALID_ARG;
-    if (cfg->emu_slice_bits < 0 || cfg->emu_slice_bits > 8) return COSMA_ERR_INVALID_ARG;
-    if (cfg->wait_limit < 0) return COSMA_ERR_INVALID_ARG;
-    if (cfg->grouped_tile != 0 && cfg->grouped_tile != 64 && cfg->grouped_tile != 128 &&
-        cfg->grouped_tile != 256)
-      return COSMA_ERR_INVALID_ARG;
-  }
+  if (cfg && !config_valid(*cfg)) return COSMA_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(g_mu);
   if (cfg) g_cfg = *cfg;
   int rc;

@@ -222,3 +222,25 @@ def test_zgemm_rejects_other_engines_and_bad_ops(lib):
                              cosma.COSMA_F64, 0) == cosma.COSMA_ERR_INVALID_ARG
     assert cosma.cosma_zgemm(1, 0, 8, 4, 4, al, 0, 7, 0, 4, al, 0, 4,
                              cosma.COSMA_F64, 0) == cosma.COSMA_ERR_INVALID_ARG  # lda < m
+
+
+
+def test_environment_sets_config_defaults(lib):
+    """COSMA_* variables are read when the library loads (a fresh process here);
+    bad values leave the built-in default."""
+    import json
+    import subprocess
+    import sys
+    code = ("from paper_1908_09606_gb300 import cosma; cosma.load(); c = cosma.cosma_get_config(); "
+            "import json; print(json.dumps([c.delta, c.selector, c.emu_slices, "
+            "c.emu_slice_bits, c.wait_limit, c.grouped_tile]))")
+    env = dict(os.environ, COSMA_DELTA="0.1", COSMA_SELECTOR="learned", COSMA_EMU_SLICES="7",
+               COSMA_EMU_SLICE_BITS="7", COSMA_WAIT_LIMIT="12345", COSMA_GROUPED_TILE="256")
+    out = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True,
+                         text=True, check=True).stdout
+    assert json.loads(out) == [0.1, 1, 7, 7, 12345, 256]
+    env = dict(os.environ, COSMA_DELTA="1.5", COSMA_SELECTOR="fast", COSMA_EMU_SLICES="x",
+               COSMA_GROUPED_TILE="100")
+    out = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True,
+                         text=True, check=True).stdout
+    assert json.loads(out) == [0.03, 0, 0, 0, 0, 0]

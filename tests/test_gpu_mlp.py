@@ -127,6 +127,31 @@ def test_training_fits_a_known_cost_model():
     assert hist[-1] < 0.1 * hist[0], hist[::10]
 
 
+def test_training_resumes_from_checkpoint_bit_for_bit():
+    """Parameters, Adam moments, step count and the permutation stream are restored:
+    8 epochs + resume to 20 equals 20 epochs in one run (deterministic kernels)."""
+    import os
+    import tempfile
+    from paper_1908_09606_gb300 import autotune
+    lib()
+    N = 1500
+    u = ci.matrix(N, 3, "uniform", "f64", 14, 0)
+    dims = np.round(256 * 256 ** ((u + 1) / 2)).astype(int)
+    cand = ((ci.entries(np.arange(N), np.zeros(N), 1, "integer", "f64", 14, 1) + 8) % 16).astype(np.int32)
+    rows = [{"m": int(m), "n": int(n), "k": int(k), "dtype": 2, "cand": int(c),
+             "seconds": float(2.0 * m * n * k / (1e15 * (0.5 + 0.03 * c)) + 1e-5)}
+            for (m, n, k), c in zip(dims, cand)]
+    X, c, y = autotune.features(rows)
+    whole, hist_whole, _ = autotune.train(X, c, y, epochs=20, batch=128, lr=3e-3, seed=4)
+    with tempfile.TemporaryDirectory() as d:
+        ck = os.path.join(d, "ck.npz")
+        autotune.train(X, c, y, epochs=8, batch=128, lr=3e-3, seed=4, checkpoint=ck)
+        resumed, hist_res, _ = autotune.train(X, c, y, epochs=20, batch=128, lr=3e-3, seed=4,
+                                              checkpoint=ck)
+    assert np.array_equal(whole, resumed)
+    assert np.array_equal(np.array(hist_whole), np.array(hist_res))
+
+
 def test_selector_end_to_end_small():
     import torch
     from paper_1908_09606_gb300 import autotune
