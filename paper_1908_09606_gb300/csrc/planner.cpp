@@ -265,13 +265,15 @@ int plan_gemm(int64_t m, int64_t n, int64_t k, int dtype, int selector, const De
     const TileChoice& t = tiles[ti];
     const int64_t mt = cdiv(mm, t.tile_m), ntl = cdiv(nn, t.tile_n), kbt = cdiv(kk, t.k_block);
     const int64_t tiles_total = mt * ntl;
-    // Candidate k splits: 1, and those that fill the SMs when tiles are few.
+    // Candidate k splits: 1, powers of two while the units stay within 16 waves
+    // (a split also evens out the last, partial wave of tiles), and the one that
+    // fills the SMs when tiles are few.
     int pks[16];
     int npk = 0;
     pks[npk++] = 1;
     if (d.kernel != COSMA_KERNEL_EMU_BF16) {
       for (int pk = 2; pk <= 64 && npk < 16; pk *= 2)
-        if (pk <= kbt && tiles_total * pk <= 4LL * P) pks[npk++] = pk;
+        if (pk <= kbt && tiles_total * pk <= 16LL * P) pks[npk++] = pk;
       const int64_t fill = cdiv(P, tiles_total);
       if (fill > 1 && fill <= kbt && npk < 16) pks[npk++] = (int)fill;
     }
