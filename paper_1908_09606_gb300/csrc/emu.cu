@@ -47,6 +47,12 @@ namespace cosma {
 namespace {
 
 constexpr int EBM = 128, EBN = 128, EBK = 64, ESTAGES = 5;
+// Slice layout, k-blocked (the paper's blocked data layout, Sec. 7.6): slice q of
+// an operand with R rows is stored as ceil(k / EKB) panels of R x EKB, element
+// (i, t) at ((q nkb + t / EKB) R + i) EKB + t % EKB, zero beyond k.  A TMA box
+// (64 k by 128 rows) then spans 128 rows of 4 KB -- a few pages -- however long
+// k is (row-major slices with k = 2^20 put every row of a box in its own page).
+constexpr int64_t EKB = 2048;
 constexpr int TPITCH = EBN + 1;  // padded row pitch of the running total in shared memory
 constexpr int EMU_MAX_SLICES = 8;
 constexpr int kExpNone = (int)0x80808080;  // memset(0x80) pattern: "no nonzero seen"
@@ -55,6 +61,14 @@ int emu_slices(const cosma_config& c) { return c.emu_slices > 0 ? c.emu_slices :
 int emu_bits(const cosma_config& c) { return c.emu_slice_bits > 0 ? c.emu_slice_bits : 8; }
 
 inline int64_t rup(int64_t x, int64_t r) { return (x + r - 1) / r * r; }
+
+// k rounded up to whole layout panels.
+inline int64_t emu_kpad(int64_t k) { return rup(k > 0 ? k : 1, EKB); }
+
+__device__ __forceinline__ int64_t slice_at(int q, int64_t i, int64_t t, int64_t rows,
+                                            int64_t nkb) {
+  return (((int64_t)q * nkb + t / EKB) * rows + i) * EKB + (t % EKB);
+}
 
 // ---- K-SPLIT ----------------------------------------------------------------
 
@@ -141,31 +155,36 @@ __global__ void col_exp_kernel(const double* __restrict__ B, int64_t k, int64_t 
   if (e != kExpNone) atomicMax(&eB[j], e);
 }
 
-// Slices of A: S[q][i][t] (ld kp, slice_rows rows between slices), one thread
-// per element.
+// Slices of A in the k-blocked layout (slice_rows rows per panel), zeros for
+// k <= t < kpad; one thread per element.
 __global__ void split_a_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda,
                                const int* __restrict__ eA, __nv_bfloat16* __restrict__ S,
-                               int64_t kp, int64_t slice_rows, int s, int beta) {
+                               int64_t kpad, int64_t slice_rows, int s, int beta) {
   const int L = beta * s - 1;
-  const int64_t total = m * k;
+  const int64_t total = m * kpad, nkb = kpad / EKB;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / k, t = e - i * k;
+    const int64_t i = e / kpad, t = e - i * kpad;
     int d[EMU_MAX_SLICES];
-    split_digits(A[i * lda + t], eA[i], L, beta, s, d);
+    if (t < k)
+      split_digits(A[i * lda + t], eA[i], L, beta, s, d);
+    else
+#pragma unroll
+      for (int q = 0; q < EMU_MAX_SLICES; ++q) d[q] = 0;
 #pragma unroll
     for (int q = 0; q < EMU_MAX_SLICES; ++q)
-      if (q < s) S[((int64_t)q * slice_rows + i) * kp + t] = __float2bfloat16_rn((float)d[q]);
+      if (q < s) S[slice_at(q, i, t, slice_rows, nkb)] = __float2bfloat16_rn((float)d[q]);
   }
 }
 
-// Slices of B, transposed to K-major: S[q][j][t] (ld kp, slice_rows rows
-// between slices).  32 x 32 tiles.
+// Slices of B, transposed to K-major, in the k-blocked layout (zeros for
+// k <= t < kpad).  32 x 32 tiles; the grid covers kpad.
 __global__ void split_b_kernel(const double* __restrict__ B, int64_t k, int64_t n, int64_t ldb,
                                const int* __restrict__ eB, __nv_bfloat16* __restrict__ S,
-                               int64_t kp, int64_t slice_rows, int s, int beta) {
+                               int64_t kpad, int64_t slice_rows, int s, int beta) {
   __shared__ __nv_bfloat16 tile[EMU_MAX_SLICES][32][34];
   const int L = beta * s - 1;
+  const int64_t nkb = kpad / EKB;
   const int64_t t0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
   for (int r = threadIdx.y; r < 32; r += 8) {
     const int64_t t = t0 + r, j = j0 + threadIdx.x;
@@ -181,8 +200,8 @@ __global__ void split_b_kernel(const double* __restrict__ B, int64_t k, int64_t 
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += 8) {
     const int64_t j = j0 + r, t = t0 + threadIdx.x;
-    if (j < n && t < k)
-      for (int q = 0; q < s; ++q) S[((int64_t)q * slice_rows + j) * kp + t] = tile[q][r][threadIdx.x];
+    if (j < n && t < kpad)
+      for (int q = 0; q < s; ++q) S[slice_at(q, j, t, slice_rows, nkb)] = tile[q][r][threadIdx.x];
   }
 }
 
@@ -218,12 +237,15 @@ struct EmuArgs {
 constexpr int NACC = 3;            // accumulator buffers in tensor memory (columns 0..383)
 constexpr uint32_t TL_COL = 384;   // low parts of the running total (columns 384..511)
 
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int32_t x, int32_t y, int32_t z) {
+// One 64 (k) x rows box of slice q at k-block kb and row y of the k-blocked layout.
+__device__ __forceinline__ void tma_load_slice(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                               int64_t kb, int32_t y, int32_t q) {
+  const int64_t t = kb * EBK;
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5}], [%2];\n" ::"r"(tc::smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(tc::smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];\n" ::"r"(tc::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(tc::smem_u32(bar)), "r"((int32_t)(t % EKB)),
+      "r"(y), "r"((int32_t)(t / EKB)), "r"(q)
       : "memory");
 }
 
@@ -463,10 +485,9 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
               if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) return false;
               tc::mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES);
               uint8_t* sa = smem + stage * L::STAGE_BYTES;
-              tma_load_3d(sa, &tmA, &full[stage], (int32_t)(kb * EBK),
-                          (int32_t)(u.tile_row * EBM), q - 1);
-              tma_load_3d(sa + L::A_BYTES, &tmB, &full[stage], (int32_t)(kb * EBK),
-                          (int32_t)(u.tile_col * EBN), lvl - q - 1);
+              tma_load_slice(sa, &tmA, &full[stage], kb, (int32_t)(u.tile_row * EBM), q - 1);
+              tma_load_slice(sa + L::A_BYTES, &tmB, &full[stage], kb,
+                             (int32_t)(u.tile_col * EBN), lvl - q - 1);
               armed |= 1u << stage;
               armed_ph = (armed_ph & ~(1u << stage)) | (ph << stage);
               if (++stage == ESTAGES) { stage = 0; ph ^= 1; }
@@ -560,13 +581,15 @@ struct E2Layout {
   static constexpr int ALLOC = TOTAL + 1024;
 };
 
-__device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* map,
-                                                 uint32_t bar_cluster, int32_t x, int32_t y,
-                                                 int32_t z) {
+__device__ __forceinline__ void tma_load_slice_pair(void* dst, const CUtensorMap* map,
+                                                    uint32_t bar_cluster, int64_t kb, int32_t y,
+                                                    int32_t q) {
+  const int64_t t = kb * EBK;
   asm volatile(
-      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5}], [%2];\n" ::"r"(tc::smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(x), "r"(y), "r"(z)
+      "cp.async.bulk.tensor.4d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];\n" ::"r"(tc::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"((int32_t)(t % EKB)), "r"(y),
+      "r"((int32_t)(t / EKB)), "r"(q)
       : "memory");
 }
 
@@ -652,10 +675,10 @@ emu_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
               if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) return false;
               if (leader) tc::mbar_arrive_expect_tx(&full[stage], 2 * L::STAGE_BYTES);
               uint8_t* sa = smem + stage * L::STAGE_BYTES;
-              tma_load_3d_pair(sa, &tmA, full_cl[stage], (int32_t)(kb * EBK),
-                               (int32_t)(u.tile_row * (2 * EBM) + rank * EBM), q - 1);
-              tma_load_3d_pair(sa + L::A_BYTES, &tmB, full_cl[stage], (int32_t)(kb * EBK),
-                               (int32_t)(u.tile_col * EBN + rank * (EBN / 2)), lvl - q - 1);
+              tma_load_slice_pair(sa, &tmA, full_cl[stage], kb,
+                                  (int32_t)(u.tile_row * (2 * EBM) + rank * EBM), q - 1);
+              tma_load_slice_pair(sa + L::A_BYTES, &tmB, full_cl[stage], kb,
+                                  (int32_t)(u.tile_col * EBN + rank * (EBN / 2)), lvl - q - 1);
               issued = true;
               if (++stage == E2_STAGES) { stage = 0; ph ^= 1; }
               return true;
@@ -727,8 +750,10 @@ emu_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
   if (warp == 1) tc::tmem_dealloc_pair(tmem_base, 512);
 }
 
-int encode_tmap_slices(CUtensorMap* map, const void* base, int64_t rows, int64_t k, int64_t kp,
-                       int s, int64_t slice_rows, int box_rows) {
+// 4-D map over the k-blocked slices of `rows` rows starting at `base` (a row
+// block of an operand with slice_rows rows): dims (EKB, rows, panels, slices).
+int encode_tmap_slices(CUtensorMap* map, const void* base, int64_t rows, int64_t k, int s,
+                       int64_t slice_rows, int box_rows) {
   static std::once_flag once;
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   std::call_once(once, [] {
@@ -740,11 +765,13 @@ int encode_tmap_slices(CUtensorMap* map, const void* base, int64_t rows, int64_t
       fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
   });
   if (!fn) return COSMA_ERR_CUDA;
-  cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)s};
-  cuuint64_t strides[2] = {(cuuint64_t)(kp * 2), (cuuint64_t)(slice_rows * kp * 2)};
-  cuuint32_t box[3] = {(cuuint32_t)EBK, (cuuint32_t)box_rows, 1};
-  cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims,
+  const int64_t nkb = emu_kpad(k) / EKB;
+  cuuint64_t dims[4] = {(cuuint64_t)EKB, (cuuint64_t)rows, (cuuint64_t)nkb, (cuuint64_t)s};
+  cuuint64_t strides[3] = {(cuuint64_t)(EKB * 2), (cuuint64_t)(slice_rows * EKB * 2),
+                           (cuuint64_t)(nkb * slice_rows * EKB * 2)};
+  cuuint32_t box[4] = {(cuuint32_t)EBK, (cuuint32_t)box_rows, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -755,14 +782,14 @@ int encode_tmap_slices(CUtensorMap* map, const void* base, int64_t rows, int64_t
 
 long long emu_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_config& cfg) {
   const int s = emu_slices(cfg);
-  const int64_t kp = rup(k, 8);
+  const int64_t kp = emu_kpad(k);
   return rup(m * 4, 256) + rup(n * 4, 256) + rup((int64_t)s * m * kp * 2, 256) +
          rup((int64_t)s * n * kp * 2, 256) + 256;
 }
 
 EmuWorkspace emu_carve(void* ws, int64_t m, int64_t n, int64_t k, const cosma_config& cfg) {
   const int s = emu_slices(cfg);
-  const int64_t kp = rup(k, 8);
+  const int64_t kp = emu_kpad(k);
   uint8_t* w = static_cast<uint8_t*>(ws);
   EmuWorkspace e;
   e.eA = reinterpret_cast<int*>(w);
@@ -774,7 +801,7 @@ EmuWorkspace emu_carve(void* ws, int64_t m, int64_t n, int64_t k, const cosma_co
   e.SB = w;
   w += rup((int64_t)s * n * kp * 2, 256);
   e.lockstep = reinterpret_cast<unsigned int*>(w);
-  e.kp = kp;
+  e.row_pitch = EKB;
   return e;
 }
 
@@ -789,16 +816,16 @@ int emu_prepare_a(const double* A, int64_t m, int64_t k, int64_t lda, int trans,
                   void* SA, int64_t slice_rows, int* status, const cosma_config& cfg,
                   cudaStream_t st) {
   const int s = emu_slices(cfg), beta = emu_bits(cfg);
-  const int64_t kp = rup(k, 8);
+  const int64_t kp = emu_kpad(k);
   if (m <= 0) return COSMA_OK;
   if (trans) {  // A stored as k x m: its rows are columns of the stored matrix
-    if ((k + 31) / 32 > 65535) return COSMA_ERR_UNSUPPORTED;
+    if ((kp + 31) / 32 > 65535) return COSMA_ERR_UNSUPPORTED;
     if (cudaMemsetAsync(eA, 0x80, (size_t)m * 4, st) != cudaSuccess)
       return (int)cudaGetLastError();
     dim3 g1((unsigned)((m + 255) / 256), (unsigned)((k + 255) / 256));
     col_exp_kernel<<<g1, 256, 0, st>>>(A, k, m, lda, eA, status);
     count_launch();
-    dim3 g2((unsigned)((m + 31) / 32), (unsigned)((k + 31) / 32));
+    dim3 g2((unsigned)((m + 31) / 32), (unsigned)((kp + 31) / 32));
     split_b_kernel<<<g2, dim3(32, 8), 0, st>>>(A, k, m, lda, eA, static_cast<__nv_bfloat16*>(SA),
                                                kp, slice_rows, s, beta);
     count_launch();
@@ -807,7 +834,7 @@ int emu_prepare_a(const double* A, int64_t m, int64_t k, int64_t lda, int trans,
   const int64_t rb = m < 65535LL * 16 ? m : 65535LL * 16;
   row_exp_kernel<<<(unsigned)rb, 256, 0, st>>>(A, m, k, lda, eA, status);
   count_launch();
-  int64_t blocks = (m * k + 255) / 256;
+  int64_t blocks = (m * kp + 255) / 256;
   if (blocks > 152LL * 64) blocks = 152LL * 64;
   split_a_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, m, k, lda, eA,
                                                    static_cast<__nv_bfloat16*>(SA), kp,
@@ -820,13 +847,13 @@ int emu_prepare_b(const double* B, int64_t k, int64_t n, int64_t ldb, int trans,
                   void* SB, int64_t slice_rows, int* status, const cosma_config& cfg,
                   cudaStream_t st) {
   const int s = emu_slices(cfg), beta = emu_bits(cfg);
-  const int64_t kp = rup(k, 8);
+  const int64_t kp = emu_kpad(k);
   if (n <= 0) return COSMA_OK;
   if (trans) {  // B stored as n x k: its columns are rows of the stored matrix
     const int64_t rb = n < 65535LL * 16 ? n : 65535LL * 16;
     row_exp_kernel<<<(unsigned)rb, 256, 0, st>>>(B, n, k, ldb, eB, status);
     count_launch();
-    int64_t blocks = (n * k + 255) / 256;
+    int64_t blocks = (n * kp + 255) / 256;
     if (blocks > 152LL * 64) blocks = 152LL * 64;
     split_a_kernel<<<(unsigned)blocks, 256, 0, st>>>(B, n, k, ldb, eB,
                                                      static_cast<__nv_bfloat16*>(SB), kp,
@@ -834,12 +861,12 @@ int emu_prepare_b(const double* B, int64_t k, int64_t n, int64_t ldb, int trans,
     count_launch();
     return (int)cudaGetLastError();
   }
-  if ((k + 31) / 32 > 65535) return COSMA_ERR_UNSUPPORTED;
+  if ((kp + 31) / 32 > 65535) return COSMA_ERR_UNSUPPORTED;
   if (cudaMemsetAsync(eB, 0x80, (size_t)n * 4, st) != cudaSuccess) return (int)cudaGetLastError();
   dim3 g1((unsigned)((n + 255) / 256), (unsigned)((k + 255) / 256));
   col_exp_kernel<<<g1, 256, 0, st>>>(B, k, n, ldb, eB, status);
   count_launch();
-  dim3 g2((unsigned)((n + 31) / 32), (unsigned)((k + 31) / 32));
+  dim3 g2((unsigned)((n + 31) / 32), (unsigned)((kp + 31) / 32));
   split_b_kernel<<<g2, dim3(32, 8), 0, st>>>(B, k, n, ldb, eB, static_cast<__nv_bfloat16*>(SB),
                                              kp, slice_rows, s, beta);
   count_launch();
@@ -857,7 +884,6 @@ int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cos
   if ((sch.tile_m != EBM && !pairs) || sch.tile_n != EBN || sch.k_block != EBK || sch.pk != 1)
     return COSMA_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(C) & 7) return COSMA_ERR_INVALID_ARG;
-  const int64_t kp = rup(k, 8);
   // COSMA_EMU_LOCKSTEP=0 in the environment (read once) runs the pairs free:
   // profilers that cannot launch cooperative cluster kernels need it.
   static const bool lockstep_on = [] {
@@ -867,9 +893,9 @@ int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cos
   unsigned int* lockstep_counter = lockstep_on && 2 * sch.ctas <= p.sms ? lockstep : nullptr;
 
   CUtensorMap ta, tb;
-  int rc = encode_tmap_slices(&ta, SA, m, k, kp, s, a_slice_rows, EBM);
+  int rc = encode_tmap_slices(&ta, SA, m, k, s, a_slice_rows, EBM);
   if (rc != COSMA_OK) return rc;
-  rc = encode_tmap_slices(&tb, SB, n, k, kp, s, b_slice_rows, pairs ? EBN / 2 : EBN);
+  rc = encode_tmap_slices(&tb, SB, n, k, s, b_slice_rows, pairs ? EBN / 2 : EBN);
   if (rc != COSMA_OK) return rc;
 
   EmuArgs args;
@@ -951,7 +977,7 @@ int launch_emu_bf16(const GemmArgs& g, const cosma_plan& p, const cosma_config& 
   if (rc != COSMA_OK) return rc;
   const int64_t m = g.m, n = g.n, k = g.k;
   if (emu_workspace_bytes(m, n, k, cfg) > ws_bytes) return COSMA_ERR_NO_WORKSPACE;
-  if ((k + 31) / 32 > 65535) return COSMA_ERR_UNSUPPORTED;
+  if ((emu_kpad(k) + 31) / 32 > 65535) return COSMA_ERR_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(g.A) & 7) || (reinterpret_cast<uintptr_t>(g.B) & 7) ||
       (reinterpret_cast<uintptr_t>(g.C) & 7))
     return COSMA_ERR_INVALID_ARG;

@@ -159,7 +159,7 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
   if (emu) {
     rc = emu_check_config(ctx.cfg);
     if (rc != COSMA_OK) return rc;
-    if ((k + 31) / 32 > 65535) return COSMA_ERR_UNSUPPORTED;
+    if ((k + 2047) / 2048 * 2048 / 32 > 65535) return COSMA_ERR_UNSUPPORTED;
     void* ws = nullptr;
     rc = lib_scratch(emu_workspace_bytes(m, n, k, ctx.cfg), st, &ws);
     if (rc != COSMA_OK) return rc;
@@ -215,7 +215,7 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
       if ((rc = ok(cudaStreamWaitEvent(st, ev_a[i], 0))) != COSMA_OK) return rc;
       if (emu) {
         rc = emu_prepare_a(reinterpret_cast<const double*>(Ad) + r0 * lda_d, r1 - r0, k, lda_d,
-                           0, ew.eA + r0, static_cast<uint8_t*>(ew.SA) + (size_t)r0 * ew.kp * 2,
+                           0, ew.eA + r0, static_cast<uint8_t*>(ew.SA) + (size_t)r0 * ew.row_pitch * 2,
                            m, ctx.status, ctx.cfg, st);
         if (rc > 0) return COSMA_ERR_CUDA;
         if (rc < 0) return rc;
@@ -227,7 +227,7 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
           if ((rc = ok(cudaStreamWaitEvent(st, ev_b[j], 0))) != COSMA_OK) return rc;
           if (emu) {
             rc = emu_prepare_b(reinterpret_cast<const double*>(Bd) + c0, k, nb, ldb_d, 0,
-                               ew.eB + c0, static_cast<uint8_t*>(ew.SB) + (size_t)c0 * ew.kp * 2,
+                               ew.eB + c0, static_cast<uint8_t*>(ew.SB) + (size_t)c0 * ew.row_pitch * 2,
                                n, ctx.status, ctx.cfg, st);
             if (rc > 0) return COSMA_ERR_CUDA;
             if (rc < 0) return rc;
@@ -239,8 +239,8 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
           rc = plan_gemm(mb, nb, k, dtype, ctx.cfg.selector, ctx.info, ctx.cfg, &p, !capturing(st));
           if (rc != COSMA_OK) return rc;
           rc = emu_multiply(mb, nb, k, p, ctx.cfg, ew.eA + r0,
-                            static_cast<uint8_t*>(ew.SA) + (size_t)r0 * ew.kp * 2, m, ew.eB + c0,
-                            static_cast<uint8_t*>(ew.SB) + (size_t)c0 * ew.kp * 2, n,
+                            static_cast<uint8_t*>(ew.SA) + (size_t)r0 * ew.row_pitch * 2, m, ew.eB + c0,
+                            static_cast<uint8_t*>(ew.SB) + (size_t)c0 * ew.row_pitch * 2, n,
                             reinterpret_cast<double*>(Cblk), ldc_d, 1.0, 0.0, ew.lockstep,
                             ctx.status, ctx.wait_limit, st);
           if (rc > 0) return COSMA_ERR_CUDA;

@@ -93,10 +93,11 @@ int launch_transpose(int elem_bytes, const void* src, int64_t rows, int64_t cols
 struct EmuWorkspace {
   int* eA;                 // row exponents of A [m]
   int* eB;                 // column exponents of B [n]
-  void* SA;                // bf16 slices of A [s][m][kp]
-  void* SB;                // bf16 slices of B^T [s][n][kp]
+  void* SA;                // bf16 slices of A, k-blocked: [s][k panels][m][row_pitch]
+  void* SB;                // bf16 slices of B^T, k-blocked: [s][k panels][n][row_pitch]
   unsigned int* lockstep;  // one counter for lock-step rounds
-  int64_t kp;              // k rounded up to 8
+  int64_t row_pitch;       // elements per row of one k panel (a row block starts at
+                           // row * row_pitch)
 };
 long long emu_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_config& cfg);
 EmuWorkspace emu_carve(void* ws, int64_t m, int64_t n, int64_t k, const cosma_config& cfg);
