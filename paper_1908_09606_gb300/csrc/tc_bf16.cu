@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <mutex>
+#include <string.h>
 
 #include "tc_common.cuh"
 
@@ -59,6 +60,21 @@ int encode_tmap_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t c
   return r == CUDA_SUCCESS ? COSMA_OK : COSMA_ERR_CUDA;
 }
 
+// f32 map for tensor stores of C: 32 x 32 boxes, 128-byte swizzle.
+int encode_tmap_f32_store(CUtensorMap* map, void* base, int64_t rows, int64_t cols, int64_t ld) {
+  auto fn = get_encode();
+  if (!fn) return COSMA_ERR_CUDA;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 4) & 15)) return COSMA_ERR_INVALID_ARG;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? COSMA_OK : COSMA_ERR_CUDA;
+}
+
 namespace {
 
 constexpr int BM = 128;
@@ -89,6 +105,7 @@ struct TcArgs {
   long long wait_limit;
   int vec_ok;  // C rows 16-byte aligned
   float alpha, beta;  // C = alpha A B + beta C (C read only when beta != 0)
+  int c_tma;          // C written by tensor stores (pk == 1, beta == 0, aligned rows)
 };
 
 template <int BN, int STAGES>
@@ -96,7 +113,10 @@ struct Layout {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int BAR_OFF = STAGES * STAGE_BYTES;
+  // epilogue staging: per epilogue warp two 32 x 32 f32 boxes (128-byte swizzle)
+  static constexpr int EPI_OFF = STAGES * STAGE_BYTES;
+  static constexpr int EPI_BYTES = 4 * 2 * 4096;
+  static constexpr int BAR_OFF = EPI_OFF + EPI_BYTES;
   static constexpr int NBARS = 2 * STAGES + 5;  // full, empty, tfull[2], tempty[2], drain
   static constexpr int TOTAL = BAR_OFF + NBARS * 8 + 16;
   static constexpr int ALLOC = TOTAL + 1024;
@@ -130,7 +150,7 @@ __device__ __forceinline__ void store_row32(float* dst, int64_t col0, int64_t n,
 template <int BN, int STAGES, bool A_MN, bool B_MN>
 __global__ void __launch_bounds__(192, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               TcArgs a) {
+               const __grid_constant__ CUtensorMap tmC, TcArgs a) {
   using L = Layout<BN, STAGES>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -263,11 +283,16 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int q = warp & 3;  // tensor-memory lane quadrant this warp may access
     uint32_t acc = 0;
     uint32_t tph[2] = {0, 0};
+    uint8_t* stage_c = smem + L::EPI_OFF + q * 8192;  // this warp's two staging boxes
+    uint32_t stores = 0;                               // tensor stores committed so far
+    const int64_t n4 = a.s.n & ~(int64_t)3;            // columns the C map covers
+    if (warp == 2 && lane == 0 && a.c_tma) tc::prefetch_tmap(&tmC);
     for (int64_t ui = 0; ui < nunits; ++ui) {
       const Unit u = unit_of_cta(a.s, cta, ui);
       if (!tc::mbar_wait(&tfull[acc], tph[acc], w)) break;
       tc::tc_fence_after();
-      const int64_t row = u.tile_row * BM + q * 32 + lane;
+      const int64_t row0 = u.tile_row * BM + q * 32;
+      const int64_t row = row0 + lane;
       float* dst_row = nullptr;
       if (row < a.s.m) {
         dst_row = a.s.pk > 1 ? a.partial + (int64_t)u.ks * a.s.m * a.s.n + row * a.s.n
@@ -280,6 +305,38 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         tc::tmem_ld_32x32(tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN + c, r);
         tc::tmem_wait_ld();
         const int64_t col0 = u.tile_col * BN + c;
+        if (a.c_tma) {
+          // Columns below n4: this warp's 32 rows -> one 32 x 32 box in shared memory
+          // (16-byte chunk j of row l at chunk j ^ (l % 8): the 128-byte swizzle), then
+          // one tensor store clipped at m and n4 (a store clips in whole 16-byte units);
+          // columns n4..n-1 are written by the lanes.
+          if (row0 >= a.s.m || col0 >= a.s.n) continue;
+          if (col0 < n4) {
+            uint8_t* box = stage_c + (stores & 1) * 4096;
+            if (lane == 0) tc::bulk_wait_read<1>();  // the box's previous store has read it
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              float4 v = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                     __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+              if (a.alpha != 1.f) { v.x *= a.alpha; v.y *= a.alpha; v.z *= a.alpha; v.w *= a.alpha; }
+              *reinterpret_cast<float4*>(box + lane * 128 + ((j ^ (lane & 7)) * 16)) = v;
+            }
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+              tc::tma_store_2d(&tmC, box, (int32_t)col0, (int32_t)row0);
+              tc::bulk_commit();
+            }
+            ++stores;
+          }
+          if (dst_row && col0 + 32 > n4) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (col0 + j >= n4 && col0 + j < a.s.n) dst_row[col0 + j] = a.alpha * __uint_as_float(r[j]);
+          }
+          continue;
+        }
         if (dst_row && col0 < a.s.n) {
           if (a.s.pk > 1) store_row32(dst_row + col0, col0, a.s.n, r, vec);
           else store_row32(dst_row + col0, col0, a.s.n, r, vec, a.alpha, a.beta);
@@ -291,6 +348,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       tph[acc] ^= 1;
       acc ^= 1;
     }
+    if (lane == 0) tc::bulk_wait_all();  // stores done before shared memory goes away
+    __syncwarp();
   }
   __syncthreads();
   if (warp == 1) {
@@ -300,8 +359,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 }
 
 template <int BN, int STAGES, bool A_MN, bool B_MN>
-int launch_kernel(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& args,
-                  cudaStream_t st) {
+int launch_kernel(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tcm,
+                  const TcArgs& args, cudaStream_t st) {
   using L = Layout<BN, STAGES>;
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
@@ -311,7 +370,7 @@ int launch_kernel(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& ar
   });
   if (attr != cudaSuccess) return (int)attr;
   prof_mark(st, true);
-  tc_gemm_kernel<BN, STAGES, A_MN, B_MN><<<args.s.ctas, 192, L::ALLOC, st>>>(ta, tb, args);
+  tc_gemm_kernel<BN, STAGES, A_MN, B_MN><<<args.s.ctas, 192, L::ALLOC, st>>>(ta, tb, tcm, args);
   prof_mark(st, false);
   count_launch();
   return (int)cudaGetLastError();
@@ -411,20 +470,30 @@ int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void*
   args.vec_ok = ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0 && (g.ldc & 3) == 0) ? 1 : 0;
   args.alpha = (float)g.alpha;
   args.beta = (float)g.beta;
+  // C by tensor stores when it is written directly with 16-byte aligned rows and
+  // not read (beta == 0); the map is n rounded down to 4 wide.
+  CUtensorMap tcm;
+  memset(&tcm, 0, sizeof(tcm));
+  args.c_tma = 0;
+  if (p.pk == 1 && g.beta == 0.0 && g.n >= 4 && args.vec_ok) {
+    rc = encode_tmap_f32_store(&tcm, g.C, g.m, g.n & ~(int64_t)3, g.ldc);
+    if (rc != COSMA_OK) return rc;
+    args.c_tma = 1;
+  }
   const bool wide = p.tile_n == 256;
   int err;
   if (cp.a_mn && cp.b_mn)
-    err = wide ? launch_kernel<256, 4, true, true>(ta, tb, args, st)
-               : launch_kernel<128, 6, true, true>(ta, tb, args, st);
+    err = wide ? launch_kernel<256, 4, true, true>(ta, tb, tcm, args, st)
+               : launch_kernel<128, 6, true, true>(ta, tb, tcm, args, st);
   else if (cp.a_mn)
-    err = wide ? launch_kernel<256, 4, true, false>(ta, tb, args, st)
-               : launch_kernel<128, 6, true, false>(ta, tb, args, st);
+    err = wide ? launch_kernel<256, 4, true, false>(ta, tb, tcm, args, st)
+               : launch_kernel<128, 6, true, false>(ta, tb, tcm, args, st);
   else if (cp.b_mn)
-    err = wide ? launch_kernel<256, 4, false, true>(ta, tb, args, st)
-               : launch_kernel<128, 6, false, true>(ta, tb, args, st);
+    err = wide ? launch_kernel<256, 4, false, true>(ta, tb, tcm, args, st)
+               : launch_kernel<128, 6, false, true>(ta, tb, tcm, args, st);
   else
-    err = wide ? launch_kernel<256, 4, false, false>(ta, tb, args, st)
-               : launch_kernel<128, 6, false, false>(ta, tb, args, st);
+    err = wide ? launch_kernel<256, 4, false, false>(ta, tb, tcm, args, st)
+               : launch_kernel<128, 6, false, false>(ta, tb, tcm, args, st);
   if (err) return err;
   if (p.pk > 1) return launch_reduce(COSMA_F32, g, p.pk, partial, st);
   return 0;
