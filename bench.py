@@ -83,6 +83,10 @@ DRAM_TRAFFIC = {
     ("4096", "f32"): 0.298e9 + 0.054e9,       # simt_f32_kernel<128,4>
     ("4096", "f64"): 0.969e9 + 0.133e9,       # simt_gemm_kernel<double,64,64,8,4,4>
     ("grouped512", "bf16"): 4.718e9 + 2.027e9,  # grouped_tc_kernel<256,4>
+    # emu_gemm_pair_kernel: the lock-step schedule captured under a plain cluster
+    # launch (COSMA_EMU_LOCKSTEP=2; ncu cannot launch the cooperative one)
+    ("square", "f64_emu_bf16"): 151.47e9 + 2.24e9,
+    ("emu8192", "f64_emu_bf16"): 21.01e9 + 0.546e9,
 }
 
 
@@ -546,9 +550,12 @@ def main():
                                 if dtype == "f64_emu_bf16" else "2mnk flop per launch")}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = DRAM_TRAFFIC.get((args.workload, dtype))
-    if roof["traffic"] is None and roof["kernel"] == "emu_gemm_pair_kernel":
-        roof["traffic_note"] = ("null: ncu cannot launch the cooperative (lock-step) cluster "
-                                "kernel; captures with the pairs free are under profiles/")
+    if roof["kernel"] == "emu_gemm_pair_kernel":
+        roof["traffic_note"] = (
+            "ncu cannot launch the cooperative cluster kernel: traffic is the same lock-step "
+            "schedule captured under a plain cluster launch (COSMA_EMU_LOCKSTEP=2)"
+            if roof["traffic"] is not None else
+            "null: no capture of this workload's lock-step schedule")
     roof["kernel_ms"] = kern_ms
     roof["kernel_launches_timed"] = kern_n
 

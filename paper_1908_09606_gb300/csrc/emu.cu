@@ -884,13 +884,18 @@ int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cos
   if ((sch.tile_m != EBM && !pairs) || sch.tile_n != EBN || sch.k_block != EBK || sch.pk != 1)
     return COSMA_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(C) & 7) return COSMA_ERR_INVALID_ARG;
-  // COSMA_EMU_LOCKSTEP=0 in the environment (read once) runs the pairs free:
-  // profilers that cannot launch cooperative cluster kernels need it.
-  static const bool lockstep_on = [] {
+  // COSMA_EMU_LOCKSTEP in the environment (read once): unset or 1 = lock-step
+  // rounds under a cooperative launch; 0 = pairs free; 2 = lock-step rounds under
+  // a plain cluster launch, for profilers that cannot launch cooperative cluster
+  // kernels -- it relies on the one-pair-per-two-SMs grid being resident, and a
+  // pair that is not would only make the others' bounded waits expire (status
+  // COSMA_ERR_TIMEOUT), never hang.
+  static const int lockstep_mode = [] {
     const char* e = getenv("COSMA_EMU_LOCKSTEP");
-    return !(e && e[0] == '0');
+    return e && e[0] == '0' ? 0 : (e && e[0] == '2' ? 2 : 1);
   }();
-  unsigned int* lockstep_counter = lockstep_on && 2 * sch.ctas <= p.sms ? lockstep : nullptr;
+  unsigned int* lockstep_counter =
+      lockstep_mode != 0 && 2 * sch.ctas <= p.sms ? lockstep : nullptr;
 
   CUtensorMap ta, tb;
   int rc = encode_tmap_slices(&ta, SA, m, k, s, a_slice_rows, EBM);
@@ -943,7 +948,7 @@ int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cos
     cfgl.attrs = at;
     // Lock-step rounds need every pair resident at once: launch cooperatively
     // (at most one CTA per SM here); without that guarantee run free.
-    cfgl.numAttrs = lockstep_counter ? 2 : 1;
+    cfgl.numAttrs = lockstep_counter && lockstep_mode == 1 ? 2 : 1;
     args.lockstep = lockstep_counter;
     if (lockstep_counter &&
         cudaMemsetAsync(lockstep_counter, 0, sizeof(unsigned int), st) != cudaSuccess)
