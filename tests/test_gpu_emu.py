@@ -96,21 +96,26 @@ def test_emu_nonfinite_flagged():
     _run(64, 64, 64)
 
 
-@pytest.mark.parametrize("size,kind", [(8192, "uniform"), (8192, "loguniform"),
-                                       (16384, "uniform")])
-def test_emu_full_size_sampled(size, kind):
+@pytest.mark.parametrize("shape,kind", [((8192,) * 3, "uniform"), ((8192,) * 3, "loguniform"),
+                                        ((16384,) * 3, "uniform"),
+                                        ((4096, 4096, 1 << 20), "uniform"),    # largeK
+                                        ((1 << 20, 4096, 4096), "uniform"),    # largeM
+                                        ((65536, 65536, 1024), "uniform")])    # flat
+def test_emu_full_size_sampled(shape, kind):
     import torch
     cosma = lib()
-    m = n = k = size
+    m, n, k = shape
     A, B = device_operands(m, n, k, DT, kind=kind, seed=0)
     C, _ = out_tensor(m, n, DT)
     cosma.gemm(A, B, C, DT)
     torch.cuda.synchronize()
     assert cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream) == 0
     del A, B
-    rr, cc = sample_indices(m, n, 256, seed=size)
+    rr, cc = sample_indices(m, n, 128 if k > 1 << 16 else 256, seed=m ^ n ^ k)
     ref, _, _, _, _ = sampled_reference(m, n, k, DT, rr, cc, kind=kind)
     got = C[torch.as_tensor(rr, device="cuda"), torch.as_tensor(cc, device="cuda")].cpu().numpy()
+    del C
+    torch.cuda.empty_cache()
     err = og.normwise_rel_error(got, ref)
     assert err <= 1e-12, err
 
