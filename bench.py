@@ -82,7 +82,7 @@ DRAM_TRAFFIC = {
     ("flat", "bf16"): 4.30e9 + 17.15e9,       # same kernel, 16 GB of f32 C
     ("4096", "f32"): 0.298e9 + 0.054e9,       # simt_f32_kernel<128,4>
     ("4096", "f64"): 0.969e9 + 0.133e9,       # simt_gemm_kernel<double,64,64,8,4,4>
-    ("grouped512", "bf16"): 4.718e9 + 2.027e9,  # grouped_tc_kernel<256,4>
+    ("grouped512", "bf16"): 2.27e9 + 1.98e9,    # grouped_tc_kernel<256,4>
     # emu_gemm_pair_kernel: the lock-step schedule captured under a plain cluster
     # launch (COSMA_EMU_LOCKSTEP=2; ncu cannot launch the cooperative one)
     ("square", "f64_emu_bf16"): 151.47e9 + 2.24e9,

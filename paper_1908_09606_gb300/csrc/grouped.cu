@@ -4,7 +4,8 @@
 // group, a device table: per problem its TMA tensor maps and sizes, and a
 // static assignment of all (problem, tile) work units to CTAs -- units sorted
 // by cost (k blocks) and handed to the least-loaded CTA (longest processing
-// time first), so no atomics or device queue are needed.  Each CTA then runs
+// time first, each CTA running its units in that order), so no atomics or device
+// queue are needed.  Each CTA then runs
 // the C-stationary schedule of Listing 1 on its units exactly as the
 // single-product kernels do: bf16 on tcgen05 (TMA ring, TMEM accumulators),
 // f32 on the FMA pipes.  B_i (k x n) is first transposed into the workspace
@@ -624,8 +625,9 @@ int get_table(int dev, int count, const cosma_problem* pr, int dtype, int tile, 
   flat.reserve(U);
   std::vector<int> off(ctas + 1, 0);
   for (int c = 0; c < ctas; ++c) {
-    // within a CTA keep problem / tile order so panels of one problem stay hot
-    std::sort(per[c].begin(), per[c].end());
+    // Each CTA runs its units in assignment order: the CTAs' j-th units are then
+    // neighbours in the cost-sorted, problem-major list -- mostly tiles of one
+    // problem -- so concurrent CTAs share that problem's panels in L2.
     for (int64_t id : per[c]) flat.push_back(units[id]);
     off[c + 1] = (int)flat.size();
   }
