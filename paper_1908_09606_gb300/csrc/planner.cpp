@@ -40,7 +40,7 @@ int tiles_for(int kernel, TileChoice* out) {
       out[0] = {128, 128, 8, 2}; out[1] = {64, 64, 8, 2};
       return 2;
     case COSMA_KERNEL_SIMT_F32:  // 256 x 128 runs 512 threads at a 128-register cap
-      out[0] = {128, 128, 16, 4, 1.0}; out[1] = {256, 128, 16, 4, 0.95};
+      out[0] = {128, 128, 32, 4, 1.0}; out[1] = {256, 128, 32, 4, 0.95};
       return 2;
     case COSMA_KERNEL_TC_BF16:
       out[0] = {128, 256, 64, 4}; out[1] = {128, 128, 64, 6};

@@ -7,10 +7,10 @@
 // of the warp tile and columns 4x..4x+3, 16+4x..16+4x+3.
 //
 // Both panels keep their global layout in shared memory: A row-major with a
-// 20-float pitch (k contiguous), so one 16-byte read gives a thread four k
+// 36-float pitch (k contiguous), so one 16-byte read gives a thread four k
 // steps of one row and the 8 rows a warp reads at once fall in distinct bank
 // quads; B row-major, two 16-byte reads per k step (4 distinct per warp).  Per
-// 4 k steps a thread issues 8 + 8 shared loads for 256 FFMAs.  16-deep k panels
+// 4 k steps a thread issues 8 + 8 shared loads for 256 FFMAs.  32-deep k panels
 // stream through F32_STAGES buffers by cp.async (16-byte copies when A and B
 // are 16-byte aligned with pitches a multiple of 4 floats, else 4-byte): the
 // panels of round t + STAGES - 1 are in flight while round t is multiplied
@@ -21,7 +21,7 @@
 
 namespace cosma {
 
-constexpr int F32_BN = 128, F32_BK = 16, F32_STAGES = 4, F32_APITCH = F32_BK + 4;
+constexpr int F32_BN = 128, F32_BK = 32, F32_STAGES = 4, F32_APITCH = F32_BK + 4;
 
 template <int BM>
 struct F32Smem {
