@@ -246,9 +246,14 @@ def evaluate(shapes, dtype=cosma.COSMA_BF16, cap_bytes=16e9, max_ws_bytes=24e9, 
     return recs
 
 
-def install(params_path, log2_lo=8.0, log2_hi=16.0):
-    """Installs trained selector weights saved by main() (an .npy vector)."""
-    p = np.load(params_path).astype(np.float32)
+SHIPPED_PARAMS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data",
+                              "selector_bf16_gb300.npy")
+
+
+def install(params_path=None, log2_lo=8.0, log2_hi=16.0):
+    """Installs trained selector weights saved by main() (an .npy vector); by default
+    the bf16 weights shipped with the package (trained on a GB300)."""
+    p = np.load(params_path or SHIPPED_PARAMS).astype(np.float32)
     rc = cosma.cosma_selector_set(p, log2_lo, log2_hi)
     if rc != 0:
         raise cosma.CosmaError(rc, "cosma_selector_set")
