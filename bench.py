@@ -80,7 +80,7 @@ def _alu_peak_tflops(dtype, sms):
 DRAM_TRAFFIC = {
     ("square", "bf16"): 10.38e9 + 1.07e9,     # tc_gemm_kernel<256,4,A K,B MN>, tensor-store C
     ("flat", "bf16"): 4.30e9 + 17.15e9,       # same kernel, 16 GB of f32 C
-    ("4096", "f32"): 0.298e9 + 0.054e9,       # simt_f32_kernel<128,4>
+    ("4096", "f32"): 0.289e9 + 0.054e9,       # simt_f32_kernel<128,4>, 32-deep panels
     ("4096", "f64"): 0.969e9 + 0.133e9,       # simt_gemm_kernel<double,64,64,8,4,4>
     ("grouped512", "bf16"): 2.27e9 + 1.98e9,    # grouped_tc_kernel<256,4>
     # emu_gemm_pair_kernel: the lock-step schedule captured under a plain cluster
