@@ -780,6 +780,8 @@ int encode_tmap_slices(CUtensorMap* map, const void* base, int64_t rows, int64_t
 
 }  // namespace
 
+int64_t emu_padded_k(int64_t k) { return emu_kpad(k); }
+
 long long emu_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_config& cfg) {
   const int s = emu_slices(cfg);
   const int64_t kp = emu_kpad(k);

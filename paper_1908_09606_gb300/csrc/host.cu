@@ -159,7 +159,7 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
   if (emu) {
     rc = emu_check_config(ctx.cfg);
     if (rc != COSMA_OK) return rc;
-    if ((k + 2047) / 2048 * 2048 / 32 > 65535) return COSMA_ERR_UNSUPPORTED;
+    if ((emu_padded_k(k) + 31) / 32 > 65535) return COSMA_ERR_UNSUPPORTED;
     void* ws = nullptr;
     rc = lib_scratch(emu_workspace_bytes(m, n, k, ctx.cfg), st, &ws);
     if (rc != COSMA_OK) return rc;

@@ -100,6 +100,8 @@ struct EmuWorkspace {
                            // row * row_pitch)
 };
 long long emu_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_config& cfg);
+// k rounded up to whole panels of the k-blocked slice layout.
+int64_t emu_padded_k(int64_t k);
 EmuWorkspace emu_carve(void* ws, int64_t m, int64_t n, int64_t k, const cosma_config& cfg);
 int emu_check_config(const cosma_config& cfg);
 // Exponents and slices of rows [0, m) of A into eA[0..m) and SA (slice_rows

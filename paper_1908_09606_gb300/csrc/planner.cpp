@@ -13,6 +13,9 @@
 //                       kernel implements, shrunk when (mnk/P)^(1/3) is small --
 //                       eq. optTileShape), the k split pk and the assignment
 //                       order, by an explicit cost model (below).
+//   sched_from_plan     the work-unit schedule of a plan, including the raster
+//                       group of the tiles in flight (the square-tile rule one
+//                       level up, with L2 as the fast memory of the wave).
 #include <math.h>
 #include <string.h>
 #include <algorithm>
