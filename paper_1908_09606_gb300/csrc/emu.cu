@@ -89,9 +89,9 @@ __device__ __forceinline__ int exp_above(double x, int* status) {
   return E - 1022;
 }
 
-// Balanced digits of x relative to the scale exponent sigma (see file header).
-__device__ __forceinline__ void split_digits(double x, int sigma, int L, int beta, int s,
-                                             int (&d)[EMU_MAX_SLICES]) {
+// F = round(|x| 2^(L - sigma)) with the sign of x, from the FP64 bit pattern
+// (0 for zero, non-finite x or an all-zero row / column).
+__device__ __forceinline__ long long scaled_integer(double x, int sigma, int L) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int E = (int)((b >> 52) & 0x7FF);
   unsigned long long M = b & ((1ull << 52) - 1);
@@ -108,6 +108,13 @@ __device__ __forceinline__ void split_digits(double x, int sigma, int L, int bet
     }
     if (b >> 63) F = -F;
   }
+  return F;
+}
+
+// Balanced digits of x relative to the scale exponent sigma (see file header).
+__device__ __forceinline__ void split_digits(double x, int sigma, int L, int beta, int s,
+                                             int (&d)[EMU_MAX_SLICES]) {
+  long long F = scaled_integer(x, sigma, L);
   const long long base = 1LL << beta, half = base >> 1;
 #pragma unroll
   for (int q = EMU_MAX_SLICES - 1; q >= 1; --q) {
@@ -121,6 +128,33 @@ __device__ __forceinline__ void split_digits(double x, int sigma, int L, int bet
     }
   }
   d[0] = (int)F;  // |F| <= 2^(beta-1) here
+}
+
+// The same digits for the default 6 slices of 8 bits (L = 47) in 32-bit
+// arithmetic: with F = hi 2^24 + lo, 0 <= lo < 2^24, the three low digits come
+// from lo alone, their carry (0 or 1) joins hi, and hi gives the rest.
+__device__ __forceinline__ void split_digits_6x8(double x, int sigma, int (&d)[EMU_MAX_SLICES]) {
+  const long long F = scaled_integer(x, sigma, 47);
+  int lo = (int)(F & 0xFFFFFF);
+  int hi = (int)(F >> 24);
+#pragma unroll
+  for (int q = 5; q >= 3; --q) {
+    int r = lo & 255;
+    if (r >= 128) r -= 256;
+    d[q] = r;
+    lo = (lo - r) >> 8;
+  }
+  hi += lo;
+#pragma unroll
+  for (int q = 2; q >= 1; --q) {
+    int r = hi & 255;
+    if (r >= 128) r -= 256;
+    d[q] = r;
+    hi = (hi - r) >> 8;
+  }
+  d[0] = hi;
+#pragma unroll
+  for (int q = 6; q < EMU_MAX_SLICES; ++q) d[q] = 0;
 }
 
 // sigma_i for every row of A (one block per row).
@@ -156,52 +190,77 @@ __global__ void col_exp_kernel(const double* __restrict__ B, int64_t k, int64_t 
 }
 
 // Slices of A in the k-blocked layout (slice_rows rows per panel), zeros for
-// k <= t < kpad; one thread per element.
+// k <= t < kpad.  Each thread takes 4 consecutive t of a row (x: columns in
+// groups of 4, y: rows in steps of gridDim.y) and writes 8 bytes per slice.
 __global__ void split_a_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda,
                                const int* __restrict__ eA, __nv_bfloat16* __restrict__ S,
                                int64_t kpad, int64_t slice_rows, int s, int beta) {
   const int L = beta * s - 1;
-  const int64_t total = m * kpad, nkb = kpad / EKB;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / kpad, t = e - i * kpad;
-    int d[EMU_MAX_SLICES];
-    if (t < k)
-      split_digits(A[i * lda + t], eA[i], L, beta, s, d);
-    else
+  const int64_t nkb = kpad / EKB;
+  const int64_t t0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (t0 >= kpad) return;
+  const bool fast = s == 6 && beta == 8;
+  for (int64_t i = blockIdx.y; i < m; i += gridDim.y) {
+    const int sigma = eA[i];
+    const double* row = A + i * lda;
+    int d[4][EMU_MAX_SLICES];
 #pragma unroll
-      for (int q = 0; q < EMU_MAX_SLICES; ++q) d[q] = 0;
+    for (int v = 0; v < 4; ++v) {
+      const int64_t t = t0 + v;
+      const double x = t < k ? row[t] : 0.0;
+      if (fast) split_digits_6x8(x, sigma, d[v]);
+      else split_digits(x, sigma, L, beta, s, d[v]);
+    }
 #pragma unroll
-    for (int q = 0; q < EMU_MAX_SLICES; ++q)
-      if (q < s) S[slice_at(q, i, t, slice_rows, nkb)] = __float2bfloat16_rn((float)d[q]);
+    for (int q = 0; q < EMU_MAX_SLICES; ++q) {
+      if (q >= s) break;
+      __nv_bfloat162 lo2, hi2;
+      lo2.x = __float2bfloat16_rn((float)d[0][q]);
+      lo2.y = __float2bfloat16_rn((float)d[1][q]);
+      hi2.x = __float2bfloat16_rn((float)d[2][q]);
+      hi2.y = __float2bfloat16_rn((float)d[3][q]);
+      uint2 pk;
+      pk.x = *reinterpret_cast<uint32_t*>(&lo2);
+      pk.y = *reinterpret_cast<uint32_t*>(&hi2);
+      *reinterpret_cast<uint2*>(S + slice_at(q, i, t0, slice_rows, nkb)) = pk;
+    }
   }
 }
 
 // Slices of B, transposed to K-major, in the k-blocked layout (zeros for
-// k <= t < kpad).  32 x 32 tiles; the grid covers kpad.
+// k <= t < kpad).  32 x 32 tiles through shared memory (row pitch 36: 8-byte
+// aligned rows); each thread then writes 4 consecutive t of one column j per
+// slice as one 8-byte store.  The grid covers kpad.
 __global__ void split_b_kernel(const double* __restrict__ B, int64_t k, int64_t n, int64_t ldb,
                                const int* __restrict__ eB, __nv_bfloat16* __restrict__ S,
                                int64_t kpad, int64_t slice_rows, int s, int beta) {
-  __shared__ __nv_bfloat16 tile[EMU_MAX_SLICES][32][34];
+  __shared__ __align__(8) __nv_bfloat16 tile[EMU_MAX_SLICES][32][36];
   const int L = beta * s - 1;
   const int64_t nkb = kpad / EKB;
   const int64_t t0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+  const bool fast = s == 6 && beta == 8;
   for (int r = threadIdx.y; r < 32; r += 8) {
     const int64_t t = t0 + r, j = j0 + threadIdx.x;
     int d[EMU_MAX_SLICES];
-    if (t < k && j < n) split_digits(B[t * ldb + j], eB[j], L, beta, s, d);
-    else
+    if (t < k && j < n) {
+      if (fast) split_digits_6x8(B[t * ldb + j], eB[j], d);
+      else split_digits(B[t * ldb + j], eB[j], L, beta, s, d);
+    } else {
 #pragma unroll
       for (int q = 0; q < EMU_MAX_SLICES; ++q) d[q] = 0;
+    }
 #pragma unroll
     for (int q = 0; q < EMU_MAX_SLICES; ++q)
       if (q < s) tile[q][threadIdx.x][r] = __float2bfloat16_rn((float)d[q]);
   }
   __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    const int64_t j = j0 + r, t = t0 + threadIdx.x;
-    if (j < n && t < kpad)
-      for (int q = 0; q < s; ++q) S[slice_at(q, j, t, slice_rows, nkb)] = tile[q][r][threadIdx.x];
+  const int lid = threadIdx.y * 32 + threadIdx.x;  // 0..255: column jj, 4-group g
+  const int jj = lid >> 3, g = lid & 7;
+  const int64_t j = j0 + jj, t = t0 + 4 * g;
+  if (j < n && t < kpad) {
+    for (int q = 0; q < s; ++q)
+      *reinterpret_cast<uint2*>(S + slice_at(q, j, t, slice_rows, nkb)) =
+          *reinterpret_cast<const uint2*>(&tile[q][jj][4 * g]);
   }
 }
 
@@ -782,6 +841,19 @@ int encode_tmap_slices(CUtensorMap* map, const void* base, int64_t rows, int64_t
 
 int64_t emu_padded_k(int64_t k) { return emu_kpad(k); }
 
+namespace {
+// split_a_kernel grid: x covers kpad in 1024-column groups, y enough rows to fill
+// the GPU (the kernel strides over the rest).
+dim3 split_a_grid(int64_t rows, int64_t kpad) {
+  const int64_t gx = (kpad + 1023) / 1024;
+  int64_t gy = (152LL * 16 + gx - 1) / gx;
+  if (gy > rows) gy = rows;
+  if (gy > 65535) gy = 65535;
+  if (gy < 1) gy = 1;
+  return dim3((unsigned)gx, (unsigned)gy);
+}
+}  // namespace
+
 long long emu_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_config& cfg) {
   const int s = emu_slices(cfg);
   const int64_t kp = emu_kpad(k);
@@ -836,11 +908,9 @@ int emu_prepare_a(const double* A, int64_t m, int64_t k, int64_t lda, int trans,
   const int64_t rb = m < 65535LL * 16 ? m : 65535LL * 16;
   row_exp_kernel<<<(unsigned)rb, 256, 0, st>>>(A, m, k, lda, eA, status);
   count_launch();
-  int64_t blocks = (m * kp + 255) / 256;
-  if (blocks > 152LL * 64) blocks = 152LL * 64;
-  split_a_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, m, k, lda, eA,
-                                                   static_cast<__nv_bfloat16*>(SA), kp,
-                                                   slice_rows, s, beta);
+  split_a_kernel<<<split_a_grid(m, kp), 256, 0, st>>>(A, m, k, lda, eA,
+                                                      static_cast<__nv_bfloat16*>(SA), kp,
+                                                      slice_rows, s, beta);
   count_launch();
   return (int)cudaGetLastError();
 }
@@ -855,11 +925,9 @@ int emu_prepare_b(const double* B, int64_t k, int64_t n, int64_t ldb, int trans,
     const int64_t rb = n < 65535LL * 16 ? n : 65535LL * 16;
     row_exp_kernel<<<(unsigned)rb, 256, 0, st>>>(B, n, k, ldb, eB, status);
     count_launch();
-    int64_t blocks = (n * kp + 255) / 256;
-    if (blocks > 152LL * 64) blocks = 152LL * 64;
-    split_a_kernel<<<(unsigned)blocks, 256, 0, st>>>(B, n, k, ldb, eB,
-                                                     static_cast<__nv_bfloat16*>(SB), kp,
-                                                     slice_rows, s, beta);
+    split_a_kernel<<<split_a_grid(n, kp), 256, 0, st>>>(B, n, k, ldb, eB,
+                                                        static_cast<__nv_bfloat16*>(SB), kp,
+                                                        slice_rows, s, beta);
     count_launch();
     return (int)cudaGetLastError();
   }
