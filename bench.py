@@ -85,8 +85,7 @@ DRAM_TRAFFIC = {
     ("grouped512", "bf16"): 2.27e9 + 1.98e9,    # grouped_tc_kernel<256,4>
     # emu_gemm_pair_kernel: the lock-step schedule captured under a plain cluster
     # launch (COSMA_EMU_LOCKSTEP=2; ncu cannot launch the cooperative one)
-    ("square", "f64_emu_bf16"): 151.47e9 + 2.24e9,
-    ("emu8192", "f64_emu_bf16"): 21.01e9 + 0.546e9,
+    ("square", "f64_emu_bf16"): 73.60e9 + 2.24e9,
 }
 
 

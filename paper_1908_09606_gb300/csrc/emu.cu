@@ -18,7 +18,7 @@
 //           products; the k loop is cut into groups of that size, and each
 //           group's exact integer sum is drained by the epilogue warps into an
 //           int32 level sum held in registers.  k is walked in super-chunks of
-//           2048 (all levels per chunk), so a level sum stays below 2^31 for any
+//           1024 (all levels per chunk), so a level sum stays below 2^31 for any
 //           k and the slice panels a wave of tiles touches stay in L2.  Three
 //           accumulator buffers let the MMAs of the next groups overlap a drain.
 //  K-RECOMB At the end of each (chunk, level) the exact level sum joins a
@@ -990,11 +990,12 @@ int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cos
   args.alpha = alpha;
   args.beta_c = beta_c;
   // Super-chunk: short enough for the slice panels of a wave of tiles to stay in
-  // L2 (2048 k), and for every level sum of a chunk to fit in int32 exactly
-  // (at most s pairs x chunk x 2^(2 beta - 2)).
+  // L2 across all levels (1024 k: at 16384^3 half the DRAM bytes of 2048, at the
+  // same time; 512 would double the merges again), and for every level sum of a
+  // chunk to fit in int32 exactly (at most s pairs x chunk x 2^(2 beta - 2)).
   {
     const double lim = 2147483647.0 / ((double)s * std::ldexp(1.0, 2 * beta - 2));
-    int64_t ck = 2048 / EBK;
+    int64_t ck = 1024 / EBK;
     while (ck > 1 && (double)ck * EBK > lim) --ck;
     args.chunk_kb = (int)ck;
   }
