@@ -8,7 +8,7 @@ recombination.  Inputs are generated on the device by the shared seeded
 generator before the timed region and are larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload square]
-                  [--dtype f64_emu_bf16|f64|f32|bf16] [--impl reference]
+                  [--dtype f64_emu_bf16|f64|f32|bf16|f32_emu_tf32] [--impl reference]
 
 Under torchrun each rank runs its own replica of the workload (the path needs
 no exchange between GPUs): value = all ranks' flops / max-over-ranks time.
@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="square", choices=list(WORKLOADS))
     ap.add_argument("--dtype", default=DEFAULT_DTYPE,
-                    choices=["f64", "f32", "bf16", "f64_emu_bf16"])
+                    choices=["f64", "f32", "bf16", "f64_emu_bf16", "f32_emu_tf32"])
     ap.add_argument("--impl", default="cosma", choices=["cosma", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -93,24 +93,29 @@ def io_report(m, n, k, dtype, plan, traffic, l2_bytes, sms, smem_per_sm):
     """Planned L2->SM words against Theorem 1 at one SM's S, and DRAM bytes
     against Theorem 1 at the chip's fast memory (L2 + all SMs) and against the
     compulsory bytes."""
-    w_in = {"f64": 8, "f32": 4, "bf16": 2, "f64_emu_bf16": 2}[dtype]
-    w_out = {"f64": 8, "f32": 4, "bf16": 4, "f64_emu_bf16": 8}[dtype]
+    w_in = {"f64": 8, "f32": 4, "bf16": 2, "f64_emu_bf16": 2, "f32_emu_tf32": 4}[dtype]
+    w_out = {"f64": 8, "f32": 4, "bf16": 4, "f64_emu_bf16": 8, "f32_emu_tf32": 4}[dtype]
     reg_or_tmem = 262144
     s_chip = (l2_bytes + sms * (smem_per_sm + reg_or_tmem)) / w_in
-    products = 1
+    passes = 1  # times the operands are read over: slice pairs, or TF32 parts
     compulsory = w_in * (m * k + k * n) + w_out * m * n
     if dtype == "f64_emu_bf16":
         slices = 6
-        products = slices * (slices + 1) // 2
+        passes = slices * (slices + 1) // 2
         compulsory = w_in * slices * (m * k + k * n) + w_out * m * n
-    thm1_chip_words = products * 2.0 * m * n * k / math.sqrt(s_chip) + m * n
+    if dtype == "f32_emu_tf32":
+        # hi and lo parts of both operands: read as one product of inner dimension
+        # 2k ([A_h A_l] times [B_h; B_l]), of which three of the four blocks are used
+        passes = 2
+        compulsory = w_in * 2 * (m * k + k * n) + w_out * m * n
+    thm1_chip_words = passes * 2.0 * m * n * k / math.sqrt(s_chip) + m * n
     out = {"S_sm_words": plan.fast_words, "S_chip_words": s_chip,
-           "l2_to_sm_words_planned": plan.io_words * products,
-           "theorem1_words_at_S_sm": products * (plan.bound_words - m * n) + m * n,
+           "l2_to_sm_words_planned": plan.io_words * passes,
+           "theorem1_words_at_S_sm": passes * (plan.bound_words - m * n) + m * n,
            "dram_bytes_per_launch": traffic,
            "theorem1_bytes_at_S_chip": thm1_chip_words * w_in,
            "compulsory_bytes": compulsory,
-           "products_per_call": products}
+           "operand_passes_per_call": passes}
     out["ratio_l2_sm"] = out["l2_to_sm_words_planned"] / out["theorem1_words_at_S_sm"]
     if traffic:
         out["ratio_dram_vs_theorem1_chip"] = traffic / out["theorem1_bytes_at_S_chip"]
@@ -119,7 +124,7 @@ def io_report(m, n, k, dtype, plan, traffic, l2_bytes, sms, smem_per_sm):
 
 
 def workload_config(name, m, n, k, dtype):
-    w = {"f64": 8, "f32": 4, "bf16": 2, "f64_emu_bf16": 8}[dtype]
+    w = {"f64": 8, "f32": 4, "bf16": 2, "f64_emu_bf16": 8, "f32_emu_tf32": 4}[dtype]
     return {"workload": f"{name} m={m} n={n} k={k} {dtype} uniform[-1,1) seed 0",
             "m": m, "n": n, "k": k, "operands": "row-major, device-generated (Philox4x32-10)",
             "l2": "inputs larger than L2" if (m * k + k * n) * w > 130e6 else "inputs fit in L2"}
@@ -240,7 +245,7 @@ def run_reference(args):
         return 0
     m, n, k = WORKLOADS[args.workload]
     dtype = args.dtype
-    gen = "f32" if dtype == "f32" else "f64"
+    gen = "f32" if dtype in ("f32", "f32_emu_tf32") else "f64"
     vals = []
     rows = None
     for i in range(args.warmup + args.steps):
@@ -469,9 +474,10 @@ def main():
     m, n, k = WORKLOADS[args.workload]
     dtype = args.dtype
     code = cosma.DTYPES[dtype]
-    gen = {"f64": "f64", "f32": "f32", "bf16": "bf16", "f64_emu_bf16": "f64"}[dtype]
+    gen = {"f64": "f64", "f32": "f32", "bf16": "bf16", "f64_emu_bf16": "f64",
+           "f32_emu_tf32": "f32"}[dtype]
     tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[gen]
-    out_dt = torch.float32 if dtype in ("f32", "bf16") else torch.float64
+    out_dt = torch.float32 if dtype in ("f32", "bf16", "f32_emu_tf32") else torch.float64
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
 
@@ -535,6 +541,15 @@ def main():
                 "peak": _alu_peak_tflops(dtype, sms), "unit": "TFLOP/s",
                 "peak_source": "derived: SMs x FMA lanes/clk x 2 x 2070 MHz",
                 "algorithmic": "2mnk flop per launch"}
+    elif dtype == "f32_emu_tf32":
+        # tf32 peak: the measured bf16 peak x the nominal tf32 / bf16 ratio (1.1 / 2.25)
+        roof = {"kernel": "tf32x3_gemm_kernel", "bound": "tensor",
+                "achieved": 3 * flops / (kern_ms * 1e-3) / 1e12,
+                "peak": peaks.get("bf16_tflops_sustained", 1700.0) * 1.1 / 2.25,
+                "unit": "TFLOP/s",
+                "peak_source": f"bf16_tflops_sustained of {peak_src} peaks x 1.1/2.25 "
+                               "(nominal dense tf32 / bf16)",
+                "algorithmic": "3 part products x 2mnk tf32 flop per launch"}
     else:
         work = flops * (pairs if dtype == "f64_emu_bf16" else 1)
         if dtype == "f64_emu_bf16":
@@ -627,7 +642,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         import numpy as np
         from oracle import gemm as og
-        gen_o = "f32" if dtype == "f32" else ("bf16" if dtype == "bf16" else "f64")
+        gen_o = gen
         fl, dt, rows, ref = oracle_sample(m, n, k, 12.0, gen=gen_o, seed=rank, keep=True)
         cpu = {"value": fl / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
                "sample": f"oracle naive FP64 loop, {rows}x{rows} leading block of C, "
@@ -650,7 +665,8 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {"f64": "f64", "f32": "f32", "bf16": "bf16",
-                          "f64_emu_bf16": "bf16 slices -> f64"}[dtype],
+                          "f64_emu_bf16": "bf16 slices -> f64",
+                          "f32_emu_tf32": "tf32 parts -> f32"}[dtype],
                 "data": "synthetic", "config": cfg, "roofline": roof, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
                 "native_f64": native, "error_vs_oracle": errors,

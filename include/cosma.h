@@ -42,13 +42,17 @@ extern "C" {
 /* Element types of a call.  BF16: A and B are bf16, C is fp32.
  * F64_EMU_BF16: A, B, C are fp64; the product is formed from bf16 slices on
  * the tensor cores (Ozaki-style splitting) and recombined in high precision.
- * F64_EMU_INT8 is reserved (returns COSMA_ERR_UNSUPPORTED). */
+ * F64_EMU_INT8 is reserved (returns COSMA_ERR_UNSUPPORTED).
+ * F32_EMU_TF32: A, B, C are fp32; each operand is split into TF32 hi and lo
+ * parts and C = A_hi B_hi + A_hi B_lo + A_lo B_hi is accumulated in fp32 on the
+ * tensor cores (elementwise error within (gamma_3k(2^-23) + 3 2^-22) |A||B|). */
 typedef enum {
   COSMA_F64 = 0,
   COSMA_F32 = 1,
   COSMA_BF16 = 2,
   COSMA_F64_EMU_BF16 = 3,
-  COSMA_F64_EMU_INT8 = 4
+  COSMA_F64_EMU_INT8 = 4,
+  COSMA_F32_EMU_TF32 = 5
 } cosma_dtype;
 
 typedef enum {
@@ -74,7 +78,8 @@ typedef enum {
   COSMA_KERNEL_SIMT_F64 = 0,  /* FP64 FMA, C tile in registers          */
   COSMA_KERNEL_SIMT_F32 = 1,  /* FP32 FMA, C tile in registers          */
   COSMA_KERNEL_TC_BF16 = 2,   /* tcgen05 kind::f16, C tile in TMEM       */
-  COSMA_KERNEL_EMU_BF16 = 3   /* tcgen05 bf16 slices, FP64 recombination */
+  COSMA_KERNEL_EMU_BF16 = 3,  /* tcgen05 bf16 slices, FP64 recombination */
+  COSMA_KERNEL_TF32X3 = 4     /* tcgen05 kind::tf32, three part products   */
 } cosma_kernel;
 
 /* Library configuration (all fields have defaults; see cosma_init).  The

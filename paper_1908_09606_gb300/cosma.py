@@ -11,9 +11,11 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libcosma_gb300.so")
 
-COSMA_F64, COSMA_F32, COSMA_BF16, COSMA_F64_EMU_BF16, COSMA_F64_EMU_INT8 = range(5)
+(COSMA_F64, COSMA_F32, COSMA_BF16, COSMA_F64_EMU_BF16, COSMA_F64_EMU_INT8,
+ COSMA_F32_EMU_TF32) = range(6)
 DTYPES = {"f64": COSMA_F64, "f32": COSMA_F32, "bf16": COSMA_BF16,
-          "f64_emu_bf16": COSMA_F64_EMU_BF16, "f64_emu_int8": COSMA_F64_EMU_INT8}
+          "f64_emu_bf16": COSMA_F64_EMU_BF16, "f64_emu_int8": COSMA_F64_EMU_INT8,
+          "f32_emu_tf32": COSMA_F32_EMU_TF32}
 COSMA_OK = 0
 COSMA_ERR_INVALID_ARG = -1
 COSMA_ERR_UNSUPPORTED = -2
@@ -22,7 +24,7 @@ COSMA_ERR_TIMEOUT = -4
 COSMA_ERR_NONFINITE = -5
 COSMA_ERR_NO_WORKSPACE = -6
 COSMA_SELECT_ANALYTIC, COSMA_SELECT_LEARNED = 0, 1
-KERNELS = {0: "simt_f64", 1: "simt_f32", 2: "tc_bf16", 3: "emu_bf16"}
+KERNELS = {0: "simt_f64", 1: "simt_f32", 2: "tc_bf16", 3: "emu_bf16", 4: "tf32x3"}
 
 
 class cosma_config(ctypes.Structure):

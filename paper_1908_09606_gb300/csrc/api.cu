@@ -16,6 +16,9 @@ int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void*
                    long long ws_bytes, int* status, long long wait_limit, cudaStream_t st);
 long long tc_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const void* A,
                              int64_t lda, int trans_a, const void* B, int64_t ldb, int trans_b);
+long long tf32x3_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_plan& p);
+int launch_tc_tf32x3(const GemmArgs& g, const Sched& s, const cosma_plan& p, void* ws,
+                     long long ws_bytes, int* status, long long wait_limit, cudaStream_t st);
 int grouped_gemm(int count, const cosma_problem* problems, int dtype, const DeviceInfo& dev,
                  void* ws, long long ws_bytes, int* status, long long wait_limit, cudaStream_t st,
                  long long* needed, int requested_tile);
@@ -191,16 +194,19 @@ bool is_device_ptr(const void* p) {
 
 int elem_bytes_in(int dtype) {
   switch (dtype) {
-    case COSMA_F32: return 4;
+    case COSMA_F32:
+    case COSMA_F32_EMU_TF32: return 4;
     case COSMA_BF16: return 2;
     default: return 8;
   }
 }
-int elem_bytes_out(int dtype) { return dtype == COSMA_F32 || dtype == COSMA_BF16 ? 4 : 8; }
+int elem_bytes_out(int dtype) {
+  return dtype == COSMA_F32 || dtype == COSMA_BF16 || dtype == COSMA_F32_EMU_TF32 ? 4 : 8;
+}
 
 int check_args(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void* B,
                int64_t ldb, const void* C, int64_t ldc, int dtype, int ta = 0, int tb = 0) {
-  if (dtype < COSMA_F64 || dtype > COSMA_F64_EMU_INT8) return COSMA_ERR_INVALID_ARG;
+  if (dtype < COSMA_F64 || dtype > COSMA_F32_EMU_TF32) return COSMA_ERR_INVALID_ARG;
   if (m < 0 || n < 0 || k < 0) return COSMA_ERR_INVALID_ARG;
   if ((ta != 0 && ta != 1) || (tb != 0 && tb != 1)) return COSMA_ERR_INVALID_ARG;
   const int64_t a_cols = ta ? m : k, b_cols = tb ? k : n;
@@ -224,6 +230,7 @@ long long total_workspace(int64_t m, int64_t n, int64_t k, int dtype, const cosm
                           int64_t ldb = 0, int ta = 0, int tb = 0) {
   if (dtype == COSMA_F64_EMU_BF16) return emu_workspace_bytes(m, n, k, g_cfg);
   if (dtype == COSMA_BF16) return tc_workspace_bytes(m, n, k, p, A, lda, ta, B, ldb, tb);
+  if (dtype == COSMA_F32_EMU_TF32) return tf32x3_workspace_bytes(m, n, k, p);
   // FMA paths: split-k partials, then untransposed copies of transposed operands
   const int w = dtype == COSMA_F32 ? 4 : 8;
   long long b = workspace_bytes(m, n, k, dtype, p);
@@ -314,6 +321,9 @@ int run(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void*
       break;
     case COSMA_KERNEL_EMU_BF16:
       err = launch_emu_bf16(g, p, g_cfg, ws, have, s->d_status, wl, st);
+      break;
+    case COSMA_KERNEL_TF32X3:
+      err = launch_tc_tf32x3(g, sc, p, ws, have, s->d_status, wl, st);
       break;
     default:
       return COSMA_ERR_INVALID_ARG;

@@ -87,8 +87,12 @@ int staging(HostState& h, size_t bytes, cudaStream_t st, uint8_t** out) {
   return COSMA_OK;
 }
 
-int in_bytes(int dtype) { return dtype == COSMA_F32 ? 4 : dtype == COSMA_BF16 ? 2 : 8; }
-int out_bytes(int dtype) { return dtype == COSMA_F32 || dtype == COSMA_BF16 ? 4 : 8; }
+int in_bytes(int dtype) {
+  return dtype == COSMA_F32 || dtype == COSMA_F32_EMU_TF32 ? 4 : dtype == COSMA_BF16 ? 2 : 8;
+}
+int out_bytes(int dtype) {
+  return dtype == COSMA_F32 || dtype == COSMA_BF16 || dtype == COSMA_F32_EMU_TF32 ? 4 : 8;
+}
 
 // Block boundaries along a dimension: 1 block, or 2 split at a multiple of 256.
 int blocks_of(int64_t len, int64_t cut[kMaxR + 1]) {
@@ -123,7 +127,7 @@ using namespace cosma;
 extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda,
                                const void* B, int64_t ldb, void* C, int64_t ldc, int dtype,
                                void* stream) {
-  if (dtype < COSMA_F64 || dtype > COSMA_F64_EMU_INT8) return COSMA_ERR_INVALID_ARG;
+  if (dtype < COSMA_F64 || dtype > COSMA_F32_EMU_TF32) return COSMA_ERR_INVALID_ARG;
   if (m < 0 || n < 0 || k < 0) return COSMA_ERR_INVALID_ARG;
   if (lda < (k > 1 ? k : 1) || ldb < (n > 1 ? n : 1) || ldc < (n > 1 ? n : 1))
     return COSMA_ERR_INVALID_ARG;

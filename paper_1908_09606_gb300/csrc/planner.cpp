@@ -51,6 +51,9 @@ int tiles_for(int kernel, TileChoice* out) {
     case COSMA_KERNEL_EMU_BF16:  // 256-row tiles run on CTA pairs (2 SMs per tile)
       out[0] = {256, 128, 64, 6}; out[1] = {128, 128, 64, 5};
       return 2;
+    case COSMA_KERNEL_TF32X3:  // k blocks of 32 f32 (one 128-byte row); C sums in registers
+      out[0] = {128, 128, 32, 3};
+      return 1;
   }
   return 0;
 }
@@ -72,6 +75,10 @@ KernelDesc desc_for(int dtype, const DeviceInfo& dev) {
     case COSMA_BF16:
       d.kernel = COSMA_KERNEL_TC_BF16; d.w_in = 2; d.w_acc = 4; d.w_out = 4;
       d.fast_bytes = smem + tmem; d.flops_per_clk_sm = 8192.0; d.efficiency = 0.8;
+      break;
+    case COSMA_F32_EMU_TF32:  // three tf32 products at half the bf16 rate
+      d.kernel = COSMA_KERNEL_TF32X3; d.w_in = 4; d.w_acc = 4; d.w_out = 4;
+      d.fast_bytes = smem + tmem; d.flops_per_clk_sm = 4096.0 / 3.0; d.efficiency = 0.8;
       break;
     default:  // emulated FP64: bf16 slices
       d.kernel = COSMA_KERNEL_EMU_BF16; d.w_in = 2; d.w_acc = 8; d.w_out = 8;
@@ -138,7 +145,7 @@ int fit_ranks_weighted(int64_t m, int64_t n, int64_t k, int p, double delta, dou
 long long workspace_bytes(int64_t m, int64_t n, int64_t k, int dtype, const cosma_plan& p) {
   auto align = [](long long x) { return (x + 255) / 256 * 256; };
   long long bytes = 0;
-  const int w_acc = (dtype == COSMA_F32 || dtype == COSMA_BF16) ? 4 : 8;
+  const int w_acc = (dtype == COSMA_F32 || dtype == COSMA_BF16 || dtype == COSMA_F32_EMU_TF32) ? 4 : 8;
   if (p.pk > 1) bytes += align((long long)p.pk * m * n * w_acc);
   if (dtype == COSMA_BF16) bytes += align((long long)n * k * 2);  // B^T (k-major) copy
   return bytes;
@@ -246,7 +253,7 @@ int plan_candidate(int64_t m, int64_t n, int64_t k, int dtype, int c, const Devi
 int plan_gemm(int64_t m, int64_t n, int64_t k, int dtype, int selector, const DeviceInfo& dev,
               const cosma_config& cfg, cosma_plan* out, bool may_sync) {
   if (!out || m < 0 || n < 0 || k < 0) return COSMA_ERR_INVALID_ARG;
-  if (dtype < COSMA_F64 || dtype > COSMA_F64_EMU_INT8) return COSMA_ERR_INVALID_ARG;
+  if (dtype < COSMA_F64 || dtype > COSMA_F32_EMU_TF32) return COSMA_ERR_INVALID_ARG;
   if (dtype == COSMA_F64_EMU_INT8) return COSMA_ERR_UNSUPPORTED;
   if (selector == COSMA_SELECT_LEARNED) {
     const int rc = learned_plan(m, n, k, dtype, dev, cfg, out, may_sync);

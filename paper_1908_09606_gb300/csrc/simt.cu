@@ -141,7 +141,7 @@ int launch_scale(int dtype, const GemmArgs& g, cudaStream_t st) {
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
   if (blocks < 1) return 0;
-  if (dtype == COSMA_F32 || dtype == COSMA_BF16)
+  if (dtype == COSMA_F32 || dtype == COSMA_BF16 || dtype == COSMA_F32_EMU_TF32)
     scale_kernel<float><<<(unsigned)blocks, 256, 0, st>>>(g.m, g.n, static_cast<float*>(g.C),
                                                           g.ldc, (float)g.beta);
   else
@@ -204,7 +204,7 @@ int launch_reduce(int dtype, const GemmArgs& g, int pk, const void* partial, cud
   const int64_t total = g.m * g.n;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  if (dtype == COSMA_F64)
+  if (dtype == COSMA_F64 || dtype == COSMA_F64_EMU_BF16)
     reduce_kernel<double><<<(unsigned)blocks, 256, 0, st>>>(
         g.m, g.n, pk, static_cast<const double*>(partial), static_cast<double*>(g.C), g.ldc,
         g.alpha, g.beta);

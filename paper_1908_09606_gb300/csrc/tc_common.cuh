@@ -110,6 +110,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int32_t x, int32_t y, int32_t z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
 // Tensor store shared -> global of one box at (x, y), tracked by the bulk group
 // of the issuing thread.
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int32_t x,
@@ -178,6 +187,16 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
           smem_u32(bar))
+      : "memory");
+}
+
+// D (+)= A B with A, B tf32 (f32 containers), K = 8 per instruction.
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -273,6 +292,14 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
          | ((uint32_t)(N >> 3) << 17)
          | ((uint32_t)(M >> 4) << 24);
 }
+// Instruction descriptor, kind::tf32: A, B tf32 (K-major), D f32, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32_f32(int M, int N) {
+  return (1u << 4)                 // D format f32
+         | (2u << 7)               // A format tf32
+         | (2u << 10)              // B format tf32
+         | ((uint32_t)(N >> 3) << 17)
+         | ((uint32_t)(M >> 4) << 24);
+}
 // Same with B MN-major (the B operand's "transpose" bit).
 __host__ __device__ constexpr uint32_t idesc_bf16_f32_bmn(int M, int N) {
   return idesc_bf16_f32(M, N) | (1u << 16);
@@ -343,5 +370,11 @@ __device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
 // box of box_cols x box_rows and 128-byte swizzle.  Returns 0 on success.
 int encode_tmap_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
                      int box_cols, int box_rows);
+
+// Host: encode a 3-D f32 map of two stacked parts [2][rows][kp] (k columns used,
+// row pitch kp elements, kp a multiple of 4) with 32 x box_rows x 1 boxes and
+// 128-byte swizzle.  Returns 0 on success.
+int encode_tmap_f32_parts(CUtensorMap* map, const float* base, int64_t rows, int64_t k,
+                          int64_t kp, int box_rows);
 
 }  // namespace cosma

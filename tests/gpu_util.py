@@ -7,8 +7,10 @@ from oracle import gemm as og
 
 TORCH_DT = {"f64": "float64", "f32": "float32", "bf16": "bfloat16"}
 # operand element type generated for each library dtype
-GEN_DT = {"f64": "f64", "f32": "f32", "bf16": "bf16", "f64_emu_bf16": "f64"}
-OUT_DT = {"f64": "float64", "f32": "float32", "bf16": "float32", "f64_emu_bf16": "float64"}
+GEN_DT = {"f64": "f64", "f32": "f32", "bf16": "bf16", "f64_emu_bf16": "f64",
+          "f32_emu_tf32": "f32"}
+OUT_DT = {"f64": "float64", "f32": "float32", "bf16": "float32", "f64_emu_bf16": "float64",
+          "f32_emu_tf32": "float32"}
 
 
 def lib():

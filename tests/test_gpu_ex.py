@@ -3,7 +3,8 @@ gemm_ex, through the C ABI, for every dtype and all four transpose cases.
 
 Bound, elementwise: |C_hat - C| <= |alpha| err_prod + 4 u_out (|alpha P| + |beta C0|),
 err_prod being each path's product bound -- gamma_k |A||B| for the FMA and bf16
-paths (u = 2^-53 / 2^-24 / 2^-23), 1e-12 ||a_i|| ||b_j|| for the emulation -- and
+paths (u = 2^-53 / 2^-24 / 2^-23), 1e-12 ||a_i|| ||b_j|| for the FP64 emulation,
+(1.002 gamma_3k(2^-23) + 3.01 2^-22) |A||B| for three TF32 products -- and
 u_out the unit roundoff of C's type (alpha and beta are applied in it).  alpha and
 beta are chosen exactly representable in f32.
 """
@@ -15,9 +16,10 @@ from oracle import gemm as og
 
 pytestmark = pytest.mark.gpu
 
-DTYPES = ["f64", "f32", "bf16", "f64_emu_bf16"]
+DTYPES = ["f64", "f32", "bf16", "f64_emu_bf16", "f32_emu_tf32"]
 U_PROD = {"f64": 2.0 ** -53, "f32": 2.0 ** -24, "bf16": 2.0 ** -23}
-U_OUT = {"f64": 2.0 ** -53, "f32": 2.0 ** -24, "bf16": 2.0 ** -24, "f64_emu_bf16": 2.0 ** -53}
+U_OUT = {"f64": 2.0 ** -53, "f32": 2.0 ** -24, "bf16": 2.0 ** -24, "f64_emu_bf16": 2.0 ** -53,
+         "f32_emu_tf32": 2.0 ** -24}
 
 
 def _operands(m, n, k, dtype, ta, tb, seed):
@@ -48,6 +50,9 @@ def _bound(dtype, Ah, Bh, ta, tb, C0, alpha, beta):
     P = og.gemm(opA, opB, "dot2")
     if dtype == "f64_emu_bf16":
         prod = 1e-12 * np.sqrt((opA ** 2).sum(1))[:, None] * np.sqrt((opB ** 2).sum(0))[None, :]
+    elif dtype == "f32_emu_tf32":
+        g = 3 * k * 2.0 ** -23 / (1 - 3 * k * 2.0 ** -23)
+        prod = (1.002 * g + 3.01 * 2.0 ** -22) * og.gemm(np.abs(opA), np.abs(opB), "naive")
     else:
         u = U_PROD[dtype]
         prod = (k * u / (1 - k * u)) * og.gemm(np.abs(opA), np.abs(opB), "naive")
@@ -77,7 +82,7 @@ def test_gemm_ex_matches_oracle(dtype, ta, tb, alpha, beta):
     assert not bad.any(), f"{bad.sum()} entries out of bound, first at {np.argwhere(bad)[0]}"
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "f32_emu_tf32"])
 def test_gemm_ex_split_k_reduce_applies_alpha_beta(dtype):
     cosma = lib()
     m, n, k = 96, 80, 6000
