@@ -86,6 +86,8 @@ DRAM_TRAFFIC = {
     # emu_gemm_pair_kernel: the lock-step schedule captured under a plain cluster
     # launch (COSMA_EMU_LOCKSTEP=2; ncu cannot launch the cooperative one)
     ("square", "f64_emu_bf16"): 73.60e9 + 2.24e9,
+    # tf32x3_gemm_kernel: lock-step ticks under a plain launch (COSMA_TF32_LOCKSTEP=2)
+    ("square", "f32_emu_tf32"): 56.46e9 + 1.07e9,
 }
 
 
@@ -570,6 +572,9 @@ def main():
             "schedule captured under a plain cluster launch (COSMA_EMU_LOCKSTEP=2)"
             if roof["traffic"] is not None else
             "null: no capture of this workload's lock-step schedule")
+    if roof["kernel"] == "tf32x3_gemm_kernel" and roof["traffic"] is not None:
+        roof["traffic_note"] = ("captured with the lock-step ticks under a plain launch "
+                                "(COSMA_TF32_LOCKSTEP=2); the bench launches cooperatively")
     roof["kernel_ms"] = kern_ms
     roof["kernel_launches_timed"] = kern_n
 

@@ -25,9 +25,17 @@
 // f32 each (one 128-byte swizzled row per tile row), by four 3-D TMA copies.
 // Warp roles as in K-BF16: warp 0 TMA, warp 1 tensor memory + MMA, warps 2-5
 // segment sums and stores (warp w reads tensor-memory lanes 32 (w % 4) ..).
+//
+// Lock-step ticks (balanced-stripe plans under a cooperative launch): the k
+// range of every unit is walked in ticks of TICK k blocks; each producer adds
+// one to a global counter per tick and does not start tick T before the
+// counter says the CTAs have, on average, finished tick T - WINDOW.  The
+// CTAs of a wave then stream the same k slices of their part panels, which
+// stay in L2 (a wave's panels over all of k do not: 413 MB at 16384^3).
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <mutex>
+#include <stdlib.h>
 #include <string.h>
 
 #include "tc_common.cuh"
@@ -41,6 +49,8 @@ constexpr int TN = 128;    // tile columns: accumulator columns
 constexpr int TK = 32;     // k per block: one 128-byte row of f32
 constexpr int STAGES = 3;
 constexpr int SEG = 2;     // k blocks per tensor-memory segment
+constexpr int TICK = 32;   // k blocks per lock-step tick (1024 k)
+constexpr int WINDOW = 2;  // ticks a producer may run ahead of the average
 
 struct TfLayout {
   static constexpr int PART = TM * TK * 4;  // one part tile, 16 KB (TN == TM)
@@ -61,6 +71,9 @@ struct TfArgs {
   long long wait_limit;
   int vec_ok;      // destination rows 16-byte aligned
   float alpha, beta;
+  unsigned int* lockstep;  // zeroed tick counter (all CTAs resident), else null
+  int64_t rounds;          // lock-step: units per CTA rounded up over the grid
+  int64_t ticks;           // lock-step: ticks per round
 };
 
 // x = hi + lo + e with hi = tf32(x), lo = tf32(x - hi) (round to nearest, ties
@@ -195,24 +208,54 @@ tf32x3_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
       uint32_t ph = 0;
       uint32_t armed = 0;  // bit s: stage s armed at least once; last parity in armed_ph
       uint32_t armed_ph = 0;
-      for (int64_t ui = 0; ui < nunits && !*abort_flag; ++ui) {
-        const Unit u = unit_of_cta(a.s, cta, ui);
-        bool ok = true;
+      const bool lock = a.lockstep != nullptr;
+      const int64_t rounds = lock ? a.rounds : nunits;
+      const int64_t ticks = lock ? a.ticks : 1;
+      bool ok = true;
+      for (int64_t ui = 0; ui < rounds && ok && !*abort_flag; ++ui) {
+        Unit u{};
+        if (ui < nunits) u = unit_of_cta(a.s, cta, ui);
         const int32_t ya = (int32_t)(u.tile_row * TM), yb = (int32_t)(u.tile_col * TN);
-        for (int64_t kb = u.kb0; kb < u.kb1; ++kb) {
-          if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) { ok = false; break; }
-          tc::mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES);
-          uint8_t* sa = smem + stage * L::STAGE_BYTES;
-          const int32_t x = (int32_t)(kb * TK);
-          tc::tma_load_3d(sa, &tmA, &full[stage], x, ya, 0);                 // A_h
-          tc::tma_load_3d(sa + L::PART, &tmA, &full[stage], x, ya, 1);       // A_l
-          tc::tma_load_3d(sa + 2 * L::PART, &tmB, &full[stage], x, yb, 0);   // B_h
-          tc::tma_load_3d(sa + 3 * L::PART, &tmB, &full[stage], x, yb, 1);   // B_l
-          armed |= 1u << stage;
-          armed_ph = (armed_ph & ~(1u << stage)) | (ph << stage);
-          if (++stage == STAGES) { stage = 0; ph ^= 1; }
+        for (int64_t t = 0; t < ticks && ok; ++t) {
+          if (lock) {
+            const int64_t T = ui * ticks + t;
+            if (T >= WINDOW) {
+              const unsigned int want = (unsigned int)((T - WINDOW + 1) * gridDim.x);
+              const long long t0 = clock64();
+              while (*reinterpret_cast<volatile unsigned int*>(a.lockstep) < want) {
+                if (*abort_flag) break;
+                if (clock64() - t0 > w.limit) {
+                  atomicCAS(a.status, 0, (int)COSMA_ERR_TIMEOUT);
+                  *abort_flag = 1;
+                  break;
+                }
+                __nanosleep(256);
+              }
+              if (*abort_flag) { ok = false; break; }
+            }
+          }
+          int64_t kb_lo = u.kb0, kb_hi = u.kb1;  // the whole unit, or this tick of it
+          if (ui >= nunits) kb_hi = kb_lo;
+          if (lock) {
+            kb_lo = u.kb0 + t * TICK;
+            if (kb_lo > kb_hi) kb_lo = kb_hi;
+            if (kb_lo + TICK < kb_hi) kb_hi = kb_lo + TICK;
+          }
+          for (int64_t kb = kb_lo; kb < kb_hi; ++kb) {
+            if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) { ok = false; break; }
+            tc::mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES);
+            uint8_t* sa = smem + stage * L::STAGE_BYTES;
+            const int32_t x = (int32_t)(kb * TK);
+            tc::tma_load_3d(sa, &tmA, &full[stage], x, ya, 0);                 // A_h
+            tc::tma_load_3d(sa + L::PART, &tmA, &full[stage], x, ya, 1);       // A_l
+            tc::tma_load_3d(sa + 2 * L::PART, &tmB, &full[stage], x, yb, 0);   // B_h
+            tc::tma_load_3d(sa + 3 * L::PART, &tmB, &full[stage], x, yb, 1);   // B_l
+            armed |= 1u << stage;
+            armed_ph = (armed_ph & ~(1u << stage)) | (ph << stage);
+            if (++stage == STAGES) { stage = 0; ph ^= 1; }
+          }
+          if (lock) atomicAdd(a.lockstep, 1u);
         }
-        if (!ok) break;
       }
       if (*abort_flag) {
         // Let every copy this thread started land before shared memory is released.
@@ -330,7 +373,7 @@ long long tf32x3_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_pl
   long long b = 0;
   if (p.pk > 1) b += round_up((long long)p.pk * m * n * 4, 256);
   b += round_up(2 * m * kp * 4, 256) + round_up(2 * n * kp * 4, 256);
-  return b;
+  return b + 256;  // lock-step tick counter
 }
 
 // Splits A and B into K-major TF32 parts in the workspace, then runs the
@@ -350,6 +393,8 @@ int launch_tc_tf32x3(const GemmArgs& g, const Sched& s, const cosma_plan& p, voi
   float* PA = reinterpret_cast<float*>(w + off);
   off += round_up(2 * g.m * kp * 4, 256);
   float* PB = reinterpret_cast<float*>(w + off);
+  off += round_up(2 * g.n * kp * 4, 256);
+  unsigned int* counter = reinterpret_cast<unsigned int*>(w + off);
   const float* A = static_cast<const float*>(g.A);
   const float* B = static_cast<const float*>(g.B);
   auto rows_grid = [](int64_t rows, int64_t cols) {
@@ -397,6 +442,30 @@ int launch_tc_tf32x3(const GemmArgs& g, const Sched& s, const cosma_plan& p, voi
   args.vec_ok = ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0 && (g.ldc & 3) == 0) ? 1 : 0;
   args.alpha = (float)g.alpha;
   args.beta = (float)g.beta;
+  args.lockstep = nullptr;
+  args.rounds = 0;
+  args.ticks = 0;
+
+  // Lock-step ticks need every CTA resident at once: balanced-stripe plans with
+  // at most one CTA per SM, launched cooperatively.  COSMA_TF32_LOCKSTEP=0 runs
+  // the CTAs free; =2 keeps the ticks under a plain launch (for profilers that
+  // cannot launch cooperative kernels: every CTA is resident there too, and
+  // every wait is bounded).
+  static const int lockstep_mode = [] {
+    const char* v = getenv("COSMA_TF32_LOCKSTEP");
+    return v && v[0] == '0' ? 0 : (v && v[0] == '2' ? 2 : 1);
+  }();
+  if (lockstep_mode != 0 && s.order == 1 && s.ctas <= p.sms) {
+    const int64_t rounds = (s.mt * s.nt * s.pk + s.ctas - 1) / s.ctas;
+    const int64_t ticks = ((s.kbt + s.pk - 1) / s.pk + TICK - 1) / TICK;
+    if (rounds * ticks * s.ctas < (1LL << 31)) {
+      args.lockstep = counter;
+      args.rounds = rounds;
+      args.ticks = ticks;
+      if (cudaMemsetAsync(counter, 0, sizeof(unsigned int), st) != cudaSuccess)
+        return (int)cudaGetLastError();
+    }
+  }
 
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
@@ -405,11 +474,27 @@ int launch_tc_tf32x3(const GemmArgs& g, const Sched& s, const cosma_plan& p, voi
                                 TfLayout::ALLOC);
   });
   if (attr != cudaSuccess) return (int)attr;
+  cudaLaunchConfig_t cfgl = {};
+  cfgl.gridDim = dim3((unsigned)s.ctas);
+  cfgl.blockDim = dim3(192);
+  cfgl.dynamicSmemBytes = TfLayout::ALLOC;
+  cfgl.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfgl.attrs = at;
+  cfgl.numAttrs = args.lockstep && lockstep_mode == 1 ? 1 : 0;
   prof_mark(st, true);
-  tf32x3_gemm_kernel<<<s.ctas, 192, TfLayout::ALLOC, st>>>(ta, tb, args);
+  e = cudaLaunchKernelEx(&cfgl, tf32x3_gemm_kernel, ta, tb, args);
+  if (e != cudaSuccess && args.lockstep) {
+    // not launchable cooperatively: run the CTAs free
+    cudaGetLastError();
+    cfgl.numAttrs = 0;
+    args.lockstep = nullptr;
+    e = cudaLaunchKernelEx(&cfgl, tf32x3_gemm_kernel, ta, tb, args);
+  }
   prof_mark(st, false);
   count_launch();
-  e = cudaGetLastError();
   if (e != cudaSuccess) return (int)e;
   if (p.pk > 1) return launch_reduce(COSMA_F32, g, p.pk, partial, st);
   return 0;

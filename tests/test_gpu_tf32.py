@@ -161,3 +161,60 @@ def test_tf32x3_host_path_equals_device_path(shape):
     cosma.gemm_host(Ah, Bh, Ch, DT)
     torch.cuda.synchronize()
     assert torch.equal(Ch, C.cpu())
+
+
+_SUB = """
+import sys, numpy as np, torch
+sys.path.insert(0, {root!r})
+import cosma_inputs as ci
+from cosma_inputs import device as cid
+from paper_1908_09606_gb300 import cosma
+cosma.load()
+m, n, k = {m}, {n}, {k}
+A = cid.new(m, k, "uniform", "f32", seed=2, stream_id=ci.STREAM_A)
+B = cid.new(k, n, "uniform", "f32", seed=2, stream_id=ci.STREAM_B)
+C = torch.empty((m, n), dtype=torch.float32, device="cuda")
+cosma.gemm(A, B, C, "f32_emu_tf32")
+torch.cuda.synchronize()
+assert cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream) == 0
+np.save({out!r}, C.cpu().numpy())
+"""
+
+
+def test_tf32x3_lockstep_ticks_do_not_change_results(tmp_path):
+    """Lock-step ticks (default: cooperative launch), ticks under a plain launch
+    (COSMA_TF32_LOCKSTEP=2) and free CTAs (=0) only reorder the loads: every
+    entry's sum is formed in the same order, so the results are bit-equal."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    m, n, k = 1100, 1536, 2500   # 108 tiles on 152 SMs, 79 k blocks = 3 ticks
+    outs = []
+    for mode in ("1", "2", "0"):
+        out = str(tmp_path / f"c{mode}.npy")
+        code = _SUB.format(root=root, m=m, n=n, k=k, out=out)
+        env = dict(os.environ, COSMA_TF32_LOCKSTEP=mode)
+        subprocess.run([sys.executable, "-c", code], env=env, cwd=root, check=True,
+                       timeout=600)
+        outs.append(np.load(out))
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    A, B = host_operands(m, n, k, DT, seed=2)
+    _check(outs[0].astype(np.float64), A, B)
+
+
+def test_tf32x3_bounded_wait_reports_timeout_and_context_survives():
+    import torch
+    cosma = lib()
+    try:
+        assert cosma.cosma_init(wait_limit=1) == 0
+        A, B = device_operands(1024, 1024, 4096, DT)
+        C, _ = out_tensor(1024, 1024, DT)
+        cosma.gemm(A, B, C, DT)
+        st = cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream)
+        assert st == cosma.COSMA_ERR_TIMEOUT
+    finally:
+        assert cosma.cosma_init(wait_limit=0) == 0
+    C = _run(256, 384, 320, seed=9)
+    A, B = host_operands(256, 384, 320, DT, seed=9)
+    _check(C, A, B)
