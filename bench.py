@@ -241,6 +241,64 @@ def oracle_sample(m, n, k, target_s, kind="uniform", gen="f64", seed=0, keep=Fal
         r = int(min(min(m, n), max(r + 1, r * min(grow, 4.0))))
 
 
+def step_stats(step_ms):
+    """Median, minimum and a 95 % confidence interval (Student t) of the mean of
+    the timed steps' CUDA-event times."""
+    n = len(step_ms)
+    mean = sum(step_ms) / n
+    out = {"median_ms": statistics.median(step_ms), "min_ms": min(step_ms), "mean_ms": mean}
+    if n > 1:
+        t975 = {2: 12.706, 3: 4.303, 4: 3.182, 5: 2.776, 6: 2.571, 7: 2.447, 8: 2.365,
+                9: 2.306, 10: 2.262}.get(n, 1.96 if n > 30 else 2.23)
+        half = t975 * statistics.stdev(step_ms) / math.sqrt(n)
+        out["ci95_ms"] = [mean - half, mean + half]
+    return out
+
+
+def host_info():
+    """Host cores and CPU model, for the CPU timings."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu": model}
+
+
+def listing1_sample(A_dev, B_dev, target_s):
+    """Time the paper's sequential schedule (Listing 1) on the host cores: an
+    r x r corner of C (full k) of the workload's own operands (their leading
+    rows / columns copied from the device), a x b tiles from FindSeqSchedule at
+    S = 32768 doubles (256 KB, a core's cache), tiles over all OpenMP threads;
+    r is sized from one probe to take about target_s seconds.  Returns
+    (flop/s, seconds, r, threads, a, b)."""
+    import numpy as np
+    from oracle import bounds
+    from oracle import gemm as og
+
+    m, k = A_dev.shape
+    n = B_dev.shape[1]
+    a, b = bounds.find_seq_schedule(32768)
+    # probe with about four tiles per core, so the probe's rate is the run's
+    r = min(a * int(math.ceil(math.sqrt(4 * (os.cpu_count() or 1)))), m, n)
+    for attempt in range(2):
+        A = np.ascontiguousarray(A_dev[:r].double().cpu().numpy())
+        B = np.ascontiguousarray(B_dev[:, :r].double().cpu().numpy())
+        t0 = time.perf_counter()
+        _, used = og.listing1(A, B, a, b)
+        dt = time.perf_counter() - t0
+        if attempt == 1 or dt >= target_s or r >= min(m, n):
+            break
+        r = int(min(min(m, n), r * math.sqrt(target_s / max(dt, 1e-3))))
+    return 2.0 * r * r * k / dt, dt, r, used, a, b
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -654,6 +712,13 @@ def main():
                          f"full k={k}, {dt:.1f} s"}
         got = C[:rows, :rows].double().cpu().numpy()
         errors = {"block": f"{rows}x{rows}", "this_path": og.normwise_rel_error(got, ref)}
+        # the paper's tiled schedule on all host cores, beside the naive oracle
+        fl1, dt1, r1, used1, ta1, tb1 = listing1_sample(A, B, 6.0)
+        cpu["listing1_all_cores"] = {
+            "value": fl1 / 1e12, "unit": "TFLOP/s", "cores": used1,
+            "sample": f"Listing 1 on the host: {ta1}x{tb1} C tiles over {used1} OpenMP "
+                      f"threads, {r1}x{r1} leading block of C, full k={k}, {dt1:.1f} s"}
+        cpu["host"] = host_info()
         if native is not None:
             errors["native_f64"] = og.normwise_rel_error(
                 Cn[:rows, :rows].double().cpu().numpy(), ref)
@@ -674,6 +739,7 @@ def main():
                           "f32_emu_tf32": "tf32 parts -> f32"}[dtype],
                 "data": "synthetic", "config": cfg, "roofline": roof, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+                "step_stats": step_stats(step_ms),
                 "native_f64": native, "error_vs_oracle": errors,
                 "io": io_report(m, n, k, dtype, plan, roof["traffic"],
                                 props.L2_cache_size, props.multi_processor_count,

@@ -4,6 +4,10 @@ Test infrastructure only (see the package docstring).  The arithmetic lives in
 gemm_oracle.c; this module compiles it with gcc (no fused multiply-add
 contraction, no fast-math) and calls it through ctypes.
 
+listing1 (liblisting1_cpu.so, OpenMP) runs the same chain under the tiled
+schedule of Listing 1 on the host cores for the benchmark's CPU timing; it is
+pinned by bit-equality with the naive loop.
+
 Pins (tests/test_oracle_gemm.py): exact integer products against Python
 integers, identity / diagonal / rank-1 closed forms, exact rational arithmetic
 (fractions) on tiny inputs for Dot2, the classical bound |C_naive - C| <= gamma_k
@@ -23,21 +27,34 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gemm_oracle.c")
+_SRC_L1 = os.path.join(_HERE, "listing1_cpu.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libgemm_oracle.so")
+_LIB_L1 = os.path.join(_BUILD, "liblisting1_cpu.so")
 _lock = threading.Lock()
 _lib = None
+_lib_l1 = None
+
+
+def _compile(src, out, flags):
+    if os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc"] + flags + ["-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                                             "-shared", "-o", tmp, src, "-lm"])
+    os.replace(tmp, out)
+    return out
 
 
 def build():
-    """Compile the C oracle (idempotent; rebuilds when the source is newer)."""
+    """Compile the C oracle and the host Listing-1 loop (idempotent; rebuilds
+    when a source is newer)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                           "-shared", "-o", tmp, _SRC, "-lm"])
-    os.replace(tmp, _LIB)
+    _compile(_SRC, _LIB, ["-O2"])
+    try:
+        _compile(_SRC_L1, _LIB_L1, ["-O3", "-fopenmp"])
+    except subprocess.CalledProcessError:  # no OpenMP: one thread
+        _compile(_SRC_L1, _LIB_L1, ["-O3"])
     return _LIB
 
 
@@ -79,6 +96,36 @@ def gemm(A, B, method="dot2"):
         fn = {"naive": _load().oracle_gemm_naive, "dot2": _load().oracle_gemm_dot2}[method]
         fn(m, n, k, _ptr(A), max(k, 1), _ptr(B), max(n, 1), _ptr(C), max(n, 1))
     return C
+
+
+def listing1(A, B, a, b, threads=0):
+    """C = A B by the paper's sequential schedule (Listing 1) on the host cores:
+    a x b C tiles, k outer products each, tiles spread over OpenMP threads
+    (threads = 0: all).  Every entry is the chain t = 0..k-1, so the result
+    equals gemm(A, B, 'naive') bit for bit.  Returns (C, threads used)."""
+    global _lib_l1
+    A, B = _f64(A), _f64(B)
+    m, k = A.shape
+    k2, n = B.shape
+    assert k == k2
+    with _lock:
+        if _lib_l1 is None:
+            build()
+            lib = ctypes.CDLL(_LIB_L1)
+            d = ctypes.POINTER(ctypes.c_double)
+            i64 = ctypes.c_int64
+            lib.listing1_gemm.argtypes = [i64, i64, i64, d, i64, d, i64, d, i64, i64, i64,
+                                          ctypes.c_int]
+            lib.listing1_gemm.restype = ctypes.c_int
+            _lib_l1 = lib
+    C = np.zeros((m, n), dtype=np.float64)
+    used = 0
+    if m and n:
+        used = _lib_l1.listing1_gemm(m, n, k, _ptr(A), max(k, 1), _ptr(B), max(n, 1), _ptr(C),
+                                     max(n, 1), int(a), int(b), int(threads))
+        if used < 1:
+            raise MemoryError("listing1: tile buffer allocation failed")
+    return C, used
 
 
 def gemm_ex(A, B, C0, alpha, beta, trans_a=False, trans_b=False, method="dot2"):
