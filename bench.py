@@ -33,6 +33,7 @@ WORKLOADS = {
     "largeK": (4096, 4096, 1 << 20),
     "largeM": (1 << 20, 4096, 4096),
     "flat": (65536, 65536, 1024),
+    "flat16k": (16384, 16384, 1024),   # the flat family at profiling size
     "emu8192": (8192, 8192, 8192),
     "4096": (4096, 4096, 4096),
     "512": (512, 512, 512),

@@ -389,7 +389,7 @@ __device__ __forceinline__ void emu_epilogue(const EmuArgs& a, int unit_cta, int
           }
           tc::tc_fence_before();
           __syncwarp();
-          if (lane == 0) tc::mbar_arrive_remote(tempty_addr[acc]);
+          if (lane == 0) tc::mbar_arrive_remote_relaxed(tempty_addr[acc]);
           tph[acc] ^= 1;
           acc = (acc + 1) == NACC ? 0 : acc + 1;
           if (last) {
@@ -419,31 +419,58 @@ __device__ __forceinline__ void emu_epilogue(const EmuArgs& a, int unit_cta, int
       }
     }
     if (!ok) break;
-    // Final FP64 store of this thread's 64 columns of one row:
-    // C = (Th + Tl) 2^(sigma_i + tau_j + 2 - 2 beta).
-    const int64_t row = u.tile_row * tile_rows + row_off + q4 * 32 + lane;
+    // Final FP64 store: C = (Th + Tl) 2^(sigma_i + tau_j + 2 - 2 beta) for this
+    // thread's row, 64 columns.  Each 8-column chunk is formed in the row's lane,
+    // transposed within groups of 8 lanes (three butterfly stages of shuffles:
+    // at stage s, entries whose row and column differ in bit s trade places with
+    // lane ^ s), and written as four 64-byte row segments per instruction
+    // instead of 32 scattered 8-byte ones.
+    const int64_t row0 = u.tile_row * tile_rows + row_off + q4 * 32;  // the warp's first row
+    const int64_t row = row0 + lane;
     const int64_t cbase = u.tile_col * EBN + col_lo;
     const int ea = row < a.sch.m ? a.eA[row] : kExpNone;
-    double* dst = a.C + row * a.ldc;
+    const int l8 = lane & 7, g8 = lane >> 3;
 #pragma unroll
     for (int c = 0; c < 64; c += 8) {
-      uint32_t t[8];
-      tc::tmem_ld_32x8(tl + c, t);
-      tc::tmem_wait_ld();
-      if (row < a.sch.m) {
+      uint32_t tl8[8];
+      tc::tmem_ld_32x8(tl + c, tl8);
+      int eb[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int64_t col = cbase + c + j;
-          if (col < a.sch.n) {
-            const int eb = a.eB[col];
-            const double val = (double)Th[c + j] + (double)__uint_as_float(t[j]);
-            double v = (ea == kExpNone || eb == kExpNone)
-                           ? 0.0
-                           : scale_pow2(val, ea + eb + 2 - 2 * a.beta);
-            if (a.alpha != 1.0) v *= a.alpha;
-            if (a.beta_c != 0.0) v = fma(a.beta_c, dst[col], v);
-            dst[col] = v;
-          }
+      for (int j = 0; j < 8; ++j) eb[j] = cbase + c + j < a.sch.n ? a.eB[cbase + c + j] : kExpNone;
+      double v[8];
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t lo = tl8[j];
+        const double val = (double)Th[c + j] + (double)__uint_as_float(lo);
+        double x = (ea == kExpNone || eb[j] == kExpNone)
+                       ? 0.0
+                       : scale_pow2(val, ea + eb[j] + 2 - 2 * a.beta);
+        if (a.alpha != 1.0) x *= a.alpha;
+        v[j] = x;
+      }
+#pragma unroll
+      for (int sb = 4; sb >= 1; sb >>= 1) {
+#pragma unroll
+        for (int i0 = 0; i0 < 8; ++i0) {
+          if (i0 & sb) continue;
+          const bool up = (l8 & sb) != 0;
+          const double send = up ? v[i0] : v[i0 | sb];
+          const double recv = __shfl_xor_sync(0xffffffffu, send, sb);
+          if (up) v[i0] = recv;
+          else v[i0 | sb] = recv;
+        }
+      }
+      // now v[i] = C(row0 + 8 g8 + i, cbase + c + l8)
+      const int64_t col = cbase + c + l8;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int64_t r = row0 + 8 * g8 + i;
+        if (r < a.sch.m && col < a.sch.n) {
+          double* dst = a.C + r * a.ldc + col;
+          double x = v[i];
+          if (a.beta_c != 0.0) x = fma(a.beta_c, *dst, x);
+          *dst = x;
         }
       }
     }

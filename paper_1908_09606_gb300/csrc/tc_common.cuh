@@ -331,6 +331,16 @@ __device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
                : "memory");
 }
 
+// The same without release semantics: for a barrier that only reports that this
+// thread's tensor-memory loads have completed (tcgen05.wait::ld returned and
+// tcgen05.fence::before_thread_sync issued), which orders nothing in memory --
+// a release at cluster scope would first wait for every global store of the
+// thread still in flight.
+__device__ __forceinline__ void mbar_arrive_remote_relaxed(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];\n" ::"r"(cluster_addr)
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_alloc_pair(uint32_t* slot, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                    smem_u32(slot)),
