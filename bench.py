@@ -86,7 +86,7 @@ DRAM_TRAFFIC = {
     ("grouped512", "bf16"): 2.27e9 + 1.98e9,    # grouped_tc_kernel<256,4>
     # emu_gemm_pair_kernel: the lock-step schedule captured under a plain cluster
     # launch (COSMA_EMU_LOCKSTEP=2; ncu cannot launch the cooperative one)
-    ("square", "f64_emu_bf16"): 73.60e9 + 2.24e9,
+    ("square", "f64_emu_bf16"): 73.51e9 + 2.15e9,
     # tf32x3_gemm_kernel: lock-step ticks under a plain launch (COSMA_TF32_LOCKSTEP=2)
     ("square", "f32_emu_tf32"): 56.46e9 + 1.07e9,
 }
