@@ -190,6 +190,16 @@ int cosma_zgemm(int op_a, int op_b, int64_t m, int64_t n, int64_t k, const doubl
                 const void* A, int64_t lda, const void* B, int64_t ldb, const double* beta,
                 void* C, int64_t ldc, int engine, void* stream);
 
+/* Complex single: as cosma_zgemm over interleaved float (re, im) pairs (C99 float
+ * complex layout, 8-byte aligned), the four real products on `engine` COSMA_F32
+ * (FMA) or COSMA_F32_EMU_TF32 (three TF32 products each); else
+ * COSMA_ERR_UNSUPPORTED.  alpha, beta: HOST float arrays {re, im}, applied in
+ * single precision.  Staging (2 (mk + kn + mn) floats) shares cosma_zgemm's
+ * library-owned buffer, with the same capture and serialisation rules. */
+int cosma_cgemm(int op_a, int op_b, int64_t m, int64_t n, int64_t k, const float* alpha,
+                const void* A, int64_t lda, const void* B, int64_t ldb, const float* beta,
+                void* C, int64_t ldc, int engine, void* stream);
+
 /* Same as cosma_gemm but runs the given plan (e.g. from cosma_plan_query or an
  * autotuner).  The plan is validated against the kernel's limits first. */
 int cosma_gemm_planned(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda,

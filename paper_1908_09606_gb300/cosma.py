@@ -75,6 +75,9 @@ SIGNATURES = [
                              _I64, _INT, _VP]),
     ("cosma_zgemm", _INT, [_INT, _INT, _I64, _I64, _I64, ctypes.POINTER(_D), _VP, _I64, _VP,
                            _I64, ctypes.POINTER(_D), _VP, _I64, _INT, _VP]),
+    ("cosma_cgemm", _INT, [_INT, _INT, _I64, _I64, _I64, ctypes.POINTER(ctypes.c_float), _VP,
+                           _I64, _VP, _I64, ctypes.POINTER(ctypes.c_float), _VP, _I64, _INT,
+                           _VP]),
     ("cosma_gemm_grouped", _INT, [_INT, ctypes.POINTER(cosma_problem), _INT, _VP]),
     ("cosma_gemm_host", _INT, [_I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _INT, _VP]),
     ("cosma_plan_query", _INT, [_I64, _I64, _I64, _INT, _INT, ctypes.POINTER(cosma_plan)]),
@@ -184,6 +187,13 @@ def cosma_zgemm(op_a, op_b, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, engine
     al = (_D * 2)(alpha.real, alpha.imag)
     be = (_D * 2)(beta.real, beta.imag)
     return load().cosma_zgemm(op_a, op_b, m, n, k, al, A, lda, B, ldb, be, C, ldc, engine, stream)
+
+
+def cosma_cgemm(op_a, op_b, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, engine, stream=0):
+    """alpha, beta: Python complex numbers (passed as float pairs)."""
+    al = (ctypes.c_float * 2)(alpha.real, alpha.imag)
+    be = (ctypes.c_float * 2)(beta.real, beta.imag)
+    return load().cosma_cgemm(op_a, op_b, m, n, k, al, A, lda, B, ldb, be, C, ldc, engine, stream)
 
 
 def cosma_gemm_host(m, n, k, A, lda, B, ldb, C, ldc, dtype, stream=0):
@@ -341,9 +351,10 @@ def gemm_ex(A, B, C, dtype, alpha=1.0, beta=0.0, trans_a=False, trans_b=False, s
 
 def gemm_complex(A, B, C, engine="f64_emu_bf16", alpha=1.0, beta=0.0, op_a=0, op_b=0,
                  stream=None):
-    """C = alpha op(A) op(B) + beta C for row-major torch complex128 CUDA tensors; op
-    0 none, 1 transpose, 2 conjugate transpose (A / B then hold the stored
-    transposes).  Raises on error."""
+    """C = alpha op(A) op(B) + beta C for row-major torch complex128 (cosma_zgemm;
+    engine f64 or f64_emu_bf16) or complex64 (cosma_cgemm; engine f32 or
+    f32_emu_tf32) CUDA tensors; op 0 none, 1 transpose, 2 conjugate transpose (A / B
+    then hold the stored transposes).  Raises on error."""
     m, n = C.shape
     k = A.shape[0] if op_a else A.shape[1]
     assert (A.shape[1] if op_a else A.shape[0]) == m
@@ -354,10 +365,12 @@ def gemm_complex(A, B, C, engine="f64_emu_bf16", alpha=1.0, beta=0.0, op_a=0, op
     if isinstance(engine, str):
         engine = DTYPES[engine]
     s = _stream_handle(stream)
-    rc = cosma_zgemm(int(op_a), int(op_b), m, n, k, complex(alpha), A.data_ptr(),
-                     max(A.stride(0), 1), B.data_ptr(), max(B.stride(0), 1), complex(beta),
-                     C.data_ptr(), max(C.stride(0), 1), engine, s)
-    return _check(rc, "cosma_zgemm")
+    single = str(C.dtype) == "torch.complex64"
+    fn = cosma_cgemm if single else cosma_zgemm
+    rc = fn(int(op_a), int(op_b), m, n, k, complex(alpha), A.data_ptr(),
+            max(A.stride(0), 1), B.data_ptr(), max(B.stride(0), 1), complex(beta),
+            C.data_ptr(), max(C.stride(0), 1), engine, s)
+    return _check(rc, "cosma_cgemm" if single else "cosma_zgemm")
 
 
 def gemm_host(A, B, C, dtype, stream=None):

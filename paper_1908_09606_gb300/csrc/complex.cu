@@ -1,6 +1,6 @@
-// Complex double products (cosma_zgemm): C = alpha op(A) op(B) + beta C over
-// interleaved (re, im) storage, run as four real products on a real engine
-// (native FP64 or emulated FP64) -- the "4M" form:
+// Complex products (cosma_zgemm: double, cosma_cgemm: single):
+// C = alpha op(A) op(B) + beta C over interleaved (re, im) storage, run as four
+// real products on a real engine of the same precision -- the "4M" form:
 //   Tr = Ar Br - Ai Bi,   Ti = Ar Bi + Ai Br,   C = alpha (Tr + i Ti) + beta C.
 // op is the identity, the transpose, or the conjugate transpose; a transposed
 // operand is stored transposed (A as k x m, B as n x k) and split into planar
@@ -44,36 +44,43 @@ bool on_device(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+template <class R> struct Cplx;
+template <> struct Cplx<double> { using T = double2; };
+template <> struct Cplx<float> { using T = float2; };
+
 // re / im (rows x cols, ld cols) from interleaved src (ld_src complex elements);
 // im negated when conj.
-__global__ void split_complex_kernel(const double2* __restrict__ src, int64_t rows, int64_t cols,
-                                     int64_t ld_src, double* __restrict__ re,
-                                     double* __restrict__ im, int conj) {
+template <class R>
+__global__ void split_complex_kernel(const typename Cplx<R>::T* __restrict__ src, int64_t rows,
+                                     int64_t cols, int64_t ld_src, R* __restrict__ re,
+                                     R* __restrict__ im, int conj) {
   const int64_t total = rows * cols;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / cols, c = e - r * cols;
-    const double2 v = src[r * ld_src + c];
+    const typename Cplx<R>::T v = src[r * ld_src + c];
     re[e] = v.x;
     im[e] = conj ? -v.y : v.y;
   }
 }
 
-// C = alpha (Tr + i Ti) + beta C (C read only when beta != 0).
-__global__ void combine_complex_kernel(int64_t m, int64_t n, const double* __restrict__ tr,
-                                       const double* __restrict__ ti, double2* __restrict__ C,
-                                       int64_t ldc, double ar, double ai, double br, double bi) {
+// C = alpha (Tr + i Ti) + beta C (C read only when beta != 0), in R.
+template <class R>
+__global__ void combine_complex_kernel(int64_t m, int64_t n, const R* __restrict__ tr,
+                                       const R* __restrict__ ti,
+                                       typename Cplx<R>::T* __restrict__ C, int64_t ldc, R ar,
+                                       R ai, R br, R bi) {
   const int64_t total = m * n;
-  const bool read_c = br != 0.0 || bi != 0.0;
+  const bool read_c = br != R(0) || bi != R(0);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / n, c = e - r * n;
-    const double x = tr[e], y = ti[e];
-    double2 out;
+    const R x = tr[e], y = ti[e];
+    typename Cplx<R>::T out;
     out.x = ar * x - ai * y;
     out.y = ar * y + ai * x;
     if (read_c) {
-      const double2 v = C[r * ldc + c];
+      const typename Cplx<R>::T v = C[r * ldc + c];
       out.x += br * v.x - bi * v.y;
       out.y += br * v.y + bi * v.x;
     }
@@ -98,13 +105,16 @@ void complex_release(int dev) {
 
 }  // namespace cosma
 
-using namespace cosma;
+namespace cosma {
+namespace {
 
-extern "C" int cosma_zgemm(int op_a, int op_b, int64_t m, int64_t n, int64_t k,
-                           const double* alpha, const void* A, int64_t lda, const void* B,
-                           int64_t ldb, const double* beta, void* C, int64_t ldc, int engine,
-                           void* stream) {
-  if (engine != COSMA_F64 && engine != COSMA_F64_EMU_BF16) return COSMA_ERR_UNSUPPORTED;
+// Both precisions: R the real type, engine a real dtype of that precision.
+template <class R>
+int complex_gemm(int op_a, int op_b, int64_t m, int64_t n, int64_t k, const R* alpha,
+                 const void* A, int64_t lda, const void* B, int64_t ldb, const R* beta, void* C,
+                 int64_t ldc, int engine, void* stream) {
+  using C2 = typename Cplx<R>::T;
+  const uintptr_t amask = sizeof(C2) - 1;
   if (op_a < 0 || op_a > 2 || op_b < 0 || op_b > 2 || !alpha || !beta) return COSMA_ERR_INVALID_ARG;
   if (m < 0 || n < 0 || k < 0) return COSMA_ERR_INVALID_ARG;
   const int ta = op_a != 0, tb = op_b != 0;
@@ -114,10 +124,10 @@ extern "C" int cosma_zgemm(int op_a, int op_b, int64_t m, int64_t n, int64_t k,
       ldc < (n > 1 ? n : 1))
     return COSMA_ERR_INVALID_ARG;
   if (m == 0 || n == 0) return COSMA_OK;
-  if (!C || (reinterpret_cast<uintptr_t>(C) & 15) || !on_device(C)) return COSMA_ERR_INVALID_ARG;
-  const bool no_ab = k == 0 || (alpha[0] == 0.0 && alpha[1] == 0.0);
-  if (!no_ab && (!A || !B || (reinterpret_cast<uintptr_t>(A) & 15) ||
-                 (reinterpret_cast<uintptr_t>(B) & 15) || !on_device(A) || !on_device(B)))
+  if (!C || (reinterpret_cast<uintptr_t>(C) & amask) || !on_device(C)) return COSMA_ERR_INVALID_ARG;
+  const bool no_ab = k == 0 || (alpha[0] == R(0) && alpha[1] == R(0));
+  if (!no_ab && (!A || !B || (reinterpret_cast<uintptr_t>(A) & amask) ||
+                 (reinterpret_cast<uintptr_t>(B) & amask) || !on_device(A) || !on_device(B)))
     return COSMA_ERR_INVALID_ARG;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return COSMA_ERR_CUDA;
@@ -127,9 +137,10 @@ extern "C" int cosma_zgemm(int op_a, int op_b, int64_t m, int64_t n, int64_t k,
 
   // staging: Ar, Ai (a_rows x a_cols), Br, Bi (b_rows x b_cols), Tr, Ti (m x n)
   const int64_t kk = no_ab ? 0 : k;
-  const size_t a_b = (size_t)rup(a_rows * a_cols * 8 * (kk > 0), 256);
-  const size_t b_b = (size_t)rup(b_rows * b_cols * 8 * (kk > 0), 256);
-  const size_t t_b = (size_t)rup(m * n * 8, 256);
+  const int64_t w = (int64_t)sizeof(R);
+  const size_t a_b = (size_t)rup(a_rows * a_cols * w * (kk > 0), 256);
+  const size_t b_b = (size_t)rup(b_rows * b_cols * w * (kk > 0), 256);
+  const size_t t_b = (size_t)rup(m * n * w, 256);
   const size_t need = 2 * a_b + 2 * b_b + 2 * t_b;
   if (cs.stage_bytes < need) {
     if (capturing(st)) return COSMA_ERR_NO_WORKSPACE;
@@ -146,21 +157,21 @@ extern "C" int cosma_zgemm(int op_a, int op_b, int64_t m, int64_t n, int64_t k,
     }
     cs.stage_bytes = want;
   }
-  uint8_t* w = static_cast<uint8_t*>(cs.stage);
-  double* Ar = reinterpret_cast<double*>(w);
-  double* Ai = reinterpret_cast<double*>(w + a_b);
-  double* Br = reinterpret_cast<double*>(w + 2 * a_b);
-  double* Bi = reinterpret_cast<double*>(w + 2 * a_b + b_b);
-  double* Tr = reinterpret_cast<double*>(w + 2 * a_b + 2 * b_b);
-  double* Ti = reinterpret_cast<double*>(w + 2 * a_b + 2 * b_b + t_b);
+  uint8_t* wp = static_cast<uint8_t*>(cs.stage);
+  R* Ar = reinterpret_cast<R*>(wp);
+  R* Ai = reinterpret_cast<R*>(wp + a_b);
+  R* Br = reinterpret_cast<R*>(wp + 2 * a_b);
+  R* Bi = reinterpret_cast<R*>(wp + 2 * a_b + b_b);
+  R* Tr = reinterpret_cast<R*>(wp + 2 * a_b + 2 * b_b);
+  R* Ti = reinterpret_cast<R*>(wp + 2 * a_b + 2 * b_b + t_b);
 
   int rc = COSMA_OK;
   if (!no_ab) {
-    split_complex_kernel<<<grid_for(a_rows * a_cols), 256, 0, st>>>(
-        static_cast<const double2*>(A), a_rows, a_cols, lda, Ar, Ai, op_a == 2);
+    split_complex_kernel<R><<<grid_for(a_rows * a_cols), 256, 0, st>>>(
+        static_cast<const C2*>(A), a_rows, a_cols, lda, Ar, Ai, op_a == 2);
     count_launch();
-    split_complex_kernel<<<grid_for(b_rows * b_cols), 256, 0, st>>>(
-        static_cast<const double2*>(B), b_rows, b_cols, ldb, Br, Bi, op_b == 2);
+    split_complex_kernel<R><<<grid_for(b_rows * b_cols), 256, 0, st>>>(
+        static_cast<const C2*>(B), b_rows, b_cols, ldb, Br, Bi, op_b == 2);
     count_launch();
     if (cudaGetLastError() != cudaSuccess) return COSMA_ERR_CUDA;
     // Tr = Ar Br - Ai Bi,  Ti = Ar Bi + Ai Br
@@ -176,8 +187,31 @@ extern "C" int cosma_zgemm(int op_a, int op_b, int64_t m, int64_t n, int64_t k,
   } else {
     if (cudaMemsetAsync(Tr, 0, 2 * t_b, st) != cudaSuccess) return COSMA_ERR_CUDA;
   }
-  combine_complex_kernel<<<grid_for(m * n), 256, 0, st>>>(
-      m, n, Tr, Ti, static_cast<double2*>(C), ldc, alpha[0], alpha[1], beta[0], beta[1]);
+  combine_complex_kernel<R><<<grid_for(m * n), 256, 0, st>>>(
+      m, n, Tr, Ti, static_cast<C2*>(C), ldc, alpha[0], alpha[1], beta[0], beta[1]);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? COSMA_OK : COSMA_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace cosma
+
+using namespace cosma;
+
+extern "C" int cosma_zgemm(int op_a, int op_b, int64_t m, int64_t n, int64_t k,
+                           const double* alpha, const void* A, int64_t lda, const void* B,
+                           int64_t ldb, const double* beta, void* C, int64_t ldc, int engine,
+                           void* stream) {
+  if (engine != COSMA_F64 && engine != COSMA_F64_EMU_BF16) return COSMA_ERR_UNSUPPORTED;
+  return complex_gemm<double>(op_a, op_b, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, engine,
+                              stream);
+}
+
+extern "C" int cosma_cgemm(int op_a, int op_b, int64_t m, int64_t n, int64_t k,
+                           const float* alpha, const void* A, int64_t lda, const void* B,
+                           int64_t ldb, const float* beta, void* C, int64_t ldc, int engine,
+                           void* stream) {
+  if (engine != COSMA_F32 && engine != COSMA_F32_EMU_TF32) return COSMA_ERR_UNSUPPORTED;
+  return complex_gemm<float>(op_a, op_b, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, engine,
+                             stream);
 }

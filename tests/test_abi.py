@@ -224,6 +224,20 @@ def test_zgemm_rejects_other_engines_and_bad_ops(lib):
                              cosma.COSMA_F64, 0) == cosma.COSMA_ERR_INVALID_ARG  # lda < m
 
 
+def test_cgemm_rejects_other_engines_and_bad_arguments(lib):
+    cosma = lib
+    al = 1.0 + 0j
+    for eng in (cosma.COSMA_F64, cosma.COSMA_BF16, cosma.COSMA_F64_EMU_BF16):
+        assert cosma.cosma_cgemm(0, 0, 4, 4, 4, al, 0, 4, 0, 4, al, 0, 4,
+                                 eng, 0) == cosma.COSMA_ERR_UNSUPPORTED
+    assert cosma.cosma_cgemm(0, 3, 4, 4, 4, al, 0, 4, 0, 4, al, 0, 4,
+                             cosma.COSMA_F32, 0) == cosma.COSMA_ERR_INVALID_ARG
+    assert cosma.cosma_cgemm(0, 2, 4, 8, 6, al, 0, 6, 0, 5, al, 0, 8,
+                             cosma.COSMA_F32_EMU_TF32, 0) == cosma.COSMA_ERR_INVALID_ARG  # ldb < k
+    assert cosma.cosma_cgemm(0, 0, 0, 4, 4, al, 0, 4, 0, 4, al, 0, 4,
+                             cosma.COSMA_F32, 0) == cosma.COSMA_OK  # m == 0: nothing to do
+
+
 
 def test_environment_sets_config_defaults(lib):
     """COSMA_* variables are read when the library loads (a fresh process here);
