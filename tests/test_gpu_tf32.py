@@ -218,3 +218,32 @@ def test_tf32x3_bounded_wait_reports_timeout_and_context_survives():
     C = _run(256, 384, 320, seed=9)
     A, B = host_operands(256, 384, 320, DT, seed=9)
     _check(C, A, B)
+
+
+def test_tf32x3_nonfinite_inputs_give_nonfinite_entries():
+    """An Inf or NaN in A or B makes exactly the entries non-finite that an IEEE
+    product makes non-finite (every operand entry here is nonzero); an Inf may come
+    out as NaN (Inf times a zero or opposite-signed lo part).  The other entries
+    stay within the bound."""
+    import torch
+    cosma = lib()
+    m, n, k = 130, 140, 150
+    A, B = device_operands(m, n, k, DT, "uniform", 4)
+    A[3, 17] = float("inf")
+    A[5, 40] = float("nan")
+    B[99, 7] = float("-inf")
+    C, _ = out_tensor(m, n, DT)
+    cosma.gemm(A, B, C, DT)
+    torch.cuda.synchronize()
+    got = C.double().cpu().numpy()
+    bad = np.zeros((m, n), dtype=bool)
+    bad[3, :] = bad[5, :] = True
+    bad[:, 7] = True
+    assert not np.isfinite(got[bad]).any()
+    Ah = A.double().cpu().numpy()
+    Bh = B.double().cpu().numpy()
+    Ah[3, 17] = Ah[5, 40] = 0.0
+    Bh[99, 7] = 0.0
+    ref = og.gemm(Ah, Bh, "dot2")
+    tol = bound(Ah, Bh)
+    assert np.all(np.abs(got[~bad] - ref[~bad]) <= tol[~bad])
