@@ -60,6 +60,23 @@ int encode_tmap_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t c
   return r == CUDA_SUCCESS ? COSMA_OK : COSMA_ERR_CUDA;
 }
 
+// bf16 map of a k-blocked operand [kbt][rows][64] (64 k per 128-byte row):
+// 64 x box_rows x 1 boxes, 128-byte swizzle.
+static int encode_tmap_bf16_blocked(CUtensorMap* map, const void* base, int64_t rows,
+                                    int64_t kbt, int box_rows) {
+  auto fn = get_encode();
+  if (!fn) return COSMA_ERR_CUDA;
+  if (reinterpret_cast<uintptr_t>(base) & 15) return COSMA_ERR_INVALID_ARG;
+  cuuint64_t dims[3] = {64, (cuuint64_t)rows, (cuuint64_t)kbt};
+  cuuint64_t strides[2] = {128, (cuuint64_t)(rows * 128)};
+  cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? COSMA_OK : COSMA_ERR_CUDA;
+}
+
 // f32 map for tensor stores of C: 32 x 32 boxes, 128-byte swizzle.
 int encode_tmap_f32_store(CUtensorMap* map, void* base, int64_t rows, int64_t cols, int64_t ld) {
   auto fn = get_encode();
@@ -96,6 +113,36 @@ __global__ void transpose_bf16(const __nv_bfloat16* __restrict__ B, int64_t k, i
   }
 }
 
+// k-blocked copy of A (m x k, lda): Ab[kb][i][0..63] = A[i][64 kb .. 64 kb + 63],
+// zero beyond k.  One 16-byte chunk (8 bf16) per thread step, walking A row by
+// row (contiguous reads; the writes land 128 bytes at a time in the panels).
+// vec: A 16-byte aligned and lda a multiple of 8.
+__global__ void block_a_bf16(const __nv_bfloat16* __restrict__ A, int64_t m, int64_t k,
+                             int64_t lda, __nv_bfloat16* __restrict__ Ab, int64_t kbt, int vec) {
+  const int64_t chunks = m * kbt * 8;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < chunks;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = e & 7, rk = e >> 3;  // chunk q of (row i, block kb)
+    const int64_t i = rk / kbt, kb = rk - i * kbt;
+    const int64_t t0 = kb * 64 + q * 8;
+    uint4 v;
+    if (vec && t0 + 8 <= k) {
+      v = *reinterpret_cast<const uint4*>(A + i * lda + t0);
+    } else {
+      uint32_t w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t t = t0 + 2 * j;
+        const uint16_t lo = t < k ? __bfloat16_as_ushort(A[i * lda + t]) : 0;
+        const uint16_t hi = t + 1 < k ? __bfloat16_as_ushort(A[i * lda + t + 1]) : 0;
+        w[j] = (uint32_t)lo | ((uint32_t)hi << 16);
+      }
+      v = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    *reinterpret_cast<uint4*>(Ab + ((kb * m + i) * 64 + q * 8)) = v;
+  }
+}
+
 struct TcArgs {
   Sched s;
   float* C;
@@ -106,6 +153,7 @@ struct TcArgs {
   int vec_ok;  // C rows 16-byte aligned
   float alpha, beta;  // C = alpha A B + beta C (C read only when beta != 0)
   int c_tma;          // C written by tensor stores (pk == 1, beta == 0, aligned rows)
+  int a_blocked;      // A read from its k-blocked copy [kbt][m][64] (3-D map)
 };
 
 template <int BN, int STAGES>
@@ -208,6 +256,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int j = 0; j < BM / 64; ++j)  // box j: rows j*64.. of the tile, k rows kb*64..
               tc::tma_load_2d(sa + j * (64 * BK * 2), &tmA, &full[stage],
                               (int32_t)(u.tile_row * BM + j * 64), (int32_t)(kb * BK));
+          } else if (a.a_blocked) {
+            tc::tma_load_3d(sa, &tmA, &full[stage], 0, (int32_t)(u.tile_row * BM), (int32_t)kb);
           } else {
             tc::tma_load_2d(sa, &tmA, &full[stage], (int32_t)(kb * BK),
                             (int32_t)(u.tile_row * BM));
@@ -387,15 +437,22 @@ struct TcCopies {
   bool a_mn, b_mn;      // operands multiplied MN-major
   bool pack_a, copy_b;  // A copied to the workspace; B copied (transposed or packed)
   bool b_transpose;     // the B copy is a transpose (else a packed copy of B^T)
+  bool block_a;         // A copied k-blocked: its rows are too far apart for one box
 };
 
+// Row pitch (bytes) from which a K-major A is read through its k-blocked copy: a
+// 128-row box then touches 128 pages of memory (16 at 256 KB), and the tensor
+// cores wait on translation -- 0.66 of peak at k = 2^20 (rows 2 MB apart).
+constexpr int64_t kBlockARowBytes = 256 << 10;
+
 static TcCopies tc_copies(const void* A, int64_t lda, int trans_a, const void* B, int64_t ldb,
-                          int trans_b) {
+                          int trans_b, int64_t k) {
   TcCopies c;
   const bool a_ok = A && (reinterpret_cast<uintptr_t>(A) & 15) == 0 && ((lda * 2) & 15) == 0;
   const bool b_ok = B && (reinterpret_cast<uintptr_t>(B) & 15) == 0 && ((ldb * 2) & 15) == 0;
   c.a_mn = trans_a != 0;
-  c.pack_a = !a_ok;
+  c.block_a = !trans_a && lda * 2 >= kBlockARowBytes && k >= 8 * BK;
+  c.pack_a = !a_ok && !c.block_a;
   c.b_mn = !trans_b && b_ok;
   c.copy_b = !c.b_mn && !(trans_b && b_ok);
   c.b_transpose = !trans_b;
@@ -405,7 +462,7 @@ static TcCopies tc_copies(const void* A, int64_t lda, int trans_a, const void* B
 int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void* ws,
                    long long ws_bytes, int* status, long long wait_limit, cudaStream_t st) {
   const int64_t kp = round_up(g.k, 8), mp = round_up(g.m, 8);
-  const TcCopies cp = tc_copies(g.A, g.lda, g.trans_a, g.B, g.ldb, g.trans_b);
+  const TcCopies cp = tc_copies(g.A, g.lda, g.trans_a, g.B, g.ldb, g.trans_b, g.k);
   uint8_t* w = static_cast<uint8_t*>(ws);
   long long off = 0;
   float* partial = nullptr;
@@ -452,10 +509,26 @@ int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void*
     Ause = Ap;
     lda = pitch;
   }
+  const int64_t kbt = (g.k + BK - 1) / BK;
+  if (cp.block_a) {
+    __nv_bfloat16* Ab = reinterpret_cast<__nv_bfloat16*>(w + off);
+    off += round_up(kbt * g.m * BK * 2, 256);
+    if (off > ws_bytes) return COSMA_ERR_NO_WORKSPACE;
+    int64_t blocks = (g.m * kbt * 8 + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    const int vec = ((reinterpret_cast<uintptr_t>(g.A) & 15) == 0 && (g.lda & 7) == 0) ? 1 : 0;
+    block_a_bf16<<<(unsigned)blocks, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(g.A), g.m,
+                                                    g.k, g.lda, Ab, kbt, vec);
+    count_launch();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return (int)e;
+    Ause = Ab;
+  }
   if (off > ws_bytes) return COSMA_ERR_NO_WORKSPACE;
   CUtensorMap ta, tb;
-  int rc = cp.a_mn ? encode_tmap_bf16(&ta, Ause, g.k, g.m, lda, 64, BK)   // k rows of m
-                   : encode_tmap_bf16(&ta, Ause, g.m, g.k, lda, BK, BM);  // m rows of k
+  int rc = cp.block_a ? encode_tmap_bf16_blocked(&ta, Ause, g.m, kbt, BM)
+           : cp.a_mn  ? encode_tmap_bf16(&ta, Ause, g.k, g.m, lda, 64, BK)   // k rows of m
+                      : encode_tmap_bf16(&ta, Ause, g.m, g.k, lda, BK, BM);  // m rows of k
   if (rc != COSMA_OK) return rc;
   rc = cp.b_mn ? encode_tmap_bf16(&tb, Buse, g.k, g.n, ldb, 64, BK)        // k rows of n
                : encode_tmap_bf16(&tb, Buse, g.n, g.k, ldb, BK, p.tile_n);  // n rows of k
@@ -468,6 +541,7 @@ int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void*
   args.status = status;
   args.wait_limit = wait_limit;
   args.vec_ok = ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0 && (g.ldc & 3) == 0) ? 1 : 0;
+  args.a_blocked = cp.block_a ? 1 : 0;
   args.alpha = (float)g.alpha;
   args.beta = (float)g.beta;
   // C by tensor stores when it is written directly with 16-byte aligned rows and
@@ -522,11 +596,12 @@ bool tc_b_direct(const void* B, int64_t ldb) {
 long long tc_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const void* A,
                              int64_t lda, int trans_a, const void* B, int64_t ldb, int trans_b) {
   const int64_t kp = round_up(k, 8), mp = round_up(m, 8);
-  const TcCopies cp = tc_copies(A, lda, trans_a, B, ldb, trans_b);
+  const TcCopies cp = tc_copies(A, lda, trans_a, B, ldb, trans_b, k);
   long long b = 0;
   if (p.pk > 1) b += round_up((long long)p.pk * m * n * 4, 256);
   if (cp.copy_b) b += round_up(n * kp * 2, 256);
   if (cp.pack_a) b += round_up((cp.a_mn ? k * mp : m * kp) * 2, 256);
+  if (cp.block_a) b += round_up((k + BK - 1) / BK * m * BK * 2, 256);
   return b;
 }
 

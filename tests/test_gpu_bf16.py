@@ -63,6 +63,17 @@ def test_bf16_odd_leading_dimensions_pack_path():
     _check(_run(m, n, k, lda=133, ldb=171, ldc=173), m, n, k)
 
 
+@pytest.mark.parametrize("kind", ["integer", "uniform"])
+@pytest.mark.parametrize("lda", [140001, 140008])
+def test_bf16_far_apart_rows_read_through_k_blocked_copy(kind, lda):
+    """Rows of A 280 KB apart (>= 256 KB) are read through a k-blocked copy
+    [k/64][m][64]: ragged k (140001 = 2187 x 64 + 33, zero-filled), an odd pitch
+    (element-wise copy) and a pitch of 8 elements (16-byte copy).  Integer inputs
+    bit-exact, uniform ones within gamma_k |A||B|."""
+    m, n, k = 130, 136, 140001
+    _check(_run(m, n, k, kind=kind, seed=8, lda=lda), m, n, k, kind=kind, seed=8)
+
+
 @pytest.mark.parametrize("tile_n,pk,order,ctas,pm,pn", [
     (256, 1, 1, 5, 1, 1), (128, 1, 1, 3, 1, 1), (256, 3, 1, 40, 1, 1), (128, 2, 0, 8, 2, 2),
     (256, 2, 0, 4, 2, 1)])
