@@ -573,16 +573,17 @@ int launch_tc_bf16(const GemmArgs& g, const Sched& s, const cosma_plan& p, void*
   return 0;
 }
 
-// f32 parts [2][rows][kp]: dims (k, rows, 2), 32 x box_rows x 1 boxes, 128-byte swizzle.
-int encode_tmap_f32_parts(CUtensorMap* map, const float* base, int64_t rows, int64_t k,
-                          int64_t kp, int box_rows) {
+// f32 parts [2][kbt][rows][32]: dims (32, rows, kbt, 2), 32 x box_rows x 1 x 1 boxes,
+// 128-byte swizzle.
+int encode_tmap_f32_parts(CUtensorMap* map, const float* base, int64_t rows, int64_t kbt,
+                          int box_rows) {
   auto fn = get_encode();
   if (!fn) return COSMA_ERR_CUDA;
-  cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, 2};
-  cuuint64_t strides[2] = {(cuuint64_t)(kp * 4), (cuuint64_t)(rows * kp * 4)};
-  cuuint32_t box[3] = {32, (cuuint32_t)box_rows, 1};
-  cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims,
+  cuuint64_t dims[4] = {32, (cuuint64_t)rows, (cuuint64_t)kbt, 2};
+  cuuint64_t strides[3] = {128, (cuuint64_t)(rows * 128), (cuuint64_t)(kbt * rows * 128)};
+  cuuint32_t box[4] = {32, (cuuint32_t)box_rows, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

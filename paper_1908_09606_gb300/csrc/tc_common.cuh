@@ -119,6 +119,15 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int32_t x, int32_t y, int32_t z, int32_t w) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "r"(w)
+      : "memory");
+}
+
 // Tensor store shared -> global of one box at (x, y), tracked by the bulk group
 // of the issuing thread.
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int32_t x,
@@ -381,10 +390,9 @@ __device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
 int encode_tmap_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
                      int box_cols, int box_rows);
 
-// Host: encode a 3-D f32 map of two stacked parts [2][rows][kp] (k columns used,
-// row pitch kp elements, kp a multiple of 4) with 32 x box_rows x 1 boxes and
-// 128-byte swizzle.  Returns 0 on success.
-int encode_tmap_f32_parts(CUtensorMap* map, const float* base, int64_t rows, int64_t k,
-                          int64_t kp, int box_rows);
+// Host: encode a 4-D f32 map of two stacked k-blocked parts [2][kbt][rows][32]
+// with 32 x box_rows x 1 x 1 boxes and 128-byte swizzle.  Returns 0 on success.
+int encode_tmap_f32_parts(CUtensorMap* map, const float* base, int64_t rows, int64_t kbt,
+                          int box_rows);
 
 }  // namespace cosma

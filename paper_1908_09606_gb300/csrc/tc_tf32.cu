@@ -10,8 +10,9 @@
 // rounded to nearest, so x = h + l + e with |e| <= 2^-22 |x|, and
 //     A B ~ A_h B_h + A_h B_l + A_l B_h,
 // the dropped A_l B_l and split remainders staying below about 3 2^-22 |A||B|.
-// The parts are written K-major as [2][rows][kp] f32 arrays (kp = k rounded
-// up to 4, so rows start on 16-byte boundaries).
+// The parts are written K-major and k-blocked, [2][kbt][rows][32] f32 (zero
+// beyond k): one TMA box is then 128 contiguous rows of 128 bytes whatever k
+// is (row-major parts at k = 2^20 would put every row of a box in its own page).
 //
 // Accumulation: the tensor cores' fp32 accumulator does not round to nearest,
 // and over a long k the error drifts one way (about 1e-4 relative at k =
@@ -93,43 +94,91 @@ __device__ __forceinline__ void tf32_parts(float x, float& hi, float& lo) {
   lo = __uint_as_float(l);
 }
 
-// Parts of a rows x cols matrix (ld) in its own orientation: P[q][r][t], row
-// pitch kp, q = 0 hi, 1 lo.
+// Index of element (part q, row r, k index t) in the k-blocked parts array.
+__device__ __forceinline__ int64_t part_index(int q, int64_t r, int64_t t, int64_t rows,
+                                              int64_t kbt) {
+  return (((int64_t)q * kbt + (t >> 5)) * rows + r) * TK + (t & 31);
+}
+
+// Parts of a rows x cols matrix (ld) in its own orientation (cols = k), zero
+// for k <= t < 32 kbt.  Each thread step takes 4 consecutive k (16-byte loads
+// when vec: X 16-byte aligned and ld a multiple of 4) and writes one 16-byte
+// chunk of each part; four steps are loaded before any is converted, so each
+// thread keeps 64 bytes in flight.
 __global__ void tf32_split_rows(const float* __restrict__ X, int64_t rows, int64_t cols,
-                                int64_t ld, float* __restrict__ P, int64_t kp) {
+                                int64_t ld, float* __restrict__ P, int64_t kbt, int vec) {
+  const int64_t q4 = kbt * (TK / 4);  // 4-element chunks per row
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
     const float* x = X + r * ld;
-    float* ph = P + r * kp;
-    float* pl = P + (rows + r) * kp;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cols;
-         t += (int64_t)gridDim.x * blockDim.x) {
-      float hi, lo;
-      tf32_parts(x[t], hi, lo);
-      ph[t] = hi;
-      pl[t] = lo;
+    for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < q4; c0 += 4 * stride) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t t = 4 * (c0 + u * stride);
+        if (vec && t + 4 <= cols) {
+          v[u] = *reinterpret_cast<const float4*>(x + t);
+        } else {
+          v[u].x = t < cols ? x[t] : 0.f;
+          v[u].y = t + 1 < cols ? x[t + 1] : 0.f;
+          v[u].z = t + 2 < cols ? x[t + 2] : 0.f;
+          v[u].w = t + 3 < cols ? x[t + 3] : 0.f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t c = c0 + u * stride;
+        if (c >= q4) break;
+        const int64_t t = 4 * c;
+        float4 h, l;
+        tf32_parts(v[u].x, h.x, l.x);
+        tf32_parts(v[u].y, h.y, l.y);
+        tf32_parts(v[u].z, h.z, l.z);
+        tf32_parts(v[u].w, h.w, l.w);
+        *reinterpret_cast<float4*>(P + part_index(0, r, t, rows, kbt)) = h;
+        *reinterpret_cast<float4*>(P + part_index(1, r, t, rows, kbt)) = l;
+      }
     }
   }
 }
 
-// Parts of the transpose of a k x n matrix (ld): P[q][j][t], row pitch kp.
-// 32 x 32 tiles through shared memory.
+// Parts of the transpose of a k x n matrix (ld): rows j < n, k index t, zero
+// for k <= t < 32 kbt.  A block takes 32 k x 64 j through shared memory
+// (grid.y = kbt): reads are 256-byte row segments of X, writes one 16-byte
+// chunk per thread and part.
 __global__ void tf32_split_transpose(const float* __restrict__ X, int64_t k, int64_t n,
-                                     int64_t ld, float* __restrict__ P, int64_t kp) {
-  __shared__ float th[32][33], tl[32][33];
-  const int64_t t0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    const int64_t t = t0 + r, j = j0 + threadIdx.x;
-    float hi = 0.f, lo = 0.f;
-    if (t < k && j < n) tf32_parts(X[t * ld + j], hi, lo);
-    th[threadIdx.x][r] = hi;
-    tl[threadIdx.x][r] = lo;
+                                     int64_t ld, float* __restrict__ P, int64_t kbt) {
+  __shared__ float th[64][33], tl[64][33];
+  const int64_t t0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 64;
+  const int tid = threadIdx.y * 32 + threadIdx.x;  // 256 threads
+  float v[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {  // element (t0 + 4u + ty/2 .., j0 + 32 (ty & 1) + tx)
+    const int r = 4 * u + (threadIdx.y >> 1);
+    const int64_t t = t0 + r, j = j0 + 32 * (threadIdx.y & 1) + threadIdx.x;
+    v[u] = (t < k && j < n) ? X[t * ld + j] : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int r = 4 * u + (threadIdx.y >> 1);
+    const int jj = 32 * (threadIdx.y & 1) + threadIdx.x;
+    float hi, lo;
+    tf32_parts(v[u], hi, lo);
+    th[jj][r] = hi;
+    tl[jj][r] = lo;
   }
   __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    const int64_t j = j0 + r, t = t0 + threadIdx.x;
-    if (j < n && t < k) {
-      P[j * kp + t] = th[r][threadIdx.x];
-      P[(n + j) * kp + t] = tl[r][threadIdx.x];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {  // 64 rows j x 8 chunks of 4 t = 512 chunks per part
+    const int id = tid + 256 * u;
+    const int jj = id >> 3, tq = (id & 7) * 4;
+    const int64_t j = j0 + jj;
+    if (j < n) {
+      const int64_t t = t0 + tq;
+      *reinterpret_cast<float4*>(P + part_index(0, j, t, n, kbt)) =
+          make_float4(th[jj][tq], th[jj][tq + 1], th[jj][tq + 2], th[jj][tq + 3]);
+      *reinterpret_cast<float4*>(P + part_index(1, j, t, n, kbt)) =
+          make_float4(tl[jj][tq], tl[jj][tq + 1], tl[jj][tq + 2], tl[jj][tq + 3]);
     }
   }
 }
@@ -245,11 +294,11 @@ tf32x3_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
             if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) { ok = false; break; }
             tc::mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES);
             uint8_t* sa = smem + stage * L::STAGE_BYTES;
-            const int32_t x = (int32_t)(kb * TK);
-            tc::tma_load_3d(sa, &tmA, &full[stage], x, ya, 0);                 // A_h
-            tc::tma_load_3d(sa + L::PART, &tmA, &full[stage], x, ya, 1);       // A_l
-            tc::tma_load_3d(sa + 2 * L::PART, &tmB, &full[stage], x, yb, 0);   // B_h
-            tc::tma_load_3d(sa + 3 * L::PART, &tmB, &full[stage], x, yb, 1);   // B_l
+            const int32_t z = (int32_t)kb;
+            tc::tma_load_4d(sa, &tmA, &full[stage], 0, ya, z, 0);                 // A_h
+            tc::tma_load_4d(sa + L::PART, &tmA, &full[stage], 0, ya, z, 1);       // A_l
+            tc::tma_load_4d(sa + 2 * L::PART, &tmB, &full[stage], 0, yb, z, 0);   // B_h
+            tc::tma_load_4d(sa + 3 * L::PART, &tmB, &full[stage], 0, yb, z, 1);   // B_l
             armed |= 1u << stage;
             armed_ph = (armed_ph & ~(1u << stage)) | (ph << stage);
             if (++stage == STAGES) { stage = 0; ph ^= 1; }
@@ -369,10 +418,10 @@ inline int64_t round_up(int64_t x, int64_t r) { return (x + r - 1) / r * r; }
 }  // namespace
 
 long long tf32x3_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_plan& p) {
-  const int64_t kp = round_up(k, 4);
+  const int64_t kpad = round_up(k, TK);
   long long b = 0;
   if (p.pk > 1) b += round_up((long long)p.pk * m * n * 4, 256);
-  b += round_up(2 * m * kp * 4, 256) + round_up(2 * n * kp * 4, 256);
+  b += round_up(2 * m * kpad * 4, 256) + round_up(2 * n * kpad * 4, 256);
   return b + 256;  // lock-step tick counter
 }
 
@@ -381,8 +430,9 @@ long long tf32x3_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_pl
 int launch_tc_tf32x3(const GemmArgs& g, const Sched& s, const cosma_plan& p, void* ws,
                      long long ws_bytes, int* status, long long wait_limit, cudaStream_t st) {
   if (p.tile_m != TM || p.tile_n != TN || p.k_block != TK) return COSMA_ERR_INVALID_ARG;
-  const int64_t kp = round_up(g.k, 4);
+  const int64_t kbt = (g.k + TK - 1) / TK, kpad = kbt * TK;
   if (tf32x3_workspace_bytes(g.m, g.n, g.k, p) > ws_bytes) return COSMA_ERR_NO_WORKSPACE;
+  if (kbt > 65535) return COSMA_ERR_UNSUPPORTED;  // split grids' y extent
   uint8_t* w = static_cast<uint8_t*>(ws);
   long long off = 0;
   float* partial = nullptr;
@@ -391,46 +441,45 @@ int launch_tc_tf32x3(const GemmArgs& g, const Sched& s, const cosma_plan& p, voi
     off += round_up((long long)p.pk * g.m * g.n * 4, 256);
   }
   float* PA = reinterpret_cast<float*>(w + off);
-  off += round_up(2 * g.m * kp * 4, 256);
+  off += round_up(2 * g.m * kpad * 4, 256);
   float* PB = reinterpret_cast<float*>(w + off);
-  off += round_up(2 * g.n * kp * 4, 256);
+  off += round_up(2 * g.n * kpad * 4, 256);
   unsigned int* counter = reinterpret_cast<unsigned int*>(w + off);
   const float* A = static_cast<const float*>(g.A);
   const float* B = static_cast<const float*>(g.B);
-  auto rows_grid = [](int64_t rows, int64_t cols) {
-    int64_t x = (cols + 255) / 256;
-    if (x > 16) x = 16;
-    int64_t y = rows < 4096 ? rows : 4096;
+  // rows kernel: x covers a row's 4-element chunks (4 per thread per pass, at most 8
+  // blocks), y the rows
+  auto rows_grid = [kpad](int64_t rows) {
+    int64_t x = (kpad / 4 + 1023) / 1024;
+    if (x > 8) x = 8;
+    const int64_t y = rows < 8192 ? rows : 8192;
     return dim3((unsigned)(x < 1 ? 1 : x), (unsigned)(y < 1 ? 1 : y));
   };
-  auto t_grid = [](int64_t k, int64_t n) {
-    return dim3((unsigned)((n + 31) / 32), (unsigned)((k + 31) / 32));
+  auto t_grid = [kbt](int64_t n) { return dim3((unsigned)((n + 63) / 64), (unsigned)kbt); };
+  auto vec_of = [](const float* X, int64_t ld) {
+    return ((reinterpret_cast<uintptr_t>(X) & 15) == 0 && (ld & 3) == 0) ? 1 : 0;
   };
-  // A parts, K-major m x kp: A row by row, or the transpose of a stored k x m
-  if (!g.trans_a) {
-    tf32_split_rows<<<rows_grid(g.m, g.k), 256, 0, st>>>(A, g.m, g.k, g.lda, PA, kp);
-  } else {
-    const dim3 grid = t_grid(g.k, g.m);
-    if (grid.y > 65535) return COSMA_ERR_UNSUPPORTED;
-    tf32_split_transpose<<<grid, dim3(32, 8), 0, st>>>(A, g.k, g.m, g.lda, PA, kp);
-  }
+  // A parts: A row by row, or the transpose of a stored k x m
+  if (!g.trans_a)
+    tf32_split_rows<<<rows_grid(g.m), 256, 0, st>>>(A, g.m, g.k, g.lda, PA, kbt,
+                                                    vec_of(A, g.lda));
+  else
+    tf32_split_transpose<<<t_grid(g.m), dim3(32, 8), 0, st>>>(A, g.k, g.m, g.lda, PA, kbt);
   count_launch();
-  // B parts, K-major n x kp: the transpose of B, or a stored n x k row by row
-  if (!g.trans_b) {
-    const dim3 grid = t_grid(g.k, g.n);
-    if (grid.y > 65535) return COSMA_ERR_UNSUPPORTED;
-    tf32_split_transpose<<<grid, dim3(32, 8), 0, st>>>(B, g.k, g.n, g.ldb, PB, kp);
-  } else {
-    tf32_split_rows<<<rows_grid(g.n, g.k), 256, 0, st>>>(B, g.n, g.k, g.ldb, PB, kp);
-  }
+  // B parts: the transpose of B, or a stored n x k row by row
+  if (!g.trans_b)
+    tf32_split_transpose<<<t_grid(g.n), dim3(32, 8), 0, st>>>(B, g.k, g.n, g.ldb, PB, kbt);
+  else
+    tf32_split_rows<<<rows_grid(g.n), 256, 0, st>>>(B, g.n, g.k, g.ldb, PB, kbt,
+                                                    vec_of(B, g.ldb));
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return (int)e;
 
   CUtensorMap ta, tb;
-  int rc = encode_tmap_f32_parts(&ta, PA, g.m, g.k, kp, TM);
+  int rc = encode_tmap_f32_parts(&ta, PA, g.m, kbt, TM);
   if (rc != COSMA_OK) return rc;
-  rc = encode_tmap_f32_parts(&tb, PB, g.n, g.k, kp, TN);
+  rc = encode_tmap_f32_parts(&tb, PB, g.n, kbt, TN);
   if (rc != COSMA_OK) return rc;
   TfArgs args;
   args.s = s;
