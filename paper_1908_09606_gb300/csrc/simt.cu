@@ -49,11 +49,11 @@ simt_gemm_kernel(GemmArgs g, Sched s, T* partial) {
 }
 
 // K-F32: the cp.async multi-stage tile of simt_f32.cuh (BM x 128, 2 BM threads).
-template <int BM, int VEC>
+template <int BM, int VEC, int BN = F32_BN>
 __global__ void __launch_bounds__(f32_threads<BM>(), 1)
 simt_f32_kernel(GemmArgs g, Sched s, float* partial, int vec_c) {
   extern __shared__ __align__(16) uint8_t f32_smem[];
-  F32Smem<BM>& sm = *reinterpret_cast<F32Smem<BM>*>(f32_smem);
+  F32Smem<BM, BN>& sm = *reinterpret_cast<F32Smem<BM, BN>*>(f32_smem);
   const float* A = static_cast<const float*>(g.A);
   const float* B = static_cast<const float*>(g.B);
   const int cta = blockIdx.x;
@@ -73,9 +73,9 @@ simt_f32_kernel(GemmArgs g, Sched s, float* partial, int vec_c) {
       vec = vec_c != 0;
     }
     const float al = s.pk > 1 ? 1.f : (float)g.alpha, be = s.pk > 1 ? 0.f : (float)g.beta;
-    f32_tile<BM, VEC>(A, g.lda, B, g.ldb, dst, ld, g.m, g.n, u.tile_row * BM,
-                      u.tile_col * F32_BN, u.kb0 * (int64_t)s.k_block,
-                      min(u.kb1 * (int64_t)s.k_block, g.k), vec, sm, al, be);
+    f32_tile<BM, VEC, BN>(A, g.lda, B, g.ldb, dst, ld, g.m, g.n, u.tile_row * BM,
+                          u.tile_col * BN, u.kb0 * (int64_t)s.k_block,
+                          min(u.kb1 * (int64_t)s.k_block, g.k), vec, sm, al, be);
   }
 }
 
@@ -174,14 +174,20 @@ int launch_simt(int dtype, const GemmArgs& g, const Sched& s, void* partial, int
     if (s.tile_m == 128) return launch_tile<double, 128, 128, 8, 8, 8>(g, s, partial, st);
     return launch_tile<double, 64, 64, 8, 4, 4>(g, s, partial, st);
   }
-  if ((s.tile_m != 128 && s.tile_m != 256) || s.tile_n != F32_BN || s.k_block % F32_BK)
+  const bool wide = s.tile_m == 128 && s.tile_n == 256;
+  if (!wide && ((s.tile_m != 128 && s.tile_m != 256) || s.tile_n != F32_BN))
     return COSMA_ERR_INVALID_ARG;
+  if (s.k_block % F32_BK) return COSMA_ERR_INVALID_ARG;
   const bool vec_ab = (reinterpret_cast<uintptr_t>(g.A) & 15) == 0 && (g.lda & 3) == 0 &&
                      (reinterpret_cast<uintptr_t>(g.B) & 15) == 0 && (g.ldb & 3) == 0;
   const int vec_c = (reinterpret_cast<uintptr_t>(g.C) & 15) == 0 && (g.ldc & 3) == 0;
   void (*kern)(GemmArgs, Sched, float*, int);
   int threads, smem;
-  if (s.tile_m == 256) {
+  if (wide) {
+    kern = vec_ab ? simt_f32_kernel<128, 4, 256> : simt_f32_kernel<128, 1, 256>;
+    threads = f32_threads<128>();
+    smem = (int)sizeof(F32Smem<128, 256>);
+  } else if (s.tile_m == 256) {
     kern = vec_ab ? simt_f32_kernel<256, 4> : simt_f32_kernel<256, 1>;
     threads = f32_threads<256>();
     smem = (int)sizeof(F32Smem<256>);

@@ -1,16 +1,18 @@
 // FP32 C-stationary tile on the FFMA pipe (K-F32).
 //
-// A BM x 128 C tile stays in registers, 8 x 8 per thread.  Warps own 64 x 32
-// sub-tiles (BM = 128: 2 x 4 warps, 256 threads; BM = 256: 4 x 4 warps, 512
-// threads, four warps per SM quarter to hide shared-memory latency).  The 32
-// lanes of a warp form an 8 x 4 grid: lane (y, x) owns rows y, y + 8, ..., y + 56
-// of the warp tile and columns 4x..4x+3, 16+4x..16+4x+3.
+// A BM x BN C tile stays in registers, 8 x (BN / 16) per thread.  Warps own
+// 64 x (BN / 4) sub-tiles (BM = 128: 2 x 4 warps, 256 threads; BM = 256: 4 x 4
+// warps, 512 threads, four warps per SM quarter to hide shared-memory latency).
+// The 32 lanes of a warp form an 8 x 4 grid: lane (y, x) owns rows y, y + 8, ...,
+// y + 56 of the warp tile and the column quads 4x + 16 g, g < BN / 64.
 //
 // Both panels keep their global layout in shared memory: A row-major with a
 // 36-float pitch (k contiguous), so one 16-byte read gives a thread four k
 // steps of one row and the 8 rows a warp reads at once fall in distinct bank
 // quads; B row-major, two 16-byte reads per k step (4 distinct per warp).  Per
-// 4 k steps a thread issues 8 + 8 shared loads for 256 FFMAs.  32-deep k panels
+// 4 k steps a thread issues 8 + 8 shared loads for 256 FMAs, as 128 packed
+// fma.rn.f32x2 (two round-to-nearest FMAs per issue slot: the results are those
+// of scalar FMAs).  32-deep k panels
 // stream through F32_STAGES buffers by cp.async (16-byte copies when A and B
 // are 16-byte aligned with pitches a multiple of 4 floats, else 4-byte): the
 // panels of round t + STAGES - 1 are in flight while round t is multiplied
@@ -23,10 +25,10 @@ namespace cosma {
 
 constexpr int F32_BN = 128, F32_BK = 32, F32_STAGES = 4, F32_APITCH = F32_BK + 4;
 
-template <int BM>
+template <int BM, int BN = F32_BN>
 struct F32Smem {
   float As[F32_STAGES][BM][F32_APITCH];  // row-major A panel
-  float Bs[F32_STAGES][F32_BK][F32_BN];  // row-major B panel
+  float Bs[F32_STAGES][F32_BK][BN];      // row-major B panel
 };
 
 // Threads of a CTA running f32_tile<BM>.
@@ -54,19 +56,36 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// C[row0 : row0 + BM, col0 : col0 + 128] (clipped to m x n) = A[rows, kbeg:kend] B[kbeg:kend, cols],
+// Two fp32 lanes in one 64-bit register pair, and the packed FMA on them
+// (fma.rn.f32x2: two IEEE round-to-nearest FMAs, one issue slot).
+__device__ __forceinline__ uint64_t f32x2_pack(float x, float y) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ void f32x2_unpack(uint64_t v, float& x, float& y) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
+}
+__device__ __forceinline__ void f32x2_fma(uint64_t& d, uint64_t a, uint64_t b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+
+// C[row0 : row0 + BM, col0 : col0 + BN] (clipped to m x n) = A[rows, kbeg:kend] B[kbeg:kend, cols],
 // written to dst (leading dimension ld).  Every thread of the CTA calls it.
-template <int BM, int VEC>
+template <int BM, int VEC, int BN = F32_BN>
 __device__ __forceinline__ void f32_tile(const float* __restrict__ A, int64_t lda,
                                          const float* __restrict__ B, int64_t ldb, float* dst,
                                          int64_t ld, int64_t m, int64_t n, int64_t row0,
                                          int64_t col0, int64_t kbeg, int64_t kend, bool vec_out,
-                                         F32Smem<BM>& sm, float alpha = 1.f, float beta = 0.f) {
+                                         F32Smem<BM, BN>& sm, float alpha = 1.f,
+                                         float beta = 0.f) {
+  static_assert(BN == 128 || BN == 256, "tile width");
   constexpr int NT = f32_threads<BM>();
+  constexpr int NG = BN / 64;  // column quads per thread: 4x + 16 g
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int ar = (warp >> 2) * 64 + (lane >> 2);   // rows ar + 8 i, i = 0..7
-  const int bc = (warp & 3) * 32 + (lane & 3) * 4;  // cols bc..bc+3, bc+16..bc+19
+  const int ar = (warp >> 2) * 64 + (lane >> 2);         // rows ar + 8 i, i = 0..7
+  const int bc = (warp & 3) * (BN / 4) + (lane & 3) * 4;  // cols bc + 16 g .. + 3
   const int64_t nsteps = (kend - kbeg + F32_BK - 1) / F32_BK;
 
   // A copies: VEC-float chunks; this thread's chunk column a_c and rows
@@ -78,7 +97,7 @@ __device__ __forceinline__ void f32_tile(const float* __restrict__ A, int64_t ld
   const int a_r = tid / A_COLS, a_c = (tid % A_COLS) * VEC;
   const float* a_src = A + (kbeg + a_c);
   // B copies: a fixed chunk column per thread, rows b_k0 + e * B_STEP.
-  constexpr int B_COLS = F32_BN / VEC;
+  constexpr int B_COLS = BN / VEC;
   constexpr int B_STEP = NT / B_COLS;
   constexpr int B_PER = F32_BK / B_STEP;
   const int b_k0 = tid / B_COLS, b_c = (tid % B_COLS) * VEC;
@@ -86,11 +105,13 @@ __device__ __forceinline__ void f32_tile(const float* __restrict__ A, int64_t ld
   const int b_bytes = b_gc >= n ? 0 : (n - b_gc >= VEC ? 4 * VEC : (int)(n - b_gc) * 4);
   const float* b_src = B + (b_bytes ? b_gc : 0) + (kbeg + b_k0) * ldb;
 
-  float acc[8][8];
+  // acc2[i][2 g + h] holds C(ar + 8 i, bc + 16 g + 2 h .. + 1): packed pairs for
+  // fma.rn.f32x2
+  uint64_t acc2[8][2 * NG];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int p = 0; p < 2 * NG; ++p) acc2[i][p] = f32x2_pack(0.f, 0.f);
 
   auto issue = [&](int64_t step, int buf) {
     const int64_t kk0 = step * F32_BK;  // offset from kbeg
@@ -141,19 +162,29 @@ __device__ __forceinline__ void f32_tile(const float* __restrict__ A, int64_t ld
         a4[i] = *reinterpret_cast<const float4*>(&sm.As[buf][ar + 8 * i][kq]);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
-        const float4 u = *reinterpret_cast<const float4*>(&sm.Bs[buf][kq + kk][bc]);
-        const float4 v = *reinterpret_cast<const float4*>(&sm.Bs[buf][kq + kk][bc + 16]);
-        const float b[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+        uint64_t b2[2 * NG];
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+          const float4 u = *reinterpret_cast<const float4*>(&sm.Bs[buf][kq + kk][bc + 16 * g]);
+          b2[2 * g] = f32x2_pack(u.x, u.y);
+          b2[2 * g + 1] = f32x2_pack(u.z, u.w);
+        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const float a = kk == 0 ? a4[i].x : kk == 1 ? a4[i].y : kk == 2 ? a4[i].z : a4[i].w;
+          const uint64_t a2 = f32x2_pack(a, a);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a, b[j], acc[i][j]);
+          for (int p = 0; p < 2 * NG; ++p) f32x2_fma(acc2[i][p], a2, b2[p]);
         }
       }
     }
   }
   cp_async_wait<0>();
+  float acc[8][4 * NG];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int p = 0; p < 2 * NG; ++p) f32x2_unpack(acc2[i][p], acc[i][2 * p], acc[i][2 * p + 1]);
 
   // C = alpha acc + beta C (C read only when beta != 0)
   const bool plain = alpha == 1.f && beta == 0.f;
@@ -163,7 +194,7 @@ __device__ __forceinline__ void f32_tile(const float* __restrict__ A, int64_t ld
     if (r >= m) continue;
     float* drow = dst + r * ld;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < NG; ++h) {
       const int64_t c = col0 + bc + 16 * h;
       if (!plain) {
 #pragma unroll

@@ -96,7 +96,8 @@ def _forced_plan(m, n, k, dtype, tile, pk, order, ctas, pm=1, pn=1):
     return p
 
 
-# the two tiles of each family: FP64 128 x 128 / 64 x 64, FP32 128 x 128 / 256 x 128
+# two tiles of each family: FP64 128 x 128 / 64 x 64, FP32 128 x 128 / 256 x 128 (the
+# FP32 128 x 256 tile has its own tests below)
 TILES = {"f64": [(128, 128), (64, 64)], "f32": [(128, 128), (256, 128)]}
 
 
@@ -115,6 +116,29 @@ def test_forced_plans_split_k_and_orders(dtype, ti, pk, order, ctas, pm, pn):
     else:
         absref = og.gemm(np.abs(A), np.abs(B), "naive")
         assert np.all(np.abs(C - ref) <= _gamma(k, 2.0 ** -24) * absref * (1 + 1e-12))
+
+
+@pytest.mark.parametrize("pk,order,ctas,pm,pn", [(1, 1, 7, 1, 1), (3, 1, 20, 1, 1),
+                                                  (2, 0, 2 * 2 * 2, 2, 2), (5, 1, 148, 1, 1)])
+@pytest.mark.parametrize("vec", [True, False])
+def test_f32_wide_tile_forced_plans(pk, order, ctas, pm, pn, vec):
+    # 128 x 256 tiles (16 columns per thread); ragged m, n, k; unaligned pitches
+    # take the 4-byte copies
+    m, n, k = 300, 520, 515
+    p = _forced_plan(m, n, k, "f32", (128, 256), pk, order, ctas, pm, pn)
+    C = _run(m, n, k, "f32", plan=p, lda=None if vec else 517, ldb=None if vec else 523)
+    A, B = host_operands(m, n, k, "f32")
+    ref = og.gemm(A, B, "dot2")
+    absref = og.gemm(np.abs(A), np.abs(B), "naive")
+    assert np.all(np.abs(C - ref) <= _gamma(k, 2.0 ** -24) * absref * (1 + 1e-12))
+
+
+def test_f32_wide_tile_integer_bit_exact():
+    m, n, k = 257, 600, 333
+    p = _forced_plan(m, n, k, "f32", (128, 256), 1, 1, 10)
+    C = _run(m, n, k, "f32", kind="integer", seed=3, plan=p)
+    A, B = host_operands(m, n, k, "f32", kind="integer", seed=3)
+    assert np.array_equal(C, og.gemm(A, B, "naive"))
 
 
 def test_invalid_plan_rejected():
