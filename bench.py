@@ -81,7 +81,7 @@ def _alu_peak_tflops(dtype, sms):
 DRAM_TRAFFIC = {
     ("square", "bf16"): 10.38e9 + 1.07e9,     # tc_gemm_kernel<256,4,A K,B MN>, tensor-store C
     ("flat", "bf16"): 4.30e9 + 17.15e9,       # same kernel, 16 GB of f32 C
-    ("4096", "f32"): 0.289e9 + 0.054e9,       # simt_f32_kernel<128,4>, 32-deep panels
+    ("4096", "f32"): 0.328e9 + 0.109e9,       # simt_f32_kernel<128,4,256>, pk = 2, f32x2 FMAs
     ("4096", "f64"): 0.969e9 + 0.133e9,       # simt_gemm_kernel<double,64,64,8,4,4>
     ("grouped512", "bf16"): 2.27e9 + 1.98e9,    # grouped_tc_kernel<256,4>
     # emu_gemm_pair_kernel: the lock-step schedule captured under a plain cluster
@@ -597,7 +597,8 @@ def main():
     slices = cfg_lib.emu_slices or 6
     pairs = slices * (slices + 1) // 2
     if dtype in ("f64", "f32"):
-        roof = {"kernel": f"simt_gemm_kernel<{dtype}>", "bound": "alu",
+        roof = {"kernel": "simt_f32_kernel" if dtype == "f32" else "simt_gemm_kernel<double>",
+                "bound": "alu",
                 "achieved": flops / (kern_ms * 1e-3) / 1e12,
                 "peak": _alu_peak_tflops(dtype, sms), "unit": "TFLOP/s",
                 "peak_source": "derived: SMs x FMA lanes/clk x 2 x 2070 MHz",
