@@ -349,18 +349,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                              : a.C + row * a.ldc;
       }
       const bool vec = a.s.pk > 1 ? ((a.s.n & 3) == 0) : (a.vec_ok != 0);
-#pragma unroll 1
-      for (int c = 0; c < BN; c += 32) {
-        uint32_t r[32];
-        tc::tmem_ld_32x32(tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN + c, r);
-        tc::tmem_wait_ld();
+      // One 32-column chunk of the accumulator, already in registers.
+      auto chunk = [&](const uint32_t (&r)[32], int c) {
         const int64_t col0 = u.tile_col * BN + c;
         if (a.c_tma) {
           // Columns below n4: this warp's 32 rows -> one 32 x 32 box in shared memory
           // (16-byte chunk j of row l at chunk j ^ (l % 8): the 128-byte swizzle), then
           // one tensor store clipped at m and n4 (a store clips in whole 16-byte units);
           // columns n4..n-1 are written by the lanes.
-          if (row0 >= a.s.m || col0 >= a.s.n) continue;
+          if (row0 >= a.s.m || col0 >= a.s.n) return;
           if (col0 < n4) {
             uint8_t* box = stage_c + (stores & 1) * 4096;
             if (lane == 0) tc::bulk_wait_read<1>();  // the box's previous store has read it
@@ -385,12 +382,27 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int j = 0; j < 32; ++j)
               if (col0 + j >= n4 && col0 + j < a.s.n) dst_row[col0 + j] = a.alpha * __uint_as_float(r[j]);
           }
-          continue;
+          return;
         }
         if (dst_row && col0 < a.s.n) {
           if (a.s.pk > 1) store_row32(dst_row + col0, col0, a.s.n, r, vec);
           else store_row32(dst_row + col0, col0, a.s.n, r, vec, a.alpha, a.beta);
         }
+      };
+      // Two register sets: the next chunk's tensor-memory load is in flight while
+      // the current one is written out.
+      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN;
+      uint32_t ra[32], rb[32];
+      tc::tmem_ld_32x32(tbase, ra);
+      tc::tmem_wait_ld_r32(ra);
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 64) {
+        tc::tmem_ld_32x32(tbase + c + 32, rb);
+        chunk(ra, c);
+        tc::tmem_wait_ld_r32(rb);
+        if (c + 64 < BN) tc::tmem_ld_32x32(tbase + c + 64, ra);
+        chunk(rb, c + 32);
+        if (c + 64 < BN) tc::tmem_wait_ld_r32(ra);
       }
       tc::tc_fence_before();
       __syncwarp();
