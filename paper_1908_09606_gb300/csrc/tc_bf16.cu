@@ -17,7 +17,9 @@
 // B arrives row-major (k x n, n contiguous).  When its rows are 16-byte aligned
 // it is loaded as it is -- 64 x 64 TMA boxes (64 n by 64 k, 128-byte swizzle) --
 // and multiplied as an MN-major operand; otherwise it is first transposed into
-// the workspace so both operands are K-major.
+// the workspace so both operands are K-major.  A is loaded in place unless its
+// rows are at least 256 KB apart (then through a k-blocked copy, so one box is
+// contiguous) or not 16-byte aligned (then through a pitch-padded copy).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>

@@ -23,7 +23,7 @@
 // while the epilogue drains the other.
 //
 // Stage (64 KB): the A_h, A_l, B_h, B_l tiles of one k block, 128 rows x 32
-// f32 each (one 128-byte swizzled row per tile row), by four 3-D TMA copies.
+// f32 each (one 128-byte swizzled row per tile row), by four 4-D TMA copies.
 // Warp roles as in K-BF16: warp 0 TMA, warp 1 tensor memory + MMA, warps 2-5
 // segment sums and stores (warp w reads tensor-memory lanes 32 (w % 4) ..).
 //
