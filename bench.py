@@ -365,6 +365,9 @@ def run_grouped(args):
         Bs.append(B)
         Cs.append(torch.empty((m, rup(n, 4)), dtype=torch.float32, device="cuda")[:, :n])
     flops = float((2 * dims.prod(axis=1)).sum())
+    # tile width by the autotuner (eager launches, before the graph is captured)
+    from paper_1908_09606_gb300 import autotune
+    tile, tile_ms = autotune.tune_grouped(As, Bs, Cs, dtype)
     stream = torch.cuda.current_stream()
     side = torch.cuda.Stream()
     side.wait_stream(stream)
@@ -497,7 +500,9 @@ def run_grouped(args):
                                        f"from a CUDA graph ({reps} replays per step)",
                            "flops_per_replay": flops, "replay_ms": replay_ms,
                            "pitches": "rows padded to 16 bytes",
-                           "l2": "inputs larger than L2"},
+                           "l2": "inputs larger than L2",
+                           "autotuned_tile": {"chosen": tile,
+                                              "eager_ms": {str(t): v for t, v in tile_ms.items()}}},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks,
                 "one_launch_per_gemm": {"value": flops / (pg_ms * 1e-3) / 1e12,

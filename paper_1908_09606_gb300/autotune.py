@@ -10,6 +10,8 @@
               checkpointing parameters and Adam state after every epoch.
   evaluate()  exhaustive timing on held-out shapes: regret of the learned
               choice and of the analytic plan against the best candidate.
+  tune_grouped()  times one grouped launch with each tile width the grouped
+              kernels implement and keeps the fastest as the configured default.
 
 Shapes: m, n, k log-uniform in [lo, hi] from the shared generator, rejecting
 shapes with an operand above `cap_bytes`.  Every compute step runs in the
@@ -248,6 +250,43 @@ def evaluate(shapes, dtype=cosma.COSMA_BF16, cap_bytes=16e9, max_ws_bytes=24e9, 
 
 SHIPPED_PARAMS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data",
                               "selector_bf16_gb300.npy")
+
+
+def tune_grouped(As, Bs, Cs, dtype, tiles=None, reps=3):
+    """Autotune the grouped launch for this group of products: time
+    cosma_gemm_grouped (CUDA events, best of `reps`) with each tile width (bf16:
+    128 x 128 and 128 x 256 C tiles; f32: 64 and 128), the library's tables for
+    a width being built by an untimed first call; set the fastest as the
+    library's grouped_tile and return (tile, {tile: milliseconds})."""
+    import torch
+    if tiles is None:
+        tiles = (128, 256) if dtype in ("bf16", cosma.COSMA_BF16) else (64, 128)
+    cfg = cosma.cosma_get_config()
+
+    def use(tile):
+        rc = cosma.cosma_init(cfg.delta, cfg.selector, cfg.emu_slices, cfg.emu_slice_bits,
+                              cfg.wait_limit, tile)
+        if rc != cosma.COSMA_OK:
+            raise cosma.CosmaError(rc, "cosma_init")
+
+    times = {}
+    for t in tiles:
+        use(t)
+        cosma.gemm_grouped(As, Bs, Cs, dtype)
+        torch.cuda.synchronize()
+        best = math.inf
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            cosma.gemm_grouped(As, Bs, Cs, dtype)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        times[t] = best
+    choice = min(times, key=times.get)
+    use(choice)
+    return choice, times
 
 
 def install(params_path=None, log2_lo=8.0, log2_hi=16.0):
