@@ -172,3 +172,20 @@ def test_grouped_bf16_padded_pitches_direct_b_and_tensor_stores():
     for (m, n, k), st in zip(dims, stores):
         if st.shape[1] > n:
             assert torch.all(st[:, n:] == -3.0)
+
+
+@pytest.mark.parametrize("dtype,tiles", [("bf16", (128, 256)), ("f32", (64, 128))])
+def test_grouped_autotuner_picks_a_tile_and_results_hold(dtype, tiles):
+    from paper_1908_09606_gb300 import autotune
+    cosma = lib()
+    dims = problem_dims(40)
+    As, Bs, Cs = make_group(dims, dtype)
+    try:
+        tile, times = autotune.tune_grouped(As, Bs, Cs, dtype, reps=2)
+        assert tile in tiles and set(times) == set(tiles)
+        assert times[tile] == min(times.values()) and all(t > 0 for t in times.values())
+        assert cosma.cosma_get_config().grouped_tile == tile
+        run_group(As, Bs, Cs, dtype)
+    finally:
+        cosma.cosma_init()
+    check_group(dims, Cs, dtype)
