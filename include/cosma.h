@@ -340,6 +340,12 @@ int cosma_mlp_adam(int n, float* params, const float* grad, float* m, float* v, 
  * selector.  params == NULL removes the network. */
 int cosma_selector_set(const float* params, double log2_lo, double log2_hi);
 
+/* Restricts the installed network to the dtypes whose bit (1 << dtype) is set in
+ * dtype_mask -- the ones it was trained on; plans of other dtypes use the
+ * analytic selector.  cosma_selector_set resets the mask to every dtype.
+ * COSMA_ERR_UNSUPPORTED when no network is installed on the current device. */
+int cosma_selector_restrict(unsigned dtype_mask);
+
 /* Runs K-MLP-FWD on `count` shapes (HOST array mnk of 3*count int64) and
  * writes, per shape, the candidate with the smallest predicted time among
  * those that apply (best, HOST, count ints) and optionally all predictions

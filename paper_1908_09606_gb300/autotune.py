@@ -289,13 +289,21 @@ def tune_grouped(As, Bs, Cs, dtype, tiles=None, reps=3):
     return choice, times
 
 
-def install(params_path=None, log2_lo=8.0, log2_hi=16.0):
+def install(params_path=None, log2_lo=8.0, log2_hi=16.0, dtypes=None):
     """Installs trained selector weights saved by main() (an .npy vector); by default
-    the bf16 weights shipped with the package (trained on a GB300)."""
+    the bf16 weights shipped with the package (trained on a GB300), restricted to
+    bf16.  dtypes: the dtypes the weights were trained on (None with params_path:
+    all)."""
     p = np.load(params_path or SHIPPED_PARAMS).astype(np.float32)
     rc = cosma.cosma_selector_set(p, log2_lo, log2_hi)
     if rc != 0:
         raise cosma.CosmaError(rc, "cosma_selector_set")
+    if dtypes is None and params_path is None:
+        dtypes = ("bf16",)
+    if dtypes is not None:
+        rc = cosma.cosma_selector_restrict(dtypes)
+        if rc != 0:
+            raise cosma.CosmaError(rc, "cosma_selector_restrict")
 
 
 def main(argv=None):

@@ -98,6 +98,7 @@ SIGNATURES = [
     ("cosma_mlp_adam", _INT, [_INT, _VP, _VP, _VP, _VP, _INT, ctypes.c_float, ctypes.c_float,
                               ctypes.c_float, ctypes.c_float, _VP]),
     ("cosma_selector_set", _INT, [ctypes.POINTER(ctypes.c_float), _D, _D]),
+    ("cosma_selector_restrict", _INT, [ctypes.c_uint]),
     ("cosma_selector_predict", _INT, [_INT, ctypes.POINTER(ctypes.c_int64), _INT,
                                       ctypes.POINTER(_INT), ctypes.POINTER(ctypes.c_float)]),
     ("cosma_gemm_splitk_static", _INT, [_I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64,
@@ -238,6 +239,14 @@ def cosma_selector_set(params, log2_lo=0.0, log2_hi=64.0):
         return load().cosma_selector_set(None, log2_lo, log2_hi)
     arr = (ctypes.c_float * COSMA_MLP_PARAMS)(*[float(x) for x in params])
     return load().cosma_selector_set(arr, log2_lo, log2_hi)
+
+
+def cosma_selector_restrict(dtypes):
+    """Limit the installed network to the given dtype codes or names."""
+    mask = 0
+    for d in dtypes:
+        mask |= 1 << (DTYPES[d] if isinstance(d, str) else int(d))
+    return load().cosma_selector_restrict(mask)
 
 
 def cosma_selector_predict(shapes, dtype):

@@ -25,6 +25,7 @@ struct Selector {
   std::vector<float> host;
   float* dev = nullptr;  // device parameters
   double lo = 0.0, hi = 0.0;
+  unsigned dtype_mask = ~0u;  // dtypes the network was trained on
   std::map<std::tuple<int64_t, int64_t, int64_t, int>, int> cache;
   cudaStream_t stream = nullptr;
   float* dX = nullptr;
@@ -110,6 +111,7 @@ int learned_plan(int64_t m, int64_t n, int64_t k, int dtype, const DeviceInfo& d
   std::lock_guard<std::mutex> lock(g_sel_mu);
   Selector& s = g_sel[d];
   if (!s.ready) return COSMA_ERR_UNSUPPORTED;
+  if (dtype < 0 || dtype >= 32 || !((s.dtype_mask >> dtype) & 1u)) return COSMA_ERR_UNSUPPORTED;
   const double lm = log2((double)m), ln = log2((double)n), lk = log2((double)k);
   if (lm < s.lo || lm > s.hi || ln < s.lo || ln > s.hi || lk < s.lo || lk > s.hi)
     return COSMA_ERR_UNSUPPORTED;
@@ -203,7 +205,19 @@ int cosma_selector_set(const float* params, double log2_lo, double log2_hi) {
     return COSMA_ERR_CUDA;
   s.lo = log2_lo;
   s.hi = log2_hi;
+  s.dtype_mask = ~0u;
   s.ready = true;
+  return COSMA_OK;
+}
+
+int cosma_selector_restrict(unsigned dtype_mask) {
+  const int d = device_index();
+  if (d < 0) return COSMA_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_sel_mu);
+  Selector& s = g_sel[d];
+  if (!s.ready) return COSMA_ERR_UNSUPPORTED;
+  s.dtype_mask = dtype_mask;
+  s.cache.clear();
   return COSMA_OK;
 }
 

@@ -212,5 +212,12 @@ def test_shipped_selector_gain_on_held_out_shapes():
               f"median gain over analytic {np.median(gain):+.3f}")
         assert len(recs) >= 20
         assert np.median(rs) <= 0.05
+        # the shipped weights are bf16's: other dtypes keep the analytic plan
+        for dt in (cosma.COSMA_F32, cosma.COSMA_F64, cosma.COSMA_F64_EMU_BF16):
+            learned = cosma.cosma_plan_query(4096, 4096, 4096, dt, cosma.COSMA_SELECT_LEARNED)
+            analytic = cosma.cosma_plan_query(4096, 4096, 4096, dt, cosma.COSMA_SELECT_ANALYTIC)
+            assert (learned.tile_m, learned.tile_n, learned.pk, learned.order, learned.ctas) == \
+                (analytic.tile_m, analytic.tile_n, analytic.pk, analytic.order, analytic.ctas)
     finally:
         cosma.cosma_init()  # back to the default (analytic) configuration
+        cosma.cosma_selector_set(None)
