@@ -23,6 +23,10 @@ returns the counts.  Schedule builders below produce the paper's Listing 1
 (rank-1-update, C-stationary tiling), the X=S schedule of Sec. 5.2, and the
 replay of a GPU plan given as a list of work units (tile rectangle, k range).
 
+`optimal_io` finds the least I/O of any complete pebbling by exhaustive search
+(0-1 breadth-first search over (red set, blue outputs) states) for tiny
+products; it returns the optimal schedule as moves, which `simulate` replays.
+
 Pins (tests/test_oracle_pebble.py): Listing-1 I/O equals the Corollary's count
 sum_tiles (k (h + w) + h w) (= mnk(1/a + 1/b) + mn when tiles divide), the X=S
 schedule matches 2mnk/(sqrt(S+1)-1) + mn, every valid schedule is >= Theorem 1,
@@ -209,3 +213,80 @@ def tile_io(m, n, k, a, b):
             w = min((j1 + 1) * b, n) - j1 * b
             q += k * (h + w) + h * w
     return q
+
+
+def optimal_io(m, n, k, S, sliding=False):
+    """Least I/O over all complete pebblings of the (m x k)(k x n) MMM CDAG with S
+    red pebbles (exhaustive; tiny sizes only), and one optimal move sequence, or
+    (None, None) when no complete pebbling exists.  Moves that never help are
+    not generated (loading a red vertex, storing an input, storing a stored
+    vertex); all others are, with loads and stores costing 1 and computes and
+    frees 0."""
+    from collections import deque
+    verts = ([("a", i, t) for i in range(m) for t in range(k)] +
+             [("b", t, j) for t in range(k) for j in range(n)] +
+             [("c", i, j, t) for i in range(m) for j in range(n) for t in range(k)])
+    index = {v: x for x, v in enumerate(verts)}
+    nv = len(verts)
+    first_c = m * k + k * n
+    inputs = (1 << first_c) - 1
+    par = [0] * nv
+    pred = [0] * nv  # sliding: the red pebble a compute takes over
+    for v, x in index.items():
+        if v[0] == "c":
+            for p in parents(v):
+                par[x] |= 1 << index[p]
+            if v[3] > 0:
+                pred[x] = 1 << index[("c", v[1], v[2], v[3] - 1)]
+    goal = 0
+    for i in range(m):
+        for j in range(n):
+            goal |= 1 << index[("c", i, j, k - 1)]
+    start = (0, 0)  # (red mask, blue mask over non-input vertices)
+    dist = {start: 0}
+    back = {start: None}
+    dq = deque([start])
+    end = None
+    while dq:
+        st = dq.popleft()
+        d = dist[st]
+        red, blue = st
+        if blue & goal == goal:
+            end = st
+            break
+        nred = bin(red).count("1")
+
+        def relax(ns, cost, move):
+            nd = d + cost
+            if ns not in dist or dist[ns] > nd:
+                dist[ns] = nd
+                back[ns] = (st, move)
+                if cost:
+                    dq.append(ns)
+                else:
+                    dq.appendleft(ns)
+
+        for x in range(nv):
+            bit = 1 << x
+            if red & bit:
+                relax((red & ~bit, blue), 0, ("free", verts[x]))
+                if x >= first_c and not blue & bit:
+                    relax((red, blue | bit), 1, ("store", verts[x]))
+                continue
+            if (inputs | blue) & bit and nred < S:
+                relax((red | bit, blue), 1, ("load", verts[x]))
+            if x >= first_c and red & par[x] == par[x]:
+                if sliding and pred[x]:
+                    relax(((red & ~pred[x]) | bit, blue), 0, ("compute", verts[x]))
+                elif nred < S:
+                    relax((red | bit, blue), 0, ("compute", verts[x]))
+    if end is None:
+        return None, None
+    moves = []
+    st = end
+    while back[st] is not None:
+        st, mv = back[st]
+        moves.append(mv)
+    moves.reverse()
+    return dist[end], moves
+

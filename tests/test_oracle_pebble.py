@@ -85,3 +85,28 @@ def test_minimal_complete_pebbling_1x1x1():
              ("store", ("c", 0, 0, 0))]
     res = pebble.simulate(1, 1, 1, 3, moves)
     assert res.io == 3 and res.max_red == 3
+
+
+@pytest.mark.parametrize("sliding", [False, True])
+@pytest.mark.parametrize("S", [3, 4])
+def test_optimal_pebbling_2x2x2_by_exhaustive_search(sliding, S):
+    """Exact least I/O of the 2x2x2 MMM CDAG: the optimal schedule replays in the
+    simulator at that cost, lies above Theorem 1 and the trivial count (every
+    input loaded, every output stored: 12), and below every Listing-1 tiling that
+    fits in S."""
+    m = n = k = 2
+    io, moves = pebble.optimal_io(m, n, k, S, sliding)
+    if not sliding and S == 3:
+        # a compute of c(i,j,1) needs its three parents and itself red
+        assert io is None
+        return
+    res = pebble.simulate(m, n, k, S, moves, sliding)
+    assert res.io == io
+    assert io >= bounds.thm1(m, n, k, S) and io >= 12
+    tilings = [(a, b) for a in (1, 2) for b in (1, 2)
+               if pebble.listing1_working_set(a, b, sliding) <= S]
+    assert tilings
+    for a, b in tilings:
+        sched = pebble.listing1_schedule(m, n, k, a, b, sliding)
+        assert io <= pebble.simulate(m, n, k, S, sched, sliding).io
+
