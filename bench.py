@@ -79,7 +79,7 @@ def _alu_peak_tflops(dtype, sms):
 # dominant kernel, from one single-pass ncu capture of exactly this workload and
 # kernel version; absent entries are reported as null.
 DRAM_TRAFFIC = {
-    ("square", "bf16"): 10.38e9 + 1.07e9,     # tc_gemm_kernel<256,4,A K,B MN>, tensor-store C
+    ("square", "bf16"): 10.25e9 + 1.07e9,     # tc_gemm_kernel<256,4,A K,B MN>, tensor-store C
     ("flat", "bf16"): 4.30e9 + 17.15e9,       # same kernel, 16 GB of f32 C
     ("4096", "f32"): 0.328e9 + 0.109e9,       # simt_f32_kernel<128,4,256>, pk = 2, f32x2 FMAs
     ("4096", "f64"): 0.969e9 + 0.133e9,       # simt_gemm_kernel<double,64,64,8,4,4>
