@@ -85,4 +85,18 @@ COSMA_HD Unit unit_of_cta(const Sched& s, int cta, int64_t i) {
   return u;
 }
 
+// The k-block range of the i-th unit of CTA `cta` alone -- what the MMA issuer
+// needs -- without decoding the tile (whose 64-bit divisions would otherwise
+// sit between two units' MMAs).
+COSMA_HD void unit_k_range(const Sched& s, int cta, int64_t i, int64_t& kb0, int64_t& kb1) {
+  if (s.pk == 1) {
+    kb0 = 0;
+    kb1 = s.kbt;
+    return;
+  }
+  const int ks = s.order == 0 ? cta % s.pk : (int)((cta + i * (int64_t)s.ctas) % s.pk);
+  kb0 = split_start(s.kbt, s.pk, ks);
+  kb1 = split_start(s.kbt, s.pk, ks + 1);
+}
+
 }  // namespace cosma

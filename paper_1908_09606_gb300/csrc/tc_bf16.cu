@@ -246,8 +246,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       uint32_t ph = 0;
       uint32_t armed = 0;  // bit s: stage s armed at least once; last parity in armed_ph
       uint32_t armed_ph = 0;
+      // the next unit is decoded while this one's first stage is in flight
+      Unit nxt = nunits > 0 ? unit_of_cta(a.s, cta, 0) : Unit{};
       for (int64_t ui = 0; ui < nunits && !*abort_flag; ++ui) {
-        const Unit u = unit_of_cta(a.s, cta, ui);
+        const Unit u = nxt;
         bool ok = true;
         for (int64_t kb = u.kb0; kb < u.kb1; ++kb) {
           if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) { ok = false; break; }
@@ -276,8 +278,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           armed |= 1u << stage;
           armed_ph = (armed_ph & ~(1u << stage)) | (ph << stage);
           if (++stage == STAGES) { stage = 0; ph ^= 1; }
+          if (kb == u.kb0 && ui + 1 < nunits) nxt = unit_of_cta(a.s, cta, ui + 1);
         }
         if (!ok) break;
+        if (u.kb0 >= u.kb1 && ui + 1 < nunits) nxt = unit_of_cta(a.s, cta, ui + 1);
       }
       if (*abort_flag) {
         // Let every copy this thread started land before shared memory is released.
@@ -298,12 +302,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       uint32_t ph = 0, acc = 0;
       uint32_t aph[2] = {0, 0};
       for (int64_t ui = 0; ui < nunits && !*abort_flag; ++ui) {
-        const Unit u = unit_of_cta(a.s, cta, ui);
+        int64_t kb0, kb1;
+        unit_k_range(a.s, cta, ui, kb0, kb1);
         if (!tc::mbar_wait(&tempty[acc], aph[acc] ^ 1, w)) break;
         tc::tc_fence_after();
         const uint32_t d = tmem_base + acc * BN;
         bool ok = true;
-        for (int64_t kb = u.kb0; kb < u.kb1; ++kb) {
+        for (int64_t kb = kb0; kb < kb1; ++kb) {
           if (!tc::mbar_wait(&full[stage], ph, w)) { ok = false; break; }
           tc::tc_fence_after();
           const uint32_t sa = tc::smem_u32(smem + stage * L::STAGE_BYTES);
@@ -315,7 +320,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                                      : tc::smem_desc_sw128(sb + kk * 32);
             const uint64_t da = A_MN ? tc::smem_desc_mn_sw128(sa + kk * 16 * 128, 64 * BK * 2, 1024)
                                      : tc::smem_desc_sw128(sa + kk * 32);
-            tc::mma_bf16(d, da, db, idesc, (kb > u.kb0 || kk > 0) ? 1u : 0u);
+            tc::mma_bf16(d, da, db, idesc, (kb > kb0 || kk > 0) ? 1u : 0u);
           }
           tc::mma_commit(&empty[stage]);
           if (++stage == STAGES) { stage = 0; ph ^= 1; }
