@@ -680,6 +680,22 @@ def main():
 
         host_step()  # sizes the library's device staging once (outside the timed region)
         torch.cuda.synchronize()
+        # this box's page-locked copy rates (1 GiB each way), context for the e2e figure
+        nb = min(Ah.numel(), (1 << 30) // Ah.element_size())
+        src_h, dst_d = Ah.view(-1)[:nb], A.view(-1)[:nb].clone()
+        rates = {}
+        for name, fn in (("h2d", lambda: dst_d.copy_(src_h, non_blocking=True)),
+                         ("d2h", lambda: src_h.copy_(dst_d, non_blocking=True))):
+            fn()
+            torch.cuda.synchronize()
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record()
+            fn()
+            c1.record()
+            torch.cuda.synchronize()
+            rates[name] = nb * Ah.element_size() / (c0.elapsed_time(c1) * 1e-3) / 1e9
+        del dst_d
         e_steps = max(1, min(args.steps, 3))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -702,6 +718,7 @@ def main():
                "h2d_bytes_per_step": (m * k + k * n) * esz,
                "d2h_bytes_per_step": m * n * C.element_size(), "steps": e_steps,
                "api": "cosma_gemm_host (page-locked host A, B, C)",
+               "copy_gbs": {kk: round(v, 1) for kk, v in rates.items()},
                "max_abs_diff_vs_device_path": diff}
         del Ah, Bh, Ch
 
