@@ -152,3 +152,29 @@ def test_emu_long_k_float_float_level_sums(cand):
     assert cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream) == 0
     Ah, Bh = host_operands(m, n, k, DT, seed=8)
     assert og.normwise_rel_error(C.cpu().numpy(), og.gemm(Ah, Bh, "dot2")) <= 1e-12
+
+
+@pytest.mark.parametrize("slices,bits", [(4, 8), (5, 8), (7, 7), (8, 7), (7, 8), (6, 6)])
+def test_emu_slice_configurations(slices, bits):
+    """Other slice counts s and digit widths beta (cosma_config): the scaled
+    integers keep beta s - 1 bits and the triangle q + r <= s + 1 of slice pairs,
+    so the error stays below 2^-(beta s - 8) relative to the row and column norms
+    (s = 6, beta = 8: 2^-40, the 1e-12 bar); integer inputs stay bit-exact (only
+    their leading digit is nonzero).  Tiles of both kinds: a CTA pair (m >= 256) and
+    single-SM tiles (m < 256)."""
+    cosma = lib()
+    try:
+        assert cosma.cosma_init(emu_slices=slices, emu_slice_bits=bits) == 0
+        for m, n, k in [(300, 260, 1000), (130, 200, 700)]:
+            C = _run(m, n, k, seed=13)
+            A, B = host_operands(m, n, k, DT, seed=13)
+            ref = og.gemm(A, B, "dot2")
+            scale = np.sqrt((A ** 2).sum(1))[:, None] * np.sqrt((B ** 2).sum(0))[None, :]
+            tol = 2.0 ** -(bits * slices - 8) * scale
+            bad = np.abs(C - ref) > tol
+            assert not bad.any(), (slices, bits, m, float(np.max(np.abs(C - ref) / scale)))
+            Ci = _run(m, n, k, kind="integer", seed=5)
+            Ai, Bi = host_operands(m, n, k, DT, kind="integer", seed=5)
+            assert np.array_equal(Ci, og.gemm(Ai, Bi, "naive"))
+    finally:
+        cosma.cosma_init()
