@@ -22,10 +22,15 @@
  *     recorded in a per-device status word read by cosma_stream_status().
  *   - There is no CPU fallback: without a usable GPU every compute entry point
  *     returns COSMA_ERR_CUDA.
- *   - Calls on one stream are ordered; calls on different streams may run
- *     concurrently only if they do not share workspace (the library arena is
- *     per device; concurrent streams must each use cosma_set_workspace with a
- *     separate buffer from a separate host thread, or serialise).
+ *   - Calls on one stream are ordered.  Calls on different streams may run
+ *     concurrently: the library keeps one workspace per stream (up to 8 per
+ *     device; a ninth stream takes the least recently used one, after the
+ *     device has finished with it).  A workspace lent with cosma_set_workspace
+ *     serves every stream, so calls using it must not overlap; inside a stream
+ *     capture a stream without a large enough workspace of its own records the
+ *     largest existing one.  cosma_gemm_host, cosma_zgemm / cosma_cgemm and
+ *     cosma_gemm_grouped also keep per-device staging or tables: their calls
+ *     must not overlap across streams.
  */
 #ifndef COSMA_GB300_H
 #define COSMA_GB300_H

@@ -49,13 +49,25 @@ void prof_mark(cudaStream_t st, bool begin) {
 
 namespace {
 
+// One library-owned workspace per stream, so that calls on different streams
+// never share scratch memory; beyond kArenas streams the least recently used
+// arena is given to the new stream (cudaFree waits for the device first).
+constexpr int kArenas = 8;
+struct Arena {
+  cudaStream_t stream = nullptr;
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  unsigned long long last_use = 0;
+  bool used = false;
+};
+
 struct DeviceState {
   bool ready = false;
   DeviceInfo info;
   int* d_status = nullptr;     // device status word (0 = ok)
-  void* arena = nullptr;       // library-owned workspace
-  size_t arena_bytes = 0;
-  void* borrowed = nullptr;    // caller-lent workspace
+  Arena arenas[kArenas];       // library-owned workspaces, one per stream
+  unsigned long long uses = 0;
+  void* borrowed = nullptr;    // caller-lent workspace (all streams)
   size_t borrowed_bytes = 0;
 };
 
@@ -162,24 +174,56 @@ int workspace(DeviceState* s, long long bytes, cudaStream_t st, void** out, long
     *have = (long long)s->borrowed_bytes;
     return COSMA_OK;
   }
-  if ((long long)s->arena_bytes < bytes) {
+  // this stream's arena, else a free slot, else the least recently used one
+  Arena* a = nullptr;
+  for (Arena& x : s->arenas)
+    if (x.used && x.stream == st) a = &x;
+  if (capturing(st) && (!a || (long long)a->bytes < bytes)) {
+    // Capture cannot allocate: the usual pattern sizes an arena with an eager
+    // call on another stream first, so a capture takes the largest arena that
+    // is big enough (the graph then shares it with that stream).
+    Arena* big = nullptr;
+    for (Arena& x : s->arenas)
+      if (x.used && (long long)x.bytes >= bytes && (!big || x.bytes > big->bytes)) big = &x;
+    if (!big) return COSMA_ERR_NO_WORKSPACE;
+    big->last_use = ++s->uses;
+    *out = big->ptr;
+    *have = (long long)big->bytes;
+    return COSMA_OK;
+  }
+  if (!a) {
+    for (Arena& x : s->arenas)
+      if (!x.used) { a = &x; break; }
+    if (!a) {
+      if (capturing(st)) return COSMA_ERR_NO_WORKSPACE;
+      a = &s->arenas[0];
+      for (Arena& x : s->arenas)
+        if (x.last_use < a->last_use) a = &x;
+      if (a->ptr) cudaFree(a->ptr);  // waits for the device
+      *a = Arena{};
+    }
+    a->used = true;
+    a->stream = st;
+  }
+  a->last_use = ++s->uses;
+  if ((long long)a->bytes < bytes) {
     if (capturing(st)) return COSMA_ERR_NO_WORKSPACE;
-    if (s->arena) {
+    if (a->ptr) {
       if (cudaStreamSynchronize(st) != cudaSuccess) return COSMA_ERR_CUDA;
-      cudaFree(s->arena);
-      s->arena = nullptr;
-      s->arena_bytes = 0;
+      cudaFree(a->ptr);
+      a->ptr = nullptr;
+      a->bytes = 0;
     }
     size_t want = (size_t)bytes;
     want = (want + (1u << 20) - 1) & ~((size_t)(1u << 20) - 1);
-    if (cudaMalloc(&s->arena, want) != cudaSuccess) {
+    if (cudaMalloc(&a->ptr, want) != cudaSuccess) {
       cudaGetLastError();
       return COSMA_ERR_NO_WORKSPACE;
     }
-    s->arena_bytes = want;
+    a->bytes = want;
   }
-  *out = s->arena;
-  *have = (long long)s->arena_bytes;
+  *out = a->ptr;
+  *have = (long long)a->bytes;
   return COSMA_OK;
 }
 
@@ -419,7 +463,8 @@ void cosma_finalize(void) {
   if (!s.ready) return;
   cudaDeviceSynchronize();
   grouped_release(d);
-  if (s.arena) cudaFree(s.arena);
+  for (Arena& x : s.arenas)
+    if (x.ptr) cudaFree(x.ptr);
   if (s.d_status) cudaFree(s.d_status);
   s = DeviceState{};
 }
