@@ -28,7 +28,8 @@
  *     device has finished with it).  A workspace lent with cosma_set_workspace
  *     serves every stream, so calls using it must not overlap; inside a stream
  *     capture a stream without a large enough workspace of its own records the
- *     largest existing one.  cosma_gemm_host, cosma_zgemm / cosma_cgemm and
+ *     most recently used one that is large enough (size it with an eager call
+ *     just before capturing).  cosma_gemm_host, cosma_zgemm / cosma_cgemm and
  *     cosma_gemm_grouped also keep per-device staging or tables: their calls
  *     must not overlap across streams.
  */

@@ -180,11 +180,12 @@ int workspace(DeviceState* s, long long bytes, cudaStream_t st, void** out, long
     if (x.used && x.stream == st) a = &x;
   if (capturing(st) && (!a || (long long)a->bytes < bytes)) {
     // Capture cannot allocate: the usual pattern sizes an arena with an eager
-    // call on another stream first, so a capture takes the largest arena that
-    // is big enough (the graph then shares it with that stream).
+    // call on another stream just before, so a capture takes the most recently
+    // used arena that is big enough -- the one that call used, whose pointer
+    // also keys the grouped tables (the graph then shares it with that stream).
     Arena* big = nullptr;
     for (Arena& x : s->arenas)
-      if (x.used && (long long)x.bytes >= bytes && (!big || x.bytes > big->bytes)) big = &x;
+      if (x.used && (long long)x.bytes >= bytes && (!big || x.last_use > big->last_use)) big = &x;
     if (!big) return COSMA_ERR_NO_WORKSPACE;
     big->last_use = ++s->uses;
     *out = big->ptr;
