@@ -165,6 +165,25 @@ def test_plan_query_host_only(lib):
                 or p.ctas < sms
 
 
+def test_plan_query_tf32_and_fp32_tiles_host_only(lib):
+    # three-TF32 plans: the kernel's one 128 x 128 tile, 32-deep k blocks; the FMA
+    # FP32 family takes its 128 x 256 tile where many tiles fill the waves and the
+    # 128 x 128 one for small products
+    for shape in [(16384, 16384, 16384), (4096, 4096, 4096), (300, 260, 515), (7, 129, 1000)]:
+        p = lib.cosma_plan_query(*shape, lib.COSMA_F32_EMU_TF32)
+        assert lib.KERNELS[p.kernel] == "tf32x3"
+        assert (p.tile_m, p.tile_n, p.k_block) == (128, 128, 32)
+        assert 1 <= p.ctas <= p.sms and 1 <= p.pk
+    wide = lib.cosma_plan_query(16384, 16384, 16384, lib.COSMA_F32)
+    assert (wide.tile_m, wide.tile_n) == (128, 256)
+    small = lib.cosma_plan_query(512, 512, 512, lib.COSMA_F32)
+    assert (small.tile_m, small.tile_n) == (128, 128)
+    # the learned selector's candidate space does not include this dtype
+    with pytest.raises(lib.CosmaError) as e:
+        lib.cosma_plan_candidate(4096, 4096, 4096, lib.COSMA_F32_EMU_TF32, 0)
+    assert e.value.status == lib.COSMA_ERR_INVALID_ARG
+
+
 def test_plan_io_accounting_matches_units(lib):
     m, n, k = 512, 512, 512
     p = lib.cosma_plan_query(m, n, k, lib.COSMA_F64)
