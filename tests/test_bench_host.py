@@ -1,10 +1,11 @@
-"""Host-side pieces of bench.py, on the CPU: the step statistics and the
-Listing-1 host timing (its product equals the naive oracle's)."""
+"""Host-side pieces of bench.py, on the CPU: the step statistics, the Listing-1
+host timing, the I/O report's Theorem-1 figures and the reference arm's line."""
 import math
 import os
 import sys
 
 import numpy as np
+import pytest
 
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
@@ -36,3 +37,49 @@ def test_host_info_fields():
     import bench
     h = bench.host_info()
     assert h["nproc"] == os.cpu_count() and h["machine"]
+
+
+def test_io_report_bounds_follow_theorem1():
+    """The bench's I/O block: Theorem 1 at the chip's fast memory (L2 + every SM's
+    shared and tensor memory, in input words) and the compulsory bytes, for the
+    plain and the emulated dtypes, against the oracle's closed form."""
+    import types
+    import bench
+    from oracle import bounds
+    m = n = k = 4096
+    plan = types.SimpleNamespace(fast_words=123904.0, io_words=1.0e9,
+                                 bound_words=bounds.thm1(m, n, k, 123904.0))
+    l2, sms, smem = 126 * 2 ** 20, 152, 233472
+    for dt, w_in, w_out, passes in [("bf16", 2, 4, 1), ("f64", 8, 8, 1),
+                                    ("f64_emu_bf16", 2, 8, 21), ("f32_emu_tf32", 4, 4, 2)]:
+        out = bench.io_report(m, n, k, dt, plan, 5e9, l2, sms, smem)
+        s_chip = (l2 + sms * (smem + 262144)) / w_in
+        assert out["S_chip_words"] == s_chip
+        thm1 = passes * 2.0 * m * n * k / math.sqrt(s_chip) + m * n
+        assert out["theorem1_bytes_at_S_chip"] == pytest.approx(thm1 * w_in)
+        assert out["operand_passes_per_call"] == passes
+        assert out["ratio_dram_vs_theorem1_chip"] == pytest.approx(5e9 / (thm1 * w_in))
+        slices = 6 if dt == "f64_emu_bf16" else (2 if dt == "f32_emu_tf32" else 1)
+        assert out["compulsory_bytes"] == w_in * slices * (m * k + k * n) + w_out * m * n
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """`bench.py --impl reference`: one JSON line with the oracle's own timing as
+    value, cpu_baseline and e2e (no host-device bytes); non-zero ranks print
+    nothing."""
+    import json
+    import types
+    import bench
+    monkeypatch.setattr(bench, "oracle_sample", lambda m, n, k, t, **kw: (2.0e9, 0.5, 64))
+    args = types.SimpleNamespace(workload="512", dtype="f64", steps=2, warmup=1, gpus=1)
+    assert bench.run_reference(args) == 0
+    line = json.loads(capsys.readouterr().out.strip())
+    assert line["impl"] == "reference" and line["unit"] == "TFLOP/s"
+    assert line["value"] == pytest.approx(2.0e-3)
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["higher_is_better"] is True and line["metric"] == bench.METRIC
+    monkeypatch.setenv("RANK", "1")
+    assert bench.run_reference(args) == 0
+    assert capsys.readouterr().out == ""
