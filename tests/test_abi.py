@@ -277,3 +277,32 @@ def test_environment_sets_config_defaults(lib):
     out = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True,
                          text=True, check=True).stdout
     assert json.loads(out) == [0.03, 0, 0, 0, 0, 0]
+
+
+def test_planner_units_partition_random_shapes(lib):
+    """Property: for any shape and dtype the planner's own plan has units that
+    partition the iteration space -- tiles cover C once, and each tile's k
+    ranges partition [0, k) -- and fits the grid it claims."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    @hyp.settings(max_examples=60, deadline=None, derandomize=True)
+    @hyp.given(m=st.integers(1, 3000), n=st.integers(1, 3000), k=st.integers(1, 40000),
+               dt=st.sampled_from([0, 1, 2, 3, 5]))
+    def check(m, n, k, dt):
+        p = lib.cosma_plan_query(m, n, k, dt)
+        assert 1 <= p.ctas <= p.sms and p.pk >= 1
+        units = lib.cosma_plan_units(m, n, k, p)
+        tiles = {}
+        for (r0, r1, c0, c1, k0, k1) in units:
+            assert 0 <= r0 < r1 <= m and 0 <= c0 < c1 <= n and 0 <= k0 < k1 <= k
+            assert r0 % p.tile_m == 0 and c0 % p.tile_n == 0
+            assert r1 == min(r0 + p.tile_m, m) and c1 == min(c0 + p.tile_n, n)
+            tiles.setdefault((r0, c0), []).append((k0, k1))
+        assert len(tiles) == -(-m // p.tile_m) * -(-n // p.tile_n)
+        for ranges in tiles.values():
+            ranges.sort()
+            assert ranges[0][0] == 0 and ranges[-1][1] == k and len(ranges) == p.pk
+            assert all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
+
+    check()
