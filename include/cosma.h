@@ -31,7 +31,11 @@
  *     most recently used one that is large enough (size it with an eager call
  *     just before capturing).  cosma_gemm_host, cosma_zgemm / cosma_cgemm and
  *     cosma_gemm_grouped also keep per-device staging or tables: their calls
- *     must not overlap across streams.
+ *     must not overlap across streams.  A workspace, staging buffer or grouped
+ *     table that a capture recorded is never freed or overwritten before
+ *     cosma_finalize (a later call that needs more takes a new buffer), so a
+ *     graph stays valid until then; replays share those buffers with the
+ *     calls that use them and must not overlap with them.
  */
 #ifndef COSMA_GB300_H
 #define COSMA_GB300_H

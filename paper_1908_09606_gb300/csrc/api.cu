@@ -52,6 +52,9 @@ namespace {
 // One library-owned workspace per stream, so that calls on different streams
 // never share scratch memory; beyond kArenas streams the least recently used
 // arena is given to the new stream (cudaFree waits for the device first).
+// A buffer that a stream capture recorded is never freed before
+// cosma_finalize: the graph may be replayed after the arena has grown or
+// changed hands, so such a buffer is retired instead.
 constexpr int kArenas = 8;
 struct Arena {
   cudaStream_t stream = nullptr;
@@ -59,6 +62,7 @@ struct Arena {
   size_t bytes = 0;
   unsigned long long last_use = 0;
   bool used = false;
+  bool captured = false;       // ptr is recorded in a captured graph
 };
 
 struct DeviceState {
@@ -69,6 +73,7 @@ struct DeviceState {
   unsigned long long uses = 0;
   void* borrowed = nullptr;    // caller-lent workspace (all streams)
   size_t borrowed_bytes = 0;
+  std::vector<void*> retired;  // captured buffers an arena gave up; freed at finalize
 };
 
 constexpr int kMaxDevices = 16;
@@ -162,6 +167,18 @@ bool capturing(cudaStream_t st) {
   return cs != cudaStreamCaptureStatusNone;
 }
 
+// Gives up an arena's buffer: freed (cudaFree waits for the device), or kept
+// until cosma_finalize when a captured graph holds its address.
+void drop_buffer(DeviceState* s, Arena* a) {
+  if (a->ptr) {
+    if (a->captured) s->retired.push_back(a->ptr);
+    else cudaFree(a->ptr);
+  }
+  a->ptr = nullptr;
+  a->bytes = 0;
+  a->captured = false;
+}
+
 // Workspace of at least `bytes`: the caller's lent buffer, else the arena
 // (grown outside capture only).
 int workspace(DeviceState* s, long long bytes, cudaStream_t st, void** out, long long* have) {
@@ -178,7 +195,8 @@ int workspace(DeviceState* s, long long bytes, cudaStream_t st, void** out, long
   Arena* a = nullptr;
   for (Arena& x : s->arenas)
     if (x.used && x.stream == st) a = &x;
-  if (capturing(st) && (!a || (long long)a->bytes < bytes)) {
+  const bool cap = capturing(st);
+  if (cap && (!a || (long long)a->bytes < bytes)) {
     // Capture cannot allocate: the usual pattern sizes an arena with an eager
     // call on another stream just before, so a capture takes the most recently
     // used arena that is big enough -- the one that call used, whose pointer
@@ -188,6 +206,7 @@ int workspace(DeviceState* s, long long bytes, cudaStream_t st, void** out, long
       if (x.used && (long long)x.bytes >= bytes && (!big || x.last_use > big->last_use)) big = &x;
     if (!big) return COSMA_ERR_NO_WORKSPACE;
     big->last_use = ++s->uses;
+    big->captured = true;
     *out = big->ptr;
     *have = (long long)big->bytes;
     return COSMA_OK;
@@ -196,24 +215,20 @@ int workspace(DeviceState* s, long long bytes, cudaStream_t st, void** out, long
     for (Arena& x : s->arenas)
       if (!x.used) { a = &x; break; }
     if (!a) {
-      if (capturing(st)) return COSMA_ERR_NO_WORKSPACE;
       a = &s->arenas[0];
       for (Arena& x : s->arenas)
         if (x.last_use < a->last_use) a = &x;
-      if (a->ptr) cudaFree(a->ptr);  // waits for the device
+      drop_buffer(s, a);
       *a = Arena{};
     }
     a->used = true;
     a->stream = st;
   }
   a->last_use = ++s->uses;
-  if ((long long)a->bytes < bytes) {
-    if (capturing(st)) return COSMA_ERR_NO_WORKSPACE;
+  if ((long long)a->bytes < bytes) {  // not capturing here
     if (a->ptr) {
       if (cudaStreamSynchronize(st) != cudaSuccess) return COSMA_ERR_CUDA;
-      cudaFree(a->ptr);
-      a->ptr = nullptr;
-      a->bytes = 0;
+      drop_buffer(s, a);
     }
     size_t want = (size_t)bytes;
     want = (want + (1u << 20) - 1) & ~((size_t)(1u << 20) - 1);
@@ -223,6 +238,7 @@ int workspace(DeviceState* s, long long bytes, cudaStream_t st, void** out, long
     }
     a->bytes = want;
   }
+  if (cap) a->captured = true;
   *out = a->ptr;
   *have = (long long)a->bytes;
   return COSMA_OK;
@@ -466,6 +482,7 @@ void cosma_finalize(void) {
   grouped_release(d);
   for (Arena& x : s.arenas)
     if (x.ptr) cudaFree(x.ptr);
+  for (void* p : s.retired) cudaFree(p);
   if (s.d_status) cudaFree(s.d_status);
   s = DeviceState{};
 }

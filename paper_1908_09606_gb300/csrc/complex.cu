@@ -10,6 +10,7 @@
 // the complex P?GEMM variants as well.
 #include <cuda_runtime.h>
 #include <mutex>
+#include <vector>
 
 #include "internal.h"
 
@@ -22,6 +23,8 @@ constexpr int kMaxDevices = 16;
 struct ComplexState {
   void* stage = nullptr;
   size_t stage_bytes = 0;
+  bool captured = false;       // stage is recorded in a captured graph
+  std::vector<void*> retired;  // captured stages given up on growth; freed at finalize
 };
 
 std::mutex g_cplx_mu;
@@ -100,6 +103,7 @@ void complex_release(int dev) {
   std::lock_guard<std::mutex> lock(g_cplx_mu);
   if (dev < 0 || dev >= kMaxDevices) return;
   if (g_cplx[dev].stage) cudaFree(g_cplx[dev].stage);
+  for (void* p : g_cplx[dev].retired) cudaFree(p);
   g_cplx[dev] = ComplexState{};
 }
 
@@ -142,13 +146,16 @@ int complex_gemm(int op_a, int op_b, int64_t m, int64_t n, int64_t k, const R* a
   const size_t b_b = (size_t)rup(b_rows * b_cols * w * (kk > 0), 256);
   const size_t t_b = (size_t)rup(m * n * w, 256);
   const size_t need = 2 * a_b + 2 * b_b + 2 * t_b;
+  const bool cap = capturing(st);
   if (cs.stage_bytes < need) {
-    if (capturing(st)) return COSMA_ERR_NO_WORKSPACE;
+    if (cap) return COSMA_ERR_NO_WORKSPACE;
     if (cs.stage) {
       if (cudaStreamSynchronize(st) != cudaSuccess) return COSMA_ERR_CUDA;
-      cudaFree(cs.stage);
+      if (cs.captured) cs.retired.push_back(cs.stage);  // a graph may still read it
+      else cudaFree(cs.stage);
       cs.stage = nullptr;
       cs.stage_bytes = 0;
+      cs.captured = false;
     }
     const size_t want = (need + (1u << 20) - 1) & ~(size_t)((1u << 20) - 1);
     if (cudaMalloc(&cs.stage, want) != cudaSuccess) {
@@ -157,6 +164,7 @@ int complex_gemm(int op_a, int op_b, int64_t m, int64_t n, int64_t k, const R* a
     }
     cs.stage_bytes = want;
   }
+  if (cap) cs.captured = true;
   uint8_t* wp = static_cast<uint8_t*>(cs.stage);
   R* Ar = reinterpret_cast<R*>(wp);
   R* Ai = reinterpret_cast<R*>(wp + a_b);

@@ -14,8 +14,9 @@
 // The table is cached (by the problems' contents, the tile and the workspace
 // address): after one eager call the same call can be captured in a CUDA
 // graph, because a cache hit launches kernels only (no allocation, no host
-// copy).  Up to kCacheSlots groups stay cached per device until
-// cosma_finalize; a captured graph stays valid while its group is cached.
+// copy).  Up to kCacheSlots groups stay cached per device; a table that a
+// capture recorded is never overwritten: when its slot is reused the table
+// moves to a retired list, freed at cosma_finalize, so the graph stays valid.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -79,11 +80,13 @@ struct Table {
   int64_t ttiles = 0;
   int64_t atiles = 0;
   int64_t nunits = 0;
+  bool captured = false;  // recorded in a captured graph
 };
 
 std::mutex g_tab_mu;
 Table g_cache[16][kCacheSlots];
 int g_next[16];
+std::vector<void*> g_retired[16];  // tables of captured graphs, freed at finalize
 
 inline int64_t rup(int64_t x, int64_t r) { return (x + r - 1) / r * r; }
 
@@ -510,7 +513,7 @@ long long ws_need(int count, const cosma_problem* pr, int dtype) {
 
 // Builds (or finds) the device table of this group.
 int get_table(int dev, int count, const cosma_problem* pr, int dtype, int tile, int sms, void* ws,
-              bool capturing, Table** out) {
+              bool capturing, cudaStream_t st, Table** out) {
   unsigned long long key = mix(0, (unsigned long long)count);
   key = mix(key, (unsigned long long)dtype);
   key = mix(key, (unsigned long long)tile);
@@ -530,6 +533,7 @@ int get_table(int dev, int count, const cosma_problem* pr, int dtype, int tile, 
   for (int s = 0; s < kCacheSlots; ++s) {
     Table& t = g_cache[dev][s];
     if (t.dev && t.key == key && t.count == count && t.dtype == dtype && t.tile_n == tile) {
+      if (capturing) t.captured = true;
       *out = &t;
       return COSMA_OK;
     }
@@ -650,6 +654,10 @@ int get_table(int dev, int count, const cosma_problem* pr, int dtype, int tile, 
 
   Table& t = g_cache[dev][g_next[dev]];
   g_next[dev] = (g_next[dev] + 1) % kCacheSlots;
+  if (t.captured) {  // a graph may still read it: keep it, take a fresh buffer
+    g_retired[dev].push_back(t.dev);
+    t = Table{};
+  }
   if (t.dev && t.bytes < total) {
     cudaFree(t.dev);  // synchronising free of an older group's table
     t.dev = nullptr;
@@ -662,8 +670,12 @@ int get_table(int dev, int count, const cosma_problem* pr, int dtype, int tile, 
     }
     t.bytes = total;
   }
-  if (cudaMemcpy(t.dev, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+  // Ordered on the call's stream, after earlier launches that may still read
+  // this slot's previous table (the pageable source is staged before return).
+  if (cudaMemcpyAsync(t.dev, host.data(), total, cudaMemcpyHostToDevice, st) != cudaSuccess) {
     cudaGetLastError();
+    cudaFree(t.dev);
+    t = Table{};
     return COSMA_ERR_CUDA;
   }
   uint8_t* d = static_cast<uint8_t*>(t.dev);
@@ -721,7 +733,7 @@ int grouped_gemm(int count, const cosma_problem* problems, int dtype, const Devi
   {
     std::lock_guard<std::mutex> lock(g_tab_mu);
     rc = get_table(dev.device, count, problems, dtype, tile, dev.sms > 0 ? dev.sms : 148, ws,
-                   cs != cudaStreamCaptureStatusNone, &t);
+                   cs != cudaStreamCaptureStatusNone, st, &t);
   }
   if (rc != COSMA_OK) return rc;
   if (t->nunits == 0) return COSMA_OK;
@@ -760,6 +772,8 @@ void grouped_release(int dev) {
     if (g_cache[dev][s].dev) cudaFree(g_cache[dev][s].dev);
     g_cache[dev][s] = Table{};
   }
+  for (void* p : g_retired[dev]) cudaFree(p);
+  g_retired[dev].clear();
   g_next[dev] = 0;
 }
 

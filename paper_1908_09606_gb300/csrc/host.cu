@@ -15,6 +15,7 @@
 // stream-ordered and may be captured into a CUDA graph.
 #include <cuda_runtime.h>
 #include <mutex>
+#include <vector>
 
 #include "internal.h"
 
@@ -33,6 +34,8 @@ struct HostState {
   cudaEvent_t ev[kEvents] = {};
   void* stage = nullptr;
   size_t stage_bytes = 0;
+  bool captured = false;       // stage is recorded in a captured graph
+  std::vector<void*> retired;  // captured stages given up on growth; freed at finalize
 };
 
 std::mutex g_host_mu;
@@ -68,13 +71,16 @@ int init_state(HostState& h) {
 }
 
 int staging(HostState& h, size_t bytes, cudaStream_t st, uint8_t** out) {
+  const bool cap = capturing(st);
   if (h.stage_bytes < bytes) {
-    if (capturing(st)) return COSMA_ERR_NO_WORKSPACE;
+    if (cap) return COSMA_ERR_NO_WORKSPACE;
     if (h.stage) {
       if (cudaStreamSynchronize(st) != cudaSuccess) return COSMA_ERR_CUDA;
-      cudaFree(h.stage);
+      if (h.captured) h.retired.push_back(h.stage);  // a graph may still read it
+      else cudaFree(h.stage);
       h.stage = nullptr;
       h.stage_bytes = 0;
+      h.captured = false;
     }
     const size_t want = (bytes + (1u << 20) - 1) & ~(size_t)((1u << 20) - 1);
     if (cudaMalloc(&h.stage, want) != cudaSuccess) {
@@ -83,6 +89,7 @@ int staging(HostState& h, size_t bytes, cudaStream_t st, uint8_t** out) {
     }
     h.stage_bytes = want;
   }
+  if (cap) h.captured = true;
   *out = static_cast<uint8_t*>(h.stage);
   return COSMA_OK;
 }
@@ -113,6 +120,7 @@ void host_release(int dev) {
   HostState& h = g_host[dev];
   if (!h.ready) return;
   if (h.stage) cudaFree(h.stage);
+  for (void* p : h.retired) cudaFree(p);
   for (int i = 0; i < kEvents; ++i)
     if (h.ev[i]) cudaEventDestroy(h.ev[i]);
   if (h.in) cudaStreamDestroy(h.in);

@@ -35,3 +35,35 @@ def test_gemm_graph_replay_equals_eager(dtype, shape):
     torch.cuda.synchronize()
     assert cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream) == 0
     assert torch.equal(Cg, C)
+
+
+@pytest.mark.parametrize("dtype", ["f32_emu_tf32", "f64_emu_bf16"])
+def test_graph_stays_valid_after_the_workspace_grows(dtype):
+    """A later call that needs a larger workspace on the stream whose arena the
+    capture recorded takes a new buffer; the recorded one is kept until
+    cosma_finalize, so a replay still equals the eager call bit for bit."""
+    import torch
+    cosma = lib()
+    m, n, k = 300, 260, 700
+    A, B = device_operands(m, n, k, dtype, "uniform", 1)
+    C, _ = out_tensor(m, n, dtype)
+    side = torch.cuda.Stream()   # a new stream: a new, small arena
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        cosma.gemm(A, B, C, dtype)
+    torch.cuda.synchronize()
+    Cg, _ = out_tensor(m, n, dtype)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        cosma.gemm(A, B, Cg, dtype)
+    # a product whose workspace is many times larger grows that arena
+    A2, B2 = device_operands(2048, 2048, 4096, dtype, "uniform", 3)
+    C2, _ = out_tensor(2048, 2048, dtype)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        cosma.gemm(A2, B2, C2, dtype)
+    torch.cuda.synchronize()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream) == 0
+    assert torch.equal(Cg, C)

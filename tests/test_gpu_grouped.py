@@ -189,3 +189,41 @@ def test_grouped_autotuner_picks_a_tile_and_results_hold(dtype, tiles):
     finally:
         cosma.cosma_init()
     check_group(dims, Cs, dtype)
+
+
+def test_grouped_graph_stays_valid_after_the_table_cache_turns_over():
+    """Nine other groups pass through the eight-slot table cache after a group
+    was captured; its table is retired, not overwritten, so the replay still
+    equals the eager call."""
+    import torch
+    cosma = lib()
+    dtype = "f32"
+    dims = problem_dims(16, seed=4)
+    As, Bs, Cs = make_group(dims, dtype)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        cosma.gemm_grouped(As, Bs, Cs, dtype)      # eager: builds and caches the table
+    torch.cuda.synchronize()
+    eager = [c.clone() for c in Cs]
+    for c in Cs:
+        c.fill_(float("nan"))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        cosma.gemm_grouped(As, Bs, Cs, dtype)
+    others = []
+    for j in range(9):
+        d = np.minimum(problem_dims(3, seed=20 + j), 1024)
+        Ao, Bo, Co = make_group(d, dtype)
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            cosma.gemm_grouped(Ao, Bo, Co, dtype)
+        others.append((d, Ao, Bo, Co))
+    torch.cuda.synchronize()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream) == 0
+    for c, e in zip(Cs, eager):
+        assert torch.equal(c, e)
+    d, _, _, Co = others[-1]
+    check_group(d, Co, dtype, per_problem=3)
