@@ -56,8 +56,9 @@ extern "C" {
  * F32_EMU_TF32: A, B, C are fp32; each operand is split into TF32 hi and lo
  * parts and C = A_hi B_hi + A_hi B_lo + A_lo B_hi is accumulated in fp32 on the
  * tensor cores, 64-deep k segments summed in fp32 round to nearest (elementwise
- * error within (1.002 gamma_3k(2^-23) + 3.01 2^-22) |A||B|); k <= 2^21 (else
- * COSMA_ERR_UNSUPPORTED); Inf / NaN inputs give non-finite entries where an
+ * error within (1.002 gamma_3k(2^-23) + 3.01 2^-22) |A||B|); k <= 2^21 - 32
+ * (65535 k blocks of 32; else COSMA_ERR_UNSUPPORTED before any launch or
+ * allocation); Inf / NaN inputs give non-finite entries where an
  * IEEE product does, possibly NaN for Inf. */
 typedef enum {
   COSMA_F64 = 0,

@@ -67,6 +67,18 @@ def test_rejects_bad_arguments_without_launch(lib):
     assert lib.cosma_gemm_grouped([], lib.COSMA_F64) == lib.COSMA_ERR_UNSUPPORTED
 
 
+def test_tf32x3_k_limit_is_refused_before_any_launch(lib):
+    # 65535 k blocks of 32 is the longest k; one more element is unsupported,
+    # decided before the pointers are even looked at
+    kmax = 65535 * 32
+    dt = lib.COSMA_F32_EMU_TF32
+    assert lib.cosma_gemm(4, 4, kmax + 1, 16, kmax + 1, 16, 4, 16, 4, dt) == \
+        lib.COSMA_ERR_UNSUPPORTED
+    assert lib.cosma_gemm(4, 4, kmax, 16, kmax, 16, 4, 16, 4, dt) == lib.COSMA_ERR_INVALID_ARG
+    assert lib.cosma_gemm(4, 4, kmax + 1, 16, kmax + 1, 16, 4, 16, 4, lib.COSMA_F32) == \
+        lib.COSMA_ERR_INVALID_ARG
+
+
 def test_host_entry_rejects_bad_arguments(lib):
     bad = lib.COSMA_ERR_INVALID_ARG
     assert lib.cosma_gemm_host(-1, 4, 4, 0, 4, 0, 4, 0, 4, lib.COSMA_F64) == bad
