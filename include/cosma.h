@@ -51,7 +51,9 @@ extern "C" {
 
 /* Element types of a call.  BF16: A and B are bf16, C is fp32.
  * F64_EMU_BF16: A, B, C are fp64; the product is formed from bf16 slices on
- * the tensor cores (Ozaki-style splitting) and recombined in high precision.
+ * the tensor cores (Ozaki-style splitting) and recombined in high precision;
+ * k <= 2^21 - 2048 (1023 slice panels of 2048; else COSMA_ERR_UNSUPPORTED
+ * before any launch or allocation).
  * F64_EMU_INT8 is reserved (returns COSMA_ERR_UNSUPPORTED).
  * F32_EMU_TF32: A, B, C are fp32; each operand is split into TF32 hi and lo
  * parts and C = A_hi B_hi + A_hi B_lo + A_lo B_hi is accumulated in fp32 on the

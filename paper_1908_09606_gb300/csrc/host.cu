@@ -144,6 +144,8 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
   if (k > 0 && (!A || !B || !is_host_ptr(A) || !is_host_ptr(B))) return COSMA_ERR_INVALID_ARG;
   if (dtype == COSMA_F64_EMU_INT8) return COSMA_ERR_UNSUPPORTED;
   if (dtype == COSMA_F32_EMU_TF32 && k > 65535LL * 32) return COSMA_ERR_UNSUPPORTED;  // k blocks
+  if (dtype == COSMA_F64_EMU_BF16 && (emu_padded_k(k) + 31) / 32 > 65535)
+    return COSMA_ERR_UNSUPPORTED;
 
   LibContext ctx;
   int rc = lib_context(&ctx);

@@ -67,7 +67,7 @@ def test_rejects_bad_arguments_without_launch(lib):
     assert lib.cosma_gemm_grouped([], lib.COSMA_F64) == lib.COSMA_ERR_UNSUPPORTED
 
 
-def test_tf32x3_k_limit_is_refused_before_any_launch(lib):
+def test_k_limits_are_refused_before_any_launch(lib):
     # 65535 k blocks of 32 is the longest k; one more element is unsupported,
     # decided before the pointers are even looked at
     kmax = 65535 * 32
@@ -77,6 +77,12 @@ def test_tf32x3_k_limit_is_refused_before_any_launch(lib):
     assert lib.cosma_gemm(4, 4, kmax, 16, kmax, 16, 4, 16, 4, dt) == lib.COSMA_ERR_INVALID_ARG
     assert lib.cosma_gemm(4, 4, kmax + 1, 16, kmax + 1, 16, 4, 16, 4, lib.COSMA_F32) == \
         lib.COSMA_ERR_INVALID_ARG
+    # the emulated path: 1023 slice panels of 2048
+    emax = 1023 * 2048
+    dt = lib.COSMA_F64_EMU_BF16
+    assert lib.cosma_gemm(4, 4, emax + 1, 16, emax + 1, 16, 4, 16, 4, dt) == \
+        lib.COSMA_ERR_UNSUPPORTED
+    assert lib.cosma_gemm(4, 4, emax, 16, emax, 16, 4, 16, 4, dt) == lib.COSMA_ERR_INVALID_ARG
 
 
 def test_host_entry_rejects_bad_arguments(lib):
