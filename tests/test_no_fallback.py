@@ -88,3 +88,49 @@ def test_shared_input_generators_import_neither_side():
                 text = open(os.path.join(dirpath, f), errors="replace").read()
                 for inc in re.findall(r'#\s*include\s*[<"]([^>"]+)[>"]', text):
                     assert "oracle" not in inc and "cosma.h" not in inc, (f, inc)
+
+
+def test_bench_reaches_the_oracle_only_in_its_cpu_legs():
+    """bench.py imports the oracle only inside the CPU-timing helpers, the
+    reference arm, or a branch guarded by the --no-cpu switch (the CPU-baseline
+    leg), never on the timed GPU path."""
+    path = os.path.join(ROOT, "bench.py")
+    src = open(path).read()
+    tree = ast.parse(src)
+    parents = {}
+    for node in ast.walk(tree):
+        for child in ast.iter_child_nodes(node):
+            parents[child] = node
+    helpers = {"oracle_sample", "listing1_sample", "run_reference"}
+    found = 0
+    for node in ast.walk(tree):
+        names = []
+        if isinstance(node, ast.ImportFrom) and node.module:
+            names = [node.module]
+        elif isinstance(node, ast.Import):
+            names = [a.name for a in node.names]
+        if not any(nm.split(".")[0] == "oracle" for nm in names):
+            continue
+        found += 1
+        p, ok = parents.get(node), False
+        while p is not None and not ok:
+            if isinstance(p, ast.FunctionDef) and p.name in helpers:
+                ok = True
+            if isinstance(p, ast.If) and "no_cpu" in ast.get_source_segment(src, p.test):
+                ok = True
+            p = parents.get(p)
+        assert ok, f"oracle import at bench.py:{node.lineno} outside the CPU legs"
+    assert found >= 3
+    # and the CPU-timing helpers are called only from those places too
+    for node in ast.walk(tree):
+        if not (isinstance(node, ast.Call) and isinstance(node.func, ast.Name)
+                and node.func.id in ("oracle_sample", "listing1_sample")):
+            continue
+        p, ok = parents.get(node), False
+        while p is not None and not ok:
+            if isinstance(p, ast.FunctionDef) and p.name == "run_reference":
+                ok = True
+            if isinstance(p, ast.If) and "no_cpu" in ast.get_source_segment(src, p.test):
+                ok = True
+            p = parents.get(p)
+        assert ok, f"{node.func.id} called at bench.py:{node.lineno} outside the CPU legs"
