@@ -300,27 +300,70 @@ def listing1_sample(A_dev, B_dev, target_s):
     return 2.0 * r * r * k / dt, dt, r, used, a, b
 
 
+GROUPED_WORKLOAD = ("grouped: 512 independent products, m,n,k log-uniform in [64,4096] "
+                    "seed 1")
+
+
+def grouped_oracle_sample(dims, target_s):
+    """Time the oracle's plain product over the first problems of a grouped
+    workload for about target_s seconds (a problem above 3e8 multiply-adds
+    contributes the 64 x 64 leading corner of its C, full k; input generation
+    is inside the time).  Returns (flop, seconds, problems)."""
+    import numpy as np
+    import cosma_inputs as ci
+    from oracle import gemm as og
+    t0 = time.perf_counter()
+    done, i = 0.0, 0
+    while time.perf_counter() - t0 < target_s and i < len(dims):
+        m, n, k = (int(x) for x in dims[i])
+        A = np.asarray(ci.matrix(m, k, "uniform", "f32", 1000 + i, ci.STREAM_A), np.float64)
+        B = np.asarray(ci.matrix(k, n, "uniform", "f32", 1000 + i, ci.STREAM_B), np.float64)
+        if m * n * k > 3e8:
+            A, B = A[:64], B[:, :64]
+        og.gemm(A, B, "naive")
+        done += 2.0 * A.shape[0] * B.shape[1] * k
+        i += 1
+    return done, time.perf_counter() - t0, i
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    m, n, k = WORKLOADS[args.workload]
     dtype = args.dtype
-    gen = "f32" if dtype in ("f32", "f32_emu_tf32") else "f64"
-    vals = []
-    rows = None
-    for i in range(args.warmup + args.steps):
-        fl, dt, rows = oracle_sample(m, n, k, 8.0 if i >= args.warmup else 2.0, gen=gen)[:3]
-        if i >= args.warmup:
-            vals.append(fl)
-    value = statistics.median(vals) / 1e12
-    sample = f"oracle naive FP64 loop on the {rows}x{rows} leading block of C, full k={k}"
+    vals, secs = [], []
+    if args.workload == "grouped512":
+        import cosma_inputs as ci
+        dims = ci.grouped_dims(512, seed=1)
+        count = 0
+        for i in range(args.warmup + args.steps):
+            fl, dt, count = grouped_oracle_sample(dims, 8.0 if i >= args.warmup else 2.0)
+            if i >= args.warmup:
+                vals.append(fl / dt)
+                secs.append(dt)
+        sample = (f"oracle naive loop over the first {count} problems (>3e8 MACs: 64x64 "
+                  "corner), incl. input generation")
+        config = {"workload": GROUPED_WORKLOAD, "l2": "inputs larger than L2"}
+        ms_per_step = statistics.median(secs) * 1e3
+        value = statistics.median(vals) / 1e12
+    else:
+        m, n, k = WORKLOADS[args.workload]
+        gen = "f32" if dtype in ("f32", "f32_emu_tf32") else "f64"
+        rows = None
+        for i in range(args.warmup + args.steps):
+            fl, dt, rows = oracle_sample(m, n, k, 8.0 if i >= args.warmup else 2.0, gen=gen)[:3]
+            if i >= args.warmup:
+                vals.append(fl)
+        value = statistics.median(vals) / 1e12
+        sample = f"oracle naive FP64 loop on the {rows}x{rows} leading block of C, full k={k}"
+        config = workload_config(args.workload, m, n, k, dtype)
+        ms_per_step = 2.0 * rows * rows * k / (value * 1e12) * 1e3
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 2.0 * rows * rows * k / (value * 1e12) * 1e3,
+            "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.workload, m, n, k, dtype),
+            "config": config,
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
@@ -470,23 +513,7 @@ def run_grouped(args):
            "d2h_bytes_per_step": int(sum(c.numel() for c in Cs) * 4), "steps": 1}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        from oracle import gemm as og
-        t0 = time.perf_counter()
-        done = 0.0
-        i = 0
-        while time.perf_counter() - t0 < 12.0 and i < len(dims):
-            m, n, k = dims[i]
-            Ah_ = np.asarray(ci.matrix(m, k, "uniform", "f32", 1000 + i, ci.STREAM_A), np.float64)
-            Bh_ = np.asarray(ci.matrix(k, n, "uniform", "f32", 1000 + i, ci.STREAM_B), np.float64)
-            if m * n * k > 3e8:
-                Ah_, Bh_ = Ah_[:64], Bh_[:, :64]
-                m2, n2 = Ah_.shape[0], Bh_.shape[1]
-            else:
-                m2, n2 = m, n
-            og.gemm(Ah_, Bh_, "naive")
-            done += 2.0 * m2 * n2 * k
-            i += 1
-        dt = time.perf_counter() - t0
+        done, dt, i = grouped_oracle_sample(dims, 12.0)
         cpu = {"value": done / dt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
                "sample": f"oracle naive loop over the first {i} problems "
                          f"(>3e8 MACs: 64x64 corner), {dt:.1f} s incl. input generation"}
@@ -495,8 +522,7 @@ def run_grouped(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": dtype, "data": "synthetic",
-                "config": {"workload": "grouped: 512 independent products, m,n,k log-uniform "
-                                       "in [64,4096] seed 1, one persistent launch replayed "
+                "config": {"workload": GROUPED_WORKLOAD + ", one persistent launch replayed "
                                        f"from a CUDA graph ({reps} replays per step)",
                            "flops_per_replay": flops, "replay_ms": replay_ms,
                            "pitches": "rows padded to 16 bytes",

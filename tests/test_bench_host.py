@@ -83,3 +83,33 @@ def test_reference_arm_line(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     assert bench.run_reference(args) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_grouped_oracle_sample_counts_the_problems_it_ran():
+    # a short budget covers the first problems; their flop are 2 m n k each (or
+    # the 64 x 64 corner of a problem above 3e8 multiply-adds)
+    import bench
+    import cosma_inputs as ci
+    dims = ci.grouped_dims(512, seed=1)
+    flop, dt, count = bench.grouped_oracle_sample(dims, 0.3)
+    assert 1 <= count <= len(dims) and dt > 0
+    want = 0.0
+    for m, n, k in dims[:count]:
+        m, n, k = int(m), int(n), int(k)
+        want += 2.0 * (64 * 64 if m * n * k > 3e8 else m * n) * k
+    assert flop == want
+    assert bench.grouped_oracle_sample(dims[:2], 60.0)[2] == 2
+
+
+def test_reference_arm_grouped_workload(monkeypatch, capsys):
+    import json
+    import types
+    import bench
+    monkeypatch.setattr(bench, "grouped_oracle_sample", lambda dims, t: (3.0e9, 1.5, 40))
+    args = types.SimpleNamespace(workload="grouped512", dtype="bf16", steps=2, warmup=1, gpus=1)
+    assert bench.run_reference(args) == 0
+    line = json.loads(capsys.readouterr().out.strip())
+    assert line["impl"] == "reference" and line["value"] == pytest.approx(2.0e-3)
+    assert line["ms_per_step"] == pytest.approx(1500.0)
+    assert line["config"]["workload"].startswith(bench.GROUPED_WORKLOAD)
+    assert "first 40 problems" in line["cpu_baseline"]["sample"]
