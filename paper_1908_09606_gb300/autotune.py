@@ -306,9 +306,8 @@ def install(params_path=None, log2_lo=8.0, log2_hi=16.0, dtypes=None):
             raise cosma.CosmaError(rc, "cosma_selector_restrict")
 
 
-def main(argv=None):
+def parser():
     import argparse
-    import torch
     ap = argparse.ArgumentParser(description="collect timings, train the selector, report regret")
     ap.add_argument("--out", required=True)
     ap.add_argument("--train-shapes", type=int, default=1250)
@@ -317,7 +316,12 @@ def main(argv=None):
     ap.add_argument("--collect-budget-s", type=float, default=900)
     ap.add_argument("--eval-budget-s", type=float, default=600)
     ap.add_argument("--seed", type=int, default=0)
-    a = ap.parse_args(argv)
+    return ap
+
+
+def main(argv=None):
+    import torch
+    a = parser().parse_args(argv)
     os.makedirs(a.out, exist_ok=True)
     torch.cuda.set_device(0)
     cosma.load()

@@ -1,7 +1,7 @@
 """The ncu summaries under profiles/ (CPU): each is short text, names the
 command that produced it, every ncu command leaves the clocks alone
 (--clock-control none), and every bench.py command line in them is still
-accepted by bench.py's own argument parser."""
+accepted by bench.py's own argument parser (the autotuner's by its own)."""
 import os
 import re
 import shlex
@@ -40,3 +40,11 @@ def test_bench_command_lines_parse(name, monkeypatch):
     for args in cmds:
         monkeypatch.setattr(sys, "argv", ["bench.py"] + shlex.split(args))
         bench.parse()   # raises SystemExit on an option bench.py no longer has
+
+
+@pytest.mark.parametrize("name", FILES)
+def test_autotune_command_lines_parse(name):
+    from paper_1908_09606_gb300 import autotune
+    text = _joined(open(os.path.join(PROFILES, name)).read())
+    for args in re.findall(r"python -m paper_1908_09606_gb300\.autotune([^\"`\n|>$]*)", text):
+        autotune.parser().parse_args(shlex.split(args))
