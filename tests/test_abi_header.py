@@ -1,7 +1,8 @@
 """The Python binding against include/cosma.h, without a GPU: every prototype's
 parameters and result have the kind and width of the binding's ctypes
 signature, and the binding's structures have the header's field offsets and
-sizes as gcc lays them out (a mismatch would pass garbage through the ABI)."""
+sizes as gcc lays them out, and the enumerators carry the values the binding
+uses (a mismatch would pass garbage through the ABI)."""
 import ctypes
 import os
 import re
@@ -103,3 +104,29 @@ def test_struct_layouts_match_gcc(binding, tmp_path):
         for field, t in s._fields_:
             assert (getattr(s, field).offset, ctypes.sizeof(t)) == table[(name, field)], \
                 (name, field)
+
+
+def _enums():
+    text = _strip_comments(open(HEADER).read())
+    out = {}
+    for body in re.findall(r"typedef\s+enum\s*\{(.*?)\}\s*\w+\s*;", text, flags=re.S):
+        for name, value in re.findall(r"(COSMA_\w+)\s*=\s*(-?\d+)", body):
+            out[name] = int(value)
+    return out
+
+
+def test_enum_values_match_the_binding(binding):
+    enums = _enums()
+    assert len(enums) >= 20
+    # the binding's dtype names map to the header's enumerators
+    assert binding.DTYPES == {name.lower(): enums["COSMA_" + name.upper()] for name in
+                              binding.DTYPES}
+    for name, value in enums.items():
+        if hasattr(binding, name):
+            assert getattr(binding, name) == value, name
+    kernels = {v: k[len("COSMA_KERNEL_"):].lower() for k, v in enums.items()
+               if k.startswith("COSMA_KERNEL_")}
+    assert kernels == binding.KERNELS
+    for s in ("OK", "ERR_INVALID_ARG", "ERR_UNSUPPORTED", "ERR_CUDA", "ERR_TIMEOUT",
+              "ERR_NONFINITE", "ERR_NO_WORKSPACE"):
+        assert getattr(binding, "COSMA_" + s) == enums["COSMA_" + s]
