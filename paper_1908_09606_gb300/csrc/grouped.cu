@@ -728,14 +728,17 @@ int grouped_gemm(int count, const cosma_problem* problems, int dtype, const Devi
   const int tile = pick_tile(count, problems, dtype, requested_tile);
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusNone;
-  Table* t = nullptr;
+  Table snap;  // the launch reads a copy taken under the lock, not the shared slot
   int rc;
   {
     std::lock_guard<std::mutex> lock(g_tab_mu);
+    Table* slot = nullptr;
     rc = get_table(dev.device, count, problems, dtype, tile, dev.sms > 0 ? dev.sms : 148, ws,
-                   cs != cudaStreamCaptureStatusNone, st, &t);
+                   cs != cudaStreamCaptureStatusNone, st, &slot);
+    if (rc == COSMA_OK) snap = *slot;
   }
   if (rc != COSMA_OK) return rc;
+  const Table* t = &snap;
   if (t->nunits == 0) return COSMA_OK;
   GArgs args{t->maps, t->meta, t->units, t->cta_off, status, wait_limit};
   if (dtype == COSMA_BF16) {
