@@ -265,7 +265,21 @@ int elem_bytes_out(int dtype) {
   return dtype == COSMA_F32 || dtype == COSMA_BF16 || dtype == COSMA_F32_EMU_TF32 ? 4 : 8;
 }
 
+}  // namespace
+
 constexpr int64_t kTf32MaxK = 65535LL * 32;
+
+// Three-TF32 parts are written by grids with one y row per 32-deep k block; the
+// bf16 slices likewise, per 32 columns of k padded to 2048-deep panels.  Every
+// entry point refuses a longer k before it sizes or allocates anything.
+int k_supported(int dtype, int64_t k) {
+  if (dtype == COSMA_F32_EMU_TF32 && k > kTf32MaxK) return COSMA_ERR_UNSUPPORTED;
+  if (dtype == COSMA_F64_EMU_BF16 && (emu_padded_k(k) + 31) / 32 > 65535)
+    return COSMA_ERR_UNSUPPORTED;
+  return COSMA_OK;
+}
+
+namespace {
 
 int check_args(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, const void* B,
                int64_t ldb, const void* C, int64_t ldc, int dtype, int ta = 0, int tb = 0) {
@@ -276,11 +290,7 @@ int check_args(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, cons
   if (lda < (a_cols > 1 ? a_cols : 1) || ldb < (b_cols > 1 ? b_cols : 1) || ldc < (n > 1 ? n : 1))
     return COSMA_ERR_INVALID_ARG;
   if (m == 0 || n == 0) return COSMA_OK;
-  // three-TF32 parts are written by grids with one y row per 32-deep k block;
-  // the bf16 slices likewise, per 32 columns of k padded to 2048-deep panels
-  if (dtype == COSMA_F32_EMU_TF32 && k > kTf32MaxK) return COSMA_ERR_UNSUPPORTED;
-  if (dtype == COSMA_F64_EMU_BF16 && (emu_padded_k(k) + 31) / 32 > 65535)
-    return COSMA_ERR_UNSUPPORTED;
+  if (k_supported(dtype, k) != COSMA_OK) return COSMA_ERR_UNSUPPORTED;
   if (!C) return COSMA_ERR_INVALID_ARG;
   if (k > 0 && (!A || !B)) return COSMA_ERR_INVALID_ARG;
   if ((uintptr_t)C % elem_bytes_out(dtype)) return COSMA_ERR_INVALID_ARG;

@@ -128,6 +128,7 @@ int complex_gemm(int op_a, int op_b, int64_t m, int64_t n, int64_t k, const R* a
       ldc < (n > 1 ? n : 1))
     return COSMA_ERR_INVALID_ARG;
   if (m == 0 || n == 0) return COSMA_OK;
+  if (k_supported(engine, k) != COSMA_OK) return COSMA_ERR_UNSUPPORTED;  // before any staging
   if (!C || (reinterpret_cast<uintptr_t>(C) & amask) || !on_device(C)) return COSMA_ERR_INVALID_ARG;
   const bool no_ab = k == 0 || (alpha[0] == R(0) && alpha[1] == R(0));
   if (!no_ab && (!A || !B || (reinterpret_cast<uintptr_t>(A) & amask) ||

@@ -143,9 +143,7 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
   if (!C || !is_host_ptr(C)) return COSMA_ERR_INVALID_ARG;
   if (k > 0 && (!A || !B || !is_host_ptr(A) || !is_host_ptr(B))) return COSMA_ERR_INVALID_ARG;
   if (dtype == COSMA_F64_EMU_INT8) return COSMA_ERR_UNSUPPORTED;
-  if (dtype == COSMA_F32_EMU_TF32 && k > 65535LL * 32) return COSMA_ERR_UNSUPPORTED;  // k blocks
-  if (dtype == COSMA_F64_EMU_BF16 && (emu_padded_k(k) + 31) / 32 > 65535)
-    return COSMA_ERR_UNSUPPORTED;
+  if (k_supported(dtype, k) != COSMA_OK) return COSMA_ERR_UNSUPPORTED;
 
   LibContext ctx;
   int rc = lib_context(&ctx);
@@ -174,7 +172,6 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
   if (emu) {
     rc = emu_check_config(ctx.cfg);
     if (rc != COSMA_OK) return rc;
-    if ((emu_padded_k(k) + 31) / 32 > 65535) return COSMA_ERR_UNSUPPORTED;
     void* ws = nullptr;
     rc = lib_scratch(emu_workspace_bytes(m, n, k, ctx.cfg), st, &ws);
     if (rc != COSMA_OK) return rc;

@@ -102,6 +102,9 @@ struct EmuWorkspace {
 long long emu_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_config& cfg);
 // k rounded up to whole panels of the k-blocked slice layout.
 int64_t emu_padded_k(int64_t k);
+// COSMA_OK when the element format's operand preparation covers this k, else
+// COSMA_ERR_UNSUPPORTED (api.cu); checked before anything is sized or allocated.
+int k_supported(int dtype, int64_t k);
 EmuWorkspace emu_carve(void* ws, int64_t m, int64_t n, int64_t k, const cosma_config& cfg);
 int emu_check_config(const cosma_config& cfg);
 // Exponents and slices of rows [0, m) of A into eA[0..m) and SA (slice_rows

@@ -85,6 +85,27 @@ def test_k_limits_are_refused_before_any_launch(lib):
     assert lib.cosma_gemm(4, 4, emax, 16, emax, 16, 4, 16, 4, dt) == lib.COSMA_ERR_INVALID_ARG
 
 
+def test_complex_k_limits_are_refused_before_any_staging(lib):
+    # the complex entries reach the same limits as the real ones (their four real
+    # products run on the same engines); the refusal precedes the pointer checks,
+    # so it also precedes the sizing and allocation of the planar staging buffer
+    cosma = lib
+    al = 1.0 + 0j
+    kmax, emax = 65535 * 32, 1023 * 2048
+    assert cosma.cosma_cgemm(0, 0, 4, 4, kmax + 1, al, 0, kmax + 1, 0, 4, al, 0, 4,
+                             cosma.COSMA_F32_EMU_TF32, 0) == cosma.COSMA_ERR_UNSUPPORTED
+    assert cosma.cosma_zgemm(0, 0, 4, 4, emax + 1, al, 0, emax + 1, 0, 4, al, 0, 4,
+                             cosma.COSMA_F64_EMU_BF16, 0) == cosma.COSMA_ERR_UNSUPPORTED
+    # one element shorter: the same call fails on its null pointers instead
+    assert cosma.cosma_cgemm(0, 0, 4, 4, kmax, al, 0, kmax, 0, 4, al, 0, 4,
+                             cosma.COSMA_F32_EMU_TF32, 0) == cosma.COSMA_ERR_INVALID_ARG
+    assert cosma.cosma_zgemm(0, 0, 4, 4, emax, al, 0, emax, 0, 4, al, 0, 4,
+                             cosma.COSMA_F64_EMU_BF16, 0) == cosma.COSMA_ERR_INVALID_ARG
+    # the engines without such a limit take the long k to the pointer checks
+    assert cosma.cosma_cgemm(0, 0, 4, 4, kmax + 1, al, 0, kmax + 1, 0, 4, al, 0, 4,
+                             cosma.COSMA_F32, 0) == cosma.COSMA_ERR_INVALID_ARG
+
+
 def test_host_entry_rejects_bad_arguments(lib):
     bad = lib.COSMA_ERR_INVALID_ARG
     assert lib.cosma_gemm_host(-1, 4, 4, 0, 4, 0, 4, 0, 4, lib.COSMA_F64) == bad
