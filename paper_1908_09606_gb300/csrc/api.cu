@@ -306,7 +306,7 @@ int check_args(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, cons
 long long total_workspace(int64_t m, int64_t n, int64_t k, int dtype, const cosma_plan& p,
                           const void* A = nullptr, int64_t lda = 0, const void* B = nullptr,
                           int64_t ldb = 0, int ta = 0, int tb = 0) {
-  if (dtype == COSMA_F64_EMU_BF16) return emu_workspace_bytes(m, n, k, g_cfg);
+  if (dtype == COSMA_F64_EMU_BF16) return emu_workspace_bytes(m, n, k, g_cfg, p.sms);
   if (dtype == COSMA_BF16) return tc_workspace_bytes(m, n, k, p, A, lda, ta, B, ldb, tb);
   if (dtype == COSMA_F32_EMU_TF32) return tf32x3_workspace_bytes(m, n, k, p);
   // FMA paths: split-k partials, then untransposed copies of transposed operands

@@ -36,9 +36,11 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <mutex>
+#include <type_traits>
 
 #include "tc_common.cuh"
 
@@ -290,6 +292,8 @@ struct EmuArgs {
   int* status;
   long long wait_limit;
   unsigned int* lockstep;  // cooperative launches: per-unit progress counter (zeroed), else null
+  long long* T;            // pair kernel: per-CTA running totals, 128 x tile_n int64 each
+  int t_base;              // pair kernel: fixed-point base of T (see the pair kernel)
   double alpha, beta_c;    // C = alpha A B + beta_c C (C read only when beta_c != 0)
 };
 
@@ -646,23 +650,45 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   }
 }
 
-// ---- 2-SM variant ------------------------------------------------------------------
+// ---- CTA-pair kernel ----------------------------------------------------------------
 //
-// A cluster of two CTAs computes a 256 x 128 tile with tcgen05.mma.cta_group::2
-// (M = 256): each CTA loads its own 128 rows of the A slice and its own 64 of
-// the 128 columns of the B slice (no multicast), the even CTA issues the MMAs
-// and commits to the barriers of both, and each CTA drains its own 128 x 128
-// accumulator exactly as the single-SM kernel does.  Per SM an MMA step then
-// reads 6 KB of operands instead of 8 KB, and the ring is 6 stages deep.
-constexpr int E2_STAGES = 6;
+// A cluster of two CTAs computes a 256 x BN tile (BN = 256 or 128) with
+// tcgen05.mma.cta_group::2 (M = 256, N = BN): each CTA loads its own 128 rows of
+// the A slice and its own BN / 2 of the BN columns of the B slice (no multicast),
+// the even CTA issues the MMAs and commits to the barriers of both, and each CTA
+// drains its own 128 x BN accumulator.  N = 256 instructions run the tensor
+// cores at their full rate per clock (N = 128 ones reach about 81 % of it), and
+// per SM an MMA step reads 8 KB of operands for 128 x 256 x 16 products.
+//
+// Tensor memory holds only accumulators (512 / BN buffers of BN columns).  The
+// exact level sum of the current super-chunk stays in registers (BN / 2 int32
+// per epilogue thread), and the running total of the tile is an exact int64
+// fixed-point number T = sum_chunks sum_l 2^(beta (s + 1 - l) - base) L_l kept
+// in a per-CTA scratch region in global memory: the first merge of a tile
+// stores, later ones are reductions performed in L2, and the thread that made
+// them reads the total back (L2 only) to form the FP64 result,
+// C = T 2^(sigma_i + tau_j + 2 - beta (s + 1) + base).  `base` (host, from k)
+// keeps |T| < 2^62; levels whose weight is below 2^base are rounded to it.
 
-struct E2Layout {
-  static constexpr int A_BYTES = EBM * EBK * 2;        // own 128 rows
-  static constexpr int B_BYTES = (EBN / 2) * EBK * 2;  // own 64 columns
+// Threads of the pair kernel: warps 0-3 (producer, MMA issuer, two idle), one
+// on each SM quarter, and the epilogue warps 4-11, two on each quarter.
+constexpr int kPairThreads = 384;
+// Registers per thread the pair kernel's register split assumes at launch: the
+// register file is split by SM quarter, and on each quarter the control warp's
+// 56 plus two epilogue warps' 216 must fit in the three warps' launch share,
+// 56 + 2 x 216 <= 3 x 168.
+constexpr int kPairMinRegs = 168;
+
+template <int BN>
+struct PairLayout {
+  static constexpr int NACC = 512 / BN;                   // accumulator buffers
+  static constexpr int A_BYTES = EBM * EBK * 2;           // own 128 rows
+  static constexpr int B_BYTES = (BN / 2) * EBK * 2;      // own BN / 2 columns
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int T_OFF = E2_STAGES * STAGE_BYTES;
-  static constexpr int BAR_OFF = T_OFF + EBM * TPITCH * 4;
-  static constexpr int NBARS = 2 * E2_STAGES + 2 * NACC + 1;
+  static constexpr int STAGES = BN == 256 ? 7 : 9;
+  static constexpr int BAR_OFF = STAGES * STAGE_BYTES;
+  // full, empty, tfull, tempty, drain, peer-count exchange
+  static constexpr int NBARS = 2 * STAGES + 2 * NACC + 2;
   static constexpr int TOTAL = BAR_OFF + NBARS * 8 + 16;
   static constexpr int ALLOC = TOTAL + 1024;
 };
@@ -679,35 +705,193 @@ __device__ __forceinline__ void tma_load_slice_pair(void* dst, const CUtensorMap
       : "memory");
 }
 
-__global__ void __launch_bounds__(320, 1)
-emu_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
-                     const __grid_constant__ CUtensorMap tmB, EmuArgs a) {
-  using L = E2Layout;
+// v 2^sh as an int64 (sh < 0: rounded to nearest, ties up).
+__device__ __forceinline__ long long fx_shift(int v, int sh) {
+  if (sh >= 0) return (long long)v << sh;
+  return ((long long)v + (1LL << (-sh - 1))) >> (-sh);
+}
+
+// Epilogue warps (4..11) of the pair kernel: warp -> tensor-memory lane quadrant
+// q4 = warp % 4 and column half h; each thread owns one row and BN / 2 columns.
+// Its entries of the running total sit at Tt + c * 128 (c = its column), so a
+// warp touches 32 consecutive int64 per column.
+template <int BN>
+__device__ __forceinline__ void emu_pair_epilogue(const EmuArgs& a, int pair, int64_t nunits,
+                                                  uint32_t rank, uint32_t tmem_base,
+                                                  uint64_t* tfull, const uint32_t* tempty_addr,
+                                                  const tc::WaitCtx& w, int warp, int lane) {
+  constexpr int HC = BN / 2;
+  constexpr int NACC = PairLayout<BN>::NACC;
+  const int64_t kbt = a.sch.kbt;
+  const int top = a.s + 1;
+  const int q4 = warp & 3;
+  const int h = (warp - 4) >> 2;
+  const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
+  const uint32_t col_lo = (uint32_t)(HC * h);
+  long long* Tt = a.T + (int64_t)blockIdx.x * (128 * BN) + ((int64_t)h * HC * 4 + q4) * 32 + lane;
+  uint32_t acc = 0;
+  uint32_t tph[NACC];
+#pragma unroll
+  for (int b = 0; b < NACC; ++b) tph[b] = 0;
+  bool ok = true;
+  for (int64_t ui = 0; ui < nunits && ok; ++ui) {
+    const Unit u = unit_of_cta(a.sch, pair, ui);
+    int Lv[HC];  // exact level sum of the current super-chunk
+    bool stored = false;
+    for (int64_t sc0 = 0; sc0 < kbt && ok; sc0 += a.chunk_kb) {
+      const int64_t sc1 = min(sc0 + (int64_t)a.chunk_kb, kbt);
+      for (int lvl = top; lvl >= 2 && ok; --lvl) {
+        const int gk = group_blocks(a.group_kb, lvl - 1);
+        // one exact group: its integer sums join Lv (the level's first group sets it)
+        auto drain = [&](auto first_tag) -> bool {
+          constexpr bool kFirst = decltype(first_tag)::value;
+          if (!tc::mbar_wait(&tfull[acc], tph[acc], w)) return false;
+          tc::tc_fence_after();
+          const uint32_t src = tmem_base + lane_off + acc * BN + col_lo;
+#pragma unroll
+          for (int c = 0; c < HC; c += 16) {
+            uint32_t v[16];
+            tc::tmem_ld_32x16(src + c, v);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int iv = __float2int_rn(__uint_as_float(v[j]));  // exact integer
+              Lv[c + j] = kFirst ? iv : Lv[c + j] + iv;
+            }
+          }
+          tc::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive_remote_relaxed(tempty_addr[acc]);
+          tph[acc] ^= 1;
+          acc = (acc + 1) == NACC ? 0 : acc + 1;
+          return true;
+        };
+        if (!drain(std::true_type{})) { ok = false; break; }
+        for (int64_t c0 = sc0 + gk; c0 < sc1; c0 += gk)
+          if (!drain(std::false_type{})) { ok = false; break; }
+        if (!ok) break;
+        // K-RECOMB: T += L 2^(beta (top - lvl) - base), exactly
+        const int sh = a.beta * (top - lvl) - a.t_base;
+        // (8 columns at a time: each batch's shifted values are sent before the next
+        // is formed, which keeps the 64-bit temporaries few)
+#pragma unroll
+        for (int c = 0; c < HC; c += 8) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const long long x = fx_shift(Lv[c + j], sh);
+            // relaxed gpu-scope store, reductions and read-back: same-address
+            // operations of one thread stay in program order (coherence)
+            if (!stored)
+              asm volatile("st.relaxed.gpu.global.s64 [%0], %1;" ::"l"(Tt + (c + j) * 128), "l"(x)
+                           : "memory");
+            else
+              asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(Tt + (c + j) * 128),
+                           "l"(x)
+                           : "memory");
+          }
+        }
+        stored = true;
+      }
+    }
+    if (!ok) break;
+    // Final FP64 store: C = T 2^(sigma_i + tau_j + 2 - beta (s + 1) + base) for this
+    // thread's row, HC columns.  Each 8-column chunk is formed in the row's lane,
+    // transposed within groups of 8 lanes (three butterfly stages of shuffles: at
+    // stage s, entries whose row and column differ in bit s trade places with
+    // lane ^ s), and written as four 64-byte row segments per instruction.
+    const int64_t row0 = u.tile_row * (2 * EBM) + (int64_t)rank * EBM + q4 * 32;
+    const int64_t row = row0 + lane;
+    const int64_t cbase = u.tile_col * BN + col_lo;
+    const int ea = row < a.sch.m ? a.eA[row] : kExpNone;
+    const int eoff = 2 - a.beta * top + a.t_base;
+    const int l8 = lane & 7, g8 = lane >> 3;
+    // the read-back addresses from an opaque copy of the base, so the compiler does
+    // not keep the merges' per-column addresses live across the loops
+    long long* Tf = Tt;
+    asm volatile("" : "+l"(Tf));
+#pragma unroll
+    for (int c = 0; c < HC; c += 8) {
+      long long tv[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        asm volatile("ld.relaxed.gpu.global.s64 %0, [%1];" : "=l"(tv[j]) : "l"(Tf + (c + j) * 128)
+                     : "memory");
+      int eb[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) eb[j] = cbase + c + j < a.sch.n ? a.eB[cbase + c + j] : kExpNone;
+      double v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        double x = (ea == kExpNone || eb[j] == kExpNone)
+                       ? 0.0
+                       : scale_pow2((double)tv[j], ea + eb[j] + eoff);
+        if (a.alpha != 1.0) x *= a.alpha;
+        v[j] = x;
+      }
+#pragma unroll
+      for (int sb = 4; sb >= 1; sb >>= 1) {
+#pragma unroll
+        for (int i0 = 0; i0 < 8; ++i0) {
+          if (i0 & sb) continue;
+          const bool up = (l8 & sb) != 0;
+          const double send = up ? v[i0] : v[i0 | sb];
+          const double recv = __shfl_xor_sync(0xffffffffu, send, sb);
+          if (up) v[i0] = recv;
+          else v[i0 | sb] = recv;
+        }
+      }
+      // now v[i] = C(row0 + 8 g8 + i, cbase + c + l8)
+      const int64_t col = cbase + c + l8;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int64_t r = row0 + 8 * g8 + i;
+        if (r < a.sch.m && col < a.sch.n) {
+          double* dst = a.C + r * a.ldc + col;
+          double x = v[i];
+          if (a.beta_c != 0.0) x = fma(a.beta_c, *dst, x);
+          *dst = x;
+        }
+      }
+    }
+  }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kPairThreads, 1)
+emu_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                EmuArgs a) {
+  using L = PairLayout<BN>;
+  constexpr int S = L::STAGES;
+  constexpr int NACC = L::NACC;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
-  uint64_t* empty = full + E2_STAGES;
-  uint64_t* tfull = empty + E2_STAGES;
+  uint64_t* empty = full + S;
+  uint64_t* tfull = empty + S;
   uint64_t* tempty = tfull + NACC;
   uint64_t* drain = tempty + NACC;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* xchg = drain + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(xchg + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  uint32_t* peer_issued = tslot + 2;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const uint32_t rank = tc::cluster_ctarank();
   const bool leader = rank == 0;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < E2_STAGES; ++s) {
+    for (int s = 0; s < S; ++s) {
       tc::mbar_init(&full[s], 1);   // leader: its producer's arrival + both CTAs' bytes
       tc::mbar_init(&empty[s], 1);  // the leader's commit, multicast to both CTAs
     }
     for (int b = 0; b < NACC; ++b) {
       tc::mbar_init(&tfull[b], 1);
-      tc::mbar_init(&tempty[b], 16);  // leader: 8 epilogue warps of each CTA
+      tc::mbar_init(&tempty[b], 16);  // leader: the 8 epilogue warps of each CTA
     }
     tc::mbar_init(drain, 1);
+    tc::mbar_init(xchg, 1);  // leader: the odd CTA's count of issued stages
     *abort_flag = 0;
+    *peer_issued = 0;
     tc::fence_barrier_init();
   }
   if (warp == 1) tc::tmem_alloc_pair(tslot, 512);
@@ -719,14 +903,26 @@ emu_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
   const int pair = blockIdx.x >> 1;
   const int64_t nunits = units_of_cta(a.sch, pair);
 
+  // Register split: the control warps give registers back to the epilogue warps
+  // on their own SM quarter (warp w runs on quarter w % 4); the epilogue threads
+  // hold BN / 2 level sums each.  The launch provides kPairMinRegs per thread
+  // (the host checks before launching).
+  if (warp >= 4) {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 216;\n" ::: "memory");
+    uint32_t te[NACC];
+#pragma unroll
+    for (int b = 0; b < NACC; ++b) te[b] = tc::mapa_shared(&tempty[b], 0);
+    emu_pair_epilogue<BN>(a, pair, nunits, rank, tmem_base, tfull, te, w, warp, lane);
+  } else {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 56;\n" ::: "memory");
   if (warp == 0) {
     if (tc::elect_one()) {
       int stage = 0;
       uint32_t ph = 0;
-      bool issued = false;
-      uint32_t full_cl[E2_STAGES];
+      uint32_t issued = 0;  // stages whose copies this CTA issued
+      uint32_t full_cl[S];
 #pragma unroll
-      for (int s = 0; s < E2_STAGES; ++s) full_cl[s] = tc::mapa_shared(&full[s], 0);
+      for (int s = 0; s < S; ++s) full_cl[s] = tc::mapa_shared(&full[s], 0);
       // Lock-step rounds (cooperative launches only): the leader's producer of
       // every pair announces each issued unit on a global counter and does not
       // start round r + 1 before all pairs have issued round r, so concurrent
@@ -764,29 +960,51 @@ emu_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
               tma_load_slice_pair(sa, &tmA, full_cl[stage], kb,
                                   (int32_t)(u.tile_row * (2 * EBM) + rank * EBM), q - 1);
               tma_load_slice_pair(sa + L::A_BYTES, &tmB, full_cl[stage], kb,
-                                  (int32_t)(u.tile_col * EBN + rank * (EBN / 2)), lvl - q - 1);
-              issued = true;
-              if (++stage == E2_STAGES) { stage = 0; ph ^= 1; }
+                                  (int32_t)(u.tile_col * BN + rank * (BN / 2)), lvl - q - 1);
+              ++issued;
+              if (++stage == S) { stage = 0; ph ^= 1; }
               return true;
             },
             [] {});
         if (a.lockstep && leader) atomicAdd(a.lockstep, 1u);
         if (!ok) break;
       }
-      if (*abort_flag && issued) {
-        // Copies of this CTA signal the leader's barriers: give any still in
-        // flight time to land before the pair leaves.
+      // The odd CTA's copies signal the leader's barriers: it reports how many
+      // stages it issued, and on an abort the leader waits (bounded) until every
+      // stage either CTA may still have in flight has landed, so neither CTA
+      // leaves (final cluster barrier) with a copy still writing into it.
+      if (*abort_flag) tc::st_cluster_u32(tc::mapa_shared(const_cast<int*>(abort_flag), rank ^ 1), 1u);
+      if (!leader) {
+        tc::st_cluster_u32(tc::mapa_shared(peer_issued, 0), issued);
+        tc::mbar_arrive_remote(tc::mapa_shared(xchg, 0));
+      } else if (*abort_flag) {
         const long long t0 = clock64();
-        while (clock64() - t0 < (1LL << 22)) {
+        bool got = false;
+        while (!(got = tc::mbar_try_wait_cluster(xchg, 0)) && clock64() - t0 < tc::kDrainCycles) {
+        }
+        if (got) {
+          const uint32_t n0 = issued, n1 = *reinterpret_cast<volatile uint32_t*>(peer_issued);
+          const uint32_t top = n0 > n1 ? n0 : n1;
+          for (uint32_t i = top > (uint32_t)S ? top - S : 0u; i < top; ++i) {
+            const int s = (int)(i % S);
+            const uint32_t par = (i / S) & 1u;
+            if (i >= n0) tc::mbar_arrive_expect_tx(&full[s], L::STAGE_BYTES);  // only the peer's
+            else if (i >= n1) tc::mbar_complete_tx(&full[s], L::STAGE_BYTES);  // the peer's never come
+            const long long t1 = clock64();
+            while (!tc::mbar_try_wait(&full[s], par) && clock64() - t1 < tc::kDrainCycles) {
+            }
+          }
         }
       }
     }
   } else if (warp == 1) {
     if (leader && tc::elect_one()) {
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(2 * EBM, EBN);
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(2 * EBM, BN);
       int stage = 0;
       uint32_t ph = 0, acc = 0;
-      uint32_t aph[NACC] = {0, 0, 0};
+      uint32_t aph[NACC];
+#pragma unroll
+      for (int b = 0; b < NACC; ++b) aph[b] = 0;
       for (int64_t ui = 0; ui < nunits && !*abort_flag; ++ui) {
         const bool ok = emu_walk(
             a,
@@ -800,14 +1018,14 @@ emu_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
               tc::tc_fence_after();
               const uint32_t sa = tc::smem_u32(smem + stage * L::STAGE_BYTES);
               const uint32_t sb = sa + L::A_BYTES;
-              const uint32_t d = tmem_base + acc * EBN;
+              const uint32_t d = tmem_base + acc * BN;
 #pragma unroll
               for (int kk = 0; kk < EBK / 16; ++kk)
                 tc::mma_bf16_pair(d, tc::smem_desc_sw128(sa + kk * 32),
                                   tc::smem_desc_sw128(sb + kk * 32), idesc,
                                   (first && kk == 0) ? 0u : 1u);
               tc::mma_commit_pair(&empty[stage]);
-              if (++stage == E2_STAGES) { stage = 0; ph ^= 1; }
+              if (++stage == S) { stage = 0; ph ^= 1; }
               return true;
             },
             [&] {
@@ -822,12 +1040,7 @@ emu_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
       while (!tc::mbar_try_wait(drain, 0) && clock64() - t0 < tc::kDrainCycles) {
       }
     }
-  } else {
-    uint32_t te[NACC];
-#pragma unroll
-    for (int b = 0; b < NACC; ++b) te[b] = tc::mapa_shared(&tempty[b], 0);
-    emu_epilogue(a, pair, nunits, (int64_t)rank * EBM, 2 * EBM, tmem_base, smem + L::T_OFF,
-                 tfull, te, w, warp, lane);
+  }
   }
   __syncthreads();
   tc::tc_fence_before();
@@ -881,14 +1094,26 @@ dim3 split_a_grid(int64_t rows, int64_t kpad) {
 }
 }  // namespace
 
-long long emu_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_config& cfg) {
+namespace {
+// Bytes of the pair kernel's running totals: at most one 128 x 256 int64 region
+// per CTA of the largest pair grid the problem can use.
+int64_t emu_total_bytes(int64_t m, int64_t n, int sms) {
+  const int64_t tiles = ((m + 2 * EBM - 1) / (2 * EBM)) * ((n + EBN - 1) / EBN);
+  const int64_t pairs = std::min<int64_t>(std::max(1, sms / 2), std::max<int64_t>(tiles, 1));
+  return rup(2 * pairs * (int64_t)EBM * 256 * 8, 256);
+}
+}  // namespace
+
+long long emu_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_config& cfg,
+                              int sms) {
   const int s = emu_slices(cfg);
   const int64_t kp = emu_kpad(k);
   return rup(m * 4, 256) + rup(n * 4, 256) + rup((int64_t)s * m * kp * 2, 256) +
-         rup((int64_t)s * n * kp * 2, 256) + 256;
+         rup((int64_t)s * n * kp * 2, 256) + emu_total_bytes(m, n, sms) + 256;
 }
 
-EmuWorkspace emu_carve(void* ws, int64_t m, int64_t n, int64_t k, const cosma_config& cfg) {
+EmuWorkspace emu_carve(void* ws, int64_t m, int64_t n, int64_t k, const cosma_config& cfg,
+                       int sms) {
   const int s = emu_slices(cfg);
   const int64_t kp = emu_kpad(k);
   uint8_t* w = static_cast<uint8_t*>(ws);
@@ -901,6 +1126,8 @@ EmuWorkspace emu_carve(void* ws, int64_t m, int64_t n, int64_t k, const cosma_co
   w += rup((int64_t)s * m * kp * 2, 256);
   e.SB = w;
   w += rup((int64_t)s * n * kp * 2, 256);
+  e.T = reinterpret_cast<long long*>(w);
+  w += emu_total_bytes(m, n, sms);
   e.lockstep = reinterpret_cast<unsigned int*>(w);
   e.row_pitch = EKB;
   return e;
@@ -973,13 +1200,16 @@ int emu_prepare_b(const double* B, int64_t k, int64_t n, int64_t ldb, int trans,
 int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cosma_config& cfg,
                  const int* eA, const void* SA, int64_t a_slice_rows, const int* eB,
                  const void* SB, int64_t b_slice_rows, double* C, int64_t ldc, double alpha,
-                 double beta_c, unsigned int* lockstep, int* status, long long wait_limit,
-                 cudaStream_t st) {
+                 double beta_c, long long* T, unsigned int* lockstep, int* status,
+                 long long wait_limit, cudaStream_t st) {
   const int s = emu_slices(cfg), beta = emu_bits(cfg);
   const Sched sch = sched_from_plan(m, n, k, p);
   const bool pairs = sch.tile_m == 2 * EBM;
-  if ((sch.tile_m != EBM && !pairs) || sch.tile_n != EBN || sch.k_block != EBK || sch.pk != 1)
+  if (pairs ? (sch.tile_n != 256 && sch.tile_n != 128) : (sch.tile_m != EBM || sch.tile_n != EBN))
     return COSMA_ERR_INVALID_ARG;
+  if (sch.k_block != EBK || sch.pk != 1) return COSMA_ERR_INVALID_ARG;
+  // the running totals of the pair kernel: one 128 x tile_n int64 region per CTA
+  if (pairs && (2LL * sch.ctas > (long long)p.sms || !T)) return COSMA_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(C) & 7) return COSMA_ERR_INVALID_ARG;
   // COSMA_EMU_LOCKSTEP in the environment (read once): unset or 1 = lock-step
   // rounds under a cooperative launch; 0 = pairs free; 2 = lock-step rounds under
@@ -997,7 +1227,7 @@ int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cos
   CUtensorMap ta, tb;
   int rc = encode_tmap_slices(&ta, SA, m, k, s, a_slice_rows, EBM);
   if (rc != COSMA_OK) return rc;
-  rc = encode_tmap_slices(&tb, SB, n, k, s, b_slice_rows, pairs ? EBN / 2 : EBN);
+  rc = encode_tmap_slices(&tb, SB, n, k, s, b_slice_rows, pairs ? sch.tile_n / 2 : EBN);
   if (rc != COSMA_OK) return rc;
 
   EmuArgs args;
@@ -1026,15 +1256,37 @@ int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cos
     while (ck > 1 && (double)ck * EBK > lim) --ck;
     args.chunk_kb = (int)ck;
   }
+  // Fixed-point base of the pair kernel's running total: every super-chunk adds
+  // at most sum_{l=2}^{s+1} (l - 1) chunk 2^(2 beta - 2) 2^(beta (s + 1 - l)); the
+  // smallest base that keeps the sum over all chunks below 2^62.
+  args.T = T;
+  {
+    double per_chunk = 0.0;
+    for (int l = 2; l <= s + 1; ++l)
+      per_chunk += (double)(l - 1) * std::ldexp(1.0, 2 * beta - 2 + beta * (s + 1 - l));
+    per_chunk *= (double)args.chunk_kb * EBK;
+    const double bound = per_chunk * (double)((sch.kbt + args.chunk_kb - 1) / args.chunk_kb);
+    int base = 0;
+    while (std::ldexp(bound, -base) >= std::ldexp(1.0, 62)) ++base;
+    args.t_base = base;
+  }
   cudaError_t le;
   if (pairs) {
-    const cudaError_t attr2 = cudaFuncSetAttribute(
-        emu_gemm_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, E2Layout::ALLOC);
+    auto kern = sch.tile_n == 256 ? emu_pair_kernel<256> : emu_pair_kernel<128>;
+    const int alloc = sch.tile_n == 256 ? PairLayout<256>::ALLOC : PairLayout<128>::ALLOC;
+    {
+      // the warps' register split draws on what the launch allocates
+      cudaFuncAttributes fa;
+      if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return (int)cudaGetLastError();
+      if (fa.numRegs < kPairMinRegs) return COSMA_ERR_UNSUPPORTED;
+    }
+    const cudaError_t attr2 =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, alloc);
     if (attr2 != cudaSuccess) return (int)attr2;
     cudaLaunchConfig_t cfgl = {};
     cfgl.gridDim = dim3((unsigned)(2 * sch.ctas));
-    cfgl.blockDim = dim3(320);
-    cfgl.dynamicSmemBytes = E2Layout::ALLOC;
+    cfgl.blockDim = dim3(kPairThreads);
+    cfgl.dynamicSmemBytes = alloc;
     cfgl.stream = st;
     cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1052,12 +1304,12 @@ int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cos
         cudaMemsetAsync(lockstep_counter, 0, sizeof(unsigned int), st) != cudaSuccess)
       return (int)cudaGetLastError();
     prof_mark(st, true);
-    le = cudaLaunchKernelEx(&cfgl, emu_gemm_pair_kernel, ta, tb, args);
+    le = cudaLaunchKernelEx(&cfgl, kern, ta, tb, args);
     if (le != cudaSuccess && lockstep_counter) {
       cudaGetLastError();
       cfgl.numAttrs = 1;
       args.lockstep = nullptr;
-      le = cudaLaunchKernelEx(&cfgl, emu_gemm_pair_kernel, ta, tb, args);
+      le = cudaLaunchKernelEx(&cfgl, kern, ta, tb, args);
     }
     prof_mark(st, false);
   } else {
@@ -1079,12 +1331,12 @@ int launch_emu_bf16(const GemmArgs& g, const cosma_plan& p, const cosma_config& 
   int rc = emu_check_config(cfg);
   if (rc != COSMA_OK) return rc;
   const int64_t m = g.m, n = g.n, k = g.k;
-  if (emu_workspace_bytes(m, n, k, cfg) > ws_bytes) return COSMA_ERR_NO_WORKSPACE;
+  if (emu_workspace_bytes(m, n, k, cfg, p.sms) > ws_bytes) return COSMA_ERR_NO_WORKSPACE;
   if ((emu_kpad(k) + 31) / 32 > 65535) return COSMA_ERR_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(g.A) & 7) || (reinterpret_cast<uintptr_t>(g.B) & 7) ||
       (reinterpret_cast<uintptr_t>(g.C) & 7))
     return COSMA_ERR_INVALID_ARG;
-  const EmuWorkspace e = emu_carve(ws, m, n, k, cfg);
+  const EmuWorkspace e = emu_carve(ws, m, n, k, cfg, p.sms);
   rc = emu_prepare_a(static_cast<const double*>(g.A), m, k, g.lda, g.trans_a, e.eA, e.SA, m,
                      status, cfg, st);
   if (rc != 0) return rc;
@@ -1092,7 +1344,7 @@ int launch_emu_bf16(const GemmArgs& g, const cosma_plan& p, const cosma_config& 
                      status, cfg, st);
   if (rc != 0) return rc;
   return emu_multiply(m, n, k, p, cfg, e.eA, e.SA, m, e.eB, e.SB, n, static_cast<double*>(g.C),
-                      g.ldc, g.alpha, g.beta, e.lockstep, status, wait_limit, st);
+                      g.ldc, g.alpha, g.beta, e.T, e.lockstep, status, wait_limit, st);
 }
 
 }  // namespace cosma

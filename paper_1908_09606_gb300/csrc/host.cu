@@ -173,9 +173,9 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
     rc = emu_check_config(ctx.cfg);
     if (rc != COSMA_OK) return rc;
     void* ws = nullptr;
-    rc = lib_scratch(emu_workspace_bytes(m, n, k, ctx.cfg), st, &ws);
+    rc = lib_scratch(emu_workspace_bytes(m, n, k, ctx.cfg, ctx.info.sms), st, &ws);
     if (rc != COSMA_OK) return rc;
-    ew = emu_carve(ws, m, n, k, ctx.cfg);
+    ew = emu_carve(ws, m, n, k, ctx.cfg, ctx.info.sms);
   }
 
   int64_t rcut[kMaxR + 1], ccut[kMaxR + 1];
@@ -253,7 +253,7 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
           rc = emu_multiply(mb, nb, k, p, ctx.cfg, ew.eA + r0,
                             static_cast<uint8_t*>(ew.SA) + (size_t)r0 * ew.row_pitch * 2, m, ew.eB + c0,
                             static_cast<uint8_t*>(ew.SB) + (size_t)c0 * ew.row_pitch * 2, n,
-                            reinterpret_cast<double*>(Cblk), ldc_d, 1.0, 0.0, ew.lockstep,
+                            reinterpret_cast<double*>(Cblk), ldc_d, 1.0, 0.0, ew.T, ew.lockstep,
                             ctx.status, ctx.wait_limit, st);
           if (rc > 0) return COSMA_ERR_CUDA;
           if (rc < 0) return rc;

@@ -92,9 +92,13 @@ extern "C" int cosma_gemm_splitk_static(int64_t m, int64_t n, int64_t k, const v
     return COSMA_ERR_CUDA;
   cudaDeviceGetAttribute(&info.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&info.regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-  cosma_config cfg = {0.03, COSMA_SELECT_ANALYTIC, 0, 0, 0, 0};
+  // The active configuration (cosma_init), read without touching device state.
+  // Planning is analytic: the learned selector runs its forward kernel on
+  // buffers of its own, which this entry does not take.
+  cosma_config cfg;
+  if (cosma_get_config(&cfg) != COSMA_OK) return COSMA_ERR_INVALID_ARG;
   cosma_plan p;
-  int rc = plan_gemm(m, n, k, dtype, COSMA_SELECT_ANALYTIC, info, cfg, &p);
+  int rc = plan_gemm(m, n, k, dtype, COSMA_SELECT_ANALYTIC, info, cfg, &p, false);
   if (rc != COSMA_OK) return rc;
   // Balanced stripes over tiles x k slices.
   const int64_t tiles = ((m + p.tile_m - 1) / p.tile_m) * ((n + p.tile_n - 1) / p.tile_n);

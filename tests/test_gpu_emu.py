@@ -120,15 +120,26 @@ def test_emu_full_size_sampled(shape, kind):
     assert err <= 1e-12, err
 
 
-@pytest.mark.parametrize("cand", [1, 9])
+def _tile_plan(m, n, k, tile):
+    """An emulation plan with the given tile: 'pair256' (256 x 256 on a CTA pair,
+    candidate 1), 'single' (128 x 128 on one SM, candidate 9) or 'pair128' (the
+    256 x 128 pair tile: candidate 1's plan with narrower tiles)."""
+    cosma = lib()
+    p = cosma.cosma_plan_candidate(m, n, k, cosma.COSMA_F64_EMU_BF16, 9 if tile == "single" else 1)
+    assert (p.tile_m, p.tile_n) == ((128, 128) if tile == "single" else (256, 256))
+    if tile == "pair128":
+        p.tile_n = 128
+        p.stages = 9
+    return p
+
+
+@pytest.mark.parametrize("tile", ["pair256", "single", "pair128"])
 @pytest.mark.parametrize("shape", [(128, 128, 64), (300, 257, 999), (513, 129, 2048)])
-def test_emu_pair_and_single_sm_tiles(cand, shape):
-    # candidate 1: 256 x 128 tiles on CTA pairs; candidate 9: 128 x 128 on one SM
+def test_emu_pair_and_single_sm_tiles(tile, shape):
     import torch
     cosma = lib()
     m, n, k = shape
-    p = cosma.cosma_plan_candidate(m, n, k, cosma.COSMA_F64_EMU_BF16, cand)
-    assert p.tile_m == (256 if cand == 1 else 128)
+    p = _tile_plan(m, n, k, tile)
     A, B = device_operands(m, n, k, DT, seed=4)
     C, _ = out_tensor(m, n, DT)
     cosma.gemm(A, B, C, DT, plan=p)
@@ -138,13 +149,15 @@ def test_emu_pair_and_single_sm_tiles(cand, shape):
     assert og.normwise_rel_error(C.cpu().numpy(), og.gemm(Ah, Bh, "dot2")) <= 1e-12
 
 
-@pytest.mark.parametrize("cand", [1, 9])
-def test_emu_long_k_float_float_level_sums(cand):
-    # k > 21845: level sums no longer fit int32, the float-float path runs
+@pytest.mark.parametrize("tile", ["pair256", "single", "pair128"])
+def test_emu_long_k(tile):
+    # 22 super-chunks: the pair kernels' fixed-point base rises to 7 bits (the
+    # lowest level is rounded to it); the single-SM kernel's float-float total
+    # takes 132 merges
     import torch
     cosma = lib()
     m, n, k = 130, 129, 22001
-    p = cosma.cosma_plan_candidate(m, n, k, cosma.COSMA_F64_EMU_BF16, cand)
+    p = _tile_plan(m, n, k, tile)
     A, B = device_operands(m, n, k, DT, seed=8)
     C, _ = out_tensor(m, n, DT)
     cosma.gemm(A, B, C, DT, plan=p)
@@ -204,3 +217,52 @@ def test_emu_equals_the_methods_own_result(slices, bits, shape):
     if slices * bits < 30:
         exact = og.gemm(A, B, "dot2")
         assert np.max(np.abs(C - exact) / absab) > 2.0 ** -36
+
+
+@pytest.mark.parametrize("shape,kind", [((300, 520, 3000), "uniform"), ((513, 260, 1100), "loguniform")])
+def test_emu_pair_tile_widths_agree_bit_for_bit(shape, kind):
+    """Both CTA-pair tiles form the same exact fixed-point running total (level
+    sums are exact integers and the total is integer arithmetic), so 256- and
+    128-column tiles give identical bits, and both meet the oracle bar."""
+    import torch
+    cosma = lib()
+    m, n, k = shape
+    A, B = device_operands(m, n, k, DT, kind=kind, seed=21)
+    out = []
+    for tile in ("pair256", "pair128"):
+        C, _ = out_tensor(m, n, DT)
+        cosma.gemm(A, B, C, DT, plan=_tile_plan(m, n, k, tile))
+        torch.cuda.synchronize()
+        assert cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream) == 0
+        out.append(C.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
+    Ah, Bh = host_operands(m, n, k, DT, kind=kind, seed=21)
+    assert og.normwise_rel_error(out[0], og.gemm(Ah, Bh, "dot2")) <= 1e-12
+
+
+@pytest.mark.parametrize("tile", ["pair256", "single", "pair128"])
+def test_emu_bounded_wait_reports_timeout_and_context_survives(tile):
+    """A wait limit of one cycle makes the emulation kernel's waits run out (the
+    CTA pairs' lock-step rounds included): it must record COSMA_ERR_TIMEOUT, let
+    the copies and products in flight land, free its tensor memory and exit; the
+    next call with the default limit must be correct on the same context."""
+    import torch
+    cosma = lib()
+    m, n, k = 1024, 1024, 4096
+    A, B = device_operands(m, n, k, DT, seed=6)
+    try:
+        assert cosma.cosma_init(wait_limit=1) == 0
+        C, _ = out_tensor(m, n, DT)
+        cosma.gemm(A, B, C, DT, plan=_tile_plan(m, n, k, tile))
+        st = cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream)
+        assert st == cosma.COSMA_ERR_TIMEOUT
+    finally:
+        assert cosma.cosma_init(wait_limit=0) == 0
+    C, _ = out_tensor(m, n, DT)
+    cosma.gemm(A, B, C, DT, plan=_tile_plan(m, n, k, tile))
+    torch.cuda.synchronize()
+    assert cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream) == 0
+    rr, cc = sample_indices(m, n, 256, seed=3)
+    ref, _, _, _, _ = sampled_reference(m, n, k, DT, rr, cc, seed=6)
+    got = C[torch.as_tensor(rr, device="cuda"), torch.as_tensor(cc, device="cuda")].cpu().numpy()
+    assert og.normwise_rel_error(got, ref) <= 1e-12
