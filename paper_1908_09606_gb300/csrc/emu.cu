@@ -484,12 +484,16 @@ __device__ __forceinline__ void emu_epilogue(const EmuArgs& a, int unit_cta, int
 // Same iteration order for the producer and the MMA issuer: calls body(q, lvl,
 // kb) for every k-block of every pair, and group_begin / group_end around the
 // exact groups.  Returns false as soon as a callback does (abort).
-template <class GroupBegin, class Body, class GroupEnd>
-__device__ __forceinline__ bool emu_walk(const EmuArgs& a, GroupBegin group_begin, Body body,
-                                         GroupEnd group_end) {
+// chunk_begin(c) runs before super-chunk c (0, 1, ...) of the unit.
+template <class ChunkBegin, class GroupBegin, class Body, class GroupEnd>
+__device__ __forceinline__ bool emu_walk_chunks(const EmuArgs& a, ChunkBegin chunk_begin,
+                                                GroupBegin group_begin, Body body,
+                                                GroupEnd group_end) {
   const int64_t kbt = a.sch.kbt;
   const int top = a.s + 1;
-  for (int64_t sc0 = 0; sc0 < kbt; sc0 += a.chunk_kb) {
+  int64_t chunk = 0;
+  for (int64_t sc0 = 0; sc0 < kbt; sc0 += a.chunk_kb, ++chunk) {
+    if (!chunk_begin(chunk)) return false;
     const int64_t sc1 = min(sc0 + (int64_t)a.chunk_kb, kbt);
     for (int lvl = top; lvl >= 2; --lvl) {
       const int p = lvl - 1;
@@ -508,6 +512,12 @@ __device__ __forceinline__ bool emu_walk(const EmuArgs& a, GroupBegin group_begi
     }
   }
   return true;
+}
+
+template <class GroupBegin, class Body, class GroupEnd>
+__device__ __forceinline__ bool emu_walk(const EmuArgs& a, GroupBegin group_begin, Body body,
+                                         GroupEnd group_end) {
+  return emu_walk_chunks(a, [](int64_t) { return true; }, group_begin, body, group_end);
 }
 
 struct ELayout {
@@ -675,8 +685,8 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 constexpr int kPairThreads = 384;
 // Registers per thread the pair kernel's register split assumes at launch: the
 // register file is split by SM quarter, and on each quarter the control warp's
-// 56 plus two epilogue warps' 216 must fit in the three warps' launch share,
-// 56 + 2 x 216 <= 3 x 168.
+// 56 plus two epilogue warps' 224 must fit in the three warps' launch share,
+// 56 + 2 x 224 = 3 x 168.
 constexpr int kPairMinRegs = 168;
 
 template <int BN>
@@ -729,6 +739,10 @@ __device__ __forceinline__ void emu_pair_epilogue(const EmuArgs& a, int pair, in
   const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
   const uint32_t col_lo = (uint32_t)(HC * h);
   long long* Tt = a.T + (int64_t)blockIdx.x * (128 * BN) + ((int64_t)h * HC * 4 + q4) * 32 + lane;
+  // The running totals (about 39 MB for all CTAs) stay in L2 between merges
+  // while the slice panels stream past them: their lines are the last to go.
+  uint64_t keep;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
   uint32_t acc = 0;
   uint32_t tph[NACC];
 #pragma unroll
@@ -782,11 +796,14 @@ __device__ __forceinline__ void emu_pair_epilogue(const EmuArgs& a, int pair, in
             // relaxed gpu-scope store, reductions and read-back: same-address
             // operations of one thread stay in program order (coherence)
             if (!stored)
-              asm volatile("st.relaxed.gpu.global.s64 [%0], %1;" ::"l"(Tt + (c + j) * 128), "l"(x)
+              asm volatile("st.relaxed.gpu.global.L2::cache_hint.s64 [%0], %1, %2;" ::"l"(
+                               Tt + (c + j) * 128),
+                           "l"(x), "l"(keep)
                            : "memory");
             else
-              asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(Tt + (c + j) * 128),
-                           "l"(x)
+              asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(
+                               Tt + (c + j) * 128),
+                           "l"(x), "l"(keep)
                            : "memory");
           }
         }
@@ -814,7 +831,9 @@ __device__ __forceinline__ void emu_pair_epilogue(const EmuArgs& a, int pair, in
       long long tv[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j)
-        asm volatile("ld.relaxed.gpu.global.s64 %0, [%1];" : "=l"(tv[j]) : "l"(Tf + (c + j) * 128)
+        asm volatile("ld.relaxed.gpu.global.L2::cache_hint.s64 %0, [%1], %2;"
+                     : "=l"(tv[j])
+                     : "l"(Tf + (c + j) * 128), "l"(keep)
                      : "memory");
       int eb[8];
 #pragma unroll
@@ -908,7 +927,7 @@ emu_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   // hold BN / 2 level sums each.  The launch provides kPairMinRegs per thread
   // (the host checks before launching).
   if (warp >= 4) {
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 216;\n" ::: "memory");
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 224;\n" ::: "memory");
     uint32_t te[NACC];
 #pragma unroll
     for (int b = 0; b < NACC; ++b) te[b] = tc::mapa_shared(&tempty[b], 0);
@@ -923,36 +942,43 @@ emu_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       uint32_t full_cl[S];
 #pragma unroll
       for (int s = 0; s < S; ++s) full_cl[s] = tc::mapa_shared(&full[s], 0);
-      // Lock-step rounds (cooperative launches only): the leader's producer of
-      // every pair announces each issued unit on a global counter and does not
-      // start round r + 1 before all pairs have issued round r, so concurrent
-      // pairs stream the same slice panels through L2.
+      // Lock-step super-chunks (cooperative launches only): the leader's producer
+      // of every pair counts each super-chunk it starts on a global counter and
+      // starts super-chunk g (in the order rounds x super-chunks) only once every
+      // pair has started g - 1, so concurrent pairs stream the same slice panels
+      // through L2.  A pair without a unit in a round counts that round's
+      // super-chunks at once.
       const int npairs = (int)(gridDim.x >> 1);
       const int64_t total = a.sch.mt * a.sch.nt;
       const int64_t rounds = a.lockstep ? (total + npairs - 1) / npairs : nunits;
-      for (int64_t ui = 0; ui < rounds && !*abort_flag; ++ui) {
-        if (a.lockstep && leader && ui > 0) {
-          const unsigned int want = (unsigned int)(ui * npairs);
+      const int64_t nch = (a.sch.kbt + a.chunk_kb - 1) / a.chunk_kb;
+      auto chunk_tick = [&](int64_t g) -> bool {
+        if (!(a.lockstep && leader)) return true;
+        if (g >= 1) {
+          const unsigned int want = (unsigned int)(g * npairs);
           const long long t0 = clock64();
           while (*reinterpret_cast<volatile unsigned int*>(a.lockstep) < want) {
-            if (*abort_flag) break;
+            if (*abort_flag) return false;
             if (clock64() - t0 > w.limit) {
               atomicCAS(a.status, 0, (int)COSMA_ERR_TIMEOUT);
               *abort_flag = 1;
-              break;
+              return false;
             }
-            __nanosleep(256);
+            __nanosleep(128);
           }
           __threadfence();
-          if (*abort_flag) break;
         }
+        atomicAdd(a.lockstep, 1u);
+        return true;
+      };
+      for (int64_t ui = 0; ui < rounds && !*abort_flag; ++ui) {
         if (ui >= nunits) {
-          if (a.lockstep && leader) atomicAdd(a.lockstep, 1u);
+          if (a.lockstep && leader) atomicAdd(a.lockstep, (unsigned int)nch);
           continue;
         }
         const Unit u = unit_of_cta(a.sch, pair, ui);
-        const bool ok = emu_walk(
-            a, [] { return true; },
+        const bool ok = emu_walk_chunks(
+            a, [&](int64_t c) { return chunk_tick(ui * nch + c); }, [] { return true; },
             [&](int q, int lvl, int64_t kb, bool) {
               if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) return false;
               if (leader) tc::mbar_arrive_expect_tx(&full[stage], 2 * L::STAGE_BYTES);
@@ -966,7 +992,6 @@ emu_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
               return true;
             },
             [] {});
-        if (a.lockstep && leader) atomicAdd(a.lockstep, 1u);
         if (!ok) break;
       }
       // The odd CTA's copies signal the leader's barriers: it reports how many
@@ -1246,13 +1271,16 @@ int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cos
   args.lockstep = nullptr;
   args.alpha = alpha;
   args.beta_c = beta_c;
-  // Super-chunk: short enough for the slice panels of a wave of tiles to stay in
-  // L2 across all levels (1024 k: at 16384^3 half the DRAM bytes of 2048, at the
-  // same time; 512 would double the merges again), and for every level sum of a
-  // chunk to fit in int32 exactly (at most s pairs x chunk x 2^(2 beta - 2)).
+  // Super-chunk: every level sum of a chunk must fit in int32 exactly (at most s
+  // pairs x chunk x 2^(2 beta - 2)).  Each chunk ends in s merges of the running
+  // total.  Single-SM tiles: 1024 k, short enough for the slice panels of a wave
+  // of tiles to stay in L2 across all levels.  CTA pairs: 4096 k -- their merges
+  // are L2 reductions, and fewer of them beat the panels' L2 reuse (one GB300,
+  // square 16384^3: 512 k 66.2, 1024 k 72.6, 2048 k 77.6, 4096 k 78.3-79.6,
+  // 16384 k 80.3 TFLOP/s; largeK 4096 x 4096 x 2^20: 4096 k 64.3, 16384 k 62.7).
   {
     const double lim = 2147483647.0 / ((double)s * std::ldexp(1.0, 2 * beta - 2));
-    int64_t ck = 1024 / EBK;
+    int64_t ck = (pairs ? 4096 : 1024) / EBK;
     while (ck > 1 && (double)ck * EBK > lim) --ck;
     args.chunk_kb = (int)ck;
   }

@@ -151,9 +151,9 @@ def test_emu_pair_and_single_sm_tiles(tile, shape):
 
 @pytest.mark.parametrize("tile", ["pair256", "single", "pair128"])
 def test_emu_long_k(tile):
-    # 22 super-chunks: the pair kernels' fixed-point base rises to 7 bits (the
-    # lowest level is rounded to it); the single-SM kernel's float-float total
-    # takes 132 merges
+    # k = 22001: six 4096-deep super-chunks on the pair kernels, whose fixed-point
+    # base rises to 7 bits (the lowest level is rounded to it); 22 1024-deep ones
+    # on the single-SM kernel, whose float-float total takes 132 merges
     import torch
     cosma = lib()
     m, n, k = 130, 129, 22001
