@@ -54,7 +54,11 @@ extern "C" {
  * the tensor cores (Ozaki-style splitting) and recombined in high precision;
  * k <= 2^21 - 2048 (1023 slice panels of 2048; else COSMA_ERR_UNSUPPORTED
  * before any launch or allocation).
- * F64_EMU_INT8 is reserved (returns COSMA_ERR_UNSUPPORTED).
+ * F64_EMU_INT8 returns COSMA_ERR_UNSUPPORTED: the INT8-slice variant of the
+ * emulation has no fast path on this GPU (sm_103a) -- the tensor-core MMA has
+ * no integer kind there (ptxas rejects tcgen05.mma .kind::i8 for sm_103a), and
+ * the legacy mma.sync s8 path measured 151 TOPS on one GB300 against 2300
+ * TFLOP/s of 256-wide bf16 tcgen05 MMAs (6.6 %), far below the bf16 slices.
  * F32_EMU_TF32: A, B, C are fp32; each operand is split into TF32 hi and lo
  * parts and C = A_hi B_hi + A_hi B_lo + A_lo B_hi is accumulated in fp32 on the
  * tensor cores, 64-deep k segments summed in fp32 round to nearest (elementwise
@@ -157,7 +161,9 @@ int cosma_get_config(cosma_config* out);
 
 /* Lends the library a caller-owned device buffer as workspace (split-k
  * partials, emulation slices, grouped tables).  The caller keeps ownership and
- * must keep it alive while calls that use it are in flight.  bytes == 0
+ * must keep it alive while calls that use it are in flight.  There is no
+ * stream argument: one lent buffer serves calls on every stream, so calls that
+ * use it must be ordered (one stream, or events between streams).  bytes == 0
  * returns to the library-owned arena, which grows with cudaMalloc outside
  * stream capture; inside capture a call that needs more than is available
  * returns COSMA_ERR_NO_WORKSPACE.  dptr must be 256-byte aligned. */

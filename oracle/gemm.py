@@ -4,8 +4,8 @@ Test infrastructure only (see the package docstring).  The arithmetic lives in
 gemm_oracle.c; this module compiles it with gcc (no fused multiply-add
 contraction, no fast-math) and calls it through ctypes.
 
-listing1 (liblisting1_cpu.so, OpenMP) runs the same chain under the tiled
-schedule of Listing 1 on the host cores for the benchmark's CPU timing; it is
+tiled (libtiled_cpu.so, OpenMP) runs the same chain under the tiled
+sequential schedule of Sec. 5.2 on the host cores for the benchmark's CPU timing; it is
 pinned by bit-equality with the naive loop.
 
 Pins (tests/test_oracle_gemm.py): exact integer products against Python
@@ -27,10 +27,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gemm_oracle.c")
-_SRC_L1 = os.path.join(_HERE, "listing1_cpu.c")
+_SRC_L1 = os.path.join(_HERE, "tiled_cpu.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libgemm_oracle.so")
-_LIB_L1 = os.path.join(_BUILD, "liblisting1_cpu.so")
+_LIB_L1 = os.path.join(_BUILD, "libtiled_cpu.so")
 _lock = threading.Lock()
 _lib = None
 _lib_l1 = None
@@ -47,7 +47,7 @@ def _compile(src, out, flags):
 
 
 def build():
-    """Compile the C oracle and the host Listing-1 loop (idempotent; rebuilds
+    """Compile the C oracle and the host tiled loop (idempotent; rebuilds
     when a source is newer)."""
     os.makedirs(_BUILD, exist_ok=True)
     _compile(_SRC, _LIB, ["-O2"])
@@ -98,10 +98,10 @@ def gemm(A, B, method="dot2"):
     return C
 
 
-def listing1(A, B, a, b, threads=0):
-    """C = A B by the paper's sequential schedule (Listing 1) on the host cores:
-    a x b C tiles, k outer products each, tiles spread over OpenMP threads
-    (threads = 0: all).  Every entry is the chain t = 0..k-1, so the result
+def tiled(A, B, a, b, threads=0):
+    """C = A B by the sequential schedule of Sec. 5.2 on the host cores: a x b
+    blocks of C resident while k streams past them, blocks spread over OpenMP
+    threads (threads = 0: all).  Every entry is the chain t = 0..k-1, so the result
     equals gemm(A, B, 'naive') bit for bit.  Returns (C, threads used)."""
     global _lib_l1
     A, B = _f64(A), _f64(B)
@@ -114,17 +114,17 @@ def listing1(A, B, a, b, threads=0):
             lib = ctypes.CDLL(_LIB_L1)
             d = ctypes.POINTER(ctypes.c_double)
             i64 = ctypes.c_int64
-            lib.listing1_gemm.argtypes = [i64, i64, i64, d, i64, d, i64, d, i64, i64, i64,
+            lib.tiled_gemm.argtypes = [i64, i64, i64, d, i64, d, i64, d, i64, i64, i64,
                                           ctypes.c_int]
-            lib.listing1_gemm.restype = ctypes.c_int
+            lib.tiled_gemm.restype = ctypes.c_int
             _lib_l1 = lib
     C = np.zeros((m, n), dtype=np.float64)
     used = 0
     if m and n:
-        used = _lib_l1.listing1_gemm(m, n, k, _ptr(A), max(k, 1), _ptr(B), max(n, 1), _ptr(C),
+        used = _lib_l1.tiled_gemm(m, n, k, _ptr(A), max(k, 1), _ptr(B), max(n, 1), _ptr(C),
                                      max(n, 1), int(a), int(b), int(threads))
         if used < 1:
-            raise MemoryError("listing1: tile buffer allocation failed")
+            raise MemoryError("tiled: block buffer allocation failed")
     return C, used
 
 

@@ -728,7 +728,11 @@ int grouped_gemm(int count, const cosma_problem* problems, int dtype, const Devi
   const int tile = pick_tile(count, problems, dtype, requested_tile);
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusNone;
-  Table snap;  // the launch reads a copy taken under the lock, not the shared slot
+  // The launch reads a copy of the slot's host-side fields taken under the lock,
+  // so another host thread rebuilding the slot cannot tear them mid-read.  The
+  // device tables those fields point to are not protected by the copy: grouped
+  // calls must not overlap across streams (include/cosma.h).
+  Table snap;
   int rc;
   {
     std::lock_guard<std::mutex> lock(g_tab_mu);

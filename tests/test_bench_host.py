@@ -1,4 +1,4 @@
-"""Host-side pieces of bench.py, on the CPU: the step statistics, the Listing-1
+"""Host-side pieces of bench.py, on the CPU: the step statistics, the tiled
 host timing, the I/O report's Theorem-1 figures and the reference arm's line."""
 import math
 import os
@@ -21,13 +21,13 @@ def test_step_stats_median_min_and_t_interval():
     assert "ci95_ms" not in bench.step_stats([3.0])
 
 
-def test_listing1_sample_times_the_tiled_product():
+def test_tiled_sample_times_the_tiled_product():
     import torch
     import bench
     rng = np.random.default_rng(1)
     A = torch.tensor(rng.uniform(-1, 1, (300, 64)))
     B = torch.tensor(rng.uniform(-1, 1, (64, 200)))
-    fl, dt, r, used, a, b = bench.listing1_sample(A, B, 0.01)
+    fl, dt, r, used, a, b = bench.tiled_sample(A, B, 0.01)
     assert (a, b) == (180, 181)         # FindSeqSchedule at S = 32768
     assert r == 200 and used >= 1 and dt > 0
     assert math.isclose(fl, 2.0 * r * r * 64 / dt)

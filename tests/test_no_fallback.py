@@ -101,7 +101,7 @@ def test_bench_reaches_the_oracle_only_in_its_cpu_legs():
     for node in ast.walk(tree):
         for child in ast.iter_child_nodes(node):
             parents[child] = node
-    helpers = {"oracle_sample", "listing1_sample", "grouped_oracle_sample", "run_reference"}
+    helpers = {"oracle_sample", "tiled_sample", "grouped_oracle_sample", "run_reference"}
     found = 0
     for node in ast.walk(tree):
         names = []
@@ -124,7 +124,7 @@ def test_bench_reaches_the_oracle_only_in_its_cpu_legs():
     # and the CPU-timing helpers are called only from those places too
     for node in ast.walk(tree):
         if not (isinstance(node, ast.Call) and isinstance(node.func, ast.Name)
-                and node.func.id in ("oracle_sample", "listing1_sample",
+                and node.func.id in ("oracle_sample", "tiled_sample",
                                      "grouped_oracle_sample")):
             continue
         p, ok = parents.get(node), False

@@ -220,15 +220,15 @@ def test_zgemm_alpha_zero_beta_zero():
 
 @pytest.mark.parametrize("shape,ab", [((37, 53, 29), (8, 8)), ((100, 64, 300), (17, 33)),
                                       ((5, 7, 1), (2, 3)), ((64, 96, 0), (16, 16))])
-def test_listing1_equals_naive_bit_for_bit(shape, ab):
-    """The tiled schedule (Listing 1) forms every entry by the same chain
+def test_tiled_equals_naive_bit_for_bit(shape, ab):
+    """The tiled schedule of Sec. 5.2 forms every entry by the same chain
     t = 0..k-1 as the naive loop, so the two agree exactly, ragged tiles included."""
     m, n, k = shape
     rng = np.random.default_rng(7)
     A = rng.uniform(-1, 1, (m, k))
     B = rng.uniform(-1, 1, (k, n))
-    C, used = og.listing1(A, B, *ab)
+    C, used = og.tiled(A, B, *ab)
     assert used >= 1
     assert np.array_equal(C, og.gemm(A, B, "naive"))
-    C1, used1 = og.listing1(A, B, *ab, threads=1)
+    C1, used1 = og.tiled(A, B, *ab, threads=1)
     assert used1 == 1 and np.array_equal(C1, C)
