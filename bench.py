@@ -735,6 +735,18 @@ def main():
         rows = slice(0, m, max(1, m // 64))
         diff = float((Ch[rows].double() - C[rows].cpu().double()).abs().max())
         ems = e0.elapsed_time(e1)
+        # one more call, outside the timed region, with the library's phase events on
+        phases = None
+        if hasattr(cosma, "cosma_profile_host"):
+            cosma.cosma_profile_enable(True)
+            try:
+                host_step()
+                phases = {kk: (round(v, 2) if isinstance(v, float) else v)
+                          for kk, v in cosma.cosma_profile_host().items()}
+            finally:
+                cosma.cosma_profile_enable(False)
+                cosma.cosma_profile_read()
+            torch.cuda.synchronize()
         tt = torch.tensor([ems], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -745,6 +757,7 @@ def main():
                "d2h_bytes_per_step": m * n * C.element_size(), "steps": e_steps,
                "api": "cosma_gemm_host (page-locked host A, B, C)",
                "copy_gbs": {kk: round(v, 1) for kk, v in rates.items()},
+               "phases_ms": phases,
                "max_abs_diff_vs_device_path": diff}
         del Ah, Bh, Ch
 

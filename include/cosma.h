@@ -387,6 +387,18 @@ int cosma_profile_enable(int on);
  * milliseconds and their number, and clears them.  Either pointer may be NULL. */
 int cosma_profile_read(double* main_kernel_ms, long long* launches);
 
+/* Phases of the last cosma_gemm_host call on the current device made while
+ * profiling was enabled (and not under stream capture), in milliseconds of
+ * device time: phases[0] the whole call, [1] the head (until the first block
+ * product starts: the first blocks' host->device copies and preparation), [2]
+ * the block products together, [3] the tail (after the last block product: the
+ * last C block's device->host copy), [4] the host->device copies (call start to
+ * the last copy landed), [5] the number of block products.  phases is a HOST
+ * array of `count` doubles; at most 6 are written.  Waits for that call's end.
+ * Returns the number written, or COSMA_ERR_INVALID_ARG if no such call was
+ * recorded (or bad arguments), COSMA_ERR_CUDA without a device. */
+int cosma_profile_host(double* phases, int count);
+
 /* ---- status ----------------------------------------------------------- */
 
 /* Synchronises `stream`, then reads and clears the device status word of the

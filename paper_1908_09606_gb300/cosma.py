@@ -91,6 +91,7 @@ SIGNATURES = [
     ("cosma_launch_count", _LL, []),
     ("cosma_profile_enable", _INT, [_INT]),
     ("cosma_profile_read", _INT, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_LL)]),
+    ("cosma_profile_host", _INT, [ctypes.POINTER(ctypes.c_double), _INT]),
     ("cosma_plan_candidate", _INT, [_I64, _I64, _I64, _INT, _INT, ctypes.POINTER(cosma_plan)]),
     ("cosma_selector_features", _INT, [_I64, _I64, _I64, _INT, ctypes.POINTER(ctypes.c_float)]),
     ("cosma_mlp_forward", _INT, [_INT, _VP, _VP, _VP, _VP]),
@@ -309,6 +310,22 @@ def cosma_profile_read():
     ms, n = ctypes.c_double(), ctypes.c_longlong()
     _check(load().cosma_profile_read(ctypes.byref(ms), ctypes.byref(n)), "cosma_profile_read")
     return ms.value, n.value
+
+
+HOST_PHASES = ("total_ms", "head_ms", "block_products_ms", "tail_ms", "copy_in_ms", "blocks")
+
+
+def cosma_profile_host():
+    """Phases of the last profiled cosma_gemm_host call, as a dict keyed by
+    HOST_PHASES (milliseconds; 'blocks' is the number of block products)."""
+    buf = (ctypes.c_double * len(HOST_PHASES))()
+    n = load().cosma_profile_host(buf, len(HOST_PHASES))
+    if n < 0:
+        raise CosmaError(n, "cosma_profile_host")
+    out = {name: float(buf[i]) for i, name in enumerate(HOST_PHASES[:n])}
+    if "blocks" in out:
+        out["blocks"] = int(out["blocks"])
+    return out
 
 
 # ---- torch convenience (marshalling only) --------------------------------

@@ -34,6 +34,11 @@ static bool g_prof_on = false;
 static std::vector<cudaEvent_t> g_prof_ev;  // start, stop, start, stop, ...
 static size_t g_prof_used = 0;
 
+bool prof_enabled() {
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  return g_prof_on;
+}
+
 void prof_mark(cudaStream_t st, bool begin) {
   std::lock_guard<std::mutex> lock(g_prof_mu);
   if (!g_prof_on) return;

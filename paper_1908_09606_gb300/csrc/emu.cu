@@ -18,20 +18,22 @@
 //           products; the k loop is cut into groups of that size, and each
 //           group's exact integer sum is drained by the epilogue warps into an
 //           int32 level sum held in registers.  k is walked in super-chunks of
-//           1024 (all levels per chunk), so a level sum stays below 2^31 for any
-//           k and the slice panels a wave of tiles touches stay in L2.  Three
-//           accumulator buffers let the MMAs of the next groups overlap a drain.
-//  K-RECOMB At the end of each (chunk, level) the exact level sum joins a
-//           float-float running total T += 2^(-beta (l - 2)) L (high parts in
-//           shared memory, low parts in tensor memory); after the last chunk
-//           the tile is converted to FP64 and scaled by
-//           2^(sigma_i + tau_j + 2 - 2 beta).
+//           4096 (all levels per chunk), so a level sum stays below 2^31 for any
+//           k.  Two (pair tiles) or four (single-SM tiles) accumulator buffers
+//           let the MMAs of the next groups overlap a drain.
+//  K-RECOMB At the end of each (chunk, level) the exact level sum joins an
+//           exact int64 fixed-point running total kept in global scratch (L2
+//           reductions; see "Running total" below); after the last chunk the
+//           tile is converted to FP64 once, so every kernel and tile shape gives
+//           the same bits: the method's exact result rounded once (levels below
+//           the fixed-point base aside).
 //
-// The C tile (128 x 128 on one SM, or 256 x 128 on a CTA pair with
-// tcgen05.mma.cta_group::2) is the paper's resident a x b tile (Listing 1); the
-// slices of A and B stream through a TMA ring (5 stages single, 6 per CTA of a
-// pair).  Pairs launched cooperatively advance in lock-step rounds (bounded
-// waits) so concurrent tiles read the same slice panels from L2.
+// The C tile (128 x 128 on one SM, or 256 x 256 / 256 x 128 on a CTA pair with
+// tcgen05.mma.cta_group::2) is the resident a x b block of C of the paper's
+// sequential schedule (Sec. 5.2); the slices of A and B stream through a TMA
+// ring (7 stages of 32 KB, 9 of 24 KB for 256 x 128 pairs).  Pairs launched
+// cooperatively advance in lock-step super-chunks (bounded waits) so that
+// concurrent tiles read the same slice panels from L2.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -48,14 +50,13 @@ namespace cosma {
 
 namespace {
 
-constexpr int EBM = 128, EBN = 128, EBK = 64, ESTAGES = 5;
+constexpr int EBM = 128, EBN = 128, EBK = 64, ESTAGES = 7;
 // Slice layout, k-blocked (the paper's blocked data layout, Sec. 7.6): slice q of
 // an operand with R rows is stored as ceil(k / EKB) panels of R x EKB, element
 // (i, t) at ((q nkb + t / EKB) R + i) EKB + t % EKB, zero beyond k.  A TMA box
 // (64 k by 128 rows) then spans 128 rows of 4 KB -- a few pages -- however long
 // k is (row-major slices with k = 2^20 put every row of a box in its own page).
 constexpr int64_t EKB = 2048;
-constexpr int TPITCH = EBN + 1;  // padded row pitch of the running total in shared memory
 constexpr int EMU_MAX_SLICES = 8;
 constexpr int kExpNone = (int)0x80808080;  // memset(0x80) pattern: "no nonzero seen"
 
@@ -275,10 +276,10 @@ __global__ void split_b_kernel(const double* __restrict__ B, int64_t k, int64_t 
 //         for each pair q = 1..p:  for each k-block kb in [c0, c1):
 //           D[acc] (+)= A_q[tile rows, kb] * B_{l-q}[tile cols, kb]
 //       (the group's f32 sums are exact integers: drained into an int32 level sum)
-//     (end of level in the super-chunk: the exact level sum L joins the float-float
-//      running total T += 2^(-beta (l - 2)) L)
-// Super-chunks keep the slice panels a wave of tiles touches small enough to stay in
-// L2 across all levels (each level re-reads the same panels).
+//     (end of level in the super-chunk: the exact level sum L joins the fixed-point
+//      running total, T += L 2^(beta (s + 1 - l) - base))
+// Each level re-reads the super-chunk's slice panels; shorter super-chunks keep
+// them in L2 across the levels at the price of more merges of the running total.
 
 struct EmuArgs {
   Sched sch;           // tiles (128 or 256 rows x 128 columns), order 1, pk = 1
@@ -292,13 +293,10 @@ struct EmuArgs {
   int* status;
   long long wait_limit;
   unsigned int* lockstep;  // cooperative launches: per-unit progress counter (zeroed), else null
-  long long* T;            // pair kernel: per-CTA running totals, 128 x tile_n int64 each
-  int t_base;              // pair kernel: fixed-point base of T (see the pair kernel)
+  long long* T;            // per-CTA running totals, 128 x tile_n int64 each
+  int t_base;              // fixed-point base of T (see "Running total")
   double alpha, beta_c;    // C = alpha A B + beta_c C (C read only when beta_c != 0)
 };
-
-constexpr int NACC = 3;            // accumulator buffers in tensor memory (columns 0..383)
-constexpr uint32_t TL_COL = 384;   // low parts of the running total (columns 384..511)
 
 // One 64 (k) x rows box of slice q at k-block kb and row y of the k-blocked layout.
 __device__ __forceinline__ void tma_load_slice(void* dst, const CUtensorMap* map, uint64_t* bar,
@@ -326,69 +324,76 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
   return scale_slow(x, e);
 }
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
+// Running total (both kernels).  Tensor memory holds only accumulators (512 /
+// BN buffers of BN columns).  The exact level sum of the current super-chunk
+// stays in registers (BN / 2 int32 per epilogue thread), and the running total
+// of the tile is an exact int64 fixed-point number
+// T = sum_chunks sum_l 2^(beta (s + 1 - l) - base) L_l kept
+// in a per-CTA scratch region in global memory: the first merge of a tile
+// stores, later ones are reductions performed in L2, and the thread that made
+// them reads the total back (L2 only) to form the FP64 result,
+// C = T 2^(sigma_i + tau_j + 2 - beta (s + 1) + base).  `base` (host, from k)
+// keeps |T| < 2^62; levels whose weight is below 2^base are rounded to it.
+
+// v 2^sh as an int64 (sh < 0: rounded to nearest, ties up).
+__device__ __forceinline__ long long fx_shift(int v, int sh) {
+  if (sh >= 0) return (long long)v << sh;
+  return ((long long)v + (1LL << (-sh - 1))) >> (-sh);
 }
 
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  e = b - (s - a);
-}
-
-// Epilogue warps (2..9) of K-EMU / K-RECOMB for the units of one CTA (or CTA
-// pair): warp -> tensor-memory lane quadrant q4 = warp % 4 and column half h.
-// Rows of this CTA start at tile_row * tile_rows + row_off.  tempty_addr: cluster
-// addresses of the accumulator-free barriers of the MMA-issuing CTA.  The
-// running total T = Th + Tl keeps Th in shared memory (Tsm) and Tl in tensor
-// memory.
-__device__ __forceinline__ void emu_epilogue(const EmuArgs& a, int unit_cta, int64_t nunits,
-                                             int64_t row_off, int64_t tile_rows,
-                                             uint32_t tmem_base, uint8_t* Tsm, uint64_t* tfull,
-                                             const uint32_t* tempty_addr, const tc::WaitCtx& w,
-                                             int warp, int lane) {
+// Epilogue warps W0 .. W0 + 7 of K-EMU / K-RECOMB for the units of one CTA (or
+// CTA pair): warp -> tensor-memory lane quadrant q4 = warp % 4 and column half
+// h; each thread owns one row and BN / 2 columns of this CTA's 128 rows, which
+// start at row tile_row * TM + row_off.  Its entries of the running total sit
+// at Tt + c * 128 (c = its column), so a warp touches 32 consecutive int64 per
+// column.  tempty_addr: cluster addresses of the accumulator-free barriers of
+// the MMA-issuing CTA.
+template <int BN, int TM, int W0>
+__device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, int64_t nunits,
+                                                int64_t row_off, uint32_t tmem_base,
+                                                uint64_t* tfull, const uint32_t* tempty_addr,
+                                                const tc::WaitCtx& w, int warp, int lane) {
+  constexpr int HC = BN / 2;
+  constexpr int NACC = 512 / BN;
   const int64_t kbt = a.sch.kbt;
   const int top = a.s + 1;
   const int q4 = warp & 3;
-  const int h = (warp - 2) >> 2;
+  const int h = (warp - W0) >> 2;
   const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
-  const uint32_t col_lo = (uint32_t)(64 * h);
-  const uint32_t tl = tmem_base + lane_off + TL_COL + col_lo;
-  float* Th = reinterpret_cast<float*>(Tsm) + (q4 * 32 + lane) * TPITCH + col_lo;
+  const uint32_t col_lo = (uint32_t)(HC * h);
+  long long* Tt = a.T + (int64_t)blockIdx.x * (128 * BN) + ((int64_t)h * HC * 4 + q4) * 32 + lane;
+  // The running totals (about 39 MB for all CTAs) stay in L2 between merges
+  // while the slice panels stream past them: their lines are the last to go.
+  uint64_t keep;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
   uint32_t acc = 0;
-  uint32_t tph[NACC] = {0, 0, 0};
+  uint32_t tph[NACC];
+#pragma unroll
+  for (int b = 0; b < NACC; ++b) tph[b] = 0;
   bool ok = true;
   for (int64_t ui = 0; ui < nunits && ok; ++ui) {
     const Unit u = unit_of_cta(a.sch, unit_cta, ui);
-    int Lv[64];  // exact level sum of the current super-chunk
-    {
-      uint32_t z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-#pragma unroll
-      for (int j = 0; j < 64; ++j) Th[j] = 0.f;
-#pragma unroll
-      for (int c = 0; c < 64; c += 8) tc::tmem_st_32x8(tl + c, z);
-      tc::tmem_wait_st();
-    }
+    int Lv[HC];  // exact level sum of the current super-chunk
+    bool stored = false;
     for (int64_t sc0 = 0; sc0 < kbt && ok; sc0 += a.chunk_kb) {
       const int64_t sc1 = min(sc0 + (int64_t)a.chunk_kb, kbt);
       for (int lvl = top; lvl >= 2 && ok; --lvl) {
         const int gk = group_blocks(a.group_kb, lvl - 1);
-        // 2^(-beta (lvl - 2)): exact power of two
-        const float scale = __int_as_float((127 - a.beta * (lvl - 2)) << 23);
-        for (int64_t c0 = sc0; c0 < sc1; c0 += gk) {
-          if (!tc::mbar_wait(&tfull[acc], tph[acc], w)) { ok = false; break; }
+        // one exact group: its integer sums join Lv (the level's first group sets it)
+        auto drain = [&](auto first_tag) -> bool {
+          constexpr bool kFirst = decltype(first_tag)::value;
+          if (!tc::mbar_wait(&tfull[acc], tph[acc], w)) return false;
           tc::tc_fence_after();
-          const bool first = (c0 == sc0), last = (c0 + gk >= sc1);
+          const uint32_t src = tmem_base + lane_off + acc * BN + col_lo;
 #pragma unroll
-          for (int c = 0; c < 64; c += 8) {
-            uint32_t v[8];
-            tc::tmem_ld_32x8(tmem_base + lane_off + acc * EBN + col_lo + c, v);
+          for (int c = 0; c < HC; c += 16) {
+            uint32_t v[16];
+            tc::tmem_ld_32x16(src + c, v);
             tc::tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < 16; ++j) {
               const int iv = __float2int_rn(__uint_as_float(v[j]));  // exact integer
-              Lv[c + j] = first ? iv : Lv[c + j] + iv;
+              Lv[c + j] = kFirst ? iv : Lv[c + j] + iv;
             }
           }
           tc::tc_fence_before();
@@ -396,60 +401,72 @@ __device__ __forceinline__ void emu_epilogue(const EmuArgs& a, int unit_cta, int
           if (lane == 0) tc::mbar_arrive_remote_relaxed(tempty_addr[acc]);
           tph[acc] ^= 1;
           acc = (acc + 1) == NACC ? 0 : acc + 1;
-          if (last) {
-            // K-RECOMB: T += 2^(-beta (lvl - 2)) L, L split exactly into two floats.
+          return true;
+        };
+        if (!drain(std::true_type{})) { ok = false; break; }
+        for (int64_t c0 = sc0 + gk; c0 < sc1; c0 += gk)
+          if (!drain(std::false_type{})) { ok = false; break; }
+        if (!ok) break;
+        // K-RECOMB: T += L 2^(beta (top - lvl) - base), exactly
+        const int sh = a.beta * (top - lvl) - a.t_base;
+        // (8 columns at a time: each batch's shifted values are sent before the next
+        // is formed, which keeps the 64-bit temporaries few)
 #pragma unroll
-            for (int c = 0; c < 64; c += 8) {
-              uint32_t t[8];
-              tc::tmem_ld_32x8(tl + c, t);
-              tc::tmem_wait_ld();
+        for (int c = 0; c < HC; c += 8) {
 #pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const int li = Lv[c + j];
-                const float lh = (float)li;
-                const float ll = (float)(li - (int)lh);
-                float s, e, nh, nl;
-                two_sum(Th[c + j], lh * scale, s, e);
-                e += __uint_as_float(t[j]) + ll * scale;
-                fast_two_sum(s, e, nh, nl);
-                Th[c + j] = nh;
-                t[j] = __float_as_uint(nl);
-              }
-              tc::tmem_st_32x8(tl + c, t);
-            }
-            tc::tmem_wait_st();
+          for (int j = 0; j < 8; ++j) {
+            const long long x = fx_shift(Lv[c + j], sh);
+            // relaxed gpu-scope store, reductions and read-back: same-address
+            // operations of one thread stay in program order (coherence)
+            if (!stored)
+              asm volatile("st.relaxed.gpu.global.L2::cache_hint.s64 [%0], %1, %2;" ::"l"(
+                               Tt + (c + j) * 128),
+                           "l"(x), "l"(keep)
+                           : "memory");
+            else
+              asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(
+                               Tt + (c + j) * 128),
+                           "l"(x), "l"(keep)
+                           : "memory");
           }
         }
+        stored = true;
       }
     }
     if (!ok) break;
-    // Final FP64 store: C = (Th + Tl) 2^(sigma_i + tau_j + 2 - 2 beta) for this
-    // thread's row, 64 columns.  Each 8-column chunk is formed in the row's lane,
-    // transposed within groups of 8 lanes (three butterfly stages of shuffles:
-    // at stage s, entries whose row and column differ in bit s trade places with
-    // lane ^ s), and written as four 64-byte row segments per instruction
-    // instead of 32 scattered 8-byte ones.
-    const int64_t row0 = u.tile_row * tile_rows + row_off + q4 * 32;  // the warp's first row
+    // Final FP64 store: C = T 2^(sigma_i + tau_j + 2 - beta (s + 1) + base) for this
+    // thread's row, HC columns.  Each 8-column chunk is formed in the row's lane,
+    // transposed within groups of 8 lanes (three butterfly stages of shuffles: at
+    // stage s, entries whose row and column differ in bit s trade places with
+    // lane ^ s), and written as four 64-byte row segments per instruction.
+    const int64_t row0 = u.tile_row * TM + row_off + q4 * 32;
     const int64_t row = row0 + lane;
-    const int64_t cbase = u.tile_col * EBN + col_lo;
+    const int64_t cbase = u.tile_col * BN + col_lo;
     const int ea = row < a.sch.m ? a.eA[row] : kExpNone;
+    const int eoff = 2 - a.beta * top + a.t_base;
     const int l8 = lane & 7, g8 = lane >> 3;
+    // the read-back addresses from an opaque copy of the base, so the compiler does
+    // not keep the merges' per-column addresses live across the loops
+    long long* Tf = Tt;
+    asm volatile("" : "+l"(Tf));
 #pragma unroll
-    for (int c = 0; c < 64; c += 8) {
-      uint32_t tl8[8];
-      tc::tmem_ld_32x8(tl + c, tl8);
+    for (int c = 0; c < HC; c += 8) {
+      long long tv[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        asm volatile("ld.relaxed.gpu.global.L2::cache_hint.s64 %0, [%1], %2;"
+                     : "=l"(tv[j])
+                     : "l"(Tf + (c + j) * 128), "l"(keep)
+                     : "memory");
       int eb[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) eb[j] = cbase + c + j < a.sch.n ? a.eB[cbase + c + j] : kExpNone;
       double v[8];
-      tc::tmem_wait_ld();
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const uint32_t lo = tl8[j];
-        const double val = (double)Th[c + j] + (double)__uint_as_float(lo);
         double x = (ea == kExpNone || eb[j] == kExpNone)
                        ? 0.0
-                       : scale_pow2(val, ea + eb[j] + 2 - 2 * a.beta);
+                       : scale_pow2((double)tv[j], ea + eb[j] + eoff);
         if (a.alpha != 1.0) x *= a.alpha;
         v[j] = x;
       }
@@ -521,11 +538,11 @@ __device__ __forceinline__ bool emu_walk(const EmuArgs& a, GroupBegin group_begi
 }
 
 struct ELayout {
+  static constexpr int NACC = 512 / EBN;                        // accumulator buffers
   static constexpr int A_BYTES = EBM * EBK * 2;
   static constexpr int B_BYTES = EBN * EBK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int T_OFF = ESTAGES * STAGE_BYTES;           // running total, high parts
-  static constexpr int BAR_OFF = T_OFF + EBM * TPITCH * 4;
+  static constexpr int BAR_OFF = ESTAGES * STAGE_BYTES;
   static constexpr int NBARS = 2 * ESTAGES + 2 * NACC + 1;      // full, empty, tfull, tempty, drain
   static constexpr int TOTAL = BAR_OFF + NBARS * 8 + 16;
   static constexpr int ALLOC = TOTAL + 1024;
@@ -535,6 +552,7 @@ __global__ void __launch_bounds__(320, 1)
 emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 EmuArgs a) {
   using L = ELayout;
+  constexpr int NACC = L::NACC;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -611,7 +629,9 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       constexpr uint32_t idesc = tc::idesc_bf16_f32(EBM, EBN);
       int stage = 0;
       uint32_t ph = 0, acc = 0;
-      uint32_t aph[NACC] = {0, 0, 0};
+      uint32_t aph[NACC];
+#pragma unroll
+      for (int b = 0; b < NACC; ++b) aph[b] = 0;
       for (int64_t ui = 0; ui < nunits && !*abort_flag; ++ui) {
         const bool ok = emu_walk(
             a,
@@ -651,7 +671,7 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     uint32_t te[NACC];
 #pragma unroll
     for (int b = 0; b < NACC; ++b) te[b] = tc::mapa_shared(&tempty[b], 0);
-    emu_epilogue(a, cta, nunits, 0, EBM, tmem_base, smem + L::T_OFF, tfull, te, w, warp, lane);
+    emu_fx_epilogue<EBN, EBM, 2>(a, cta, nunits, 0, tmem_base, tfull, te, w, warp, lane);
   }
   __syncthreads();
   if (warp == 1) {
@@ -670,16 +690,6 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 // cores at their full rate per clock (N = 128 ones reach about 81 % of it), and
 // per SM an MMA step reads 8 KB of operands for 128 x 256 x 16 products.
 //
-// Tensor memory holds only accumulators (512 / BN buffers of BN columns).  The
-// exact level sum of the current super-chunk stays in registers (BN / 2 int32
-// per epilogue thread), and the running total of the tile is an exact int64
-// fixed-point number T = sum_chunks sum_l 2^(beta (s + 1 - l) - base) L_l kept
-// in a per-CTA scratch region in global memory: the first merge of a tile
-// stores, later ones are reductions performed in L2, and the thread that made
-// them reads the total back (L2 only) to form the FP64 result,
-// C = T 2^(sigma_i + tau_j + 2 - beta (s + 1) + base).  `base` (host, from k)
-// keeps |T| < 2^62; levels whose weight is below 2^base are rounded to it.
-
 // Threads of the pair kernel: warps 0-3 (producer, MMA issuer, two idle), one
 // on each SM quarter, and the epilogue warps 4-11, two on each quarter.
 constexpr int kPairThreads = 384;
@@ -713,166 +723,6 @@ __device__ __forceinline__ void tma_load_slice_pair(void* dst, const CUtensorMap
       "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"((int32_t)(t % EKB)), "r"(y),
       "r"((int32_t)(t / EKB)), "r"(q)
       : "memory");
-}
-
-// v 2^sh as an int64 (sh < 0: rounded to nearest, ties up).
-__device__ __forceinline__ long long fx_shift(int v, int sh) {
-  if (sh >= 0) return (long long)v << sh;
-  return ((long long)v + (1LL << (-sh - 1))) >> (-sh);
-}
-
-// Epilogue warps (4..11) of the pair kernel: warp -> tensor-memory lane quadrant
-// q4 = warp % 4 and column half h; each thread owns one row and BN / 2 columns.
-// Its entries of the running total sit at Tt + c * 128 (c = its column), so a
-// warp touches 32 consecutive int64 per column.
-template <int BN>
-__device__ __forceinline__ void emu_pair_epilogue(const EmuArgs& a, int pair, int64_t nunits,
-                                                  uint32_t rank, uint32_t tmem_base,
-                                                  uint64_t* tfull, const uint32_t* tempty_addr,
-                                                  const tc::WaitCtx& w, int warp, int lane) {
-  constexpr int HC = BN / 2;
-  constexpr int NACC = PairLayout<BN>::NACC;
-  const int64_t kbt = a.sch.kbt;
-  const int top = a.s + 1;
-  const int q4 = warp & 3;
-  const int h = (warp - 4) >> 2;
-  const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
-  const uint32_t col_lo = (uint32_t)(HC * h);
-  long long* Tt = a.T + (int64_t)blockIdx.x * (128 * BN) + ((int64_t)h * HC * 4 + q4) * 32 + lane;
-  // The running totals (about 39 MB for all CTAs) stay in L2 between merges
-  // while the slice panels stream past them: their lines are the last to go.
-  uint64_t keep;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
-  uint32_t acc = 0;
-  uint32_t tph[NACC];
-#pragma unroll
-  for (int b = 0; b < NACC; ++b) tph[b] = 0;
-  bool ok = true;
-  for (int64_t ui = 0; ui < nunits && ok; ++ui) {
-    const Unit u = unit_of_cta(a.sch, pair, ui);
-    int Lv[HC];  // exact level sum of the current super-chunk
-    bool stored = false;
-    for (int64_t sc0 = 0; sc0 < kbt && ok; sc0 += a.chunk_kb) {
-      const int64_t sc1 = min(sc0 + (int64_t)a.chunk_kb, kbt);
-      for (int lvl = top; lvl >= 2 && ok; --lvl) {
-        const int gk = group_blocks(a.group_kb, lvl - 1);
-        // one exact group: its integer sums join Lv (the level's first group sets it)
-        auto drain = [&](auto first_tag) -> bool {
-          constexpr bool kFirst = decltype(first_tag)::value;
-          if (!tc::mbar_wait(&tfull[acc], tph[acc], w)) return false;
-          tc::tc_fence_after();
-          const uint32_t src = tmem_base + lane_off + acc * BN + col_lo;
-#pragma unroll
-          for (int c = 0; c < HC; c += 16) {
-            uint32_t v[16];
-            tc::tmem_ld_32x16(src + c, v);
-            tc::tmem_wait_ld();
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int iv = __float2int_rn(__uint_as_float(v[j]));  // exact integer
-              Lv[c + j] = kFirst ? iv : Lv[c + j] + iv;
-            }
-          }
-          tc::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive_remote_relaxed(tempty_addr[acc]);
-          tph[acc] ^= 1;
-          acc = (acc + 1) == NACC ? 0 : acc + 1;
-          return true;
-        };
-        if (!drain(std::true_type{})) { ok = false; break; }
-        for (int64_t c0 = sc0 + gk; c0 < sc1; c0 += gk)
-          if (!drain(std::false_type{})) { ok = false; break; }
-        if (!ok) break;
-        // K-RECOMB: T += L 2^(beta (top - lvl) - base), exactly
-        const int sh = a.beta * (top - lvl) - a.t_base;
-        // (8 columns at a time: each batch's shifted values are sent before the next
-        // is formed, which keeps the 64-bit temporaries few)
-#pragma unroll
-        for (int c = 0; c < HC; c += 8) {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const long long x = fx_shift(Lv[c + j], sh);
-            // relaxed gpu-scope store, reductions and read-back: same-address
-            // operations of one thread stay in program order (coherence)
-            if (!stored)
-              asm volatile("st.relaxed.gpu.global.L2::cache_hint.s64 [%0], %1, %2;" ::"l"(
-                               Tt + (c + j) * 128),
-                           "l"(x), "l"(keep)
-                           : "memory");
-            else
-              asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(
-                               Tt + (c + j) * 128),
-                           "l"(x), "l"(keep)
-                           : "memory");
-          }
-        }
-        stored = true;
-      }
-    }
-    if (!ok) break;
-    // Final FP64 store: C = T 2^(sigma_i + tau_j + 2 - beta (s + 1) + base) for this
-    // thread's row, HC columns.  Each 8-column chunk is formed in the row's lane,
-    // transposed within groups of 8 lanes (three butterfly stages of shuffles: at
-    // stage s, entries whose row and column differ in bit s trade places with
-    // lane ^ s), and written as four 64-byte row segments per instruction.
-    const int64_t row0 = u.tile_row * (2 * EBM) + (int64_t)rank * EBM + q4 * 32;
-    const int64_t row = row0 + lane;
-    const int64_t cbase = u.tile_col * BN + col_lo;
-    const int ea = row < a.sch.m ? a.eA[row] : kExpNone;
-    const int eoff = 2 - a.beta * top + a.t_base;
-    const int l8 = lane & 7, g8 = lane >> 3;
-    // the read-back addresses from an opaque copy of the base, so the compiler does
-    // not keep the merges' per-column addresses live across the loops
-    long long* Tf = Tt;
-    asm volatile("" : "+l"(Tf));
-#pragma unroll
-    for (int c = 0; c < HC; c += 8) {
-      long long tv[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        asm volatile("ld.relaxed.gpu.global.L2::cache_hint.s64 %0, [%1], %2;"
-                     : "=l"(tv[j])
-                     : "l"(Tf + (c + j) * 128), "l"(keep)
-                     : "memory");
-      int eb[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) eb[j] = cbase + c + j < a.sch.n ? a.eB[cbase + c + j] : kExpNone;
-      double v[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        double x = (ea == kExpNone || eb[j] == kExpNone)
-                       ? 0.0
-                       : scale_pow2((double)tv[j], ea + eb[j] + eoff);
-        if (a.alpha != 1.0) x *= a.alpha;
-        v[j] = x;
-      }
-#pragma unroll
-      for (int sb = 4; sb >= 1; sb >>= 1) {
-#pragma unroll
-        for (int i0 = 0; i0 < 8; ++i0) {
-          if (i0 & sb) continue;
-          const bool up = (l8 & sb) != 0;
-          const double send = up ? v[i0] : v[i0 | sb];
-          const double recv = __shfl_xor_sync(0xffffffffu, send, sb);
-          if (up) v[i0] = recv;
-          else v[i0 | sb] = recv;
-        }
-      }
-      // now v[i] = C(row0 + 8 g8 + i, cbase + c + l8)
-      const int64_t col = cbase + c + l8;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int64_t r = row0 + 8 * g8 + i;
-        if (r < a.sch.m && col < a.sch.n) {
-          double* dst = a.C + r * a.ldc + col;
-          double x = v[i];
-          if (a.beta_c != 0.0) x = fma(a.beta_c, *dst, x);
-          *dst = x;
-        }
-      }
-    }
-  }
 }
 
 template <int BN>
@@ -931,7 +781,8 @@ emu_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     uint32_t te[NACC];
 #pragma unroll
     for (int b = 0; b < NACC; ++b) te[b] = tc::mapa_shared(&tempty[b], 0);
-    emu_pair_epilogue<BN>(a, pair, nunits, rank, tmem_base, tfull, te, w, warp, lane);
+    emu_fx_epilogue<BN, 2 * EBM, 4>(a, pair, nunits, (int64_t)rank * EBM, tmem_base, tfull, te,
+                                    w, warp, lane);
   } else {
   asm volatile("setmaxnreg.dec.sync.aligned.u32 56;\n" ::: "memory");
   if (warp == 0) {
@@ -1233,8 +1084,9 @@ int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cos
   if (pairs ? (sch.tile_n != 256 && sch.tile_n != 128) : (sch.tile_m != EBM || sch.tile_n != EBN))
     return COSMA_ERR_INVALID_ARG;
   if (sch.k_block != EBK || sch.pk != 1) return COSMA_ERR_INVALID_ARG;
-  // the running totals of the pair kernel: one 128 x tile_n int64 region per CTA
-  if (pairs && (2LL * sch.ctas > (long long)p.sms || !T)) return COSMA_ERR_INVALID_ARG;
+  // the running totals: one 128 x tile_n int64 region per CTA of the launch
+  if (!T || (pairs ? 2LL * sch.ctas : (long long)sch.ctas) > (long long)p.sms)
+    return COSMA_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(C) & 7) return COSMA_ERR_INVALID_ARG;
   // COSMA_EMU_LOCKSTEP in the environment (read once): unset or 1 = lock-step
   // rounds under a cooperative launch; 0 = pairs free; 2 = lock-step rounds under
@@ -1273,18 +1125,17 @@ int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cos
   args.beta_c = beta_c;
   // Super-chunk: every level sum of a chunk must fit in int32 exactly (at most s
   // pairs x chunk x 2^(2 beta - 2)).  Each chunk ends in s merges of the running
-  // total.  Single-SM tiles: 1024 k, short enough for the slice panels of a wave
-  // of tiles to stay in L2 across all levels.  CTA pairs: 4096 k -- their merges
-  // are L2 reductions, and fewer of them beat the panels' L2 reuse (one GB300,
-  // square 16384^3: 512 k 66.2, 1024 k 72.6, 2048 k 77.6, 4096 k 78.3-79.6,
-  // 16384 k 80.3 TFLOP/s; largeK 4096 x 4096 x 2^20: 4096 k 64.3, 16384 k 62.7).
+  // total, which are L2 reductions; 4096 k -- fewer merges beat keeping a chunk's
+  // slice panels in L2 across the levels (one GB300, 256 x 256 pair tiles, square
+  // 16384^3: 512 k 66.2, 1024 k 72.6, 2048 k 77.6, 4096 k 78.3-79.6, 16384 k 80.3
+  // TFLOP/s; largeK 4096 x 4096 x 2^20: 4096 k 64.3, 16384 k 62.7).
   {
     const double lim = 2147483647.0 / ((double)s * std::ldexp(1.0, 2 * beta - 2));
-    int64_t ck = (pairs ? 4096 : 1024) / EBK;
+    int64_t ck = 4096 / EBK;
     while (ck > 1 && (double)ck * EBK > lim) --ck;
     args.chunk_kb = (int)ck;
   }
-  // Fixed-point base of the pair kernel's running total: every super-chunk adds
+  // Fixed-point base of the running total: every super-chunk adds
   // at most sum_{l=2}^{s+1} (l - 1) chunk 2^(2 beta - 2) 2^(beta (s + 1 - l)); the
   // smallest base that keeps the sum over all chunks below 2^62.
   args.T = T;

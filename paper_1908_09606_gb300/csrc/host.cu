@@ -41,6 +41,28 @@ struct HostState {
 std::mutex g_host_mu;
 HostState g_host[kMaxDevices];
 
+// Phase events of the last cosma_gemm_host call made while profiling was on
+// (cosma_profile_enable) and not under stream capture.
+struct HostPhases {
+  bool ready = false, valid = false;
+  cudaEvent_t start = nullptr, in_done = nullptr, end = nullptr;
+  cudaEvent_t pb[kMaxR * kMaxR] = {}, pe[kMaxR * kMaxR] = {};
+  int nblocks = 0;
+};
+HostPhases g_phases[kMaxDevices];
+
+int phases_init(HostPhases& p) {
+  if (p.ready) return COSMA_OK;
+  cudaEvent_t* all[3] = {&p.start, &p.in_done, &p.end};
+  for (cudaEvent_t* e : all)
+    if (cudaEventCreate(e) != cudaSuccess) return COSMA_ERR_CUDA;
+  for (int i = 0; i < kMaxR * kMaxR; ++i)
+    if (cudaEventCreate(&p.pb[i]) != cudaSuccess || cudaEventCreate(&p.pe[i]) != cudaSuccess)
+      return COSMA_ERR_CUDA;
+  p.ready = true;
+  return COSMA_OK;
+}
+
 inline int64_t rup(int64_t x, int64_t r) { return (x + r - 1) / r * r; }
 
 bool capturing(cudaStream_t st) {
@@ -126,6 +148,16 @@ void host_release(int dev) {
   if (h.in) cudaStreamDestroy(h.in);
   if (h.out) cudaStreamDestroy(h.out);
   h = HostState{};
+  HostPhases& p = g_phases[dev];
+  if (p.ready) {
+    cudaEvent_t all[3] = {p.start, p.in_done, p.end};
+    for (cudaEvent_t e : all) cudaEventDestroy(e);
+    for (int i = 0; i < kMaxR * kMaxR; ++i) {
+      cudaEventDestroy(p.pb[i]);
+      cudaEventDestroy(p.pe[i]);
+    }
+  }
+  p = HostPhases{};
 }
 
 }  // namespace cosma
@@ -185,6 +217,12 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
   cudaEvent_t* ev_b = h.ev + 2 + kMaxR;
   cudaEvent_t* ev_c = h.ev + 2 + 2 * kMaxR;
 
+  HostPhases& ph = g_phases[dev];
+  const bool prof = prof_enabled() && !capturing(st) && phases_init(ph) == COSMA_OK;
+  if (prof) {
+    ph.valid = false;
+    if ((rc = ok(cudaEventRecord(ph.start, st))) != COSMA_OK) return rc;
+  }
   // fork: the copy streams start after everything already queued on `stream`
   if ((rc = ok(cudaEventRecord(ev_start, st))) != COSMA_OK) return rc;
   if ((rc = ok(cudaStreamWaitEvent(h.in, ev_start, 0))) != COSMA_OK) return rc;
@@ -246,6 +284,7 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
           }
         }
         uint8_t* Cblk = Cd + ((size_t)r0 * ldc_d + c0) * eo;
+        if (prof && (rc = ok(cudaEventRecord(ph.pb[i * Rn + j], st))) != COSMA_OK) return rc;
         if (emu) {
           cosma_plan p;
           rc = plan_gemm(mb, nb, k, dtype, ctx.cfg.selector, ctx.info, ctx.cfg, &p, !capturing(st));
@@ -262,6 +301,7 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
                           Cblk, ldc_d, dtype, st);
           if (rc != COSMA_OK) return rc;
         }
+        if (prof && (rc = ok(cudaEventRecord(ph.pe[i * Rn + j], st))) != COSMA_OK) return rc;
         cudaEvent_t evc = ev_c[i * Rn + j];
         if ((rc = ok(cudaEventRecord(evc, st))) != COSMA_OK) return rc;
         if ((rc = ok(cudaStreamWaitEvent(h.out, evc, 0))) != COSMA_OK) return rc;
@@ -275,9 +315,39 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
   };
   const int brc = body();
   // join: `stream` continues after the last copy-in and the last copy-out
+  if (prof && brc == COSMA_OK) cudaEventRecord(ph.in_done, h.in);
   rc = ok(cudaEventRecord(ev_start, h.in));
   if (rc == COSMA_OK) rc = ok(cudaStreamWaitEvent(h.out, ev_start, 0));
   if (rc == COSMA_OK) rc = ok(cudaEventRecord(ev_done, h.out));
   if (rc == COSMA_OK) rc = ok(cudaStreamWaitEvent(st, ev_done, 0));
+  if (prof && brc == COSMA_OK && rc == COSMA_OK && cudaEventRecord(ph.end, st) == cudaSuccess) {
+    ph.nblocks = Rm * Rn;
+    ph.valid = true;
+  }
   return brc != COSMA_OK ? brc : rc;
+}
+
+extern "C" int cosma_profile_host(double* phases, int count) {
+  if (!phases || count < 1) return COSMA_ERR_INVALID_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return COSMA_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_host_mu);
+  const HostPhases& p = g_phases[dev];
+  if (!p.valid) return COSMA_ERR_INVALID_ARG;
+  if (cudaEventSynchronize(p.end) != cudaSuccess) return COSMA_ERR_CUDA;
+  auto span = [](cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    return cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? (double)ms : -1.0;
+  };
+  double products = 0.0;
+  for (int i = 0; i < p.nblocks; ++i) products += span(p.pb[i], p.pe[i]);
+  const double v[6] = {span(p.start, p.end), span(p.start, p.pb[0]), products,
+                       span(p.pe[p.nblocks - 1], p.end), span(p.start, p.in_done),
+                       (double)p.nblocks};
+  const int n = count < 6 ? count : 6;
+  for (int i = 0; i < n; ++i) phases[i] = v[i];
+  return n;
 }

@@ -133,6 +133,8 @@ int launch_emu_bf16(const GemmArgs& g, const cosma_plan& p, const cosma_config& 
 void count_launch(int n = 1);
 // Event pair around the dominant kernel of a call when profiling is enabled.
 void prof_mark(cudaStream_t st, bool begin);
+// Whether cosma_profile_enable is on (api.cu).
+bool prof_enabled();
 
 // Bytes of workspace a plan needs (split-k partials, operand copies, slices).
 long long workspace_bytes(int64_t m, int64_t n, int64_t k, int dtype, const cosma_plan& p);

@@ -106,6 +106,16 @@ def test_complex_k_limits_are_refused_before_any_staging(lib):
                              cosma.COSMA_F32, 0) == cosma.COSMA_ERR_INVALID_ARG
 
 
+def test_profile_host_rejects_bad_arguments(lib):
+    import ctypes
+    raw = lib.load()
+    buf = (ctypes.c_double * 6)()
+    assert raw.cosma_profile_host(None, 6) == lib.COSMA_ERR_INVALID_ARG
+    assert raw.cosma_profile_host(buf, 0) == lib.COSMA_ERR_INVALID_ARG
+    # without a device (or before any profiled host call) nothing is reported
+    assert raw.cosma_profile_host(buf, 6) < 0
+
+
 def test_host_entry_rejects_bad_arguments(lib):
     bad = lib.COSMA_ERR_INVALID_ARG
     assert lib.cosma_gemm_host(-1, 4, 4, 0, 4, 0, 4, 0, 4, lib.COSMA_F64) == bad

@@ -151,9 +151,8 @@ def test_emu_pair_and_single_sm_tiles(tile, shape):
 
 @pytest.mark.parametrize("tile", ["pair256", "single", "pair128"])
 def test_emu_long_k(tile):
-    # k = 22001: six 4096-deep super-chunks on the pair kernels, whose fixed-point
-    # base rises to 7 bits (the lowest level is rounded to it); 22 1024-deep ones
-    # on the single-SM kernel, whose float-float total takes 132 merges
+    # k = 22001: six 4096-deep super-chunks, 36 merges of the running total, whose
+    # fixed-point base rises to 7 bits (the lowest level is rounded to it)
     import torch
     cosma = lib()
     m, n, k = 130, 129, 22001
@@ -198,9 +197,10 @@ def test_emu_slice_configurations(slices, bits):
 def test_emu_equals_the_methods_own_result(slices, bits, shape):
     """The GPU emulation against the step-by-step oracle of the method
     (oracle/ozaki.py: the same scales, digits and truncated triangle in exact
-    integer arithmetic): they differ only by the float-float merges, far below
-    the truncation itself -- with 3 slices the product is off by ~2^-22 but the
-    two agree to 2^-40 of sum |a||b|, so a wrong pair set or scale would show."""
+    integer arithmetic): both round the exact total to FP64 once, so they differ
+    only where the fixed-point base rounds the lowest level -- far below the
+    truncation itself; with 3 slices the product is off by ~2^-22 but the two
+    agree to 2^-40 of sum |a||b|, so a wrong pair set or scale would show."""
     import torch
     from oracle import ozaki
     cosma = lib()
@@ -219,23 +219,25 @@ def test_emu_equals_the_methods_own_result(slices, bits, shape):
         assert np.max(np.abs(C - exact) / absab) > 2.0 ** -36
 
 
-@pytest.mark.parametrize("shape,kind", [((300, 520, 3000), "uniform"), ((513, 260, 1100), "loguniform")])
-def test_emu_pair_tile_widths_agree_bit_for_bit(shape, kind):
-    """Both CTA-pair tiles form the same exact fixed-point running total (level
-    sums are exact integers and the total is integer arithmetic), so 256- and
-    128-column tiles give identical bits, and both meet the oracle bar."""
+@pytest.mark.parametrize("shape,kind", [((300, 520, 3000), "uniform"), ((513, 260, 1100), "loguniform"),
+                                        ((260, 300, 9000), "uniform")])
+def test_emu_tile_shapes_agree_bit_for_bit(shape, kind):
+    """Every kernel forms the same exact fixed-point running total (level sums
+    are exact integers and the total is integer arithmetic, rounded to FP64
+    once), so 256 x 256 and 256 x 128 pair tiles and 128 x 128 single-SM tiles
+    give identical bits, and all meet the oracle bar."""
     import torch
     cosma = lib()
     m, n, k = shape
     A, B = device_operands(m, n, k, DT, kind=kind, seed=21)
     out = []
-    for tile in ("pair256", "pair128"):
+    for tile in ("pair256", "pair128", "single"):
         C, _ = out_tensor(m, n, DT)
         cosma.gemm(A, B, C, DT, plan=_tile_plan(m, n, k, tile))
         torch.cuda.synchronize()
         assert cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream) == 0
         out.append(C.cpu().numpy())
-    assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
     Ah, Bh = host_operands(m, n, k, DT, kind=kind, seed=21)
     assert og.normwise_rel_error(out[0], og.gemm(Ah, Bh, "dot2")) <= 1e-12
 

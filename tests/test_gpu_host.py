@@ -179,3 +179,33 @@ def test_host_k_zero_and_errors():
                                  cosma.COSMA_F64, 0) == cosma.COSMA_ERR_INVALID_ARG
     assert cosma.cosma_gemm_host(5, 7, 3, Ah.data_ptr(), 3, Bh.data_ptr(), 7, Ch.data_ptr(), 7,
                                  cosma.COSMA_F64_EMU_INT8, 0) == cosma.COSMA_ERR_UNSUPPORTED
+
+
+def test_host_phase_profile():
+    """cosma_profile_host reports the phases of a profiled call: the head, the
+    block products and the tail lie inside the whole call, the copies in end
+    within it, and a 2 x 2 blocked call has four block products."""
+    import torch
+    cosma = lib()
+    m = n = 8200
+    k = 256
+    dtype = "f64_emu_bf16"
+    _, _, Ah, Bh = _host_copies(m, n, k, dtype, seed=3)
+    Ch = _host_out(m, n, dtype)
+    st = torch.cuda.current_stream().cuda_stream
+    code = cosma.DTYPES[dtype]
+    assert cosma.cosma_profile_enable(True) == 0
+    try:
+        rc = cosma.cosma_gemm_host(m, n, k, Ah.data_ptr(), Ah.stride(0), Bh.data_ptr(),
+                                   Bh.stride(0), Ch.data_ptr(), Ch.stride(0), code, st)
+        assert rc == 0
+        ph = cosma.cosma_profile_host()
+    finally:
+        cosma.cosma_profile_enable(False)
+        cosma.cosma_profile_read()  # clears the kernel event pairs of the call
+    torch.cuda.synchronize()
+    assert ph["blocks"] == 4
+    assert 0 < ph["head_ms"] and 0 < ph["block_products_ms"] and 0 <= ph["tail_ms"]
+    assert ph["head_ms"] + ph["block_products_ms"] + ph["tail_ms"] <= ph["total_ms"] * 1.001 + 1e-3
+    assert 0 < ph["copy_in_ms"] <= ph["total_ms"] * 1.001 + 1e-3
+    assert cosma.cosma_stream_status(st) == 0
