@@ -359,7 +359,8 @@ int cosma_mlp_adam(int n, float* params, const float* grad, float* m, float* v, 
 /* Installs a trained network (HOST parameter vector) for COSMA_SELECT_LEARNED
  * on the current device, valid for sizes with log2 in [log2_lo, log2_hi];
  * outside that range (or with no network) plans fall back to the analytic
- * selector.  params == NULL removes the network. */
+ * selector.  The network's outputs are read as log2 seconds per candidate.
+ * params == NULL removes the network. */
 int cosma_selector_set(const float* params, double log2_lo, double log2_hi);
 
 /* Restricts the installed network to the dtypes whose bit (1 << dtype) is set in
@@ -369,9 +370,12 @@ int cosma_selector_set(const float* params, double log2_lo, double log2_hi);
 int cosma_selector_restrict(unsigned dtype_mask);
 
 /* Runs K-MLP-FWD on `count` shapes (HOST array mnk of 3*count int64) and
- * writes, per shape, the candidate with the smallest predicted time among
- * those that apply (best, HOST, count ints) and optionally all predictions
- * (pred, HOST, count x OUT floats, may be NULL).  Synchronous. */
+ * writes, per shape, the learned selector's choice (best, HOST, count ints)
+ * and optionally all predictions (pred, HOST, count x OUT floats, may be
+ * NULL).  The choice is the analytic plan -- written as its candidate index
+ * when it is one of the candidates, else as -1 -- unless the network predicts
+ * another applicable candidate faster by at least 0.05 in log2 seconds (about
+ * 3.5 %), whose index is then written.  Synchronous. */
 int cosma_selector_predict(int count, const int64_t* mnk, int dtype, int* best, float* pred);
 
 /* ---- measurement ------------------------------------------------------ */

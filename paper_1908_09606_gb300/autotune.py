@@ -1,15 +1,17 @@
 """Autotuner, selector training and regret evaluation (a8 of the hot path).
 
   collect()   times every applicable plan candidate (cosma_plan_candidate,
-              cosma_gemm_planned, CUDA events, best of `reps` after a warm-up)
-              on random shapes and appends (shape, dtype, candidate, seconds)
-              rows to a JSONL file; rows already present are skipped, so an
-              interrupted run resumes where it stopped.
+              cosma_gemm_planned, CUDA events, median of `reps` after a
+              warm-up) on random shapes and appends (shape, dtype, candidate,
+              seconds) rows to a JSONL file; rows already present are skipped,
+              so an interrupted run resumes where it stopped.
   train()     fits the MLP cost model on those rows with the library's own
               kernels (cosma_mlp_loss_grad + cosma_mlp_adam on the GPU),
-              checkpointing parameters and Adam state after every epoch.
+              checkpointing parameters and Adam state after every epoch; one
+              network for every dtype (the dtype is a one-hot input).
   evaluate()  exhaustive timing on held-out shapes: regret of the learned
-              choice and of the analytic plan against the best candidate.
+              choice and of the analytic plan against the best candidate (the
+              two share a measurement where they pick the same plan).
   tune_grouped()  times one grouped launch with each tile width the grouped
               kernels implement and keeps the fastest as the configured default.
 
@@ -69,8 +71,17 @@ class Operands:
         return self.A.data_ptr(), self.B.data_ptr(), self.C.data_ptr()
 
 
-def time_plan(m, n, k, dtype, plan, ops, reps=2):
-    """Best-of-reps seconds of one product with the given plan (None -> analytic)."""
+# Per dtype: the largest product timed (2mnk; FP64 runs at about 1.2 TFLOP/s) and
+# the collection budget in seconds of main().
+TUNE = {cosma.COSMA_BF16: {"max_flops": 4e13, "budget_s": 240},
+        cosma.COSMA_F32: {"max_flops": 2e12, "budget_s": 200},
+        cosma.COSMA_F64: {"max_flops": 5e10, "budget_s": 240},
+        cosma.COSMA_F64_EMU_BF16: {"max_flops": 2e12, "budget_s": 120}}
+
+
+def time_plan(m, n, k, dtype, plan, ops, reps=3):
+    """Median seconds of `reps` products with the given plan (None -> analytic),
+    after one untimed warm-up."""
     import torch
     a, b, c = ops.ptrs()
     s = torch.cuda.current_stream()
@@ -85,16 +96,16 @@ def time_plan(m, n, k, dtype, plan, ops, reps=2):
             raise cosma.CosmaError(rc, "time_plan")
 
     run()
-    best = math.inf
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    ts = []
     for _ in range(reps):
         e0.record(s)
         run()
         e1.record(s)
         e1.synchronize()
-        best = min(best, e0.elapsed_time(e1) * 1e-3)
-    return best
+        ts.append(e0.elapsed_time(e1) * 1e-3)
+    return float(np.median(ts))
 
 
 def candidates(m, n, k, dtype, max_ws_bytes):
@@ -104,6 +115,20 @@ def candidates(m, n, k, dtype, max_ws_bytes):
         if p is not None and p.workspace_bytes <= max_ws_bytes:
             out.append((c, p))
     return out
+
+
+_PLAN_KEY = ("tile_m", "tile_n", "k_block", "pk", "order", "ctas", "pm", "pn")
+
+
+def analytic_candidate(m, n, k, dtype, cands):
+    """Index of the candidate that is the analytic plan, or None when the
+    analytic plan lies outside the candidate set."""
+    pa = cosma.cosma_plan_query(m, n, k, dtype, cosma.COSMA_SELECT_ANALYTIC)
+    want = tuple(getattr(pa, f) for f in _PLAN_KEY)
+    for c, p in cands:
+        if tuple(getattr(p, f) for f in _PLAN_KEY) == want:
+            return c
+    return None
 
 
 def _load_rows(path):
@@ -117,7 +142,7 @@ def _load_rows(path):
     return rows
 
 
-def collect(path, shapes, dtype=cosma.COSMA_BF16, cap_bytes=16e9, max_ws_bytes=24e9, reps=2,
+def collect(path, shapes, dtype=cosma.COSMA_BF16, cap_bytes=16e9, max_ws_bytes=24e9, reps=3,
             time_budget_s=None, log=None):
     """Times all applicable candidates of each shape; returns the rows of `path`."""
     done = {(r["m"], r["n"], r["k"], r["dtype"], r["cand"]) for r in _load_rows(path)}
@@ -163,6 +188,18 @@ def init_params(seed):
     p = np.concatenate(parts).astype(np.float32)
     assert p.size == cosma.COSMA_MLP_PARAMS
     return p
+
+
+def destandardize(params, mu, sigma):
+    """The same network with outputs in log2 seconds instead of standardised
+    units (the last layer scaled by sigma, shifted by mu): the form the library's
+    selector reads, so its margin has a fixed meaning."""
+    IN, H, OUT = cosma.COSMA_MLP_IN, cosma.COSMA_MLP_HIDDEN, cosma.COSMA_MLP_OUT
+    p = np.array(params, dtype=np.float64)
+    w3 = H * IN + H + H * H + H   # start of the last layer's weights
+    p[w3:w3 + OUT * H] *= sigma
+    p[w3 + OUT * H:w3 + OUT * H + OUT] = p[w3 + OUT * H:w3 + OUT * H + OUT] * sigma + mu
+    return p.astype(np.float32)
 
 
 def train(X, cand, y, epochs=300, batch=256, lr=2e-3, seed=0, checkpoint=None, log=None):
@@ -222,23 +259,28 @@ def train(X, cand, y, epochs=300, batch=256, lr=2e-3, seed=0, checkpoint=None, l
     return p.cpu().numpy(), hist, (mu, sigma)
 
 
-def evaluate(shapes, dtype=cosma.COSMA_BF16, cap_bytes=16e9, max_ws_bytes=24e9, reps=2,
+def evaluate(shapes, dtype=cosma.COSMA_BF16, cap_bytes=16e9, max_ws_bytes=24e9, reps=3,
              log=None):
     """Exhaustive timing on shapes; returns per-shape records with the best
-    candidate, the learned pick (installed selector) and the analytic plan."""
+    candidate, the learned pick (installed selector; -1 = the analytic plan) and
+    the analytic plan.  Where the analytic plan is a candidate, its time is that
+    candidate's measurement, so equal choices have equal times."""
     best_l, _ = cosma.cosma_selector_predict(shapes, dtype)
     ops = Operands(dtype, cap_bytes)
     recs = []
     for (m, n, k), pick in zip(shapes, best_l):
+        cands = candidates(m, n, k, dtype, max_ws_bytes)
         times = {}
-        for c, p in candidates(m, n, k, dtype, max_ws_bytes):
+        for c, p in cands:
             times[c] = time_plan(m, n, k, dtype, p, ops, reps)
         if not times:
             continue
         t_best = min(times.values())
-        t_ana = time_plan(m, n, k, dtype, None, ops, reps)
-        t_sel = times.get(pick, t_ana)
-        recs.append({"m": m, "n": n, "k": k, "best": min(times, key=times.get), "pick": pick,
+        ca = analytic_candidate(m, n, k, dtype, cands)
+        t_ana = times[ca] if ca is not None else time_plan(m, n, k, dtype, None, ops, reps)
+        t_sel = t_ana if pick < 0 or pick == ca else times.get(pick, t_ana)
+        recs.append({"m": m, "n": n, "k": k, "dtype": dtype, "best": min(times, key=times.get),
+                     "pick": pick, "analytic": -1 if ca is None else ca,
                      "t_best": t_best, "t_sel": t_sel, "t_analytic": t_ana,
                      "regret_sel": t_sel / t_best - 1.0, "regret_analytic": t_ana / t_best - 1.0})
         if log:
@@ -249,7 +291,7 @@ def evaluate(shapes, dtype=cosma.COSMA_BF16, cap_bytes=16e9, max_ws_bytes=24e9, 
 
 
 SHIPPED_PARAMS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data",
-                              "selector_bf16_gb300.npy")
+                              "selector_gb300.npy")
 
 
 def tune_grouped(As, Bs, Cs, dtype, tiles=None, reps=3):
@@ -290,16 +332,14 @@ def tune_grouped(As, Bs, Cs, dtype, tiles=None, reps=3):
 
 
 def install(params_path=None, log2_lo=8.0, log2_hi=16.0, dtypes=None):
-    """Installs trained selector weights saved by main() (an .npy vector); by default
-    the bf16 weights shipped with the package (trained on a GB300), restricted to
-    bf16.  dtypes: the dtypes the weights were trained on (None with params_path:
-    all)."""
+    """Installs trained selector weights saved by main() (an .npy vector of
+    log2-second outputs); by default the weights shipped with the package,
+    trained on a GB300 on all four dtypes.  dtypes: restrict the network to
+    these (None: every dtype)."""
     p = np.load(params_path or SHIPPED_PARAMS).astype(np.float32)
     rc = cosma.cosma_selector_set(p, log2_lo, log2_hi)
     if rc != 0:
         raise cosma.CosmaError(rc, "cosma_selector_set")
-    if dtypes is None and params_path is None:
-        dtypes = ("bf16",)
     if dtypes is not None:
         rc = cosma.cosma_selector_restrict(dtypes)
         if rc != 0:
@@ -310,13 +350,37 @@ def parser():
     import argparse
     ap = argparse.ArgumentParser(description="collect timings, train the selector, report regret")
     ap.add_argument("--out", required=True)
-    ap.add_argument("--train-shapes", type=int, default=1250)
-    ap.add_argument("--test-shapes", type=int, default=500)
+    ap.add_argument("--dtypes", default="bf16,f32,f64,f64_emu_bf16")
+    ap.add_argument("--train-shapes", type=int, default=4000, help="per dtype, budget permitting")
+    ap.add_argument("--test-shapes", type=int, default=500, help="held out, over all dtypes")
     ap.add_argument("--epochs", type=int, default=400)
-    ap.add_argument("--collect-budget-s", type=float, default=900)
-    ap.add_argument("--eval-budget-s", type=float, default=600)
+    ap.add_argument("--budget-scale", type=float, default=1.0,
+                    help="scales every dtype's collection budget")
+    ap.add_argument("--eval-budget-s", type=float, default=600, help="over all dtypes")
     ap.add_argument("--seed", type=int, default=0)
     return ap
+
+
+def _summary(recs):
+    rs = np.array([r["regret_sel"] for r in recs])
+    ra = np.array([r["regret_analytic"] for r in recs])
+    if not len(rs):
+        return {"test_shapes": 0}
+    dev = [r for r in recs if r["pick"] >= 0 and r["pick"] != r["analytic"]]
+    return {
+        "test_shapes": len(recs),
+        "median_regret_learned": float(np.median(rs)),
+        "mean_regret_learned": float(np.mean(rs)),
+        "p90_regret_learned": float(np.percentile(rs, 90)),
+        "median_regret_analytic": float(np.median(ra)),
+        "mean_regret_analytic": float(np.mean(ra)),
+        "p90_regret_analytic": float(np.percentile(ra, 90)),
+        "learned_differs_from_analytic": len(dev),
+        "mean_gain_where_it_differs": float(np.mean([r["t_analytic"] / r["t_sel"] - 1.0
+                                                     for r in dev])) if dev else 0.0,
+        "learned_exact_best_fraction": float(np.mean([
+            (r["pick"] if r["pick"] >= 0 else r["analytic"]) == r["best"] for r in recs])),
+    }
 
 
 def main(argv=None):
@@ -326,50 +390,51 @@ def main(argv=None):
     torch.cuda.set_device(0)
     cosma.load()
     log = lambda s: print(s, flush=True)  # noqa: E731
-    dt = cosma.COSMA_BF16
-    train_shapes = random_shapes(a.train_shapes, seed=100 + a.seed, dtype=dt)
-    test_shapes = random_shapes(a.test_shapes, seed=200 + a.seed, dtype=dt)
-    t0 = time.time()
-    rows = collect(os.path.join(a.out, "timings.jsonl"), train_shapes, dt,
-                   time_budget_s=a.collect_budget_s, reps=1)
-    t_collect = time.time() - t0
+    dts = [cosma.DTYPES[d] for d in a.dtypes.split(",")]
+    rows, t_collect = [], {}
+    for dt in dts:
+        shapes = random_shapes(a.train_shapes, seed=100 + a.seed + 1000 * dt, dtype=dt,
+                               max_flops=TUNE[dt]["max_flops"])
+        t0 = time.time()
+        rows += collect(os.path.join(a.out, f"timings_{dt}.jsonl"), shapes, dt,
+                        time_budget_s=TUNE[dt]["budget_s"] * a.budget_scale, reps=3)
+        t_collect[dt] = time.time() - t0
+        log(f"dtype {dt}: {len(rows)} rows so far")
     X, c, y = features(rows)
     t0 = time.time()
     p, hist, (mu, sigma) = train(X, c, y, epochs=a.epochs, seed=a.seed,
                                  checkpoint=os.path.join(a.out, "checkpoint.npz"), log=log)
     t_train = time.time() - t0
+    p = destandardize(p, mu, sigma)
     np.save(os.path.join(a.out, "selector_params.npy"), p)
-    lo = math.log2(256)
-    hi = math.log2(65536)
-    rc = cosma.cosma_selector_set(p, lo, hi)
+    rc = cosma.cosma_selector_set(p, math.log2(256), math.log2(65536))
     if rc != 0:
         raise cosma.CosmaError(rc, "cosma_selector_set")
-    t0 = time.time()
-    recs = []
-    for s in test_shapes:
-        if time.time() - t0 > a.eval_budget_s:
-            break
-        recs += evaluate([s], dt, reps=2)
-    t_eval = time.time() - t0
+    per = max(1, a.test_shapes // len(dts))
+    recs, t_eval = [], {}
+    for dt in dts:
+        test = random_shapes(per, seed=200 + a.seed + 1000 * dt, dtype=dt,
+                             max_flops=TUNE[dt]["max_flops"])
+        t0 = time.time()
+        for sh in test:
+            if time.time() - t0 > a.eval_budget_s / len(dts):
+                break
+            recs += evaluate([sh], dt, reps=3)
+        t_eval[dt] = time.time() - t0
     with open(os.path.join(a.out, "eval.jsonl"), "w") as f:
         for r in recs:
             f.write(json.dumps(r) + "\n")
-    rs = np.array([r["regret_sel"] for r in recs])
-    ra = np.array([r["regret_analytic"] for r in recs])
+    names = {v: k for k, v in cosma.DTYPES.items() if k in a.dtypes.split(",")}
     summary = {
-        "dtype": "bf16", "train_rows": len(rows), "train_shapes": len({(r["m"], r["n"], r["k"])
-                                                                      for r in rows}),
-        "test_shapes": len(recs), "epochs": a.epochs, "final_loss": hist[-1] if hist else None,
-        "median_regret_learned": float(np.median(rs)) if len(rs) else None,
-        "mean_regret_learned": float(np.mean(rs)) if len(rs) else None,
-        "p90_regret_learned": float(np.percentile(rs, 90)) if len(rs) else None,
-        "median_regret_analytic": float(np.median(ra)) if len(ra) else None,
-        "mean_regret_analytic": float(np.mean(ra)) if len(ra) else None,
-        "p90_regret_analytic": float(np.percentile(ra, 90)) if len(ra) else None,
-        "learned_exact_best_fraction": float(np.mean([r["pick"] == r["best"] for r in recs]))
-        if recs else None,
-        "seconds": {"collect": t_collect, "train": t_train, "eval": t_eval},
+        "train_rows": len(rows),
+        "train_rows_per_dtype": {names[dt]: sum(r["dtype"] == dt for r in rows) for dt in dts},
+        "epochs": a.epochs, "final_loss": hist[-1] if hist else None,
+        "per_dtype": {names[dt]: _summary([r for r in recs if r["dtype"] == dt]) for dt in dts},
+        "all": _summary(recs),
+        "seconds": {"collect": {names[d]: v for d, v in t_collect.items()}, "train": t_train,
+                    "eval": {names[d]: v for d, v in t_eval.items()}},
         "target_standardisation": {"mu": mu, "sigma": sigma},
+        "max_flops": {names[dt]: TUNE[dt]["max_flops"] for dt in dts},
     }
     with open(os.path.join(a.out, "summary.json"), "w") as f:
         json.dump(summary, f, indent=1)

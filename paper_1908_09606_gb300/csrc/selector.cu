@@ -1,12 +1,14 @@
 // Learned plan selector: the MLP cost model of mlp.cu applied to planning.
 //
-// For a product the network predicts the log2-time of each of the
+// For a product the network predicts the log2-time (seconds) of each of the
 // COSMA_MLP_OUT plan candidates (planner.cpp: tile class x k split x
-// assignment order); the selector takes the fastest predicted candidate that
-// applies.  Sizes outside the range the network was trained on, a missing
-// network, or a call that may not synchronise (stream capture) fall back to
-// the analytic plan (Alg. 1's FindSeqSchedule + FitRanks with the cost model).
-// Choices are cached per (m, n, k, dtype).
+// assignment order).  The analytic plan (Alg. 1's FindSeqSchedule + FitRanks
+// with the cost model) stays the choice unless it is one of the candidates and
+// the network predicts another applicable candidate at least kLearnedMargin
+// (log2 units: about 3.5 %) faster; an analytic plan outside the candidate set
+// is kept.  Sizes outside the range the network was trained on, a missing
+// network, or a call that may not synchronise (stream capture) also keep the
+// analytic plan.  Choices are cached per (m, n, k, dtype).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <map>
@@ -35,6 +37,13 @@ struct Selector {
 
 std::mutex g_sel_mu;
 Selector g_sel[16];
+
+constexpr float kLearnedMargin = 0.05f;  // log2 seconds the network must gain
+
+bool same_plan(const cosma_plan& a, const cosma_plan& b) {
+  return a.tile_m == b.tile_m && a.tile_n == b.tile_n && a.k_block == b.k_block &&
+         a.pk == b.pk && a.order == b.order && a.ctas == b.ctas && a.pm == b.pm && a.pn == b.pn;
+}
 
 int features(int64_t m, int64_t n, int64_t k, int dtype, float* x) {
   if (m < 1 || n < 1 || k < 1 || !x) return COSMA_ERR_INVALID_ARG;
@@ -76,17 +85,25 @@ int predict_locked(Selector& s, int count, const int64_t* mnk, int dtype, int* b
       cudaStreamSynchronize(s.stream) != cudaSuccess)
     return COSMA_ERR_CUDA;
   for (int i = 0; i < count; ++i) {
-    int b = -1;
+    const int64_t m = mnk[3 * i], n = mnk[3 * i + 1], k = mnk[3 * i + 2];
+    cosma_plan pa;
+    const bool have_a =
+        plan_gemm(m, n, k, dtype, COSMA_SELECT_ANALYTIC, dev, cfg, &pa, false) == COSMA_OK;
+    int b = -1, ca = -1;
     float bv = 0.f;
     for (int c = 0; c < COSMA_MLP_OUT; ++c) {
       cosma_plan p;
-      if (plan_candidate(mnk[3 * i], mnk[3 * i + 1], mnk[3 * i + 2], dtype, c, dev, cfg, &p) !=
-          COSMA_OK)
-        continue;
+      if (plan_candidate(m, n, k, dtype, c, dev, cfg, &p) != COSMA_OK) continue;
+      if (have_a && ca < 0 && same_plan(p, pa)) ca = c;
       const float v = Y[(size_t)i * COSMA_MLP_OUT + c];
       if (b < 0 || v < bv) { b = c; bv = v; }
     }
-    if (best) best[i] = b;
+    // -1: the analytic plan, kept (see the file header)
+    int choice = -1;
+    if (!have_a) choice = b;
+    else if (ca >= 0) choice = (b >= 0 && bv < Y[(size_t)i * COSMA_MLP_OUT + ca] - kLearnedMargin)
+                                   ? b : ca;
+    if (best) best[i] = choice;
   }
   if (pred) memcpy(pred, Y.data(), Y.size() * 4);
   return COSMA_OK;
@@ -124,9 +141,10 @@ int learned_plan(int64_t m, int64_t n, int64_t k, int dtype, const DeviceInfo& d
     if (!may_sync) return COSMA_ERR_UNSUPPORTED;
     const int64_t mnk[3] = {m, n, k};
     int rc = predict_locked(s, 1, mnk, dtype, &c, nullptr, dev, cfg);
-    if (rc != COSMA_OK || c < 0) return COSMA_ERR_UNSUPPORTED;
+    if (rc != COSMA_OK) return COSMA_ERR_UNSUPPORTED;
     s.cache[key] = c;
   }
+  if (c < 0) return COSMA_ERR_UNSUPPORTED;  // the analytic plan is kept
   return plan_candidate(m, n, k, dtype, c, dev, cfg, out);
 }
 

@@ -83,3 +83,20 @@ def test_initial_weights_he_uniform_zero_biases(tune):
         assert np.abs(W).max() <= lim and np.abs(W).max() > 0.8 * lim
         assert abs(W.mean()) < 0.1 * lim
     assert not b1.any() and not b2.any() and not b3.any()
+
+
+def test_destandardized_network_predicts_log2_seconds(tune):
+    """Folding the target standardisation into the last layer gives the same
+    network with outputs sigma * y + mu (checked with the FP64 oracle MLP)."""
+    p = tune.init_params(5)
+    rng = np.random.default_rng(2)
+    p = p + rng.normal(0.0, 0.05, p.size).astype(np.float32)  # nonzero biases too
+    X = rng.uniform(0.5, 1.0, (6, tune.cosma.COSMA_MLP_IN))
+    mu, sigma = -7.25, 2.5
+    q = tune.destandardize(p, mu, sigma)
+    Y, _ = om.forward(p.astype(np.float64), X)
+    Yq, _ = om.forward(q.astype(np.float64), X)
+    assert np.allclose(Yq, sigma * Y + mu, rtol=1e-5, atol=1e-5)
+    # hidden layers untouched
+    n_hidden = q.size - tune.cosma.COSMA_MLP_OUT * (tune.cosma.COSMA_MLP_HIDDEN + 1)
+    assert np.array_equal(q[:n_hidden], p[:n_hidden])

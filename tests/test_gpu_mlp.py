@@ -172,13 +172,15 @@ def test_selector_end_to_end_small():
     test = autotune.random_shapes(6, seed=6, lo=256, hi=2048)
     best, pred = cosma.cosma_selector_predict(test, cosma.COSMA_BF16)
     for (m, n, k), b in zip(test, best):
-        assert cosma.cosma_plan_candidate(m, n, k, cosma.COSMA_BF16, b) is not None
+        # -1: the analytic plan is kept (it lies outside the candidate set)
+        assert b == -1 or cosma.cosma_plan_candidate(m, n, k, cosma.COSMA_BF16, b) is not None
     # the learned selector drives planning; results stay correct
     try:
         assert cosma.cosma_init(selector=cosma.COSMA_SELECT_LEARNED) == 0
         m, n, k = test[0]
         pl = cosma.cosma_plan_query(m, n, k, cosma.COSMA_BF16, cosma.COSMA_SELECT_LEARNED)
-        want = cosma.cosma_plan_candidate(m, n, k, cosma.COSMA_BF16, best[0])
+        want = (cosma.cosma_plan_candidate(m, n, k, cosma.COSMA_BF16, best[0]) if best[0] >= 0
+                else cosma.cosma_plan_query(m, n, k, cosma.COSMA_BF16, cosma.COSMA_SELECT_ANALYTIC))
         assert (pl.tile_n, pl.pk, pl.order) == (want.tile_n, want.pk, want.order)
         A, B = device_operands(m, n, k, "bf16")
         C, _ = out_tensor(m, n, "bf16")
@@ -194,30 +196,32 @@ def test_selector_end_to_end_small():
         cosma.cosma_selector_set(None)
 
 
-def test_shipped_selector_gain_on_held_out_shapes():
-    """The shipped network (trained with the library's own kernels on a GB300) on
-    24 shapes it never saw: every candidate timed, median regret of its pick <= 5 %,
-    and what it gains over the analytic plan reported."""
+@pytest.mark.parametrize("dtype", ["bf16", "f32", "f64", "f64_emu_bf16"])
+def test_shipped_selector_gain_on_held_out_shapes(dtype):
+    """The shipped network (trained with the library's own kernels on a GB300 on
+    all four dtypes) on shapes it never saw: every candidate timed (median of 3).
+    The learned selector's median regret against exhaustive search is <= 5 %,
+    and its mean regret is no worse than the analytic plan's: where the two
+    choose the same plan they share one measurement, so the comparison is decided
+    on the shapes where the network overrides the analytic plan."""
     import numpy as np
     from paper_1908_09606_gb300 import autotune
     cosma = lib()
+    dt = cosma.DTYPES[dtype]
     autotune.install()
     try:
-        shapes = autotune.random_shapes(24, seed=300, lo=256, hi=8192, cap_bytes=512e6)
-        recs = autotune.evaluate(shapes, cosma.COSMA_BF16, cap_bytes=512e6, reps=3)
+        cap = autotune.TUNE[dt]["max_flops"] / 8
+        shapes = autotune.random_shapes(16, seed=300 + dt, lo=256, hi=8192, cap_bytes=1e9,
+                                        dtype=dt, max_flops=cap)
+        recs = autotune.evaluate(shapes, dt, cap_bytes=1e9, reps=3)
         rs = np.array([r["regret_sel"] for r in recs])
         ra = np.array([r["regret_analytic"] for r in recs])
-        gain = np.array([r["t_analytic"] / r["t_sel"] - 1.0 for r in recs])
-        print(f"learned median regret {np.median(rs):.3f}, analytic {np.median(ra):.3f}; "
-              f"median gain over analytic {np.median(gain):+.3f}")
-        assert len(recs) >= 20
+        differ = sum(r["pick"] >= 0 and r["pick"] != r["analytic"] for r in recs)
+        print(f"{dtype}: learned median / mean regret {np.median(rs):.3f} / {np.mean(rs):.3f}, "
+              f"analytic {np.median(ra):.3f} / {np.mean(ra):.3f}; overrides {differ}")
+        assert len(recs) >= 12
         assert np.median(rs) <= 0.05
-        # the shipped weights are bf16's: other dtypes keep the analytic plan
-        for dt in (cosma.COSMA_F32, cosma.COSMA_F64, cosma.COSMA_F64_EMU_BF16):
-            learned = cosma.cosma_plan_query(4096, 4096, 4096, dt, cosma.COSMA_SELECT_LEARNED)
-            analytic = cosma.cosma_plan_query(4096, 4096, 4096, dt, cosma.COSMA_SELECT_ANALYTIC)
-            assert (learned.tile_m, learned.tile_n, learned.pk, learned.order, learned.ctas) == \
-                (analytic.tile_m, analytic.tile_n, analytic.pk, analytic.order, analytic.ctas)
+        assert np.mean(rs) <= np.mean(ra) + 0.005
     finally:
         cosma.cosma_init()  # back to the default (analytic) configuration
         cosma.cosma_selector_set(None)
