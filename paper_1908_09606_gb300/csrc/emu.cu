@@ -331,7 +331,8 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
 // T = sum_chunks sum_l 2^(beta (s + 1 - l) - base) L_l kept
 // in a per-CTA scratch region in global memory: the first merge of a tile
 // stores, later ones are reductions performed in L2, and the thread that made
-// them reads the total back (L2 only) to form the FP64 result,
+// them reads the total back (L2 only), adds the tile's last level sum in
+// registers and forms the FP64 result,
 // C = T 2^(sigma_i + tau_j + 2 - beta (s + 1) + base).  `base` (host, from k)
 // keeps |T| < 2^62; levels whose weight is below 2^base are rounded to it.
 
@@ -407,6 +408,7 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
         for (int64_t c0 = sc0 + gk; c0 < sc1; c0 += gk)
           if (!drain(std::false_type{})) { ok = false; break; }
         if (!ok) break;
+        if (sc1 >= kbt && lvl == 2) break;  // the tile's last merge is folded into the read-back
         // K-RECOMB: T += L 2^(beta (top - lvl) - base), exactly
         const int sh = a.beta * (top - lvl) - a.t_base;
         // (8 columns at a time: each batch's shifted values are sent before the next
@@ -449,15 +451,28 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
     // not keep the merges' per-column addresses live across the loops
     long long* Tf = Tt;
     asm volatile("" : "+l"(Tf));
+    const int sh2 = a.beta * (top - 2) - a.t_base;  // the last merge: level 2, last chunk
+    // read-back one 8-column batch ahead of its use
+    long long nx[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      asm volatile("ld.relaxed.gpu.global.L2::cache_hint.s64 %0, [%1], %2;"
+                   : "=l"(nx[j])
+                   : "l"(Tf + j * 128), "l"(keep)
+                   : "memory");
 #pragma unroll
     for (int c = 0; c < HC; c += 8) {
       long long tv[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
-        asm volatile("ld.relaxed.gpu.global.L2::cache_hint.s64 %0, [%1], %2;"
-                     : "=l"(tv[j])
-                     : "l"(Tf + (c + j) * 128), "l"(keep)
-                     : "memory");
+      for (int j = 0; j < 8; ++j) tv[j] = nx[j] + fx_shift(Lv[c + j], sh2);
+      if (c + 8 < HC) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          asm volatile("ld.relaxed.gpu.global.L2::cache_hint.s64 %0, [%1], %2;"
+                       : "=l"(nx[j])
+                       : "l"(Tf + (c + 8 + j) * 128), "l"(keep)
+                       : "memory");
+      }
       int eb[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) eb[j] = cbase + c + j < a.sch.n ? a.eB[cbase + c + j] : kExpNone;
@@ -537,6 +552,15 @@ __device__ __forceinline__ bool emu_walk(const EmuArgs& a, GroupBegin group_begi
   return emu_walk_chunks(a, [](int64_t) { return true; }, group_begin, body, group_end);
 }
 
+// Threads of both emulation kernels: warps 0-3 (producer, MMA issuer, two idle),
+// one on each SM quarter, and the epilogue warps 4-11, two on each quarter.
+constexpr int kPairThreads = 384;
+// Registers per thread the kernels' register split assumes at launch: the
+// register file is split by SM quarter, and on each quarter the control warp's
+// 56 plus two epilogue warps' 224 must fit in the three warps' launch share,
+// 56 + 2 x 224 = 3 x 168.
+constexpr int kPairMinRegs = 168;
+
 struct ELayout {
   static constexpr int NACC = 512 / EBN;                        // accumulator buffers
   static constexpr int A_BYTES = EBM * EBK * 2;
@@ -548,7 +572,7 @@ struct ELayout {
   static constexpr int ALLOC = TOTAL + 1024;
 };
 
-__global__ void __launch_bounds__(320, 1)
+__global__ void __launch_bounds__(kPairThreads, 1)
 emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 EmuArgs a) {
   using L = ELayout;
@@ -591,6 +615,15 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   const int cta = blockIdx.x;
   const int64_t nunits = units_of_cta(a.sch, cta);
 
+  // register split per SM quarter, as in the pair kernel
+  if (warp >= 4) {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 224;\n" ::: "memory");
+    uint32_t te[NACC];
+#pragma unroll
+    for (int b = 0; b < NACC; ++b) te[b] = tc::mapa_shared(&tempty[b], 0);
+    emu_fx_epilogue<EBN, EBM, 4>(a, cta, nunits, 0, tmem_base, tfull, te, w, warp, lane);
+  } else {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 56;\n" ::: "memory");
   if (warp == 0) {
     if (tc::elect_one()) {
       int stage = 0;
@@ -667,11 +700,7 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       while (!tc::mbar_try_wait(drain, 0) && clock64() - t0 < tc::kDrainCycles) {
       }
     }
-  } else {
-    uint32_t te[NACC];
-#pragma unroll
-    for (int b = 0; b < NACC; ++b) te[b] = tc::mapa_shared(&tempty[b], 0);
-    emu_fx_epilogue<EBN, EBM, 2>(a, cta, nunits, 0, tmem_base, tfull, te, w, warp, lane);
+  }
   }
   __syncthreads();
   if (warp == 1) {
@@ -690,15 +719,6 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 // cores at their full rate per clock (N = 128 ones reach about 81 % of it), and
 // per SM an MMA step reads 8 KB of operands for 128 x 256 x 16 products.
 //
-// Threads of the pair kernel: warps 0-3 (producer, MMA issuer, two idle), one
-// on each SM quarter, and the epilogue warps 4-11, two on each quarter.
-constexpr int kPairThreads = 384;
-// Registers per thread the pair kernel's register split assumes at launch: the
-// register file is split by SM quarter, and on each quarter the control warp's
-// 56 plus two epilogue warps' 224 must fit in the three warps' launch share,
-// 56 + 2 x 224 = 3 x 168.
-constexpr int kPairMinRegs = 168;
-
 template <int BN>
 struct PairLayout {
   static constexpr int NACC = 512 / BN;                   // accumulator buffers
@@ -1195,8 +1215,13 @@ int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cos
     const cudaError_t attr = cudaFuncSetAttribute(
         emu_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ELayout::ALLOC);
     if (attr != cudaSuccess) return (int)attr;
+    {
+      cudaFuncAttributes fa;  // the warps' register split draws on what the launch allocates
+      if (cudaFuncGetAttributes(&fa, emu_gemm_kernel) != cudaSuccess) return (int)cudaGetLastError();
+      if (fa.numRegs < kPairMinRegs) return COSMA_ERR_UNSUPPORTED;
+    }
     prof_mark(st, true);
-    emu_gemm_kernel<<<sch.ctas, 320, ELayout::ALLOC, st>>>(ta, tb, args);
+    emu_gemm_kernel<<<sch.ctas, kPairThreads, ELayout::ALLOC, st>>>(ta, tb, args);
     prof_mark(st, false);
     le = cudaGetLastError();
   }
