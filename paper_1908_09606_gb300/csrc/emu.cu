@@ -387,12 +387,12 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
           tc::tc_fence_after();
           const uint32_t src = tmem_base + lane_off + acc * BN + col_lo;
 #pragma unroll
-          for (int c = 0; c < HC; c += 16) {
-            uint32_t v[16];
-            tc::tmem_ld_32x16(src + c, v);
+          for (int c = 0; c < HC; c += 32) {
+            uint32_t v[32];
+            tc::tmem_ld_32x32(src + c, v);
             tc::tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < 32; ++j) {
               const int iv = __float2int_rn(__uint_as_float(v[j]));  // exact integer
               Lv[c + j] = kFirst ? iv : Lv[c + j] + iv;
             }
