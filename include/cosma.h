@@ -363,6 +363,13 @@ int cosma_mlp_adam(int n, float* params, const float* grad, float* m, float* v, 
  * params == NULL removes the network. */
 int cosma_selector_set(const float* params, double log2_lo, double log2_hi);
 
+/* Sets, for one dtype on the current device, how much faster (log2 seconds,
+ * >= 0; INFINITY: never) the network must predict a candidate than the analytic
+ * plan before COSMA_SELECT_LEARNED takes it; the default is 0.05 (about 3.5 %).
+ * Kept across cosma_selector_set.  COSMA_ERR_INVALID_ARG for a bad dtype or a
+ * negative / NaN margin; COSMA_ERR_CUDA without a device. */
+int cosma_selector_margin(int dtype, float log2_margin);
+
 /* Restricts the installed network to the dtypes whose bit (1 << dtype) is set in
  * dtype_mask -- the ones it was trained on; plans of other dtypes use the
  * analytic selector.  cosma_selector_set resets the mask to every dtype.
@@ -374,8 +381,8 @@ int cosma_selector_restrict(unsigned dtype_mask);
  * and optionally all predictions (pred, HOST, count x OUT floats, may be
  * NULL).  The choice is the analytic plan -- written as its candidate index
  * when it is one of the candidates, else as -1 -- unless the network predicts
- * another applicable candidate faster by at least 0.05 in log2 seconds (about
- * 3.5 %), whose index is then written.  Synchronous. */
+ * another applicable candidate faster by at least the dtype's margin
+ * (cosma_selector_margin), whose index is then written.  Synchronous. */
 int cosma_selector_predict(int count, const int64_t* mnk, int dtype, int* best, float* pred);
 
 /* ---- measurement ------------------------------------------------------ */

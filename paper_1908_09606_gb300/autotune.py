@@ -167,6 +167,52 @@ def collect(path, shapes, dtype=cosma.COSMA_BF16, cap_bytes=16e9, max_ws_bytes=2
     return _load_rows(path)
 
 
+def is_calibration(m, n, k, dtype):
+    """One shape in five (by a hash of the shape) is kept out of training and used
+    to calibrate the selector's per-dtype margin."""
+    h = (int(m) * 73856093) ^ (int(n) * 19349663) ^ (int(k) * 83492791) ^ int(dtype)
+    return h % 5 == 0
+
+
+# Margins (log2 seconds) the calibration chooses from; inf: keep the analytic plan.
+MARGINS = (0.05, 0.1, 0.15, 0.2, 0.3, 0.5, 1.0, math.inf)
+
+
+def calibrate_margin(rows, dtype, max_ws_bytes=24e9):
+    """The margin (from MARGINS) whose learned choices have the least mean regret
+    on the calibration shapes of `rows` (every candidate of a shape timed), ties
+    to the larger margin; shapes whose analytic plan is not a timed candidate are
+    skipped (the selector keeps the analytic plan there anyway).  Uses the
+    installed network.  Returns (margin, {margin: mean regret}, shapes used)."""
+    by = {}
+    for r in rows:
+        if r["dtype"] == dtype and is_calibration(r["m"], r["n"], r["k"], dtype):
+            by.setdefault((r["m"], r["n"], r["k"]), {})[r["cand"]] = r["seconds"]
+    shapes = sorted(by)
+    if not shapes:
+        return 0.05, {}, 0
+    _, preds = cosma.cosma_selector_predict(shapes, dtype)
+    regrets = {mg: [] for mg in MARGINS}
+    used = 0
+    for (m, n, k), pred in zip(shapes, preds):
+        times = by[(m, n, k)]
+        ca = analytic_candidate(m, n, k, dtype, candidates(m, n, k, dtype, max_ws_bytes))
+        if ca is None or ca not in times:
+            continue
+        used += 1
+        best_t = min(times.values())
+        b = min(times, key=lambda c: pred[c])
+        for mg in MARGINS:
+            choice = b if pred[b] < pred[ca] - mg else ca
+            regrets[mg].append(times[choice] / best_t - 1.0)
+    if not used:
+        return 0.05, {}, 0
+    mean = {mg: float(np.mean(v)) for mg, v in regrets.items()}
+    lo = min(mean.values())
+    pick = max(mg for mg in MARGINS if mean[mg] <= lo + 1e-12)
+    return pick, mean, used
+
+
 def features(rows):
     X = np.array([cosma.cosma_selector_features(r["m"], r["n"], r["k"], r["dtype"]) for r in rows],
                  dtype=np.float32)
@@ -333,13 +379,22 @@ def tune_grouped(As, Bs, Cs, dtype, tiles=None, reps=3):
 
 def install(params_path=None, log2_lo=8.0, log2_hi=16.0, dtypes=None):
     """Installs trained selector weights saved by main() (an .npy vector of
-    log2-second outputs); by default the weights shipped with the package,
-    trained on a GB300 on all four dtypes.  dtypes: restrict the network to
-    these (None: every dtype)."""
-    p = np.load(params_path or SHIPPED_PARAMS).astype(np.float32)
+    log2-second outputs, with its per-dtype margins from <stem>_margins.json when
+    present); by default the weights shipped with the package, trained on a GB300
+    on all four dtypes.  dtypes: restrict the network to these (None: every
+    dtype)."""
+    path = params_path or SHIPPED_PARAMS
+    p = np.load(path).astype(np.float32)
     rc = cosma.cosma_selector_set(p, log2_lo, log2_hi)
     if rc != 0:
         raise cosma.CosmaError(rc, "cosma_selector_set")
+    mpath = os.path.splitext(path)[0] + "_margins.json"
+    if os.path.exists(mpath):
+        with open(mpath) as f:
+            for name, mg in json.load(f).items():
+                rc = cosma.cosma_selector_margin(name, math.inf if mg is None else mg)
+                if rc != 0:
+                    raise cosma.CosmaError(rc, "cosma_selector_margin")
     if dtypes is not None:
         rc = cosma.cosma_selector_restrict(dtypes)
         if rc != 0:
@@ -358,6 +413,8 @@ def parser():
                     help="scales every dtype's collection budget")
     ap.add_argument("--eval-budget-s", type=float, default=600, help="over all dtypes")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-collect", action="store_true",
+                    help="train on the timing files already in --out")
     return ap
 
 
@@ -396,11 +453,14 @@ def main(argv=None):
         shapes = random_shapes(a.train_shapes, seed=100 + a.seed + 1000 * dt, dtype=dt,
                                max_flops=TUNE[dt]["max_flops"])
         t0 = time.time()
-        rows += collect(os.path.join(a.out, f"timings_{dt}.jsonl"), shapes, dt,
-                        time_budget_s=TUNE[dt]["budget_s"] * a.budget_scale, reps=3)
+        path = os.path.join(a.out, f"timings_{dt}.jsonl")
+        rows += (_load_rows(path) if a.no_collect else
+                 collect(path, shapes, dt, time_budget_s=TUNE[dt]["budget_s"] * a.budget_scale,
+                         reps=3))
         t_collect[dt] = time.time() - t0
         log(f"dtype {dt}: {len(rows)} rows so far")
-    X, c, y = features(rows)
+    train_rows = [r for r in rows if not is_calibration(r["m"], r["n"], r["k"], r["dtype"])]
+    X, c, y = features(train_rows)
     t0 = time.time()
     p, hist, (mu, sigma) = train(X, c, y, epochs=a.epochs, seed=a.seed,
                                  checkpoint=os.path.join(a.out, "checkpoint.npz"), log=log)
@@ -410,6 +470,17 @@ def main(argv=None):
     rc = cosma.cosma_selector_set(p, math.log2(256), math.log2(65536))
     if rc != 0:
         raise cosma.CosmaError(rc, "cosma_selector_set")
+    names = {v: k for k, v in cosma.DTYPES.items() if k in a.dtypes.split(",")}
+    margins, calib = {}, {}
+    for dt in dts:
+        mg, table, used = calibrate_margin(rows, dt)
+        cosma.cosma_selector_margin(dt, mg)
+        margins[names[dt]] = None if math.isinf(mg) else mg
+        calib[names[dt]] = {"margin": margins[names[dt]], "shapes": used,
+                            "mean_regret_by_margin": {str(k): v for k, v in table.items()}}
+        log(f"dtype {dt}: margin {mg} from {used} calibration shapes")
+    with open(os.path.join(a.out, "selector_params_margins.json"), "w") as f:
+        json.dump(margins, f, indent=1)
     per = max(1, a.test_shapes // len(dts))
     recs, t_eval = [], {}
     for dt in dts:
@@ -424,10 +495,11 @@ def main(argv=None):
     with open(os.path.join(a.out, "eval.jsonl"), "w") as f:
         for r in recs:
             f.write(json.dumps(r) + "\n")
-    names = {v: k for k, v in cosma.DTYPES.items() if k in a.dtypes.split(",")}
     summary = {
-        "train_rows": len(rows),
-        "train_rows_per_dtype": {names[dt]: sum(r["dtype"] == dt for r in rows) for dt in dts},
+        "train_rows": len(train_rows), "calibration_rows": len(rows) - len(train_rows),
+        "margins": calib,
+        "train_rows_per_dtype": {names[dt]: sum(r["dtype"] == dt for r in train_rows)
+                                 for dt in dts},
         "epochs": a.epochs, "final_loss": hist[-1] if hist else None,
         "per_dtype": {names[dt]: _summary([r for r in recs if r["dtype"] == dt]) for dt in dts},
         "all": _summary(recs),

@@ -100,6 +100,7 @@ SIGNATURES = [
                               ctypes.c_float, ctypes.c_float, _VP]),
     ("cosma_selector_set", _INT, [ctypes.POINTER(ctypes.c_float), _D, _D]),
     ("cosma_selector_restrict", _INT, [ctypes.c_uint]),
+    ("cosma_selector_margin", _INT, [_INT, ctypes.c_float]),
     ("cosma_selector_predict", _INT, [_INT, ctypes.POINTER(ctypes.c_int64), _INT,
                                       ctypes.POINTER(_INT), ctypes.POINTER(ctypes.c_float)]),
     ("cosma_gemm_splitk_static", _INT, [_I64, _I64, _I64, _VP, _I64, _VP, _I64, _VP, _I64,
@@ -240,6 +241,13 @@ def cosma_selector_set(params, log2_lo=0.0, log2_hi=64.0):
         return load().cosma_selector_set(None, log2_lo, log2_hi)
     arr = (ctypes.c_float * COSMA_MLP_PARAMS)(*[float(x) for x in params])
     return load().cosma_selector_set(arr, log2_lo, log2_hi)
+
+
+def cosma_selector_margin(dtype, log2_margin):
+    """How much faster (log2 seconds) the network must predict a candidate than
+    the analytic plan before the learned selector takes it, for one dtype."""
+    code = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    return load().cosma_selector_margin(code, float(log2_margin))
 
 
 def cosma_selector_restrict(dtypes):

@@ -4,9 +4,10 @@
 // COSMA_MLP_OUT plan candidates (planner.cpp: tile class x k split x
 // assignment order).  The analytic plan (Alg. 1's FindSeqSchedule + FitRanks
 // with the cost model) stays the choice unless it is one of the candidates and
-// the network predicts another applicable candidate at least kLearnedMargin
-// (log2 units: about 3.5 %) faster; an analytic plan outside the candidate set
-// is kept.  Sizes outside the range the network was trained on, a missing
+// the network predicts another applicable candidate faster by at least the
+// dtype's margin (log2 seconds; 0.05, about 3.5 %, unless set -- the autotuner
+// calibrates one per dtype on shapes kept out of training); an analytic plan
+// outside the candidate set is kept.  Sizes outside the range the network was trained on, a missing
 // network, or a call that may not synchronise (stream capture) also keep the
 // analytic plan.  Choices are cached per (m, n, k, dtype).
 #include <cuda_runtime.h>
@@ -28,6 +29,7 @@ struct Selector {
   float* dev = nullptr;  // device parameters
   double lo = 0.0, hi = 0.0;
   unsigned dtype_mask = ~0u;  // dtypes the network was trained on
+  float margin[8] = {0.05f, 0.05f, 0.05f, 0.05f, 0.05f, 0.05f, 0.05f, 0.05f};  // log2 s
   std::map<std::tuple<int64_t, int64_t, int64_t, int>, int> cache;
   cudaStream_t stream = nullptr;
   float* dX = nullptr;
@@ -38,7 +40,6 @@ struct Selector {
 std::mutex g_sel_mu;
 Selector g_sel[16];
 
-constexpr float kLearnedMargin = 0.05f;  // log2 seconds the network must gain
 
 bool same_plan(const cosma_plan& a, const cosma_plan& b) {
   return a.tile_m == b.tile_m && a.tile_n == b.tile_n && a.k_block == b.k_block &&
@@ -101,7 +102,7 @@ int predict_locked(Selector& s, int count, const int64_t* mnk, int dtype, int* b
     // -1: the analytic plan, kept (see the file header)
     int choice = -1;
     if (!have_a) choice = b;
-    else if (ca >= 0) choice = (b >= 0 && bv < Y[(size_t)i * COSMA_MLP_OUT + ca] - kLearnedMargin)
+    else if (ca >= 0) choice = (b >= 0 && bv < Y[(size_t)i * COSMA_MLP_OUT + ca] - s.margin[dtype & 7])
                                    ? b : ca;
     if (best) best[i] = choice;
   }
@@ -225,6 +226,18 @@ int cosma_selector_set(const float* params, double log2_lo, double log2_hi) {
   s.hi = log2_hi;
   s.dtype_mask = ~0u;
   s.ready = true;
+  return COSMA_OK;
+}
+
+int cosma_selector_margin(int dtype, float log2_margin) {
+  if (dtype < COSMA_F64 || dtype > COSMA_F32_EMU_TF32 || !(log2_margin >= 0.f))
+    return COSMA_ERR_INVALID_ARG;
+  const int d = device_index();
+  if (d < 0) return COSMA_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_sel_mu);
+  Selector& s = g_sel[d];
+  s.margin[dtype] = log2_margin;
+  s.cache.clear();
   return COSMA_OK;
 }
 

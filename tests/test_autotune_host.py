@@ -100,3 +100,12 @@ def test_destandardized_network_predicts_log2_seconds(tune):
     # hidden layers untouched
     n_hidden = q.size - tune.cosma.COSMA_MLP_OUT * (tune.cosma.COSMA_MLP_HIDDEN + 1)
     assert np.array_equal(q[:n_hidden], p[:n_hidden])
+
+
+def test_calibration_shapes_are_a_fixed_fifth(tune):
+    shapes = tune.random_shapes(2000, seed=11)
+    flags = [tune.is_calibration(m, n, k, 2) for m, n, k in shapes]
+    assert flags == [tune.is_calibration(m, n, k, 2) for m, n, k in shapes]
+    assert 0.15 < np.mean(flags) < 0.25
+    assert tune.MARGINS[0] > 0 and math.isinf(tune.MARGINS[-1])
+    assert list(tune.MARGINS) == sorted(tune.MARGINS)
