@@ -415,6 +415,8 @@ def parser():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-collect", action="store_true",
                     help="train on the timing files already in --out")
+    ap.add_argument("--eval-only", metavar="PARAMS",
+                    help="install these weights (and their margins) and only evaluate")
     return ap
 
 
@@ -440,6 +442,26 @@ def _summary(recs):
     }
 
 
+def _evaluate_all(a, dts):
+    """Held-out shapes of every dtype, timed within the evaluation budget;
+    records also written to <out>/eval.jsonl."""
+    per = max(1, a.test_shapes // len(dts))
+    recs, t_eval = [], {}
+    for dt in dts:
+        test = random_shapes(per, seed=200 + a.seed + 1000 * dt, dtype=dt,
+                             max_flops=TUNE[dt]["max_flops"])
+        t0 = time.time()
+        for sh in test:
+            if time.time() - t0 > a.eval_budget_s / len(dts):
+                break
+            recs += evaluate([sh], dt, reps=3)
+        t_eval[dt] = time.time() - t0
+    with open(os.path.join(a.out, "eval.jsonl"), "w") as f:
+        for r in recs:
+            f.write(json.dumps(r) + "\n")
+    return recs, t_eval
+
+
 def main(argv=None):
     import torch
     a = parser().parse_args(argv)
@@ -448,6 +470,19 @@ def main(argv=None):
     cosma.load()
     log = lambda s: print(s, flush=True)  # noqa: E731
     dts = [cosma.DTYPES[d] for d in a.dtypes.split(",")]
+    names = {v: k for k, v in cosma.DTYPES.items() if k in a.dtypes.split(",")}
+    if a.eval_only:
+        install(a.eval_only)
+        recs, t_eval = _evaluate_all(a, dts)
+        summary = {"params": os.path.basename(a.eval_only),
+                   "per_dtype": {names[dt]: _summary([r for r in recs if r["dtype"] == dt])
+                                 for dt in dts},
+                   "all": _summary(recs),
+                   "seconds": {"eval": {names[d]: v for d, v in t_eval.items()}}}
+        with open(os.path.join(a.out, "summary.json"), "w") as f:
+            json.dump(summary, f, indent=1)
+        print(json.dumps(summary), flush=True)
+        return 0
     rows, t_collect = [], {}
     for dt in dts:
         shapes = random_shapes(a.train_shapes, seed=100 + a.seed + 1000 * dt, dtype=dt,
@@ -470,7 +505,6 @@ def main(argv=None):
     rc = cosma.cosma_selector_set(p, math.log2(256), math.log2(65536))
     if rc != 0:
         raise cosma.CosmaError(rc, "cosma_selector_set")
-    names = {v: k for k, v in cosma.DTYPES.items() if k in a.dtypes.split(",")}
     margins, calib = {}, {}
     for dt in dts:
         mg, table, used = calibrate_margin(rows, dt)
@@ -481,20 +515,7 @@ def main(argv=None):
         log(f"dtype {dt}: margin {mg} from {used} calibration shapes")
     with open(os.path.join(a.out, "selector_params_margins.json"), "w") as f:
         json.dump(margins, f, indent=1)
-    per = max(1, a.test_shapes // len(dts))
-    recs, t_eval = [], {}
-    for dt in dts:
-        test = random_shapes(per, seed=200 + a.seed + 1000 * dt, dtype=dt,
-                             max_flops=TUNE[dt]["max_flops"])
-        t0 = time.time()
-        for sh in test:
-            if time.time() - t0 > a.eval_budget_s / len(dts):
-                break
-            recs += evaluate([sh], dt, reps=3)
-        t_eval[dt] = time.time() - t0
-    with open(os.path.join(a.out, "eval.jsonl"), "w") as f:
-        for r in recs:
-            f.write(json.dumps(r) + "\n")
+    recs, t_eval = _evaluate_all(a, dts)
     summary = {
         "train_rows": len(train_rows), "calibration_rows": len(rows) - len(train_rows),
         "margins": calib,
