@@ -121,7 +121,10 @@ typedef struct cosma_config {
 /* A schedule for one product: the outcome of Alg. 1's FindSeqSchedule
  * (tile_m x tile_n C tile and k_block x stages input ring that fit in S),
  * ParallelizeSched/FitRanks (processor grid pm x pn x pk over the SMs; pk > 1
- * is a split of k followed by the Reduce step), and the assignment order. */
+ * is a split of k followed by the Reduce step), and the assignment order.
+ * COSMA_KERNEL_EMU_BF16 plans use order 1 and cut k at multiples of 4096 (the
+ * kernels' super-chunk), so 1 <= pk <= ceil(k / 4096); their k slices sum the
+ * same exact integers as an unsplit product, and C is bit-for-bit the same. */
 typedef struct cosma_plan {
   int kernel;          /* cosma_kernel */
   int tile_m, tile_n;  /* C tile held in fast memory (the paper's a x b)  */
@@ -296,7 +299,8 @@ int cosma_plan_query(int64_t m, int64_t n, int64_t k, int dtype, int selector,
                      cosma_plan* out);
 
 /* Work units of a plan in execution order, as int64 sextuples
- * (row0, row1, col0, col1, k0, k1) per CTA, CTAs one after another.  Writes
+ * (row0, row1, col0, col1, k0, k1) per CTA, CTAs one after another (for an
+ * emulated FP64 plan, as its kernels number them: k slice first).  Writes
  * at most max_units units to `units` (HOST, 6*max_units int64) and returns the
  * total number of units (so a first call with max_units = 0 sizes the buffer),
  * or a negative cosma_status. */

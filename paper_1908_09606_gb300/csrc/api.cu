@@ -311,7 +311,8 @@ int check_args(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda, cons
 long long total_workspace(int64_t m, int64_t n, int64_t k, int dtype, const cosma_plan& p,
                           const void* A = nullptr, int64_t lda = 0, const void* B = nullptr,
                           int64_t ldb = 0, int ta = 0, int tb = 0) {
-  if (dtype == COSMA_F64_EMU_BF16) return emu_workspace_bytes(m, n, k, g_cfg, p.sms);
+  if (dtype == COSMA_F64_EMU_BF16)
+    return emu_workspace_bytes(m, n, k, g_cfg, p.sms, p.pk > 1 ? m * n : 0);
   if (dtype == COSMA_BF16) return tc_workspace_bytes(m, n, k, p, A, lda, ta, B, ldb, tb);
   if (dtype == COSMA_F32_EMU_TF32) return tf32x3_workspace_bytes(m, n, k, p);
   // FMA paths: split-k partials, then untransposed copies of transposed operands
@@ -600,7 +601,8 @@ long long cosma_plan_units(int64_t m, int64_t n, int64_t k, const cosma_plan* pl
     const int64_t nu = units_of_cta(s, c);
     for (int64_t i = 0; i < nu; ++i, ++total) {
       if (total >= max_units) continue;
-      const Unit u = unit_of_cta(s, c, i);
+      const Unit u = plan->kernel == COSMA_KERNEL_EMU_BF16 ? emu_unit_of_cta(s, c, i)
+                                                          : unit_of_cta(s, c, i);
       int64_t* o = units + 6 * total;
       o[0] = u.tile_row * s.tile_m;
       o[1] = (u.tile_row + 1) * s.tile_m < m ? (u.tile_row + 1) * s.tile_m : m;

@@ -34,6 +34,12 @@
 // ring (7 stages of 32 KB, 9 of 24 KB for 256 x 128 pairs).  Pairs launched
 // cooperatively advance in lock-step super-chunks (bounded waits) so that
 // concurrent tiles read the same slice panels from L2.
+//
+// k split (the parallel schedule's pk > 1, Sec. 6.1, for products with few C
+// tiles): k is cut at super-chunk boundaries, each unit (tile, k slice) ends
+// with its exact fixed-point total, and the units' totals are summed exactly in
+// an int64 array (L2 reductions) that a finishing pass rounds to FP64 -- the
+// integers an unsplit product sums, so the split changes no bit of C.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -269,8 +275,9 @@ __global__ void split_b_kernel(const double* __restrict__ B, int64_t k, int64_t 
 
 // ---- K-EMU / K-RECOMB -------------------------------------------------------------
 //
-// Iteration order of one C tile (all roles walk it identically):
-//   for each k super-chunk [sc0, sc1) of kcb k-blocks
+// Iteration order of one unit (a C tile over the k blocks [kb0, kb1) of its k
+// slice; all roles walk it identically):
+//   for each k super-chunk [sc0, sc1) of kcb k-blocks in [kb0, kb1)
 //     for each level l = s+1 down to 2 (p = l - 1 slice pairs)
 //       for each exact group [c0, c1) of gk(p) k-blocks inside the super-chunk
 //         for each pair q = 1..p:  for each k-block kb in [c0, c1):
@@ -282,7 +289,8 @@ __global__ void split_b_kernel(const double* __restrict__ B, int64_t k, int64_t 
 // them in L2 across the levels at the price of more merges of the running total.
 
 struct EmuArgs {
-  Sched sch;           // tiles (128 or 256 rows x 128 columns), order 1, pk = 1
+  Sched sch;           // tiles (128 x 128, or 256 x 256 / 256 x 128 pairs), order 1; units
+                       // from emu_unit_of_cta (k slices of whole super-chunks)
   int s, beta;
   int group_kb;        // k blocks of one pair per exact group (2^(24 - 2 beta + 2) / 64)
   int chunk_kb;        // k blocks per super-chunk
@@ -296,6 +304,8 @@ struct EmuArgs {
   long long* T;            // per-CTA running totals, 128 x tile_n int64 each
   int t_base;              // fixed-point base of T (see "Running total")
   double alpha, beta_c;    // C = alpha A B + beta_c C (C read only when beta_c != 0)
+  long long* X;            // pk > 1: the units' totals are summed here ([m][n], zeroed),
+                           // and emu_finish_kernel forms C; null: units write C
 };
 
 // One 64 (k) x rows box of slice q at k-block kb and row y of the k-blocked layout.
@@ -342,6 +352,26 @@ __device__ __forceinline__ long long fx_shift(int v, int sh) {
   return ((long long)v + (1LL << (-sh - 1))) >> (-sh);
 }
 
+// 8 x 8 transpose within each group of 8 lanes: on entry lane l holds row l of
+// the group's block (v[j] = entry (l % 8, j)), on return column l % 8 (v[i] =
+// entry (i, l % 8)).  Three butterfly stages: at stage sb, entries whose row and
+// column differ in bit sb trade places with lane ^ sb.
+template <class V>
+__device__ __forceinline__ void transpose8(V (&v)[8], int l8) {
+#pragma unroll
+  for (int sb = 4; sb >= 1; sb >>= 1) {
+#pragma unroll
+    for (int i0 = 0; i0 < 8; ++i0) {
+      if (i0 & sb) continue;
+      const bool up = (l8 & sb) != 0;
+      const V send = up ? v[i0] : v[i0 | sb];
+      const V recv = __shfl_xor_sync(0xffffffffu, send, sb);
+      if (up) v[i0] = recv;
+      else v[i0 | sb] = recv;
+    }
+  }
+}
+
 // Epilogue warps W0 .. W0 + 7 of K-EMU / K-RECOMB for the units of one CTA (or
 // CTA pair): warp -> tensor-memory lane quadrant q4 = warp % 4 and column half
 // h; each thread owns one row and BN / 2 columns of this CTA's 128 rows, which
@@ -356,7 +386,6 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
                                                 const tc::WaitCtx& w, int warp, int lane) {
   constexpr int HC = BN / 2;
   constexpr int NACC = 512 / BN;
-  const int64_t kbt = a.sch.kbt;
   const int top = a.s + 1;
   const int q4 = warp & 3;
   const int h = (warp - W0) >> 2;
@@ -373,11 +402,11 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
   for (int b = 0; b < NACC; ++b) tph[b] = 0;
   bool ok = true;
   for (int64_t ui = 0; ui < nunits && ok; ++ui) {
-    const Unit u = unit_of_cta(a.sch, unit_cta, ui);
+    const Unit u = emu_unit_of_cta(a.sch, unit_cta, ui);
     int Lv[HC];  // exact level sum of the current super-chunk
     bool stored = false;
-    for (int64_t sc0 = 0; sc0 < kbt && ok; sc0 += a.chunk_kb) {
-      const int64_t sc1 = min(sc0 + (int64_t)a.chunk_kb, kbt);
+    for (int64_t sc0 = u.kb0; sc0 < u.kb1 && ok; sc0 += a.chunk_kb) {
+      const int64_t sc1 = min(sc0 + (int64_t)a.chunk_kb, u.kb1);
       for (int lvl = top; lvl >= 2 && ok; --lvl) {
         const int gk = group_blocks(a.group_kb, lvl - 1);
         // one exact group: its integer sums join Lv (the level's first group sets it)
@@ -408,7 +437,8 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
         for (int64_t c0 = sc0 + gk; c0 < sc1; c0 += gk)
           if (!drain(std::false_type{})) { ok = false; break; }
         if (!ok) break;
-        if (sc1 >= kbt && lvl == 2) break;  // the tile's last merge is folded into the read-back
+        // the unit's last merge is folded into the read-back (unsplit k)
+        if (sc1 >= u.kb1 && lvl == 2 && !a.X) break;
         // K-RECOMB: T += L 2^(beta (top - lvl) - base), exactly
         const int sh = a.beta * (top - lvl) - a.t_base;
         // (8 columns at a time: each batch's shifted values are sent before the next
@@ -436,17 +466,42 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
       }
     }
     if (!ok) break;
+    const int64_t row0 = u.tile_row * TM + row_off + q4 * 32;
+    const int64_t cbase = u.tile_col * BN + col_lo;
+    const int l8 = lane & 7, g8 = lane >> 3;
+    if (a.X) {
+      // k split: the unit's exact total (all its merges done) joins the product's,
+      // transposed like the FP64 store below, by L2 reductions -- integer sums, so
+      // the order of the k slices changes nothing
+#pragma unroll 1
+      for (int c = 0; c < HC; c += 8) {
+        long long tv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          asm volatile("ld.relaxed.gpu.global.L2::cache_hint.s64 %0, [%1], %2;"
+                       : "=l"(tv[j])
+                       : "l"(Tt + (c + j) * 128), "l"(keep)
+                       : "memory");
+        transpose8(tv, l8);
+        const int64_t col = cbase + c + l8;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int64_t r = row0 + 8 * g8 + i;
+          if (r < a.sch.m && col < a.sch.n)
+            asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(a.X + r * a.sch.n + col),
+                         "l"(tv[i])
+                         : "memory");
+        }
+      }
+      continue;
+    }
     // Final FP64 store: C = T 2^(sigma_i + tau_j + 2 - beta (s + 1) + base) for this
     // thread's row, HC columns.  Each 8-column chunk is formed in the row's lane,
-    // transposed within groups of 8 lanes (three butterfly stages of shuffles: at
-    // stage s, entries whose row and column differ in bit s trade places with
-    // lane ^ s), and written as four 64-byte row segments per instruction.
-    const int64_t row0 = u.tile_row * TM + row_off + q4 * 32;
+    // transposed within groups of 8 lanes, and written as four 64-byte row
+    // segments per instruction.
     const int64_t row = row0 + lane;
-    const int64_t cbase = u.tile_col * BN + col_lo;
     const int ea = row < a.sch.m ? a.eA[row] : kExpNone;
     const int eoff = 2 - a.beta * top + a.t_base;
-    const int l8 = lane & 7, g8 = lane >> 3;
     // the read-back addresses from an opaque copy of the base, so the compiler does
     // not keep the merges' per-column addresses live across the loops
     long long* Tf = Tt;
@@ -473,6 +528,7 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
                        : "l"(Tf + (c + 8 + j) * 128), "l"(keep)
                        : "memory");
       }
+      const int64_t col = cbase + c + l8;
       int eb[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) eb[j] = cbase + c + j < a.sch.n ? a.eB[cbase + c + j] : kExpNone;
@@ -485,20 +541,8 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
         if (a.alpha != 1.0) x *= a.alpha;
         v[j] = x;
       }
-#pragma unroll
-      for (int sb = 4; sb >= 1; sb >>= 1) {
-#pragma unroll
-        for (int i0 = 0; i0 < 8; ++i0) {
-          if (i0 & sb) continue;
-          const bool up = (l8 & sb) != 0;
-          const double send = up ? v[i0] : v[i0 | sb];
-          const double recv = __shfl_xor_sync(0xffffffffu, send, sb);
-          if (up) v[i0] = recv;
-          else v[i0 | sb] = recv;
-        }
-      }
+      transpose8(v, l8);
       // now v[i] = C(row0 + 8 g8 + i, cbase + c + l8)
-      const int64_t col = cbase + c + l8;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int64_t r = row0 + 8 * g8 + i;
@@ -513,20 +557,20 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
   }
 }
 
-// Same iteration order for the producer and the MMA issuer: calls body(q, lvl,
-// kb) for every k-block of every pair, and group_begin / group_end around the
-// exact groups.  Returns false as soon as a callback does (abort).
-// chunk_begin(c) runs before super-chunk c (0, 1, ...) of the unit.
+// Same iteration order for the producer and the MMA issuer over the k blocks
+// [kb0, kb1) of a unit: calls body(q, lvl, kb) for every k-block of every pair,
+// and group_begin / group_end around the exact groups.  Returns false as soon as
+// a callback does (abort).  chunk_begin(c) runs before super-chunk c (0, 1, ...)
+// of the unit.
 template <class ChunkBegin, class GroupBegin, class Body, class GroupEnd>
-__device__ __forceinline__ bool emu_walk_chunks(const EmuArgs& a, ChunkBegin chunk_begin,
-                                                GroupBegin group_begin, Body body,
-                                                GroupEnd group_end) {
-  const int64_t kbt = a.sch.kbt;
+__device__ __forceinline__ bool emu_walk_chunks(const EmuArgs& a, int64_t kb0, int64_t kb1,
+                                                ChunkBegin chunk_begin, GroupBegin group_begin,
+                                                Body body, GroupEnd group_end) {
   const int top = a.s + 1;
   int64_t chunk = 0;
-  for (int64_t sc0 = 0; sc0 < kbt; sc0 += a.chunk_kb, ++chunk) {
+  for (int64_t sc0 = kb0; sc0 < kb1; sc0 += a.chunk_kb, ++chunk) {
     if (!chunk_begin(chunk)) return false;
-    const int64_t sc1 = min(sc0 + (int64_t)a.chunk_kb, kbt);
+    const int64_t sc1 = min(sc0 + (int64_t)a.chunk_kb, kb1);
     for (int lvl = top; lvl >= 2; --lvl) {
       const int p = lvl - 1;
       const int gk = group_blocks(a.group_kb, p);
@@ -547,9 +591,21 @@ __device__ __forceinline__ bool emu_walk_chunks(const EmuArgs& a, ChunkBegin chu
 }
 
 template <class GroupBegin, class Body, class GroupEnd>
-__device__ __forceinline__ bool emu_walk(const EmuArgs& a, GroupBegin group_begin, Body body,
-                                         GroupEnd group_end) {
-  return emu_walk_chunks(a, [](int64_t) { return true; }, group_begin, body, group_end);
+__device__ __forceinline__ bool emu_walk(const EmuArgs& a, int64_t kb0, int64_t kb1,
+                                         GroupBegin group_begin, Body body, GroupEnd group_end) {
+  return emu_walk_chunks(a, kb0, kb1, [](int64_t) { return true; }, group_begin, body, group_end);
+}
+
+// k-block range of unit i of CTA (or pair) `cta` alone, for the MMA issuer.
+__device__ __forceinline__ void emu_unit_range(const Sched& s, int cta, int64_t i, int64_t& kb0,
+                                               int64_t& kb1) {
+  if (s.pk == 1) {
+    kb0 = 0;
+    kb1 = s.kbt;
+    return;
+  }
+  const int64_t unit = cta + i * (int64_t)s.ctas;
+  emu_k_range(s, (int)(unit / (s.mt * s.nt)), kb0, kb1);
 }
 
 // Threads of both emulation kernels: warps 0-3 (producer, MMA issuer, two idle),
@@ -629,9 +685,9 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       int stage = 0;
       uint32_t ph = 0, armed = 0, armed_ph = 0;
       for (int64_t ui = 0; ui < nunits && !*abort_flag; ++ui) {
-        const Unit u = unit_of_cta(a.sch, cta, ui);
+        const Unit u = emu_unit_of_cta(a.sch, cta, ui);
         const bool ok = emu_walk(
-            a, [] { return true; },
+            a, u.kb0, u.kb1, [] { return true; },
             [&](int q, int lvl, int64_t kb, bool) {
               if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) return false;
               tc::mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES);
@@ -666,8 +722,10 @@ emu_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 #pragma unroll
       for (int b = 0; b < NACC; ++b) aph[b] = 0;
       for (int64_t ui = 0; ui < nunits && !*abort_flag; ++ui) {
+        int64_t kb0, kb1;
+        emu_unit_range(a.sch, cta, ui, kb0, kb1);
         const bool ok = emu_walk(
-            a,
+            a, kb0, kb1,
             [&] {
               if (!tc::mbar_wait(&tempty[acc], aph[acc] ^ 1, w)) return false;
               tc::tc_fence_after();
@@ -819,10 +877,12 @@ emu_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       // pair has started g - 1, so concurrent pairs stream the same slice panels
       // through L2.  A pair without a unit in a round counts that round's
       // super-chunks at once.
+      // With a k split, every unit counts as many super-chunks as the longest k
+      // slice has; a shorter one counts the rest at its end.
       const int npairs = (int)(gridDim.x >> 1);
-      const int64_t total = a.sch.mt * a.sch.nt;
+      const int64_t total = a.sch.mt * a.sch.nt * a.sch.pk;
       const int64_t rounds = a.lockstep ? (total + npairs - 1) / npairs : nunits;
-      const int64_t nch = (a.sch.kbt + a.chunk_kb - 1) / a.chunk_kb;
+      const int64_t nch = cdiv64(cdiv64(a.sch.kbt, a.chunk_kb), a.sch.pk);
       auto chunk_tick = [&](int64_t g) -> bool {
         if (!(a.lockstep && leader)) return true;
         if (g >= 1) {
@@ -847,9 +907,10 @@ emu_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           if (a.lockstep && leader) atomicAdd(a.lockstep, (unsigned int)nch);
           continue;
         }
-        const Unit u = unit_of_cta(a.sch, pair, ui);
+        const Unit u = emu_unit_of_cta(a.sch, pair, ui);
         const bool ok = emu_walk_chunks(
-            a, [&](int64_t c) { return chunk_tick(ui * nch + c); }, [] { return true; },
+            a, u.kb0, u.kb1, [&](int64_t c) { return chunk_tick(ui * nch + c); },
+            [] { return true; },
             [&](int q, int lvl, int64_t kb, bool) {
               if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) return false;
               if (leader) tc::mbar_arrive_expect_tx(&full[stage], 2 * L::STAGE_BYTES);
@@ -864,6 +925,8 @@ emu_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             },
             [] {});
         if (!ok) break;
+        const int64_t used = cdiv64(u.kb1 - u.kb0, a.chunk_kb);
+        if (a.lockstep && leader && used < nch) atomicAdd(a.lockstep, (unsigned int)(nch - used));
       }
       // The odd CTA's copies signal the leader's barriers: it reports how many
       // stages it issued, and on an abort the leader waits (bounded) until every
@@ -902,8 +965,10 @@ emu_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 #pragma unroll
       for (int b = 0; b < NACC; ++b) aph[b] = 0;
       for (int64_t ui = 0; ui < nunits && !*abort_flag; ++ui) {
+        int64_t kb0, kb1;
+        emu_unit_range(a.sch, pair, ui, kb0, kb1);
         const bool ok = emu_walk(
-            a,
+            a, kb0, kb1,
             [&] {
               if (!tc::mbar_wait(&tempty[acc], aph[acc] ^ 1, w)) return false;
               tc::tc_fence_after();
@@ -943,6 +1008,27 @@ emu_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   tc::cluster_sync();  // no CTA leaves while its peer may still signal its barriers
   tc::tc_fence_after();
   if (warp == 1) tc::tmem_dealloc_pair(tmem_base, 512);
+}
+
+// k-split plans: C = alpha X 2^(sigma_i + tau_j + eoff) + beta_c C from the summed
+// exact totals X [m][n] -- the arithmetic of the kernels' own FP64 store, in the
+// same order, so a split changes no bit of C.
+__global__ void emu_finish_kernel(const long long* __restrict__ X, int64_t m, int64_t n,
+                                  const int* __restrict__ eA, const int* __restrict__ eB, int eoff,
+                                  double alpha, double beta_c, double* C, int64_t ldc) {
+  for (int64_t i = blockIdx.y; i < m; i += gridDim.y) {
+    const int ea = eA[i];
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+      const int eb = eB[j];
+      double x = (ea == kExpNone || eb == kExpNone) ? 0.0
+                                                    : scale_pow2((double)X[i * n + j], ea + eb + eoff);
+      if (alpha != 1.0) x *= alpha;
+      double* dst = C + i * ldc + j;
+      if (beta_c != 0.0) x = fma(beta_c, *dst, x);
+      *dst = x;
+    }
+  }
 }
 
 // 4-D map over the k-blocked slices of `rows` rows starting at `base` (a row
@@ -991,25 +1077,28 @@ dim3 split_a_grid(int64_t rows, int64_t kpad) {
 }  // namespace
 
 namespace {
-// Bytes of the pair kernel's running totals: at most one 128 x 256 int64 region
-// per CTA of the largest pair grid the problem can use.
-int64_t emu_total_bytes(int64_t m, int64_t n, int sms) {
+// Bytes of the kernels' running totals: one 128 x 256 int64 region per CTA of the
+// largest pair grid the problem can use (a single-SM CTA's 128 x 128 region is
+// half of one) -- with a k split, of the largest grid the device allows.
+int64_t emu_total_bytes(int64_t m, int64_t n, int sms, bool split) {
   const int64_t tiles = ((m + 2 * EBM - 1) / (2 * EBM)) * ((n + EBN - 1) / EBN);
-  const int64_t pairs = std::min<int64_t>(std::max(1, sms / 2), std::max<int64_t>(tiles, 1));
+  const int64_t pairs = split ? std::max(1, sms / 2)
+                              : std::min<int64_t>(std::max(1, sms / 2), std::max<int64_t>(tiles, 1));
   return rup(2 * pairs * (int64_t)EBM * 256 * 8, 256);
 }
 }  // namespace
 
 long long emu_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_config& cfg,
-                              int sms) {
+                              int sms, int64_t split_elems) {
   const int s = emu_slices(cfg);
   const int64_t kp = emu_kpad(k);
   return rup(m * 4, 256) + rup(n * 4, 256) + rup((int64_t)s * m * kp * 2, 256) +
-         rup((int64_t)s * n * kp * 2, 256) + emu_total_bytes(m, n, sms) + 256;
+         rup((int64_t)s * n * kp * 2, 256) + emu_total_bytes(m, n, sms, split_elems > 0) +
+         rup(split_elems * 8, 256) + 256;
 }
 
 EmuWorkspace emu_carve(void* ws, int64_t m, int64_t n, int64_t k, const cosma_config& cfg,
-                       int sms) {
+                       int sms, int64_t split_elems) {
   const int s = emu_slices(cfg);
   const int64_t kp = emu_kpad(k);
   uint8_t* w = static_cast<uint8_t*>(ws);
@@ -1023,7 +1112,10 @@ EmuWorkspace emu_carve(void* ws, int64_t m, int64_t n, int64_t k, const cosma_co
   e.SB = w;
   w += rup((int64_t)s * n * kp * 2, 256);
   e.T = reinterpret_cast<long long*>(w);
-  w += emu_total_bytes(m, n, sms);
+  e.t_bytes = emu_total_bytes(m, n, sms, split_elems > 0);
+  w += e.t_bytes;
+  e.X = split_elems > 0 ? reinterpret_cast<long long*>(w) : nullptr;
+  w += rup(split_elems * 8, 256);
   e.lockstep = reinterpret_cast<unsigned int*>(w);
   e.row_pitch = EKB;
   return e;
@@ -1096,16 +1188,20 @@ int emu_prepare_b(const double* B, int64_t k, int64_t n, int64_t ldb, int trans,
 int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cosma_config& cfg,
                  const int* eA, const void* SA, int64_t a_slice_rows, const int* eB,
                  const void* SB, int64_t b_slice_rows, double* C, int64_t ldc, double alpha,
-                 double beta_c, long long* T, unsigned int* lockstep, int* status,
-                 long long wait_limit, cudaStream_t st) {
+                 double beta_c, long long* T, int64_t t_bytes, long long* X,
+                 unsigned int* lockstep, int* status, long long wait_limit, cudaStream_t st) {
   const int s = emu_slices(cfg), beta = emu_bits(cfg);
   const Sched sch = sched_from_plan(m, n, k, p);
   const bool pairs = sch.tile_m == 2 * EBM;
   if (pairs ? (sch.tile_n != 256 && sch.tile_n != 128) : (sch.tile_m != EBM || sch.tile_n != EBN))
     return COSMA_ERR_INVALID_ARG;
-  if (sch.k_block != EBK || sch.pk != 1) return COSMA_ERR_INVALID_ARG;
+  // order 1, k slices of whole super-chunks, a total to sum them in
+  if (sch.k_block != EBK || sch.order != 1 || sch.pk < 1 ||
+      sch.pk > cdiv64(sch.kbt, kEmuChunkKb) || (sch.pk > 1 && !X))
+    return COSMA_ERR_INVALID_ARG;
   // the running totals: one 128 x tile_n int64 region per CTA of the launch
-  if (!T || (pairs ? 2LL * sch.ctas : (long long)sch.ctas) > (long long)p.sms)
+  if (!T || (pairs ? 2LL * sch.ctas : (long long)sch.ctas) > (long long)p.sms ||
+      (pairs ? 2LL : 1LL) * sch.ctas * EBM * sch.tile_n * 8 > t_bytes)
     return COSMA_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(C) & 7) return COSMA_ERR_INVALID_ARG;
   // COSMA_EMU_LOCKSTEP in the environment (read once): unset or 1 = lock-step
@@ -1149,12 +1245,14 @@ int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cos
   // slice panels in L2 across the levels (one GB300, 256 x 256 pair tiles, square
   // 16384^3: 512 k 66.2, 1024 k 72.6, 2048 k 77.6, 4096 k 78.3-79.6, 16384 k 80.3
   // TFLOP/s; largeK 4096 x 4096 x 2^20: 4096 k 64.3, 16384 k 62.7).
+  // (With at most 8 slices of at most 8 bits the bound is 16384 k, so every
+  // accepted configuration uses the 4096-k super-chunk the planner assumes.)
   {
     const double lim = 2147483647.0 / ((double)s * std::ldexp(1.0, 2 * beta - 2));
-    int64_t ck = 4096 / EBK;
-    while (ck > 1 && (double)ck * EBK > lim) --ck;
-    args.chunk_kb = (int)ck;
+    if ((double)kEmuChunkKb * EBK > lim) return COSMA_ERR_UNSUPPORTED;
+    args.chunk_kb = kEmuChunkKb;
   }
+  args.X = sch.pk > 1 ? X : nullptr;
   // Fixed-point base of the running total: every super-chunk adds
   // at most sum_{l=2}^{s+1} (l - 1) chunk 2^(2 beta - 2) 2^(beta (s + 1 - l)); the
   // smallest base that keeps the sum over all chunks below 2^62.
@@ -1169,6 +1267,8 @@ int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cos
     while (std::ldexp(bound, -base) >= std::ldexp(1.0, 62)) ++base;
     args.t_base = base;
   }
+  if (args.X && cudaMemsetAsync(args.X, 0, (size_t)(m * n) * 8, st) != cudaSuccess)
+    return (int)cudaGetLastError();
   cudaError_t le;
   if (pairs) {
     auto kern = sch.tile_n == 256 ? emu_pair_kernel<256> : emu_pair_kernel<128>;
@@ -1227,6 +1327,13 @@ int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cos
   }
   if (le != cudaSuccess) return (int)le;
   count_launch();
+  if (args.X) {
+    const int64_t gx = std::min<int64_t>((n + 255) / 256, 1024);
+    const int64_t gy = std::min<int64_t>(m, 65535);
+    emu_finish_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, st>>>(
+        args.X, m, n, eA, eB, 2 - beta * (s + 1) + args.t_base, alpha, beta_c, C, ldc);
+    count_launch();
+  }
   return (int)cudaGetLastError();
 }
 
@@ -1235,12 +1342,13 @@ int launch_emu_bf16(const GemmArgs& g, const cosma_plan& p, const cosma_config& 
   int rc = emu_check_config(cfg);
   if (rc != COSMA_OK) return rc;
   const int64_t m = g.m, n = g.n, k = g.k;
-  if (emu_workspace_bytes(m, n, k, cfg, p.sms) > ws_bytes) return COSMA_ERR_NO_WORKSPACE;
+  const int64_t split = p.pk > 1 ? m * n : 0;
+  if (emu_workspace_bytes(m, n, k, cfg, p.sms, split) > ws_bytes) return COSMA_ERR_NO_WORKSPACE;
   if ((emu_kpad(k) + 31) / 32 > 65535) return COSMA_ERR_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(g.A) & 7) || (reinterpret_cast<uintptr_t>(g.B) & 7) ||
       (reinterpret_cast<uintptr_t>(g.C) & 7))
     return COSMA_ERR_INVALID_ARG;
-  const EmuWorkspace e = emu_carve(ws, m, n, k, cfg, p.sms);
+  const EmuWorkspace e = emu_carve(ws, m, n, k, cfg, p.sms, split);
   rc = emu_prepare_a(static_cast<const double*>(g.A), m, k, g.lda, g.trans_a, e.eA, e.SA, m,
                      status, cfg, st);
   if (rc != 0) return rc;
@@ -1248,7 +1356,8 @@ int launch_emu_bf16(const GemmArgs& g, const cosma_plan& p, const cosma_config& 
                      status, cfg, st);
   if (rc != 0) return rc;
   return emu_multiply(m, n, k, p, cfg, e.eA, e.SA, m, e.eB, e.SB, n, static_cast<double*>(g.C),
-                      g.ldc, g.alpha, g.beta, e.T, e.lockstep, status, wait_limit, st);
+                      g.ldc, g.alpha, g.beta, e.T, e.t_bytes, e.X, e.lockstep, status, wait_limit,
+                      st);
 }
 
 }  // namespace cosma

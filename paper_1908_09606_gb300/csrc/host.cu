@@ -14,6 +14,7 @@
 // to it (the caller's stream waits for the last copy-out), so the call is
 // stream-ordered and may be captured into a CUDA graph.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -199,19 +200,32 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
   uint8_t* Bd = base + a_bytes;
   uint8_t* Cd = base + a_bytes + b_bytes;
 
+  int64_t rcut[kMaxR + 1], ccut[kMaxR + 1];
+  const int Rm = blocks_of(m, rcut), Rn = blocks_of(n, ccut);
+
+  // Emulated FP64: the blocks are planned first, so that the workspace holds the
+  // exact total of the largest block whose plan splits k (the blocks run one
+  // after another on `stream` and share it).
   const bool emu = dtype == COSMA_F64_EMU_BF16 && k > 0;
   EmuWorkspace ew{};
+  cosma_plan bplan[kMaxR * kMaxR];
   if (emu) {
     rc = emu_check_config(ctx.cfg);
     if (rc != COSMA_OK) return rc;
+    int64_t split = 0;
+    for (int i = 0; i < Rm; ++i)
+      for (int j = 0; j < Rn; ++j) {
+        const int64_t mb = rcut[i + 1] - rcut[i], nb = ccut[j + 1] - ccut[j];
+        rc = plan_gemm(mb, nb, k, dtype, ctx.cfg.selector, ctx.info, ctx.cfg, &bplan[i * Rn + j],
+                       !capturing(st));
+        if (rc != COSMA_OK) return rc;
+        if (bplan[i * Rn + j].pk > 1) split = std::max(split, mb * nb);
+      }
     void* ws = nullptr;
-    rc = lib_scratch(emu_workspace_bytes(m, n, k, ctx.cfg, ctx.info.sms), st, &ws);
+    rc = lib_scratch(emu_workspace_bytes(m, n, k, ctx.cfg, ctx.info.sms, split), st, &ws);
     if (rc != COSMA_OK) return rc;
-    ew = emu_carve(ws, m, n, k, ctx.cfg, ctx.info.sms);
+    ew = emu_carve(ws, m, n, k, ctx.cfg, ctx.info.sms, split);
   }
-
-  int64_t rcut[kMaxR + 1], ccut[kMaxR + 1];
-  const int Rm = blocks_of(m, rcut), Rn = blocks_of(n, ccut);
   cudaEvent_t ev_start = h.ev[0], ev_done = h.ev[1];
   cudaEvent_t* ev_a = h.ev + 2;
   cudaEvent_t* ev_b = h.ev + 2 + kMaxR;
@@ -286,13 +300,11 @@ extern "C" int cosma_gemm_host(int64_t m, int64_t n, int64_t k, const void* A, i
         uint8_t* Cblk = Cd + ((size_t)r0 * ldc_d + c0) * eo;
         if (prof && (rc = ok(cudaEventRecord(ph.pb[i * Rn + j], st))) != COSMA_OK) return rc;
         if (emu) {
-          cosma_plan p;
-          rc = plan_gemm(mb, nb, k, dtype, ctx.cfg.selector, ctx.info, ctx.cfg, &p, !capturing(st));
-          if (rc != COSMA_OK) return rc;
-          rc = emu_multiply(mb, nb, k, p, ctx.cfg, ew.eA + r0,
+          rc = emu_multiply(mb, nb, k, bplan[i * Rn + j], ctx.cfg, ew.eA + r0,
                             static_cast<uint8_t*>(ew.SA) + (size_t)r0 * ew.row_pitch * 2, m, ew.eB + c0,
                             static_cast<uint8_t*>(ew.SB) + (size_t)c0 * ew.row_pitch * 2, n,
-                            reinterpret_cast<double*>(Cblk), ldc_d, 1.0, 0.0, ew.T, ew.lockstep,
+                            reinterpret_cast<double*>(Cblk), ldc_d, 1.0, 0.0, ew.T, ew.t_bytes, ew.X,
+                            ew.lockstep,
                             ctx.status, ctx.wait_limit, st);
           if (rc > 0) return COSMA_ERR_CUDA;
           if (rc < 0) return rc;

@@ -95,20 +95,26 @@ struct EmuWorkspace {
   int* eB;                 // column exponents of B [n]
   void* SA;                // bf16 slices of A, k-blocked: [s][k panels][m][row_pitch]
   void* SB;                // bf16 slices of B^T, k-blocked: [s][k panels][n][row_pitch]
-  long long* T;            // running totals of the CTA-pair kernel (one region per CTA)
+  long long* T;            // running totals of the kernels (one region per CTA)
+  int64_t t_bytes;         // bytes at T
+  long long* X;            // k-split plans: the product's exact fixed-point total [m][n]
+                           // (null when the workspace was sized without a split)
   unsigned int* lockstep;  // one counter for lock-step rounds
   int64_t row_pitch;       // elements per row of one k panel (a row block starts at
                            // row * row_pitch)
 };
-// sms: the SM count of the plans the workspace serves (cosma_plan::sms).
-long long emu_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_config& cfg, int sms);
+// sms: the SM count of the plans the workspace serves (cosma_plan::sms);
+// split_elems: elements of the exact total a k-split plan sums into (m n for a
+// plan with pk > 1, else 0).
+long long emu_workspace_bytes(int64_t m, int64_t n, int64_t k, const cosma_config& cfg, int sms,
+                              int64_t split_elems);
 // k rounded up to whole panels of the k-blocked slice layout.
 int64_t emu_padded_k(int64_t k);
 // COSMA_OK when the element format's operand preparation covers this k, else
 // COSMA_ERR_UNSUPPORTED (api.cu); checked before anything is sized or allocated.
 int k_supported(int dtype, int64_t k);
 EmuWorkspace emu_carve(void* ws, int64_t m, int64_t n, int64_t k, const cosma_config& cfg,
-                       int sms);
+                       int sms, int64_t split_elems);
 int emu_check_config(const cosma_config& cfg);
 // Exponents and slices of rows [0, m) of A into eA[0..m) and SA (slice_rows
 // rows between slices); of columns [0, n) of B likewise.
@@ -120,12 +126,15 @@ int emu_prepare_b(const double* B, int64_t k, int64_t n, int64_t ldb, int trans,
                   void* SB, int64_t slice_rows, int* status, const cosma_config& cfg,
                   cudaStream_t st);
 // C[m x n] = alpha (product of the prepared slices) + beta C, under plan p (an
-// F64_EMU_BF16 plan for m x n x k).
+// F64_EMU_BF16 plan for m x n x k).  T: t_bytes of running-total scratch (one
+// region per CTA of the launch; COSMA_ERR_INVALID_ARG when too small).  X: at
+// least m n int64 when p.pk > 1 (the k slices' exact totals are summed there),
+// else unused.
 int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cosma_config& cfg,
                  const int* eA, const void* SA, int64_t a_slice_rows, const int* eB,
                  const void* SB, int64_t b_slice_rows, double* C, int64_t ldc, double alpha,
-                 double beta, long long* T, unsigned int* lockstep, int* status,
-                 long long wait_limit, cudaStream_t st);
+                 double beta, long long* T, int64_t t_bytes, long long* X,
+                 unsigned int* lockstep, int* status, long long wait_limit, cudaStream_t st);
 int launch_emu_bf16(const GemmArgs& g, const cosma_plan& p, const cosma_config& cfg, void* ws,
                     long long ws_bytes, int* status, long long wait_limit, cudaStream_t st);
 

@@ -168,9 +168,11 @@ Sched sched_from_plan(int64_t m, int64_t n, int64_t k, const cosma_plan& p) {
   // at once form a G x W block.  One k step of that wave reads G tile_m rows of A and
   // W tile_n columns of B through L2; with G W fixed the sum is smallest at
   // G tile_m = W tile_n -- the square-tile rule of eq. optTileShape one level up,
-  // L2 being the fast memory of the whole wave.
+  // L2 being the fast memory of the whole wave.  (The emulated FP64 kernels run
+  // the units of one k slice together: their wave is ctas tiles.)
   {
-    const double wave = std::max(1.0, (double)p.ctas / std::max(1, p.pk));
+    const bool emu = p.kernel == COSMA_KERNEL_EMU_BF16;
+    const double wave = std::max(1.0, (double)p.ctas / (emu ? 1 : std::max(1, p.pk)));
     int g = (int)std::lround(std::sqrt(wave * p.tile_n / std::max(1, p.tile_m)));
     if (g < 1) g = 1;
     if (g > s.mt) g = (int)std::max<int64_t>(1, s.mt);
@@ -285,18 +287,25 @@ int plan_gemm(int64_t m, int64_t n, int64_t k, int dtype, int selector, const De
     // Candidate k splits: 1, powers of two while the units stay within 16 waves
     // (a split also evens out the last, partial wave of tiles), and the one that
     // fills the SMs when tiles are few.
+    // The emulated FP64 kernels split k at super-chunk boundaries (4096 k), into
+    // 2 .. 16 slices: enough to even out the last wave of pair tiles.
     int pks[16];
     int npk = 0;
     pks[npk++] = 1;
-    if (d.kernel != COSMA_KERNEL_EMU_BF16) {
+    const bool emu = d.kernel == COSMA_KERNEL_EMU_BF16;
+    const int64_t nch = cdiv(kbt, kEmuChunkKb);
+    if (!emu) {
       for (int pk = 2; pk <= 64 && npk < 16; pk *= 2)
         if (pk <= kbt && tiles_total * pk <= 16LL * P) pks[npk++] = pk;
       const int64_t fill = cdiv(P, tiles_total);
       if (fill > 1 && fill <= kbt && npk < 16) pks[npk++] = (int)fill;
+    } else {
+      for (int pk = 2; pk <= 16 && npk < 16; ++pk)
+        if (pk <= nch) pks[npk++] = pk;
     }
     for (int pi = 0; pi < npk; ++pi) {
       const int pk = pks[pi];
-      const int64_t kbu = cdiv(kbt, pk);
+      const int64_t kbu = emu ? std::min<int64_t>(kbt, cdiv(nch, pk) * kEmuChunkKb) : cdiv(kbt, pk);
       // order 1: balanced stripes (a 256-row emulation tile occupies a pair of SMs)
       {
         const bool pair = d.kernel == COSMA_KERNEL_EMU_BF16 && t.tile_m == 256;
@@ -356,7 +365,10 @@ int validate_plan(int64_t m, int64_t n, int64_t k, int dtype, const DeviceInfo& 
   if (p.pk < 1 || p.ctas < 1 || p.order < 0 || p.order > 1) return COSMA_ERR_INVALID_ARG;
   const int64_t kbt = cdiv(std::max<int64_t>(k, 1), p.k_block);
   if (p.pk > kbt) return COSMA_ERR_INVALID_ARG;
-  if (d.kernel == COSMA_KERNEL_EMU_BF16 && p.pk != 1) return COSMA_ERR_INVALID_ARG;
+  // emulated FP64: order 1, each k slice at least one super-chunk
+  if (d.kernel == COSMA_KERNEL_EMU_BF16 &&
+      (p.order != 1 || p.pk > cdiv(kbt, kEmuChunkKb)))
+    return COSMA_ERR_INVALID_ARG;
   if (p.order == 0) {
     if (p.pm < 1 || p.pn < 1 || (long long)p.pm * p.pn * p.pk != p.ctas) return COSMA_ERR_INVALID_ARG;
     if (p.pm > cdiv(std::max<int64_t>(m, 1), p.tile_m) || p.pn > cdiv(std::max<int64_t>(n, 1), p.tile_n))

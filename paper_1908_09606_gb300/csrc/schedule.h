@@ -11,6 +11,9 @@
 //              pk k slices of a tile adjacent, and CTA c executes units
 //              c, c + ctas, c + 2 ctas, ...  Concurrent CTAs then work on
 //              neighbouring tiles, which share A rows and B columns in L2.
+// The emulated FP64 kernels use order 1 with the k split outermost instead
+// (emu_unit_of_cta): the units of one k range run together, and each range is
+// a whole number of super-chunks.
 #pragma once
 #include <stdint.h>
 
@@ -58,6 +61,17 @@ COSMA_HD int64_t units_of_cta(const Sched& s, int cta) {
   return cta < total ? (total - cta + s.ctas - 1) / s.ctas : 0;
 }
 
+// Tile number `tile` of the order-1 raster: groups of `group` tile rows, the
+// columns of a group one after another, rows inside a column.
+COSMA_HD void raster_tile(const Sched& s, int64_t tile, Unit& u) {
+  const int64_t g = tile / ((int64_t)s.group * s.nt);
+  const int64_t rows_in_group =
+      (s.mt - g * s.group) < s.group ? (s.mt - g * s.group) : (int64_t)s.group;
+  const int64_t idx = tile - g * (int64_t)s.group * s.nt;
+  u.tile_col = idx / rows_in_group;
+  u.tile_row = g * s.group + idx % rows_in_group;
+}
+
 // The i-th unit of CTA `cta` (0 <= i < units_of_cta).
 COSMA_HD Unit unit_of_cta(const Sched& s, int cta, int64_t i) {
   Unit u;
@@ -71,14 +85,8 @@ COSMA_HD Unit unit_of_cta(const Sched& s, int cta, int64_t i) {
     u.ks = ik;
   } else {
     const int64_t unit = cta + i * (int64_t)s.ctas;
-    const int64_t tile = unit / s.pk;
     u.ks = (int)(unit % s.pk);
-    const int64_t g = tile / ((int64_t)s.group * s.nt);
-    const int64_t rows_in_group =
-        (s.mt - g * s.group) < s.group ? (s.mt - g * s.group) : (int64_t)s.group;
-    const int64_t idx = tile - g * (int64_t)s.group * s.nt;
-    u.tile_col = idx / rows_in_group;
-    u.tile_row = g * s.group + idx % rows_in_group;
+    raster_tile(s, unit / s.pk, u);
   }
   u.kb0 = split_start(s.kbt, s.pk, u.ks);
   u.kb1 = split_start(s.kbt, s.pk, u.ks + 1);
@@ -97,6 +105,34 @@ COSMA_HD void unit_k_range(const Sched& s, int cta, int64_t i, int64_t& kb0, int
   const int ks = s.order == 0 ? cta % s.pk : (int)((cta + i * (int64_t)s.ctas) % s.pk);
   kb0 = split_start(s.kbt, s.pk, ks);
   kb1 = split_start(s.kbt, s.pk, ks + 1);
+}
+
+// Super-chunk of the emulated FP64 kernels, in 64-wide k blocks (4096 k): the
+// k extent over which their int32 level sums stay exact for every slice
+// configuration they accept (at most 8 slices of at most 8 bits).
+constexpr int kEmuChunkKb = 64;
+
+// k-block range of k slice ks of an emulated FP64 plan: the super-chunks are
+// split evenly over the pk slices, so every slice sums whole super-chunks --
+// the ones an unsplit product would sum -- and the split changes no bit of C.
+COSMA_HD void emu_k_range(const Sched& s, int ks, int64_t& kb0, int64_t& kb1) {
+  const int64_t nch = cdiv64(s.kbt, kEmuChunkKb);
+  kb0 = split_start(nch, s.pk, ks) * kEmuChunkKb;
+  kb1 = split_start(nch, s.pk, ks + 1) * kEmuChunkKb;
+  if (kb1 > s.kbt) kb1 = s.kbt;
+}
+
+// The i-th unit of CTA `cta` of an emulated FP64 plan (order 1): units are
+// numbered k slice first, so concurrent CTAs share one k range and read the
+// same slice panels from L2.
+COSMA_HD Unit emu_unit_of_cta(const Sched& s, int cta, int64_t i) {
+  Unit u;
+  const int64_t unit = cta + i * (int64_t)s.ctas;
+  const int64_t tiles = s.mt * s.nt;
+  u.ks = (int)(unit / tiles);
+  raster_tile(s, unit - (int64_t)u.ks * tiles, u);
+  emu_k_range(s, u.ks, u.kb0, u.kb1);
+  return u;
 }
 
 }  // namespace cosma

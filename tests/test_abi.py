@@ -259,7 +259,52 @@ def test_plan_candidates_host_only(lib):
                 if p.order == 0:
                     assert p.pm * p.pn * p.pk == p.ctas
             if dt == lib.COSMA_F64_EMU_BF16:
-                assert valid == [1, 9]  # CTA-pair tile 256 x 128 and single-SM tile 128 x 128
+                assert valid == [1, 9]  # CTA-pair tile 256 x 256 and single-SM tile 128 x 128
+
+
+def test_emu_plans_split_k_only_where_the_last_wave_is_short(lib):
+    # largeK: 256 pair tiles over 76 SM pairs fill 3.4 of 4 rounds; a k split of
+    # whole 4096-deep super-chunks evens the rounds out.  Square 16384^3 (4096
+    # tiles, 54 rounds at 99.8 %) and flat k = 1024 (one super-chunk) stay unsplit.
+    dt = lib.COSMA_F64_EMU_BF16
+    p = lib.cosma_plan_query(4096, 4096, 1 << 20, dt)
+    assert p.order == 1 and 1 < p.pk <= 16 and (p.tile_m, p.tile_n) == (256, 256)
+    units = 16 * 16 * p.pk
+    pairs = p.ctas
+    assert units / (pairs * -(-units // pairs)) > 0.95  # the last round nearly full
+    assert p.workspace_bytes >= 4096 * 4096 * 8        # the summed exact totals
+    assert lib.cosma_plan_query(16384, 16384, 16384, dt).pk == 1
+    assert lib.cosma_plan_query(65536, 65536, 1024, dt).pk == 1
+
+
+@pytest.mark.parametrize("tile,pk", [((256, 256), 3), ((128, 128), 4), ((256, 128), 2)])
+def test_emu_split_units_are_whole_super_chunks(lib, tile, pk):
+    # k = 4 super-chunks and a ragged 100: every (tile, k slice) once, k slices
+    # cut at multiples of 4096 and together covering [0, k); a CTA's units run
+    # k slice first (slice number non-decreasing), so concurrent CTAs share one
+    # k range
+    m, n, k = 600, 520, 4 * 4096 + 100
+    p = _small_plan(lib, tile, 64, pk, 1, 3)
+    p.kernel = 3
+    units = lib.cosma_plan_units(m, n, k, p)
+    tiles = -(-m // tile[0]) * -(-n // tile[1])
+    assert len(units) == tiles * pk
+    per_tile = {}
+    for (r0, r1, c0, c1, k0, k1) in units:
+        assert k0 % 4096 == 0 and (k1 % 4096 == 0 or k1 == k) and k0 < k1
+        per_tile.setdefault((r0, c0), []).append((k0, k1))
+    assert len(per_tile) == tiles
+    for ranges in per_tile.values():
+        ranges.sort()
+        assert ranges[0][0] == 0 and ranges[-1][1] == k
+        assert all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
+    # units come back CTA by CTA; inside a CTA the k slice never goes back
+    pos = 0
+    for c in range(3):
+        count = len(range(c, tiles * pk, 3))
+        starts = [u[4] for u in units[pos:pos + count]]
+        assert starts == sorted(starts)
+        pos += count
 
 
 def test_selector_features_match_oracle(lib):

@@ -247,26 +247,85 @@ def test_emu_tile_shapes_agree_bit_for_bit(shape, kind):
     assert og.normwise_rel_error(out[0], og.gemm(Ah, Bh, "dot2")) <= 1e-12
 
 
+def _split_plan(m, n, k, tile, pk):
+    """The tile's plan with k cut into pk slices and as many CTAs (pairs) as the
+    units can use."""
+    cosma = lib()
+    p = _tile_plan(m, n, k, tile)
+    tiles = -(-m // p.tile_m) * -(-n // p.tile_n)
+    p.pk = pk
+    p.ctas = min(p.sms // 2 if p.tile_m == 256 else p.sms, tiles * pk)
+    return p
+
+
 @pytest.mark.parametrize("tile", ["pair256", "single", "pair128"])
-def test_emu_bounded_wait_reports_timeout_and_context_survives(tile):
+@pytest.mark.parametrize("shape,kind,pks", [((300, 520, 4 * 4096 + 515), "uniform", (2, 3, 5)),
+                                            ((513, 129, 3 * 4096), "loguniform", (3,)),
+                                            ((1100, 700, 2 * 4096 + 64), "uniform", (2, 3))])
+def test_emu_split_k_changes_no_bit(tile, shape, kind, pks):
+    """k slices of whole 4096-deep super-chunks (a ragged last one included):
+    each unit's exact fixed-point total joins one int64 total per element, which
+    is rounded to FP64 once -- the sums an unsplit product forms, so every split
+    gives the unsplit product's bits, and meets the oracle bar."""
+    import torch
+    cosma = lib()
+    m, n, k = shape
+    A, B = device_operands(m, n, k, DT, kind=kind, seed=23)
+    out = []
+    for pk in (1,) + pks:
+        C, _ = out_tensor(m, n, DT)
+        cosma.gemm(A, B, C, DT, plan=_split_plan(m, n, k, tile, pk))
+        torch.cuda.synchronize()
+        assert cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream) == 0
+        out.append(C.cpu().numpy())
+    for got in out[1:]:
+        assert np.array_equal(got, out[0])
+    Ah, Bh = host_operands(m, n, k, DT, kind=kind, seed=23)
+    assert og.normwise_rel_error(out[0], og.gemm(Ah, Bh, "dot2")) <= 1e-12
+
+
+def test_emu_split_k_rejects_slices_shorter_than_a_super_chunk():
+    import torch
+    cosma = lib()
+    m, n, k = 256, 256, 2 * 4096 + 1  # three super-chunks: at most three k slices
+    A, B = device_operands(m, n, k, DT, seed=2)
+    C, _ = out_tensor(m, n, DT)
+    p = _split_plan(m, n, k, "pair256", 4)
+    rc = cosma.cosma_gemm_planned(m, n, k, A.data_ptr(), k, B.data_ptr(), n, C.data_ptr(), n,
+                                  cosma.COSMA_F64_EMU_BF16, p,
+                                  torch.cuda.current_stream().cuda_stream)
+    assert rc == cosma.COSMA_ERR_INVALID_ARG
+    p = _split_plan(m, n, k, "pair256", 3)
+    p.order = 0
+    p.pm = p.pn = 1
+    p.ctas = 3
+    rc = cosma.cosma_gemm_planned(m, n, k, A.data_ptr(), k, B.data_ptr(), n, C.data_ptr(), n,
+                                  cosma.COSMA_F64_EMU_BF16, p,
+                                  torch.cuda.current_stream().cuda_stream)
+    assert rc == cosma.COSMA_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("tile,pk", [("pair256", 1), ("single", 1), ("pair128", 1),
+                                     ("pair256", 2)])
+def test_emu_bounded_wait_reports_timeout_and_context_survives(tile, pk):
     """A wait limit of one cycle makes the emulation kernel's waits run out (the
     CTA pairs' lock-step rounds included): it must record COSMA_ERR_TIMEOUT, let
     the copies and products in flight land, free its tensor memory and exit; the
     next call with the default limit must be correct on the same context."""
     import torch
     cosma = lib()
-    m, n, k = 1024, 1024, 4096
+    m, n, k = 1024, 1024, 4096 * pk
     A, B = device_operands(m, n, k, DT, seed=6)
     try:
         assert cosma.cosma_init(wait_limit=1) == 0
         C, _ = out_tensor(m, n, DT)
-        cosma.gemm(A, B, C, DT, plan=_tile_plan(m, n, k, tile))
+        cosma.gemm(A, B, C, DT, plan=_split_plan(m, n, k, tile, pk))
         st = cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream)
         assert st == cosma.COSMA_ERR_TIMEOUT
     finally:
         assert cosma.cosma_init(wait_limit=0) == 0
     C, _ = out_tensor(m, n, DT)
-    cosma.gemm(A, B, C, DT, plan=_tile_plan(m, n, k, tile))
+    cosma.gemm(A, B, C, DT, plan=_split_plan(m, n, k, tile, pk))
     torch.cuda.synchronize()
     assert cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream) == 0
     rr, cc = sample_indices(m, n, 256, seed=3)

@@ -82,12 +82,12 @@ def test_gemm_ex_matches_oracle(dtype, ta, tb, alpha, beta):
     assert not bad.any(), f"{bad.sum()} entries out of bound, first at {np.argwhere(bad)[0]}"
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "f32_emu_tf32"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "f32_emu_tf32", "f64_emu_bf16"])
 def test_gemm_ex_split_k_reduce_applies_alpha_beta(dtype):
     cosma = lib()
-    m, n, k = 96, 80, 6000
+    m, n, k = 96, 80, 6000  # emulated FP64: two 4096-deep super-chunks, one per k slice
     plan = cosma.cosma_plan_query(m, n, k, cosma.DTYPES[dtype])
-    assert plan.pk > 1  # the Reduce applies alpha and beta
+    assert plan.pk > 1  # the Reduce (emulation: the finishing pass) applies alpha and beta
     got, Ah, Bh, C0 = _run(dtype, m, n, k, 1, 0, -1.25, 0.5)
     ref = og.gemm_ex(Ah, Bh, C0, -1.25, 0.5, True, False)
     assert np.all(np.abs(got - ref) <= _bound(dtype, Ah, Bh, 1, 0, C0, -1.25, 0.5))
