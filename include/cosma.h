@@ -239,7 +239,8 @@ int cosma_gemm_planned(int64_t m, int64_t n, int64_t k, const void* A, int64_t l
  * caches it (8 groups per device, until cosma_finalize).  A repeated call
  * with the same problems, pointers and workspace only launches kernels, so it
  * may be captured in a CUDA graph; during capture a group that is not cached
- * yet returns COSMA_ERR_NO_WORKSPACE. */
+ * yet returns COSMA_ERR_NO_WORKSPACE.  A problem with k >= 2^35 or m or n >=
+ * 2^38 returns COSMA_ERR_UNSUPPORTED. */
 int cosma_gemm_grouped(int count, const cosma_problem* problems, int dtype, void* stream);
 
 /* C = A B with A, B and C in HOST memory: the call copies the operands in and

@@ -537,6 +537,9 @@ int cosma_gemm_grouped(int count, const cosma_problem* problems, int dtype, void
     const cosma_problem& q = problems[i];
     const int rc = check_args(q.m, q.n, q.k, q.A, q.lda, q.B, q.ldb, q.C, q.ldc, dtype);
     if (rc != COSMA_OK) return rc;
+    // a work-unit record keeps the k-block count in 30 bits and tile indices in int
+    if (q.k >= (1LL << 35) || q.m >= (1LL << 38) || q.n >= (1LL << 38))
+      return COSMA_ERR_UNSUPPORTED;
   }
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lock(g_mu);
