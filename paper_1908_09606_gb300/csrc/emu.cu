@@ -341,9 +341,11 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
 // T = sum_chunks sum_l 2^(beta (s + 1 - l) - base) L_l kept
 // in a per-CTA scratch region in global memory: the first merge of a tile
 // stores, later ones are reductions performed in L2, and the thread that made
-// them reads the total back (L2 only), adds the tile's last level sum in
-// registers and forms the FP64 result,
-// C = T 2^(sigma_i + tau_j + 2 - beta (s + 1) + base).  `base` (host, from k)
+// them reads the total back (L2 only) and forms the FP64 result,
+// C = T 2^(sigma_i + tau_j + 2 - beta (s + 1) + base).  (Adding the unit's last
+// level sum in registers at the read-back instead of merging it cost 12 % on
+// 65536 x 65536 x 1024 -- one super-chunk per tile -- on one GB300; square
+// 16384^3 moved by less than the run-to-run spread.)  `base` (host, from k)
 // keeps |T| < 2^62; levels whose weight is below 2^base are rounded to it.
 
 // v 2^sh as an int64 (sh < 0: rounded to nearest, ties up).
@@ -437,8 +439,6 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
         for (int64_t c0 = sc0 + gk; c0 < sc1; c0 += gk)
           if (!drain(std::false_type{})) { ok = false; break; }
         if (!ok) break;
-        // the unit's last merge is folded into the read-back (unsplit k)
-        if (sc1 >= u.kb1 && lvl == 2 && !a.X) break;
         // K-RECOMB: T += L 2^(beta (top - lvl) - base), exactly
         const int sh = a.beta * (top - lvl) - a.t_base;
         // (8 columns at a time: each batch's shifted values are sent before the next
@@ -470,7 +470,7 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
     const int64_t cbase = u.tile_col * BN + col_lo;
     const int l8 = lane & 7, g8 = lane >> 3;
     if (a.X) {
-      // k split: the unit's exact total (all its merges done) joins the product's,
+      // k split: the unit's exact total joins the product's,
       // transposed like the FP64 store below, by L2 reductions -- integer sums, so
       // the order of the k slices changes nothing
 #pragma unroll 1
@@ -506,7 +506,6 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
     // not keep the merges' per-column addresses live across the loops
     long long* Tf = Tt;
     asm volatile("" : "+l"(Tf));
-    const int sh2 = a.beta * (top - 2) - a.t_base;  // the last merge: level 2, last chunk
     // read-back one 8-column batch ahead of its use
     long long nx[8];
 #pragma unroll
@@ -519,7 +518,7 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
     for (int c = 0; c < HC; c += 8) {
       long long tv[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) tv[j] = nx[j] + fx_shift(Lv[c + j], sh2);
+      for (int j = 0; j < 8; ++j) tv[j] = nx[j];
       if (c + 8 < HC) {
 #pragma unroll
         for (int j = 0; j < 8; ++j)
