@@ -115,7 +115,8 @@ typedef struct cosma_config {
   int emu_slice_bits;  /* digit width beta in bits, 2..8; 0 = default (8) */
   long long wait_limit;/* clock cycles before a device wait gives up; 0 = default (2^31, ~1 s) */
   int grouped_tile;    /* C tile width of cosma_gemm_grouped: 0 = chosen by the library;
-                          bf16: 128 or 256 (tile 128 x N); f32: 64 or 128 (square tile) */
+                          bf16: 128 or 256 (tile 128 x N), or 512 (256 x 256 tiles on
+                          CTA pairs); f32: 64 or 128 (square tile) */
 } cosma_config;
 
 /* A schedule for one product: the outcome of Alg. 1's FindSeqSchedule

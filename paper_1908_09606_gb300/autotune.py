@@ -343,12 +343,13 @@ SHIPPED_PARAMS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data"
 def tune_grouped(As, Bs, Cs, dtype, tiles=None, reps=3):
     """Autotune the grouped launch for this group of products: time
     cosma_gemm_grouped (CUDA events, best of `reps`) with each tile width (bf16:
-    128 x 128 and 128 x 256 C tiles; f32: 64 and 128), the library's tables for
+    128 x 128 and 128 x 256 C tiles, and 256 x 256 tiles on CTA pairs (512); f32:
+    64 and 128), the library's tables for
     a width being built by an untimed first call; set the fastest as the
     library's grouped_tile and return (tile, {tile: milliseconds})."""
     import torch
     if tiles is None:
-        tiles = (128, 256) if dtype in ("bf16", cosma.COSMA_BF16) else (64, 128)
+        tiles = (128, 256, 512) if dtype in ("bf16", cosma.COSMA_BF16) else (64, 128)
     cfg = cosma.cosma_get_config()
 
     def use(tile):

@@ -91,7 +91,7 @@ bool config_valid(const cosma_config& c) {
   if (c.emu_slice_bits < 0 || c.emu_slice_bits > 8) return false;
   if (c.wait_limit < 0) return false;
   if (c.grouped_tile != 0 && c.grouped_tile != 64 && c.grouped_tile != 128 &&
-      c.grouped_tile != 256)
+      c.grouped_tile != 256 && c.grouped_tile != 512)
     return false;
   return true;
 }

@@ -205,6 +205,92 @@ __device__ __forceinline__ void acquire_tmap(const CUtensorMap* m) {
                : "memory");
 }
 
+// Epilogue warps of the grouped tensor-core kernels, one per tensor-memory lane
+// quadrant q: for each unit, wait for its accumulator, write this CTA's 32 rows
+// of the C tile -- tensor stores through the warp's two 4 KB staging boxes
+// (stage_c) where C allows them, else the lanes' own stores -- and report the
+// accumulator free with free_acc(acc).  TM: rows of a unit's tile; row_off: this
+// CTA's first row in it.
+template <int BN, int TM, class FreeAcc>
+__device__ __forceinline__ void grouped_epilogue(const GArgs& a, int u0, int u1,
+                                                 uint32_t tmem_base, uint64_t* tfull,
+                                                 uint8_t* stage_c, int64_t row_off,
+                                                 const tc::WaitCtx& w, int q, int lane,
+                                                 FreeAcc free_acc) {
+  uint32_t acc = 0;
+  uint32_t tph[2] = {0, 0};
+  uint32_t stores = 0;  // tensor stores committed so far
+  for (int ui = u0; ui < u1; ++ui) {
+    const GUnit u = a.units[ui];
+    const GMeta& g = a.meta[u.p];
+    if (!tc::mbar_wait(&tfull[acc], tph[acc], w)) break;
+    tc::tc_fence_after();
+    const int64_t row0 = (int64_t)u.tile_row * TM + row_off + q * 32;
+    const int64_t row = row0 + lane;
+    float* dst_row = row < g.m ? static_cast<float*>(g.C) + row * g.ldc : nullptr;
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 32) {
+      uint32_t r[32];
+      tc::tmem_ld_32x32(tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN + c, r);
+      tc::tmem_wait_ld();
+      const int64_t col0 = (int64_t)u.tile_col * BN + c;
+      if (g.c_tma) {
+        // Columns below n4 = n rounded down to 4: rows of this warp -> one 32 x 32
+        // box in shared memory (16-byte chunk j of row l at chunk j ^ (l % 8): the
+        // 128-byte swizzle), then one tensor store, which clips at m and n4 (the C
+        // map is n4 wide: a store clips in whole 16-byte units).  Columns n4..n-1
+        // are written by the lanes themselves.
+        if (row0 >= g.m || col0 >= g.n) continue;
+        const int64_t n4 = g.n & ~(int64_t)3;
+        if (col0 < n4) {
+          uint8_t* box = stage_c + (stores & 1) * 4096;
+          if (lane == 0) tc::bulk_wait_read<1>();  // the box's previous store has read it
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            *reinterpret_cast<float4*>(box + lane * 128 + ((j ^ (lane & 7)) * 16)) =
+                make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                            __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+          tc::fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            tc::tma_store_2d(&a.maps[u.p].tc, box, (int32_t)col0, (int32_t)row0);
+            tc::bulk_commit();
+          }
+          ++stores;
+        }
+        if (dst_row && col0 + 32 > n4) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (col0 + j >= n4 && col0 + j < g.n) dst_row[col0 + j] = __uint_as_float(r[j]);
+        }
+        return;
+      }
+      if (dst_row && col0 < g.n) {
+        float* dst = dst_row + col0;
+        if (g.vec_ok && col0 + 32 <= g.n) {
+          float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            d4[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (col0 + j < g.n) dst[j] = __uint_as_float(r[j]);
+        }
+      }
+    }
+    tc::tc_fence_before();
+    __syncwarp();
+    if (lane == 0) free_acc(acc);
+    tph[acc] ^= 1;
+    acc ^= 1;
+  }
+  if (lane == 0) tc::bulk_wait_all();  // stores done before shared memory goes away
+  __syncwarp();
+}
+
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(192, 1) grouped_tc_kernel(GArgs a) {
   using L = GLayout<BN, STAGES>;
@@ -334,85 +420,219 @@ __global__ void __launch_bounds__(192, 1) grouped_tc_kernel(GArgs a) {
     }
   } else {
     const int q = warp & 3;
-    uint32_t acc = 0;
-    uint32_t tph[2] = {0, 0};
-    uint8_t* stage_c = smem + L::EPI_OFF + q * 8192;  // this warp's two staging boxes
-    uint32_t stores = 0;                               // tensor stores committed so far
-    for (int ui = u0; ui < u1; ++ui) {
-      const GUnit u = a.units[ui];
-      const GMeta& g = a.meta[u.p];
-      if (!tc::mbar_wait(&tfull[acc], tph[acc], w)) break;
-      tc::tc_fence_after();
-      const int64_t row0 = (int64_t)u.tile_row * GBM + q * 32;
-      const int64_t row = row0 + lane;
-      float* dst_row = row < g.m ? static_cast<float*>(g.C) + row * g.ldc : nullptr;
-#pragma unroll 1
-      for (int c = 0; c < BN; c += 32) {
-        uint32_t r[32];
-        tc::tmem_ld_32x32(tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN + c, r);
-        tc::tmem_wait_ld();
-        const int64_t col0 = (int64_t)u.tile_col * BN + c;
-        if (g.c_tma) {
-          // Columns below n4 = n rounded down to 4: rows of this warp -> one 32 x 32
-          // box in shared memory (16-byte chunk j of row l at chunk j ^ (l % 8): the
-          // 128-byte swizzle), then one tensor store, which clips at m and n4 (the C
-          // map is n4 wide: a store clips in whole 16-byte units).  Columns n4..n-1
-          // are written by the lanes themselves.
-          if (row0 >= g.m || col0 >= g.n) continue;
-          const int64_t n4 = g.n & ~(int64_t)3;
-          if (col0 < n4) {
-            uint8_t* box = stage_c + (stores & 1) * 4096;
-            if (lane == 0) tc::bulk_wait_read<1>();  // the box's previous store has read it
-            __syncwarp();
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              *reinterpret_cast<float4*>(box + lane * 128 + ((j ^ (lane & 7)) * 16)) =
-                  make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                              __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
-            tc::fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) {
-              tc::tma_store_2d(&a.maps[u.p].tc, box, (int32_t)col0, (int32_t)row0);
-              tc::bulk_commit();
-            }
-            ++stores;
-          }
-          if (dst_row && col0 + 32 > n4) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (col0 + j >= n4 && col0 + j < g.n) dst_row[col0 + j] = __uint_as_float(r[j]);
-          }
-          continue;
-        }
-        if (dst_row && col0 < g.n) {
-          float* dst = dst_row + col0;
-          if (g.vec_ok && col0 + 32 <= g.n) {
-            float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              d4[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                                  __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (col0 + j < g.n) dst[j] = __uint_as_float(r[j]);
-          }
-        }
-      }
-      tc::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&tempty[acc]);
-      tph[acc] ^= 1;
-      acc ^= 1;
-    }
-    if (lane == 0) tc::bulk_wait_all();  // stores done before shared memory goes away
-    __syncwarp();
+    grouped_epilogue<BN, GBM>(a, u0, u1, tmem_base, tfull, smem + L::EPI_OFF + q * 8192, 0, w,
+                              q, lane, [&](uint32_t b) { tc::mbar_arrive(&tempty[b]); });
   }
   __syncthreads();
   if (warp == 1) {
     tc::tc_fence_after();
     tc::tmem_dealloc(tmem_base, 2 * BN);
   }
+}
+
+// ---- CTA-pair variant (bf16, grouped_tile 512) --------------------------------------
+//
+// 256 x 256 C tiles on clusters of two CTAs (tcgen05.mma.cta_group::2, M = 256,
+// N = 256): each CTA loads its own 128 rows of A and its own 128 of the tile's 256
+// columns of B (no multicast), the even CTA issues the MMAs and commits to the
+// barriers of both, and each CTA drains its own 128 x 256 accumulator.  Per SM a
+// 64-deep k block moves 32 KB of operands for 128 x 256 x 64 products instead of
+// 48 KB, so the same shared memory keeps six k blocks in flight instead of four.
+
+constexpr int GPS = 6;  // ring stages of the pair kernel
+struct GPairLayout {
+  static constexpr int A_BYTES = GBM * GBK * 2;      // own 128 rows
+  static constexpr int B_BYTES = 128 * GBK * 2;      // own 128 columns
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int EPI_OFF = GPS * STAGE_BYTES;
+  static constexpr int EPI_BYTES = 4 * 2 * 4096;
+  static constexpr int BAR_OFF = EPI_OFF + EPI_BYTES;
+  // full, empty, tfull, tempty, drain, peer-count exchange
+  static constexpr int NBARS = 2 * GPS + 2 * 2 + 2;
+  static constexpr int TOTAL = BAR_OFF + NBARS * 8 + 16;
+  static constexpr int ALLOC = TOTAL + 1024;
+};
+
+// One box of a 2-D bf16 map into this CTA's shared memory; its bytes are counted on
+// the barrier at bar_cluster (the leader CTA's).
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map,
+                                                 uint32_t bar_cluster, int32_t x, int32_t y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];\n" ::"r"(tc::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(x), "r"(y)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(192, 1) grouped_pair_kernel(GArgs a) {
+  using L = GPairLayout;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+  uint64_t* empty = full + GPS;
+  uint64_t* tfull = empty + GPS;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint64_t* xchg = drain + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(xchg + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  uint32_t* peer_issued = tslot + 2;
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const uint32_t rank = tc::cluster_ctarank();
+  const bool leader = rank == 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < GPS; ++s) {
+      tc::mbar_init(&full[s], 1);   // leader: its producer's arrival + both CTAs' bytes
+      tc::mbar_init(&empty[s], 1);  // the leader's commit, multicast to both CTAs
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&tfull[b], 1);
+      tc::mbar_init(&tempty[b], 8);  // leader: the 4 epilogue warps of each CTA
+    }
+    tc::mbar_init(drain, 1);
+    tc::mbar_init(xchg, 1);  // leader: the odd CTA's count of issued stages
+    *abort_flag = 0;
+    *peer_issued = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) tc::tmem_alloc_pair(tslot, 512);
+  tc::tc_fence_before();
+  tc::cluster_sync();  // barriers of both CTAs initialised, tensor memory allocated
+  tc::tc_fence_after();
+  const uint32_t tmem_base = *tslot;
+  const tc::WaitCtx w{a.wait_limit, a.status, abort_flag};
+  const int pair = blockIdx.x >> 1;
+  const int u0 = a.cta_off[pair], u1 = a.cta_off[pair + 1];
+
+  if (warp == 0) {
+    if (tc::elect_one()) {
+      int stage = 0;
+      uint32_t ph = 0;
+      uint32_t issued = 0;  // stages whose copies this CTA issued
+      uint32_t full_cl[GPS];
+#pragma unroll
+      for (int s = 0; s < GPS; ++s) full_cl[s] = tc::mapa_shared(&full[s], 0);
+      int last_p = -1;
+      GUnit nu = u0 < u1 ? a.units[u0] : GUnit{};
+      for (int ui = u0; ui < u1 && !*abort_flag; ++ui) {
+        const GUnit u = nu;
+        if (ui + 1 < u1) nu = a.units[ui + 1];  // in flight while this unit's loads issue
+        const CUtensorMap* ta = &a.maps[u.p].ta;
+        const CUtensorMap* tb = &a.maps[u.p].tb;
+        if (u.p != last_p) {
+          acquire_tmap(ta);
+          acquire_tmap(tb);
+          last_p = u.p;
+        }
+        const int64_t kbt = u.kbf >> 1;
+        const bool bmn = (u.kbf & 1) != 0;
+        const int32_t arow = u.tile_row * 256 + (int32_t)rank * 128;
+        const int32_t bcol = u.tile_col * 256 + (int32_t)rank * 128;
+        bool ok = true;
+        for (int64_t kb = 0; kb < kbt; ++kb) {
+          if (!tc::mbar_wait(&empty[stage], ph ^ 1, w)) { ok = false; break; }
+          if (leader) tc::mbar_arrive_expect_tx(&full[stage], 2 * L::STAGE_BYTES);
+          uint8_t* sa = smem + stage * L::STAGE_BYTES;
+          tma_load_2d_pair(sa, ta, full_cl[stage], (int32_t)(kb * GBK), arow);
+          if (bmn) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j)  // box j: columns j*64.., k rows kb*64..
+              tma_load_2d_pair(sa + L::A_BYTES + j * (64 * GBK * 2), tb, full_cl[stage],
+                               bcol + j * 64, (int32_t)(kb * GBK));
+          } else {
+            tma_load_2d_pair(sa + L::A_BYTES, tb, full_cl[stage], (int32_t)(kb * GBK), bcol);
+          }
+          ++issued;
+          if (++stage == GPS) { stage = 0; ph ^= 1; }
+        }
+        if (!ok) break;
+      }
+      // The odd CTA's copies signal the leader's barriers: it reports how many
+      // stages it issued, and on an abort the leader waits (bounded) until every
+      // stage either CTA may still have in flight has landed, so neither CTA
+      // leaves (final cluster barrier) with a copy still writing into it.
+      if (*abort_flag) tc::st_cluster_u32(tc::mapa_shared(const_cast<int*>(abort_flag), rank ^ 1), 1u);
+      if (!leader) {
+        tc::st_cluster_u32(tc::mapa_shared(peer_issued, 0), issued);
+        tc::mbar_arrive_remote(tc::mapa_shared(xchg, 0));
+      } else if (*abort_flag) {
+        const long long t0 = clock64();
+        bool got = false;
+        while (!(got = tc::mbar_try_wait_cluster(xchg, 0)) && clock64() - t0 < tc::kDrainCycles) {
+        }
+        if (got) {
+          const uint32_t n0 = issued, n1 = *reinterpret_cast<volatile uint32_t*>(peer_issued);
+          const uint32_t top = n0 > n1 ? n0 : n1;
+          for (uint32_t i = top > (uint32_t)GPS ? top - GPS : 0u; i < top; ++i) {
+            const int s = (int)(i % GPS);
+            const uint32_t par = (i / GPS) & 1u;
+            if (i >= n0) tc::mbar_arrive_expect_tx(&full[s], L::STAGE_BYTES);  // only the peer's
+            else if (i >= n1) tc::mbar_complete_tx(&full[s], L::STAGE_BYTES);  // the peer's never come
+            const long long t1 = clock64();
+            while (!tc::mbar_try_wait(&full[s], par) && clock64() - t1 < tc::kDrainCycles) {
+            }
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (leader && tc::elect_one()) {
+      int stage = 0;
+      uint32_t ph = 0, acc = 0;
+      uint32_t aph[2] = {0, 0};
+      GUnit nu = u0 < u1 ? a.units[u0] : GUnit{};
+      for (int ui = u0; ui < u1 && !*abort_flag; ++ui) {
+        const GUnit u = nu;
+        if (ui + 1 < u1) nu = a.units[ui + 1];
+        const int64_t kbt = u.kbf >> 1;
+        const bool bmn = (u.kbf & 1) != 0;
+        const uint32_t idesc =
+            bmn ? tc::idesc_bf16_f32_bmn(256, 256) : tc::idesc_bf16_f32(256, 256);
+        if (!tc::mbar_wait(&tempty[acc], aph[acc] ^ 1, w)) break;
+        tc::tc_fence_after();
+        const uint32_t d = tmem_base + acc * 256;
+        bool ok = true;
+        for (int64_t kb = 0; kb < kbt; ++kb) {
+          if (!tc::mbar_wait(&full[stage], ph, w)) { ok = false; break; }
+          tc::tc_fence_after();
+          const uint32_t sa = tc::smem_u32(smem + stage * L::STAGE_BYTES);
+          const uint32_t sb = sa + L::A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < GBK / 16; ++kk) {
+            const uint64_t db = bmn ? tc::smem_desc_mn_sw128(sb + kk * 16 * 128, 64 * GBK * 2, 1024)
+                                    : tc::smem_desc_sw128(sb + kk * 32);
+            tc::mma_bf16_pair(d, tc::smem_desc_sw128(sa + kk * 32), db, idesc,
+                              (kb > 0 || kk > 0) ? 1u : 0u);
+          }
+          tc::mma_commit_pair(&empty[stage]);
+          if (++stage == GPS) { stage = 0; ph ^= 1; }
+        }
+        if (!ok) break;
+        tc::mma_commit_pair(&tfull[acc]);
+        aph[acc] ^= 1;
+        acc ^= 1;
+      }
+      tc::mma_commit_pair(drain);  // every MMA of the pair done (both CTAs' drain barriers)
+      const long long t0 = clock64();
+      while (!tc::mbar_try_wait(drain, 0) && clock64() - t0 < tc::kDrainCycles) {
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    uint32_t te[2];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) te[b] = tc::mapa_shared(&tempty[b], 0);
+    grouped_epilogue<256, 256>(a, u0, u1, tmem_base, tfull, smem + L::EPI_OFF + q * 8192,
+                               (int64_t)rank * 128, w, q, lane,
+                               [&](uint32_t b) { tc::mbar_arrive_remote_relaxed(te[b]); });
+  }
+  __syncthreads();
+  tc::tc_fence_before();
+  tc::cluster_sync();  // no CTA leaves while its peer may still signal its barriers
+  tc::tc_fence_after();
+  if (warp == 1) tc::tmem_dealloc_pair(tmem_base, 512);
 }
 
 template <int BMN, int BK, int TMN>
@@ -459,7 +679,7 @@ int encode(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64
 
 int pick_tile(int count, const cosma_problem* pr, int dtype, int requested) {
   if (dtype == COSMA_BF16) {
-    if (requested == 128 || requested == 256) return requested;
+    if (requested == 128 || requested == 256 || requested == 512) return requested;
     std::vector<int64_t> ns(count);
     for (int i = 0; i < count; ++i) ns[i] = pr[i].n;
     std::nth_element(ns.begin(), ns.begin() + count / 2, ns.end());
@@ -545,10 +765,12 @@ int get_table(int dev, int count, const cosma_problem* pr, int dtype, int tile, 
   }
   if (capturing) return COSMA_ERR_NO_WORKSPACE;
 
-  // Host image of the table.
+  // Host image of the table.  tile 512 (bf16): 256 x 256 tiles on CTA pairs, each CTA
+  // loading 128-row boxes of A and of a transposed B.
+  const bool pair = dtype == COSMA_BF16 && tile == 512;
   const int tm = GBM;
-  const int tn = tile;
-  const int tmm = dtype == COSMA_BF16 ? tm : tile;
+  const int tn = pair ? 256 : tile;
+  const int tmm = dtype == COSMA_BF16 ? (pair ? 256 : tm) : tile;
   std::vector<GMeta> meta(count);
   std::vector<GMap> maps(dtype == COSMA_BF16 ? count : 0);
   std::vector<int64_t> tpre(count + 1, 0);
@@ -593,7 +815,7 @@ int get_table(int dev, int count, const cosma_problem* pr, int dtype, int tile, 
         rc = encode_tmap_bf16(&maps[i].tb, q.B, q.k, q.n, q.ldb, 64, GBK);
         tpre[i + 1] = tpre[i];
       } else {
-        rc = encode(&maps[i].tb, g.Bt, q.n, q.k, kp, tn);
+        rc = encode(&maps[i].tb, g.Bt, q.n, q.k, kp, pair ? 128 : tn);
         tpre[i + 1] = tpre[i] + ((q.n + PT - 1) / PT) * ((q.k + PT - 1) / PT);
       }
       if (rc != COSMA_OK) return rc;
@@ -614,7 +836,8 @@ int get_table(int dev, int count, const cosma_problem* pr, int dtype, int tile, 
   }
   // Longest-processing-time-first assignment of units to CTAs.
   const int64_t U = (int64_t)units.size();
-  const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>(sms, U));
+  // (for pair tiles, "ctas" counts CTA pairs)
+  const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>(pair ? std::max(1, sms / 2) : sms, U));
   std::vector<int64_t> order(U);
   for (int64_t i = 0; i < U; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(),
@@ -722,6 +945,35 @@ int launch_tc(const Table& t, const GArgs& args, cudaStream_t st) {
   return (int)cudaGetLastError();
 }
 
+int launch_pair(const Table& t, const GArgs& args, cudaStream_t st) {
+  using L = GPairLayout;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(grouped_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                L::ALLOC);
+  });
+  if (attr != cudaSuccess) return (int)attr;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * t.ctas));
+  cfg.blockDim = dim3(192);
+  cfg.dynamicSmemBytes = L::ALLOC;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  prof_mark(st, true);
+  const cudaError_t le = cudaLaunchKernelEx(&cfg, grouped_pair_kernel, args);
+  prof_mark(st, false);
+  if (le != cudaSuccess) return (int)le;
+  count_launch();
+  return (int)cudaGetLastError();
+}
+
 }  // namespace
 
 int grouped_gemm(int count, const cosma_problem* problems, int dtype, const DeviceInfo& dev,
@@ -763,6 +1015,7 @@ int grouped_gemm(int count, const cosma_problem* problems, int dtype, const Devi
       const cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return (int)e;
     }
+    if (tile == 512) return launch_pair(*t, args, st);
     return tile == 256 ? launch_tc<256, 4>(*t, args, st) : launch_tc<128, 6>(*t, args, st);
   }
   if (tile == 128) {

@@ -62,8 +62,11 @@ def check_group(dims, Cs, dtype, per_problem=6, u=None):
         if k == 0:
             assert not C.any()
             continue
-        rr = np.array([0, m - 1, min(127, m - 1)] + list(rng.integers(0, m, per_problem)))
-        cc = np.array([0, n - 1, min(255, n - 1)] + list(rng.integers(0, n, per_problem)))
+        # tile corners of the 128- and 256-row tiles, the halves of pair tiles
+        rr = np.array([0, m - 1, min(127, m - 1), min(128, m - 1), min(255, m - 1)]
+                      + list(rng.integers(0, m, per_problem)))
+        cc = np.array([0, n - 1, min(127, n - 1), min(128, n - 1), min(255, n - 1)]
+                      + list(rng.integers(0, n, per_problem)))
         Ar = ci.rows(rr, k, "uniform", g, 1000 + i, ci.STREAM_A)
         Bc = ci.cols(cc, k, n, "uniform", g, 1000 + i, ci.STREAM_B)
         if g == "bf16":
@@ -84,7 +87,7 @@ def run_group(As, Bs, Cs, dtype):
     assert cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream) == 0
 
 
-@pytest.mark.parametrize("tile", [0, 128, 256])
+@pytest.mark.parametrize("tile", [0, 128, 256, 512])
 def test_grouped_bf16_512_problems(tile):
     cosma = lib()
     dims = problem_dims(512)
@@ -110,11 +113,17 @@ def test_grouped_f32(tile):
     check_group(dims, Cs, "f32")
 
 
-@pytest.mark.parametrize("dtype", ["bf16", "f32"])
-def test_grouped_empty_and_k0_problems(dtype):
-    dims = np.array([[0, 5, 7], [9, 0, 3], [130, 70, 0], [1, 1, 1], [129, 257, 65], [7, 9, 3000]])
+@pytest.mark.parametrize("dtype,tile", [("bf16", 0), ("f32", 0), ("bf16", 512)])
+def test_grouped_empty_and_k0_problems(dtype, tile):
+    cosma = lib()
+    dims = np.array([[0, 5, 7], [9, 0, 3], [130, 70, 0], [1, 1, 1], [129, 257, 65], [7, 9, 3000],
+                     [300, 520, 200], [257, 129, 64]])
     As, Bs, Cs = make_group(dims, dtype)
-    run_group(As, Bs, Cs, dtype)
+    try:
+        assert cosma.cosma_init(grouped_tile=tile) == 0
+        run_group(As, Bs, Cs, dtype)
+    finally:
+        cosma.cosma_init()
     check_group(dims, Cs, dtype)
 
 
@@ -158,23 +167,30 @@ def test_grouped_captured_in_cuda_graph(dtype):
     check_group(dims, Cs, dtype, per_problem=3)
 
 
-def test_grouped_bf16_padded_pitches_direct_b_and_tensor_stores():
+@pytest.mark.parametrize("tile", [0, 512])
+def test_grouped_bf16_padded_pitches_direct_b_and_tensor_stores(tile):
     """Every B loaded as it is (MN-major) and every C written by tensor stores;
-    the padding columns of C stay untouched."""
+    the padding columns of C stay untouched.  Tile 512: 256 x 256 tiles on CTA
+    pairs, each CTA holding 128 of the tile's B columns."""
     import torch
+    cosma = lib()
     dims = problem_dims(96, seed=4)
     As, Bs, Cs = make_group(dims, "bf16", pad=True)
     stores = [c.as_strided((c.shape[0], c.stride(0)), (c.stride(0), 1)) for c in Cs]
     for st in stores:
         st.fill_(-3.0)
-    run_group(As, Bs, Cs, "bf16")
+    try:
+        assert cosma.cosma_init(grouped_tile=tile) == 0
+        run_group(As, Bs, Cs, "bf16")
+    finally:
+        cosma.cosma_init()
     check_group(dims, Cs, "bf16", per_problem=6)
     for (m, n, k), st in zip(dims, stores):
         if st.shape[1] > n:
             assert torch.all(st[:, n:] == -3.0)
 
 
-@pytest.mark.parametrize("dtype,tiles", [("bf16", (128, 256)), ("f32", (64, 128))])
+@pytest.mark.parametrize("dtype,tiles", [("bf16", (128, 256, 512)), ("f32", (64, 128))])
 def test_grouped_autotuner_picks_a_tile_and_results_hold(dtype, tiles):
     from paper_1908_09606_gb300 import autotune
     cosma = lib()
@@ -227,3 +243,24 @@ def test_grouped_graph_stays_valid_after_the_table_cache_turns_over():
         assert torch.equal(c, e)
     d, _, _, Co = others[-1]
     check_group(d, Co, dtype, per_problem=3)
+
+
+def test_grouped_pair_bounded_wait_reports_timeout_and_context_survives():
+    """A one-cycle wait limit makes the CTA-pair kernel's waits run out: it records
+    COSMA_ERR_TIMEOUT, drains the copies both CTAs may have in flight, frees its
+    tensor memory and exits; the next call with the default limit is correct."""
+    import torch
+    cosma = lib()
+    dims = problem_dims(32, seed=6)
+    As, Bs, Cs = make_group(dims, "bf16", pad=True)
+    try:
+        assert cosma.cosma_init(grouped_tile=512, wait_limit=1) == 0
+        cosma.gemm_grouped(As, Bs, Cs, "bf16")
+        torch.cuda.synchronize()
+        assert cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream) == \
+            cosma.COSMA_ERR_TIMEOUT
+        assert cosma.cosma_init(grouped_tile=512) == 0
+        run_group(As, Bs, Cs, "bf16")
+    finally:
+        cosma.cosma_init()
+    check_group(dims, Cs, "bf16", per_problem=4)
