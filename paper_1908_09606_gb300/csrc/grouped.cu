@@ -264,7 +264,7 @@ __device__ __forceinline__ void grouped_epilogue(const GArgs& a, int u0, int u1,
           for (int j = 0; j < 32; ++j)
             if (col0 + j >= n4 && col0 + j < g.n) dst_row[col0 + j] = __uint_as_float(r[j]);
         }
-        return;
+        continue;
       }
       if (dst_row && col0 < g.n) {
         float* dst = dst_row + col0;

@@ -245,21 +245,23 @@ def test_grouped_graph_stays_valid_after_the_table_cache_turns_over():
     check_group(d, Co, dtype, per_problem=3)
 
 
-def test_grouped_pair_bounded_wait_reports_timeout_and_context_survives():
-    """A one-cycle wait limit makes the CTA-pair kernel's waits run out: it records
-    COSMA_ERR_TIMEOUT, drains the copies both CTAs may have in flight, frees its
-    tensor memory and exits; the next call with the default limit is correct."""
+@pytest.mark.parametrize("tile", [256, 512])
+def test_grouped_bounded_wait_reports_timeout_and_context_survives(tile):
+    """A one-cycle wait limit makes the tensor-core grouped kernel's waits run out
+    (one CTA per tile, or CTA pairs): it records COSMA_ERR_TIMEOUT, drains the copies
+    its CTAs may have in flight, frees its tensor memory and exits; the next call
+    with the default limit is correct."""
     import torch
     cosma = lib()
     dims = problem_dims(32, seed=6)
     As, Bs, Cs = make_group(dims, "bf16", pad=True)
     try:
-        assert cosma.cosma_init(grouped_tile=512, wait_limit=1) == 0
+        assert cosma.cosma_init(grouped_tile=tile, wait_limit=1) == 0
         cosma.gemm_grouped(As, Bs, Cs, "bf16")
         torch.cuda.synchronize()
         assert cosma.cosma_stream_status(torch.cuda.current_stream().cuda_stream) == \
             cosma.COSMA_ERR_TIMEOUT
-        assert cosma.cosma_init(grouped_tile=512) == 0
+        assert cosma.cosma_init(grouped_tile=tile) == 0
         run_group(As, Bs, Cs, "bf16")
     finally:
         cosma.cosma_init()
