@@ -506,52 +506,61 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
     // not keep the merges' per-column addresses live across the loops
     long long* Tf = Tt;
     asm volatile("" : "+l"(Tf));
-    // read-back one 8-column batch ahead of its use
-    long long nx[8];
+    // read-back four 8-column batches ahead of their use (the level sums are dead
+    // here, so their registers hold the loads in flight)
+    constexpr int RD = 4;
+    long long nx[RD][8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-      asm volatile("ld.relaxed.gpu.global.L2::cache_hint.s64 %0, [%1], %2;"
-                   : "=l"(nx[j])
-                   : "l"(Tf + j * 128), "l"(keep)
-                   : "memory");
-    // (not unrolled: the unrolled loop doubled the kernels' code, and the
-    // instruction fetches it cost slowed 65536 x 65536 x 1024 by 11 %)
+    for (int b = 0; b < RD; ++b)
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        asm volatile("ld.relaxed.gpu.global.L2::cache_hint.s64 %0, [%1], %2;"
+                     : "=l"(nx[b][j])
+                     : "l"(Tf + (8 * b + j) * 128), "l"(keep)
+                     : "memory");
+    // (the outer loop is not unrolled: a fully unrolled read-back doubled the
+    // kernels' code, and the instruction fetches it cost slowed 65536 x 65536 x 1024
+    // by 11 %)
 #pragma unroll 1
-    for (int c = 0; c < HC; c += 8) {
-      long long tv[8];
+    for (int c0 = 0; c0 < HC; c0 += 8 * RD) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) tv[j] = nx[j];
-      if (c + 8 < HC) {
+      for (int b = 0; b < RD; ++b) {
+        const int c = c0 + 8 * b;
+        long long tv[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          asm volatile("ld.relaxed.gpu.global.L2::cache_hint.s64 %0, [%1], %2;"
-                       : "=l"(nx[j])
-                       : "l"(Tf + (c + 8 + j) * 128), "l"(keep)
-                       : "memory");
-      }
-      const int64_t col = cbase + c + l8;
-      int eb[8];
+        for (int j = 0; j < 8; ++j) tv[j] = nx[b][j];
+        if (c + 8 * RD < HC) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) eb[j] = cbase + c + j < a.sch.n ? a.eB[cbase + c + j] : kExpNone;
-      double v[8];
+          for (int j = 0; j < 8; ++j)
+            asm volatile("ld.relaxed.gpu.global.L2::cache_hint.s64 %0, [%1], %2;"
+                         : "=l"(nx[b][j])
+                         : "l"(Tf + (c + 8 * RD + j) * 128), "l"(keep)
+                         : "memory");
+        }
+        const int64_t col = cbase + c + l8;
+        int eb[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        double x = (ea == kExpNone || eb[j] == kExpNone)
-                       ? 0.0
-                       : scale_pow2((double)tv[j], ea + eb[j] + eoff);
-        if (a.alpha != 1.0) x *= a.alpha;
-        v[j] = x;
-      }
-      transpose8(v, l8);
-      // now v[i] = C(row0 + 8 g8 + i, cbase + c + l8)
+        for (int j = 0; j < 8; ++j) eb[j] = cbase + c + j < a.sch.n ? a.eB[cbase + c + j] : kExpNone;
+        double v[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int64_t r = row0 + 8 * g8 + i;
-        if (r < a.sch.m && col < a.sch.n) {
-          double* dst = a.C + r * a.ldc + col;
-          double x = v[i];
-          if (a.beta_c != 0.0) x = fma(a.beta_c, *dst, x);
-          *dst = x;
+        for (int j = 0; j < 8; ++j) {
+          double x = (ea == kExpNone || eb[j] == kExpNone)
+                         ? 0.0
+                         : scale_pow2((double)tv[j], ea + eb[j] + eoff);
+          if (a.alpha != 1.0) x *= a.alpha;
+          v[j] = x;
+        }
+        transpose8(v, l8);
+        // now v[i] = C(row0 + 8 g8 + i, cbase + c + l8)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int64_t r = row0 + 8 * g8 + i;
+          if (r < a.sch.m && col < a.sch.n) {
+            double* dst = a.C + r * a.ldc + col;
+            double x = v[i];
+            if (a.beta_c != 0.0) x = fma(a.beta_c, *dst, x);
+            *dst = x;
+          }
         }
       }
     }
