@@ -86,7 +86,8 @@ DRAM_TRAFFIC = {
     ("flat", "bf16"): 4.30e9 + 17.15e9,       # same kernel, 16 GB of f32 C
     ("4096", "f32"): 0.328e9 + 0.109e9,       # simt_f32_kernel<128,4,256>, pk = 2, f32x2 FMAs
     ("4096", "f64"): 0.969e9 + 0.133e9,       # simt_gemm_kernel<double,64,64,8,4,4>
-    ("grouped512", "bf16"): 2.21e9 + 2.02e9,    # grouped_tc_kernel<256,4>
+    ("grouped512", "bf16"): 2.21e9 + 2.02e9,    # grouped_tc_kernel<256,4> (tile 256)
+    ("grouped512", "bf16", 512): 2.125e9 + 2.021e9,  # grouped_pair_kernel (tile 512)
     # emu_pair_kernel<256>: the lock-step schedule captured under a plain cluster
     # launch (COSMA_EMU_LOCKSTEP=2; ncu cannot launch the cooperative one); 16384^3
     # is 8 x the 8192^3 capture (4096^3 -> 8192^3 grew 8.05x for 8x the work)
@@ -495,7 +496,9 @@ def run_grouped(args):
     pg_ms = e0.elapsed_time(e1) / 3
     peaks, peak_src = _peaks()
     if dtype == "bf16":
-        roof = {"kernel": "grouped_tc_kernel", "bound": "tensor",
+        kname = {512: "grouped_pair_kernel", 256: "grouped_tc_kernel<256,4>",
+                 128: "grouped_tc_kernel<128,6>"}.get(tile, "grouped_tc_kernel")
+        roof = {"kernel": kname, "bound": "tensor",
                 "peak": peaks.get("bf16_tflops_sustained", 1700.0),
                 "peak_source": f"bf16_tflops_sustained of {peak_src} peaks"}
     else:
@@ -505,7 +508,10 @@ def run_grouped(args):
                 "peak_source": "derived: SMs x 128 FMA/clk x 2 x 2070 MHz"}
     roof.update({"achieved": flops / (kms * 1e-3) / 1e12, "unit": "TFLOP/s",
                  "algorithmic": "sum of 2mnk over the 512 products per launch",
-                 "kernel_ms": kms, "traffic": DRAM_TRAFFIC.get(("grouped512", dtype))})
+                 "kernel_ms": kms,
+                 "traffic": DRAM_TRAFFIC.get(("grouped512", dtype, tile)
+                                             if tile == 512 else ("grouped512", dtype))
+                 if dtype != "bf16" or tile in (256, 512) else None})
     roof["frac"] = roof["achieved"] / roof["peak"]
     # e2e: operands copied in from pinned host memory, one result read back
     Ah = [a.cpu().pin_memory() for a in As]

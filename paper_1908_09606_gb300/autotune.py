@@ -416,6 +416,9 @@ def parser():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-collect", action="store_true",
                     help="train on the timing files already in --out")
+    ap.add_argument("--collect-dtypes", default=None,
+                    help="collect fresh timings for these dtypes only (comma-separated) and "
+                         "train on the files already in --out for the others")
     ap.add_argument("--eval-only", metavar="PARAMS",
                     help="install these weights (and their margins) and only evaluate")
     return ap
@@ -490,9 +493,10 @@ def main(argv=None):
                                max_flops=TUNE[dt]["max_flops"])
         t0 = time.time()
         path = os.path.join(a.out, f"timings_{dt}.jsonl")
-        rows += (_load_rows(path) if a.no_collect else
-                 collect(path, shapes, dt, time_budget_s=TUNE[dt]["budget_s"] * a.budget_scale,
-                         reps=3))
+        fresh = not a.no_collect and (a.collect_dtypes is None or
+                                      names[dt] in a.collect_dtypes.split(","))
+        rows += (collect(path, shapes, dt, time_budget_s=TUNE[dt]["budget_s"] * a.budget_scale,
+                         reps=3) if fresh else _load_rows(path))
         t_collect[dt] = time.time() - t0
         log(f"dtype {dt}: {len(rows)} rows so far")
     train_rows = [r for r in rows if not is_calibration(r["m"], r["n"], r["k"], r["dtype"])]
