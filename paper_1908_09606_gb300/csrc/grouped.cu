@@ -35,6 +35,9 @@ namespace cosma {
 namespace {
 
 constexpr int GBM = 128, GBK = 64;
+// Problems whose A and B tensor maps a CTA remembers having acquired (a shared-memory
+// bitmap): each is acquired once per CTA; problems beyond it on every change.
+constexpr int kAcqWords = 128;
 constexpr int kCacheSlots = 8;
 
 struct alignas(128) GMap {
@@ -195,9 +198,23 @@ struct GLayout {
   static constexpr int EPI_BYTES = 4 * 2 * 4096;
   static constexpr int BAR_OFF = EPI_OFF + EPI_BYTES;
   static constexpr int NBARS = 2 * STAGES + 5;
-  static constexpr int TOTAL = BAR_OFF + NBARS * 8 + 16;
+  static constexpr int ACQ_OFF = BAR_OFF + NBARS * 8 + 16;  // tensor maps acquired
+  static constexpr int TOTAL = ACQ_OFF + 4 * kAcqWords;
   static constexpr int ALLOC = TOTAL + 1024;
 };
+
+__device__ __forceinline__ void acquire_tmap(const CUtensorMap* m);
+
+// The producer's acquire of problem p's operand maps before its first copies from
+// them: once per CTA for the problems the bitmap covers.
+__device__ __forceinline__ void acquire_maps_once(uint32_t* acq, int p, const CUtensorMap* ta,
+                                                  const CUtensorMap* tb) {
+  const bool tracked = p < kAcqWords * 32;
+  if (tracked && ((acq[p >> 5] >> (p & 31)) & 1u)) return;
+  acquire_tmap(ta);
+  acquire_tmap(tb);
+  if (tracked) acq[p >> 5] |= 1u << (p & 31);
+}
 
 __device__ __forceinline__ void acquire_tmap(const CUtensorMap* m) {
   asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(
@@ -222,12 +239,26 @@ __device__ __forceinline__ void grouped_epilogue(const GArgs& a, int u0, int u1,
   uint32_t stores = 0;  // tensor stores committed so far
   for (int ui = u0; ui < u1; ++ui) {
     const GUnit u = a.units[ui];
-    const GMeta& g = a.meta[u.p];
+    // the problem's fields are loaded before the wait, so their latency hides in it
+    struct {
+      int64_t m, n, ldc;
+      float* C;
+      int c_tma, vec_ok;
+    } g;
+    {
+      const GMeta& gm = a.meta[u.p];
+      g.m = gm.m;
+      g.n = gm.n;
+      g.ldc = gm.ldc;
+      g.C = static_cast<float*>(gm.C);
+      g.c_tma = gm.c_tma;
+      g.vec_ok = gm.vec_ok;
+    }
     if (!tc::mbar_wait(&tfull[acc], tph[acc], w)) break;
     tc::tc_fence_after();
     const int64_t row0 = (int64_t)u.tile_row * TM + row_off + q * 32;
     const int64_t row = row0 + lane;
-    float* dst_row = row < g.m ? static_cast<float*>(g.C) + row * g.ldc : nullptr;
+    float* dst_row = row < g.m ? g.C + row * g.ldc : nullptr;
 #pragma unroll 1
     for (int c = 0; c < BN; c += 32) {
       uint32_t r[32];
@@ -304,6 +335,7 @@ __global__ void __launch_bounds__(192, 1) grouped_tc_kernel(GArgs a) {
   uint64_t* drain = tempty + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  uint32_t* acq = reinterpret_cast<uint32_t*>(smem + L::ACQ_OFF);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
@@ -317,6 +349,7 @@ __global__ void __launch_bounds__(192, 1) grouped_tc_kernel(GArgs a) {
     }
     tc::mbar_init(drain, 1);
     *abort_flag = 0;
+    for (int i = 0; i < kAcqWords; ++i) acq[i] = 0;
     tc::fence_barrier_init();
   }
   if (warp == 1) tc::tmem_alloc(tslot, 2 * BN);
@@ -339,8 +372,7 @@ __global__ void __launch_bounds__(192, 1) grouped_tc_kernel(GArgs a) {
         const CUtensorMap* ta = &a.maps[u.p].ta;
         const CUtensorMap* tb = &a.maps[u.p].tb;
         if (u.p != last_p) {
-          acquire_tmap(ta);
-          acquire_tmap(tb);
+          acquire_maps_once(acq, u.p, ta, tb);
           last_p = u.p;
         }
         const int64_t kbt = u.kbf >> 1;
@@ -449,7 +481,8 @@ struct GPairLayout {
   static constexpr int BAR_OFF = EPI_OFF + EPI_BYTES;
   // full, empty, tfull, tempty, drain, peer-count exchange
   static constexpr int NBARS = 2 * GPS + 2 * 2 + 2;
-  static constexpr int TOTAL = BAR_OFF + NBARS * 8 + 16;
+  static constexpr int ACQ_OFF = BAR_OFF + NBARS * 8 + 16;  // tensor maps acquired
+  static constexpr int TOTAL = ACQ_OFF + 4 * kAcqWords;
   static constexpr int ALLOC = TOTAL + 1024;
 };
 
@@ -478,6 +511,7 @@ __global__ void __launch_bounds__(192, 1) grouped_pair_kernel(GArgs a) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(xchg + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
   uint32_t* peer_issued = tslot + 2;
+  uint32_t* acq = reinterpret_cast<uint32_t*>(smem + L::ACQ_OFF);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const uint32_t rank = tc::cluster_ctarank();
@@ -495,6 +529,7 @@ __global__ void __launch_bounds__(192, 1) grouped_pair_kernel(GArgs a) {
     tc::mbar_init(xchg, 1);  // leader: the odd CTA's count of issued stages
     *abort_flag = 0;
     *peer_issued = 0;
+    for (int i = 0; i < kAcqWords; ++i) acq[i] = 0;
     tc::fence_barrier_init();
   }
   if (warp == 1) tc::tmem_alloc_pair(tslot, 512);
@@ -522,8 +557,7 @@ __global__ void __launch_bounds__(192, 1) grouped_pair_kernel(GArgs a) {
         const CUtensorMap* ta = &a.maps[u.p].ta;
         const CUtensorMap* tb = &a.maps[u.p].tb;
         if (u.p != last_p) {
-          acquire_tmap(ta);
-          acquire_tmap(tb);
+          acquire_maps_once(acq, u.p, ta, tb);
           last_p = u.p;
         }
         const int64_t kbt = u.kbf >> 1;
