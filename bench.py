@@ -87,12 +87,12 @@ DRAM_TRAFFIC = {
     ("4096", "f32"): 0.328e9 + 0.109e9,       # simt_f32_kernel<128,4,256>, pk = 2, f32x2 FMAs
     ("4096", "f64"): 0.969e9 + 0.133e9,       # simt_gemm_kernel<double,64,64,8,4,4>
     ("grouped512", "bf16"): 2.21e9 + 2.02e9,    # grouped_tc_kernel<256,4> (tile 256)
-    ("grouped512", "bf16", 512): 2.125e9 + 2.021e9,  # grouped_pair_kernel (tile 512)
+    ("grouped512", "bf16", 512): 2.122e9 + 2.021e9,  # grouped_pair_kernel (tile 512)
     # emu_pair_kernel<256>: the lock-step schedule captured under a plain cluster
     # launch (COSMA_EMU_LOCKSTEP=2; ncu cannot launch the cooperative one); 16384^3
     # is 8 x the 8192^3 capture (4096^3 -> 8192^3 grew 8.05x for 8x the work)
-    ("emu8192", "f64_emu_bf16"): 36.34e9 + 5.95e9,
-    ("square", "f64_emu_bf16"): 8 * (36.34e9 + 5.95e9),
+    ("emu8192", "f64_emu_bf16"): 35.39e9 + 5.92e9,
+    ("square", "f64_emu_bf16"): 8 * (35.39e9 + 5.92e9),
     # tf32x3_gemm_kernel: lock-step ticks under a plain launch (COSMA_TF32_LOCKSTEP=2)
     ("square", "f32_emu_tf32"): 53.16e9 + 1.07e9,
 }

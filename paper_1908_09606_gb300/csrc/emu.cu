@@ -421,7 +421,7 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
           for (int c = 0; c < HC; c += 32) {
             uint32_t v[32];
             tc::tmem_ld_32x32(src + c, v);
-            tc::tmem_wait_ld();
+            tc::tmem_wait_ld_r32(v);  // the registers are read only after the wait
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const int iv = __float2int_rn(__uint_as_float(v[j]));  // exact integer

@@ -263,7 +263,7 @@ __device__ __forceinline__ void grouped_epilogue(const GArgs& a, int u0, int u1,
     for (int c = 0; c < BN; c += 32) {
       uint32_t r[32];
       tc::tmem_ld_32x32(tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN + c, r);
-      tc::tmem_wait_ld();
+      tc::tmem_wait_ld_r32(r);  // r is read only after the wait
       const int64_t col0 = (int64_t)u.tile_col * BN + c;
       if (g.c_tma) {
         // Columns below n4 = n rounded down to 4: rows of this warp -> one 32 x 32

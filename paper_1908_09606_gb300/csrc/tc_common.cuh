@@ -265,7 +265,8 @@ __device__ __forceinline__ void tmem_wait_ld() {
 }
 // tcgen05.wait::ld that also names the 32 destination registers of the load it
 // waits for as written here, so that no use of them is scheduled above the wait
-// (needed when other work runs between a load and its wait).
+// (the plain wait above orders memory only: a use of a loaded register could
+// otherwise move between the load and its wait).
 __device__ __forceinline__ void tmem_wait_ld_r32(uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n"
                : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),

@@ -382,7 +382,7 @@ tf32x3_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
         for (int c = 0; c < TN / 32; ++c) {
           uint32_t r[32];
           tc::tmem_ld_32x32(tmem_base + ((uint32_t)(q * 32) << 16) + acc * TN + c * 32, r);
-          tc::tmem_wait_ld();
+          tc::tmem_wait_ld_r32(r);  // r is read only after the wait
 #pragma unroll
           for (int j = 0; j < 32; ++j) sum[c * 32 + j] += __uint_as_float(r[j]);
         }
