@@ -19,8 +19,8 @@
 //           group's exact integer sum is drained by the epilogue warps into an
 //           int32 level sum held in registers.  k is walked in super-chunks of
 //           4096 (all levels per chunk), so a level sum stays below 2^31 for any
-//           k.  Two (pair tiles) or four (single-SM tiles) accumulator buffers
-//           let the MMAs of the next groups overlap a drain.
+//           k.  Two (256-wide tiles) or four (128-wide tiles) accumulator
+//           buffers let the MMAs of the next groups overlap a drain.
 //  K-RECOMB At the end of each (chunk, level) the exact level sum joins an
 //           exact int64 fixed-point running total kept in global scratch (L2
 //           reductions; see "Running total" below); after the last chunk the
