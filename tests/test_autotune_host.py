@@ -109,3 +109,16 @@ def test_calibration_shapes_are_a_fixed_fifth(tune):
     assert 0.15 < np.mean(flags) < 0.25
     assert tune.MARGINS[0] > 0 and math.isinf(tune.MARGINS[-1])
     assert list(tune.MARGINS) == sorted(tune.MARGINS)
+
+
+def test_parser_modes(tune):
+    """Collection, training on stored timings, partial re-collection and
+    evaluation of installed weights are separate, explicit modes."""
+    ap = tune.parser()
+    a = ap.parse_args(["--out", "x"])
+    assert not a.no_collect and a.collect_dtypes is None and a.eval_only is None
+    a = ap.parse_args(["--out", "x", "--collect-dtypes", "f64_emu_bf16", "--epochs", "10"])
+    assert a.collect_dtypes == "f64_emu_bf16" and a.epochs == 10
+    a = ap.parse_args(["--out", "x", "--eval-only", "w.npy", "--dtypes", "bf16"])
+    assert a.eval_only == "w.npy" and a.dtypes == "bf16"
+    assert set(a.dtypes.split(",")) <= set(tune.cosma.DTYPES)
