@@ -744,7 +744,7 @@ def main():
             torch.cuda.synchronize()
             rates[name] = nb * Ah.element_size() / (c0.elapsed_time(c1) * 1e-3) / 1e9
         del dst_d
-        e_steps = max(1, min(args.steps, 3))
+        e_steps = max(1, min(args.steps, 5))
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(e_steps + 1)]
         if world > 1:
             dist.barrier()
