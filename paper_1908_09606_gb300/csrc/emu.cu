@@ -402,6 +402,72 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
   uint32_t tph[NACC];
 #pragma unroll
   for (int b = 0; b < NACC; ++b) tph[b] = 0;
+  const int l8 = lane & 7, g8 = lane >> 3;
+  const int eoff = 2 - a.beta * top + a.t_base;
+  // the read-back addresses from an opaque copy of the base, so the compiler does
+  // not keep the merges' per-column addresses live across the loops
+  long long* Tf = Tt;
+  asm volatile("" : "+l"(Tf));
+
+  // Deferred FP64 store.  A finished unit's total is read back and stored in NB
+  // batches of 8 columns, two after each of the next unit's first-level group
+  // drains (the accumulator is already free, so the MMAs run on meanwhile), and
+  // any left before that unit's first merge overwrites the total; after the last
+  // unit, all at once.  Same thread, same addresses: each load precedes the
+  // store of the next unit in program order, so it reads the finished total.
+  constexpr int NB = HC / 8;
+  int pb = NB;  // next batch of the pending unit (NB: nothing pending)
+  int64_t p_row0 = 0, p_cbase = 0;
+  int p_ea = kExpNone;
+  long long nx[8];  // the loads of batch pb, in flight
+  auto rb_load = [&](int b) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      asm volatile("ld.relaxed.gpu.global.L2::cache_hint.s64 %0, [%1], %2;"
+                   : "=l"(nx[j])
+                   : "l"(Tf + (8 * b + j) * 128), "l"(keep)
+                   : "memory");
+  };
+  // batches pb .. lim - 1: C = T 2^(sigma_i + tau_j + 2 - beta (s + 1) + base) for
+  // the thread's row, 8 columns each, formed in the row's lane, transposed within
+  // groups of 8 lanes and written as four 64-byte row segments per instruction
+  auto rb_upto = [&](int lim) {
+#pragma unroll 1
+    for (; pb < lim; ++pb) {
+      const int c = 8 * pb;
+      long long tv[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) tv[j] = nx[j];
+      if (pb + 1 < NB) rb_load(pb + 1);
+      const int64_t col = p_cbase + c + l8;
+      int eb[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        eb[j] = p_cbase + c + j < a.sch.n ? a.eB[p_cbase + c + j] : kExpNone;
+      double v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        double x = (p_ea == kExpNone || eb[j] == kExpNone)
+                       ? 0.0
+                       : scale_pow2((double)tv[j], p_ea + eb[j] + eoff);
+        if (a.alpha != 1.0) x *= a.alpha;
+        v[j] = x;
+      }
+      transpose8(v, l8);
+      // now v[i] = C(p_row0 + 8 g8 + i, p_cbase + c + l8)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int64_t r = p_row0 + 8 * g8 + i;
+        if (r < a.sch.m && col < a.sch.n) {
+          double* dst = a.C + r * a.ldc + col;
+          double x = v[i];
+          if (a.beta_c != 0.0) x = fma(a.beta_c, *dst, x);
+          *dst = x;
+        }
+      }
+    }
+  };
+
   bool ok = true;
   for (int64_t ui = 0; ui < nunits && ok; ++ui) {
     const Unit u = emu_unit_of_cta(a.sch, unit_cta, ui);
@@ -435,9 +501,15 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
           acc = (acc + 1) == NACC ? 0 : acc + 1;
           return true;
         };
-        if (!drain(std::true_type{})) { ok = false; break; }
-        for (int64_t c0 = sc0 + gk; c0 < sc1; c0 += gk)
-          if (!drain(std::false_type{})) { ok = false; break; }
+        for (int64_t c0 = sc0; c0 < sc1; c0 += gk) {
+          if (!(c0 == sc0 ? drain(std::true_type{}) : drain(std::false_type{}))) {
+            ok = false;
+            break;
+          }
+          // the previous unit's store: two batches per group, the rest before
+          // the merge below overwrites its total
+          if (pb < NB) rb_upto(c0 + gk >= sc1 ? NB : min(NB, pb + 2));
+        }
         if (!ok) break;
         // K-RECOMB: T += L 2^(beta (top - lvl) - base), exactly
         const int sh = a.beta * (top - lvl) - a.t_base;
@@ -468,10 +540,9 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
     if (!ok) break;
     const int64_t row0 = u.tile_row * TM + row_off + q4 * 32;
     const int64_t cbase = u.tile_col * BN + col_lo;
-    const int l8 = lane & 7, g8 = lane >> 3;
     if (a.X) {
       // k split: the unit's exact total joins the product's,
-      // transposed like the FP64 store below, by L2 reductions -- integer sums, so
+      // transposed like the FP64 store, by L2 reductions -- integer sums, so
       // the order of the k slices changes nothing
 #pragma unroll 1
       for (int c = 0; c < HC; c += 8) {
@@ -495,76 +566,14 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
       }
       continue;
     }
-    // Final FP64 store: C = T 2^(sigma_i + tau_j + 2 - beta (s + 1) + base) for this
-    // thread's row, HC columns.  Each 8-column chunk is formed in the row's lane,
-    // transposed within groups of 8 lanes, and written as four 64-byte row
-    // segments per instruction.
-    const int64_t row = row0 + lane;
-    const int ea = row < a.sch.m ? a.eA[row] : kExpNone;
-    const int eoff = 2 - a.beta * top + a.t_base;
-    // the read-back addresses from an opaque copy of the base, so the compiler does
-    // not keep the merges' per-column addresses live across the loops
-    long long* Tf = Tt;
-    asm volatile("" : "+l"(Tf));
-    // read-back four 8-column batches ahead of their use (the level sums are dead
-    // here, so their registers hold the loads in flight)
-    constexpr int RD = 4;
-    long long nx[RD][8];
-#pragma unroll
-    for (int b = 0; b < RD; ++b)
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        asm volatile("ld.relaxed.gpu.global.L2::cache_hint.s64 %0, [%1], %2;"
-                     : "=l"(nx[b][j])
-                     : "l"(Tf + (8 * b + j) * 128), "l"(keep)
-                     : "memory");
-    // (the outer loop is not unrolled: a fully unrolled read-back doubled the
-    // kernels' code, and the instruction fetches it cost slowed 65536 x 65536 x 1024
-    // by 11 %)
-#pragma unroll 1
-    for (int c0 = 0; c0 < HC; c0 += 8 * RD) {
-#pragma unroll
-      for (int b = 0; b < RD; ++b) {
-        const int c = c0 + 8 * b;
-        long long tv[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) tv[j] = nx[b][j];
-        if (c + 8 * RD < HC) {
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            asm volatile("ld.relaxed.gpu.global.L2::cache_hint.s64 %0, [%1], %2;"
-                         : "=l"(nx[b][j])
-                         : "l"(Tf + (c + 8 * RD + j) * 128), "l"(keep)
-                         : "memory");
-        }
-        const int64_t col = cbase + c + l8;
-        int eb[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) eb[j] = cbase + c + j < a.sch.n ? a.eB[cbase + c + j] : kExpNone;
-        double v[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          double x = (ea == kExpNone || eb[j] == kExpNone)
-                         ? 0.0
-                         : scale_pow2((double)tv[j], ea + eb[j] + eoff);
-          if (a.alpha != 1.0) x *= a.alpha;
-          v[j] = x;
-        }
-        transpose8(v, l8);
-        // now v[i] = C(row0 + 8 g8 + i, cbase + c + l8)
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int64_t r = row0 + 8 * g8 + i;
-          if (r < a.sch.m && col < a.sch.n) {
-            double* dst = a.C + r * a.ldc + col;
-            double x = v[i];
-            if (a.beta_c != 0.0) x = fma(a.beta_c, *dst, x);
-            *dst = x;
-          }
-        }
-      }
-    }
+    // this unit's FP64 store waits for the next unit's drains
+    p_row0 = row0;
+    p_cbase = cbase;
+    p_ea = row0 + lane < a.sch.m ? a.eA[row0 + lane] : kExpNone;
+    pb = 0;
+    rb_load(0);
   }
+  if (ok && pb < NB) rb_upto(NB);
 }
 
 // Same iteration order for the producer and the MMA issuer over the k blocks
