@@ -21,12 +21,14 @@
 //           4096 (all levels per chunk), so a level sum stays below 2^31 for any
 //           k.  Two (256-wide tiles) or four (128-wide tiles) accumulator
 //           buffers let the MMAs of the next groups overlap a drain.
-//  K-RECOMB At the end of each (chunk, level) the exact level sum joins an
-//           exact int64 fixed-point running total kept in global scratch (L2
-//           reductions; see "Running total" below); after the last chunk the
-//           tile is converted to FP64 once, so every kernel and tile shape gives
-//           the same bits: the method's exact result rounded once (levels below
-//           the fixed-point base aside).
+//  K-RECOMB Within a chunk, levels are taken in pairs: the lower level's sum
+//           keeps its low beta bits as digits and carries the rest into the
+//           next level's sum, and at the end of each pair the exact value
+//           L_l + 2^beta L_(l-1) joins an exact int64 fixed-point running total
+//           kept in global scratch (L2 reductions; see "Running total" below);
+//           after the last chunk the tile is converted to FP64 once, so every
+//           kernel and tile shape gives the same bits: the method's exact result
+//           rounded once (level pairs below the fixed-point base aside).
 //
 // The C tile (128 x 128 on one SM, or 256 x 256 / 256 x 128 on a CTA pair with
 // tcgen05.mma.cta_group::2) is the resident a x b block of C of the paper's
@@ -336,8 +338,9 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
 
 // Running total (both kernels).  Tensor memory holds only accumulators (512 /
 // BN buffers of BN columns).  The exact level sum of the current super-chunk
-// stays in registers (BN / 2 int32 per epilogue thread), and the running total
-// of the tile is an exact int64 fixed-point number
+// stays in registers (BN / 2 int32 per epilogue thread, and BN / 8 words of
+// digits while a level pair is open), and the running total of the tile is an
+// exact int64 fixed-point number
 // T = sum_chunks sum_l 2^(beta (s + 1 - l) - base) L_l kept
 // in a per-CTA scratch region in global memory: the first merge of a tile
 // stores, later ones are reductions performed in L2, and the thread that made
@@ -346,12 +349,13 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
 // level sum in registers at the read-back instead of merging it cost 12 % on
 // 65536 x 65536 x 1024 -- one super-chunk per tile -- on one GB300; square
 // 16384^3 moved by less than the run-to-run spread.)  `base` (host, from k)
-// keeps |T| < 2^62; levels whose weight is below 2^base are rounded to it.
+// keeps |T| < 2^62; a level pair whose weight is below 2^base is rounded to it
+// (one rounding per pair and super-chunk).
 
 // v 2^sh as an int64 (sh < 0: rounded to nearest, ties up).
-__device__ __forceinline__ long long fx_shift(int v, int sh) {
-  if (sh >= 0) return (long long)v << sh;
-  return ((long long)v + (1LL << (-sh - 1))) >> (-sh);
+__device__ __forceinline__ long long fx_shift(long long v, int sh) {
+  if (sh >= 0) return v << sh;
+  return (v + (1LL << (-sh - 1))) >> (-sh);
 }
 
 // 8 x 8 transpose within each group of 8 lanes: on entry lane l holds row l of
@@ -410,108 +414,143 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
   asm volatile("" : "+l"(Tf));
 
   // Deferred FP64 store.  A finished unit's total is read back and stored in NB
-  // batches of 8 columns, two after each of the next unit's first-level group
-  // drains (the accumulator is already free, so the MMAs run on meanwhile), and
-  // any left before that unit's first merge overwrites the total; after the last
-  // unit, all at once.  Same thread, same addresses: each load precedes the
-  // store of the next unit in program order, so it reads the finished total.
+  // batches of 8 columns, two after each group drain of the next unit's first
+  // level (the accumulator is already free, so the MMAs run on meanwhile), and any
+  // left at the end of that level, before the unit's first merge overwrites the
+  // total; after the last unit, all at once.  Same thread, same addresses: each
+  // load precedes the next unit's store in program order, so it reads the
+  // finished total.
   constexpr int NB = HC / 8;
   int pb = NB;  // next batch of the pending unit (NB: nothing pending)
   int64_t p_row0 = 0, p_cbase = 0;
   int p_ea = kExpNone;
-  long long nx[8];  // the loads of batch pb, in flight
-  auto rb_load = [&](int b) {
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-      asm volatile("ld.relaxed.gpu.global.L2::cache_hint.s64 %0, [%1], %2;"
-                   : "=l"(nx[j])
-                   : "l"(Tf + (8 * b + j) * 128), "l"(keep)
-                   : "memory");
-  };
-  // batches pb .. lim - 1: C = T 2^(sigma_i + tau_j + 2 - beta (s + 1) + base) for
-  // the thread's row, 8 columns each, formed in the row's lane, transposed within
-  // groups of 8 lanes and written as four 64-byte row segments per instruction
+  // batches pb .. lim - 1 (lim - pb even), two at a time with both loads in flight:
+  // C = T 2^(sigma_i + tau_j + 2 - beta (s + 1) + base) for the thread's row, 8
+  // columns each, formed in the row's lane, transposed within groups of 8 lanes and
+  // written as four 64-byte row segments per instruction
   auto rb_upto = [&](int lim) {
 #pragma unroll 1
-    for (; pb < lim; ++pb) {
-      const int c = 8 * pb;
-      long long tv[8];
+    for (; pb < lim; pb += 2) {
+      long long tv[2][8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) tv[j] = nx[j];
-      if (pb + 1 < NB) rb_load(pb + 1);
-      const int64_t col = p_cbase + c + l8;
-      int eb[8];
+      for (int b = 0; b < 2; ++b)
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
-        eb[j] = p_cbase + c + j < a.sch.n ? a.eB[p_cbase + c + j] : kExpNone;
-      double v[8];
+        for (int j = 0; j < 8; ++j)
+          asm volatile("ld.relaxed.gpu.global.L2::cache_hint.s64 %0, [%1], %2;"
+                       : "=l"(tv[b][j])
+                       : "l"(Tf + (8 * (pb + b) + j) * 128), "l"(keep)
+                       : "memory");
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        double x = (p_ea == kExpNone || eb[j] == kExpNone)
-                       ? 0.0
-                       : scale_pow2((double)tv[j], p_ea + eb[j] + eoff);
-        if (a.alpha != 1.0) x *= a.alpha;
-        v[j] = x;
-      }
-      transpose8(v, l8);
-      // now v[i] = C(p_row0 + 8 g8 + i, p_cbase + c + l8)
+      for (int b = 0; b < 2; ++b) {
+        const int c = 8 * (pb + b);
+        const int64_t col = p_cbase + c + l8;
+        int eb[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int64_t r = p_row0 + 8 * g8 + i;
-        if (r < a.sch.m && col < a.sch.n) {
-          double* dst = a.C + r * a.ldc + col;
-          double x = v[i];
-          if (a.beta_c != 0.0) x = fma(a.beta_c, *dst, x);
-          *dst = x;
+        for (int j = 0; j < 8; ++j)
+          eb[j] = p_cbase + c + j < a.sch.n ? a.eB[p_cbase + c + j] : kExpNone;
+        double v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          double x = (p_ea == kExpNone || eb[j] == kExpNone)
+                         ? 0.0
+                         : scale_pow2((double)tv[b][j], p_ea + eb[j] + eoff);
+          if (a.alpha != 1.0) x *= a.alpha;
+          v[j] = x;
+        }
+        transpose8(v, l8);
+        // now v[i] = C(p_row0 + 8 g8 + i, p_cbase + c + l8)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int64_t r = p_row0 + 8 * g8 + i;
+          if (r < a.sch.m && col < a.sch.n) {
+            double* dst = a.C + r * a.ldc + col;
+            double x = v[i];
+            if (a.beta_c != 0.0) x = fma(a.beta_c, *dst, x);
+            *dst = x;
+          }
         }
       }
     }
   };
 
   bool ok = true;
+  const int dmask = (1 << a.beta) - 1;
   for (int64_t ui = 0; ui < nunits && ok; ++ui) {
     const Unit u = emu_unit_of_cta(a.sch, unit_cta, ui);
-    int Lv[HC];  // exact level sum of the current super-chunk
+    int Lv[HC];           // exact level sum of the current super-chunk
+    uint32_t dg[HC / 4];  // low digits of a pair's lower level, four 8-bit fields a word
     bool stored = false;
     for (int64_t sc0 = u.kb0; sc0 < u.kb1 && ok; sc0 += a.chunk_kb) {
       const int64_t sc1 = min(sc0 + (int64_t)a.chunk_kb, u.kb1);
-      for (int lvl = top; lvl >= 2 && ok; --lvl) {
-        const int gk = group_blocks(a.group_kb, lvl - 1);
-        // one exact group: its integer sums join Lv (the level's first group sets it)
-        auto drain = [&](auto first_tag) -> bool {
-          constexpr bool kFirst = decltype(first_tag)::value;
-          if (!tc::mbar_wait(&tfull[acc], tph[acc], w)) return false;
-          tc::tc_fence_after();
-          const uint32_t src = tmem_base + lane_off + acc * BN + col_lo;
+      // one exact group: its integer sums join Lv (the level's first group sets it,
+      // unless Lv starts from a carry)
+      auto drain = [&](auto first_tag) -> bool {
+        constexpr bool kFirst = decltype(first_tag)::value;
+        if (!tc::mbar_wait(&tfull[acc], tph[acc], w)) return false;
+        tc::tc_fence_after();
+        const uint32_t src = tmem_base + lane_off + acc * BN + col_lo;
 #pragma unroll
-          for (int c = 0; c < HC; c += 32) {
-            uint32_t v[32];
-            tc::tmem_ld_32x32(src + c, v);
-            tc::tmem_wait_ld_r32(v);  // the registers are read only after the wait
+        for (int c = 0; c < HC; c += 16) {
+          uint32_t v[16];
+          tc::tmem_ld_32x16(src + c, v);
+          tc::tmem_wait_ld_r16(v);  // the registers are read only after the wait
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int iv = __float2int_rn(__uint_as_float(v[j]));  // exact integer
-              Lv[c + j] = kFirst ? iv : Lv[c + j] + iv;
+          for (int j = 0; j < 16; ++j) {
+            const int iv = __float2int_rn(__uint_as_float(v[j]));  // exact integer
+            Lv[c + j] = kFirst ? iv : Lv[c + j] + iv;
+          }
+        }
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive_remote_relaxed(tempty_addr[acc]);
+        tph[acc] ^= 1;
+        acc = (acc + 1) == NACC ? 0 : acc + 1;
+        return true;
+      };
+      // Levels join the running total two at a time (K-RECOMB).  The lower level
+      // lvl of a pair keeps its low beta bits as digits and passes the rest,
+      // floor(L_lvl / 2^beta), on as the start of level lvl - 1's sum, which then
+      // ends at L_{lvl-1} + floor(L_lvl / 2^beta) (one super-chunk's level sums
+      // stay below 2^29, so this fits an int32); the pair's value is
+      // 2^beta (that sum) + digits = L_lvl + 2^beta L_{lvl-1}, exactly, and
+      // T += value 2^(beta (top - lvl) - base).  With an odd number of levels the
+      // last, lvl = 2, joins alone.
+      for (int lvl = top; lvl >= 2 && ok; lvl -= 2) {
+        const bool pair = lvl > 2;
+        if (pair) {
+          const int gk = group_blocks(a.group_kb, lvl - 1);
+          for (int64_t c0 = sc0; c0 < sc1; c0 += gk) {
+            if (!(c0 == sc0 ? drain(std::true_type{}) : drain(std::false_type{}))) {
+              ok = false;
+              break;
+            }
+            // the previous unit's store: two batches per group, the rest at the
+            // end of this (its first) level
+            if (pb < NB) rb_upto(c0 + gk >= sc1 ? NB : min(NB, pb + 2));
+          }
+          if (!ok) break;
+#pragma unroll
+          for (int c = 0; c < HC; c += 4) {
+            uint32_t wd = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              wd |= (uint32_t)(Lv[c + j] & dmask) << (8 * j);
+              Lv[c + j] >>= a.beta;  // floor: L = 2^beta (L >> beta) + (L & mask)
+            }
+            dg[c / 4] = wd;
+          }
+        }
+        {
+          const int hl = pair ? lvl - 1 : lvl;
+          const int gk = group_blocks(a.group_kb, hl - 1);
+          for (int64_t c0 = sc0; c0 < sc1; c0 += gk) {
+            if (!(c0 == sc0 && !pair ? drain(std::true_type{}) : drain(std::false_type{}))) {
+              ok = false;
+              break;
             }
           }
-          tc::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive_remote_relaxed(tempty_addr[acc]);
-          tph[acc] ^= 1;
-          acc = (acc + 1) == NACC ? 0 : acc + 1;
-          return true;
-        };
-        for (int64_t c0 = sc0; c0 < sc1; c0 += gk) {
-          if (!(c0 == sc0 ? drain(std::true_type{}) : drain(std::false_type{}))) {
-            ok = false;
-            break;
-          }
-          // the previous unit's store: two batches per group, the rest before
-          // the merge below overwrites its total
-          if (pb < NB) rb_upto(c0 + gk >= sc1 ? NB : min(NB, pb + 2));
+          if (!ok) break;
         }
-        if (!ok) break;
-        // K-RECOMB: T += L 2^(beta (top - lvl) - base), exactly
         const int sh = a.beta * (top - lvl) - a.t_base;
         // (8 columns at a time: each batch's shifted values are sent before the next
         // is formed, which keeps the 64-bit temporaries few)
@@ -519,7 +558,11 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
         for (int c = 0; c < HC; c += 8) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            const long long x = fx_shift(Lv[c + j], sh);
+            const long long lv =
+                pair ? ((long long)Lv[c + j] << a.beta) +
+                           (long long)((dg[(c + j) / 4] >> (8 * ((c + j) % 4))) & 0xFFu)
+                     : (long long)Lv[c + j];
+            const long long x = fx_shift(lv, sh);
             // relaxed gpu-scope store, reductions and read-back: same-address
             // operations of one thread stay in program order (coherence)
             if (!stored)
@@ -566,12 +609,12 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
       }
       continue;
     }
-    // this unit's FP64 store waits for the next unit's drains
+    // this unit's FP64 store waits for the next unit's first level, which is
+    // always the lower level of a pair (the host takes s >= 2 slices)
     p_row0 = row0;
     p_cbase = cbase;
     p_ea = row0 + lane < a.sch.m ? a.eA[row0 + lane] : kExpNone;
     pb = 0;
-    rb_load(0);
   }
   if (ok && pb < NB) rb_upto(NB);
 }
@@ -1259,15 +1302,19 @@ int emu_multiply(int64_t m, int64_t n, int64_t k, const cosma_plan& p, const cos
   args.alpha = alpha;
   args.beta_c = beta_c;
   // Super-chunk: every level sum of a chunk must fit in int32 exactly (at most s
-  // pairs x chunk x 2^(2 beta - 2)).  Each chunk ends in s merges of the running
-  // total, which are L2 reductions; 4096 k -- fewer merges beat keeping a chunk's
-  // slice panels in L2 across the levels (one GB300, 256 x 256 pair tiles, square
-  // 16384^3: 512 k 66.2, 1024 k 72.6, 2048 k 77.6, 4096 k 78.3-79.6, 16384 k 80.3
-  // TFLOP/s; largeK 4096 x 4096 x 2^20: 4096 k 64.3, 16384 k 62.7).
-  // (With at most 8 slices of at most 8 bits the bound is 16384 k, so every
-  // accepted configuration uses the 4096-k super-chunk the planner assumes.)
+  // pairs x chunk x 2^(2 beta - 2)).  Each chunk ends in ceil(s / 2) merges of the
+  // running total (levels in pairs), which are L2 reductions; 4096 k -- fewer
+  // merges beat keeping a chunk's slice panels in L2 across the levels (one GB300,
+  // 256 x 256 pair tiles, one merge per level, square 16384^3: 512 k 66.2, 1024 k
+  // 72.6, 2048 k 77.6, 4096 k 78.3-79.6, 16384 k 80.3 TFLOP/s; largeK 4096 x 4096
+  // x 2^20: 4096 k 64.3, 16384 k 62.7).
+  // (With at most 12 slices of at most 8 bits the bound is above 10000 k, so
+  // every accepted configuration uses the 4096-k super-chunk the planner assumes.)
   {
-    const double lim = 2147483647.0 / ((double)s * std::ldexp(1.0, 2 * beta - 2));
+    // (a level's sum also takes the carry of the level below: at most 2^-beta of
+    // that one's bound, plus one)
+    const double lim =
+        2147483646.0 / ((double)s * std::ldexp(1.0, 2 * beta - 2) * (1.0 + std::ldexp(1.0, -beta)));
     if ((double)kEmuChunkKb * EBK > lim) return COSMA_ERR_UNSUPPORTED;
     args.chunk_kb = kEmuChunkKb;
   }

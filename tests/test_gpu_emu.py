@@ -152,7 +152,7 @@ def test_emu_pair_and_single_sm_tiles(tile, shape):
 @pytest.mark.parametrize("tile", ["pair256", "single", "pair128"])
 def test_emu_long_k(tile):
     # k = 22001: six 4096-deep super-chunks, 36 merges of the running total, whose
-    # fixed-point base rises to 7 bits (the lowest level is rounded to it)
+    # fixed-point base rises to 7 bits (the lowest level pair is rounded to it)
     import torch
     cosma = lib()
     m, n, k = 130, 129, 22001
@@ -198,7 +198,7 @@ def test_emu_equals_the_methods_own_result(slices, bits, shape):
     """The GPU emulation against the step-by-step oracle of the method
     (oracle/ozaki.py: the same scales, digits and truncated triangle in exact
     integer arithmetic): both round the exact total to FP64 once, so they differ
-    only where the fixed-point base rounds the lowest level -- far below the
+    only where the fixed-point base rounds the lowest level pair -- far below the
     truncation itself; with 3 slices the product is off by ~2^-22 but the two
     agree to 2^-40 of sum |a||b|, so a wrong pair set or scale would show."""
     import torch
