@@ -79,8 +79,8 @@ def _alu_peak_tflops(dtype, sms):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# dominant kernel, from one single-pass ncu capture of exactly this workload and
-# kernel version; absent entries are reported as null.
+# dominant kernel, from one ncu capture of exactly this workload and kernel
+# version; absent entries are reported as null.
 DRAM_TRAFFIC = {
     ("square", "bf16"): 10.25e9 + 1.07e9,     # tc_gemm_kernel<256,4,A K,B MN>, tensor-store C
     ("flat", "bf16"): 4.30e9 + 17.15e9,       # same kernel, 16 GB of f32 C
@@ -91,8 +91,9 @@ DRAM_TRAFFIC = {
     # emu_pair_kernel<256>: the lock-step schedule captured under a plain cluster
     # launch (COSMA_EMU_LOCKSTEP=2; ncu cannot launch the cooperative one); 16384^3
     # is 8 x the 8192^3 capture (4096^3 -> 8192^3 grew 8.05x for 8x the work)
-    ("emu8192", "f64_emu_bf16"): 35.39e9 + 5.92e9,
-    ("square", "f64_emu_bf16"): 8 * (35.39e9 + 5.92e9),
+    ("emu8192", "f64_emu_bf16"): 44.24e9 + 3.08e9,
+    ("square", "f64_emu_bf16"): 8 * (44.24e9 + 3.08e9),
+    ("flat16k", "f64_emu_bf16"): 13.55e9 + 6.24e9,   # from the --set full capture
     # tf32x3_gemm_kernel: lock-step ticks under a plain launch (COSMA_TF32_LOCKSTEP=2)
     ("square", "f32_emu_tf32"): 53.16e9 + 1.07e9,
 }

@@ -511,7 +511,7 @@ __device__ __forceinline__ void emu_fx_epilogue(const EmuArgs& a, int unit_cta, 
       // lvl of a pair keeps its low beta bits as digits and passes the rest,
       // floor(L_lvl / 2^beta), on as the start of level lvl - 1's sum, which then
       // ends at L_{lvl-1} + floor(L_lvl / 2^beta) (one super-chunk's level sums
-      // stay below 2^29, so this fits an int32); the pair's value is
+      // stay below 2^29.6, so this fits an int32); the pair's value is
       // 2^beta (that sum) + digits = L_lvl + 2^beta L_{lvl-1}, exactly, and
       // T += value 2^(beta (top - lvl) - base).  With an odd number of levels the
       // last, lvl = 2, joins alone.
