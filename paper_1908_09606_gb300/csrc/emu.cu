@@ -285,8 +285,8 @@ __global__ void split_b_kernel(const double* __restrict__ B, int64_t k, int64_t 
 //         for each pair q = 1..p:  for each k-block kb in [c0, c1):
 //           D[acc] (+)= A_q[tile rows, kb] * B_{l-q}[tile cols, kb]
 //       (the group's f32 sums are exact integers: drained into an int32 level sum)
-//     (end of level in the super-chunk: the exact level sum L joins the fixed-point
-//      running total, T += L 2^(beta (s + 1 - l) - base))
+//     (end of every second level in the super-chunk: the exact value of the level
+//      pair joins the fixed-point running total, see the epilogue)
 // Each level re-reads the super-chunk's slice panels; shorter super-chunks keep
 // them in L2 across the levels at the price of more merges of the running total.
 
